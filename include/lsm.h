@@ -1,0 +1,194 @@
+/*
+ * lsm.h - C ABI of the GB300 block-row recursive least-squares migration library.
+ *
+ * The library applies the 2D shot-profile split-step Fourier de-migration operator A
+ * (Eq. 1: d = A m + n), its adjoint A^T (Eq. 2: migration with the cross-correlation imaging
+ * condition), and solves the damped least-squares problem (Eq. 3) on sliding windows of shots
+ * with CG on each window's normal equations (A_k^T A_k + lambda I) m = A_k^T d_k (Eq. 10),
+ * warm-started from the previous window's image (Eq. 11).  The operator is the one the paper's
+ * Examples section uses: one-way shot-profile propagation by phase shift in (w, kx) with the
+ * split-step slowness correction in (w, x).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Grid: nx lateral cells (a power of two, 16 <= nx <= 1024) by nz depth rows, spacing
+ *    dx, dz in metres.  Depth row j sits at z = j dz; sources and receivers are at row 0.
+ *  - Slowness: device float32 [nz][nx] in s/m (row j contiguous).  Model / image: device
+ *    float32 [nz][nx].
+ *  - Frequencies: host float32 freq_hz[nw] (Hz; w = 2 pi f) and host float32 wavelet[nw][2]
+ *    (interleaved real, imaginary source spectrum W(w)).
+ *  - Geometry: host int32 src_ix[ns] (source grid column of each shot) and host int32
+ *    rec_ix[ns][nrec] (receiver grid columns of each shot); rec_ix may be NULL when
+ *    nrec == nx, meaning receivers at every column in order.  All indices in [0, nx).
+ *  - Data: device complex64 [shots][nw][nrec] stored as interleaved float32 pairs
+ *    (receiver index fastest).
+ *  - Operator conventions (readings of the paper, which does not spell them out):
+ *    lateral DFT F u[k] = sum_x u[x] exp(-2 pi i k x / nx) with a 1/nx inverse;
+ *    kx = 2 pi k/(nx dx) for k < nx/2 and 2 pi (k - nx)/(nx dx) otherwise;
+ *    s_ref(j) = mean_x s(x, j); Phi_j = exp(+i kz dz), kz = sqrt(w^2 s_ref^2 - kx^2) on the
+ *    propagating band and exp(-sqrt(kx^2 - w^2 s_ref^2) dz) on the evanescent one;
+ *    D_j(x) = exp(+i w (s(x, j) - s_ref(j)) dz); one depth step P_j = D_j F^-1 Phi_j F.
+ *    Source S_0 = W(w) delta(x - x_s), S_{j+1} = P_j S_j.
+ *    A m = sum_j P_0 ... P_{j-1} (S_j m_j) sampled at the receivers.
+ *    A^T d: m_j(x) = Re sum_{shots, w} conj(S_j(x)) R_j(x), R_0 = injected data,
+ *    R_{j+1} = P_j^H R_j.  A and A^T are adjoint under <u, v> = Re sum conj(u) v.
+ *  - Memory: every device pointer is owned by the caller and must be 16-byte aligned.  The
+ *    library allocates no device memory: all scratch lives in a caller-provided workspace of at
+ *    least lsm_workspace_bytes(...) bytes.  Host arrays are read during the call only.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    lsm_forward and lsm_adjoint are asynchronous on that stream.  rls_window_solve
+ *    synchronises the stream once per CG iteration (to test convergence) and before returning.
+ *  - Errors: every entry point returns an LSM_* status; arguments are validated on the host
+ *    before anything is launched.  A call that fails validation launches nothing and leaves
+ *    outputs untouched.  No kernel in this library waits on another block or device, so none
+ *    can hang; LSM_ERR_TIMEOUT is reserved.
+ *  - Thread safety: calls sharing a workspace must be serialised by the caller.
+ */
+#ifndef LSM_GB300_H
+#define LSM_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LSM_OK 0
+#define LSM_ERR_ARG (-1)            /* invalid argument (null pointer, out-of-range value) */
+#define LSM_ERR_CUDA (-2)           /* a CUDA runtime call or kernel launch failed */
+#define LSM_ERR_WORKSPACE (-3)      /* workspace smaller than lsm_workspace_bytes() */
+#define LSM_ERR_BREAKDOWN (-4)      /* CG step length undefined: q^T q + lambda p^T p <= 0 or
+                                       not finite (e.g. non-finite input data) */
+#define LSM_ERR_TIMEOUT (-5)        /* reserved: a bounded device wait expired */
+#define LSM_ERR_UNSUPPORTED_NX (-6) /* nx is not a power of two in [16, 1024] */
+
+#define LSM_OP_FORWARD 0
+#define LSM_OP_ADJOINT 1
+#define LSM_OP_SOLVE 2
+
+typedef struct {
+    int nx, nz;     /* lateral cells, depth rows */
+    float dx, dz;   /* spacing in metres (> 0) */
+} lsm_grid;
+
+typedef struct {
+    int ns;              /* number of shots in the survey */
+    const int* src_ix;   /* host [ns] source grid columns */
+    int nrec;            /* receivers per shot */
+    const int* rec_ix;   /* host [ns][nrec] receiver columns, or NULL for every column */
+} lsm_geom;
+
+typedef struct {
+    int nw;                 /* number of frequencies */
+    const float* freq_hz;   /* host [nw] */
+    const float* wavelet;   /* host [nw][2] interleaved source spectrum */
+} lsm_freqs;
+
+typedef struct {
+    int start;          /* first shot of the window */
+    int iters;          /* CG iterations taken in this window */
+    double rel_res0;    /* ||A^T(d - A m0) - lambda m0|| / ||A^T d|| at the warm start m0 */
+    double rel_res;     /* same ratio at the window's final image */
+    int n_forward;      /* applications of A in this window */
+    int n_adjoint;      /* applications of A^T in this window */
+    float ms;           /* wall time of the window (host clock, includes synchronisation) */
+} lsm_window_stats;
+
+/*
+ * Workspace size in bytes for one call.
+ *   op = LSM_OP_FORWARD / LSM_OP_ADJOINT: nshots = shots processed per call.
+ *   op = LSM_OP_SOLVE: nshots = the window length K.
+ * The size depends on the current device's multiprocessor count (152 is assumed when no
+ * device is visible), so query it with the device that will run the call current.
+ * Returns 0 for invalid arguments.
+ */
+size_t lsm_workspace_bytes(const lsm_grid* grid, const lsm_geom* geom, const lsm_freqs* freqs,
+                           int nshots, int op);
+
+/*
+ * De-migration d = A m (Eq. 1 without the noise term) for shots shot0 .. shot0+nshots-1.
+ *   slowness: device [nz][nx]; m: device [nz][nx];
+ *   d_out: device complex64 [nshots][nw][nrec], overwritten.
+ * Evaluated per (shot, w) by Horner's rule from the deepest row upward:
+ *   U_{nz-1} = S_{nz-1} m_{nz-1}, U_j = S_j m_j + P_j U_{j+1}, d = U_0 at the receivers,
+ * after computing and caching S_j for every depth in the workspace.
+ */
+int lsm_forward(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs,
+                const lsm_geom* geom, const float* m, float* d_out, int shot0, int nshots,
+                void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Migration m = A^T d (Eq. 2) for shots shot0 .. shot0+nshots-1.
+ *   d: device complex64 [nshots][nw][nrec] (the data of those shots);
+ *   m_out: device [nz][nx]; overwritten when accumulate == 0, added to otherwise.
+ * The image is summed over shots and frequencies in a fixed order, so repeated calls with the
+ * same inputs and workspace size give bitwise identical results.
+ */
+int lsm_adjoint(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs,
+                const lsm_geom* geom, const float* d, float* m_out, int shot0, int nshots,
+                int accumulate, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Number of sliding windows of K shots with the given slide over ns shots: starts are
+ * 0, slide, 2 slide, ... while start + K <= ns, plus a final window at ns - K when the regular
+ * schedule stops short of the last shot.  Returns 0 for invalid arguments.
+ */
+int lsm_num_windows(int ns, int K, int slide);
+
+/*
+ * Block-row recursive least-squares migration (block-row section, Eq. 10 and Eq. 11).
+ * Windows first_window .. first_window + n_windows - 1 (n_windows <= 0: all remaining) of the
+ * schedule of lsm_num_windows are solved in order.  Each window k runs CG on
+ *   (A_k^T A_k + lambda I) m = A_k^T d_k
+ * starting from the image in m_inout (the previous window's result, Eq. 11), until
+ *   ||A_k^T (d_k - A_k m) - lambda m|| / ||A_k^T d_k|| <= cg_tol
+ * or max_iter iterations.  Dot products, step lengths and beta are float64 on the device; the
+ * vectors are float32.  Moving the window drops the first `slide` shots and adds the next ones
+ * (rank-`slide` downdate/update): only the added shots' source wavefields are computed.
+ *   d: device complex64 [ns][nw][nrec] (the whole survey);
+ *   lambda >= 0 (absolute); K in [1, ns]; slide >= 1; cg_tol >= 0; max_iter >= 0;
+ *   m_inout: device [nz][nx], the warm start on entry and the last window's image on return;
+ *   stats: host array of stats_cap entries (may be NULL), filled for each solved window.
+ * Resuming with first_window = k and the image returned after window k-1 reproduces an
+ * uninterrupted run bitwise.  Returns LSM_ERR_BREAKDOWN if a step length is undefined; m_inout
+ * then holds the last finite iterate.
+ */
+int rls_window_solve(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs,
+                     const lsm_geom* geom, const float* d, double lambda, int K, int slide,
+                     double cg_tol, int max_iter, int first_window, int n_windows,
+                     float* m_inout, lsm_window_stats* stats, int stats_cap,
+                     void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Kernel timing for benchmarks.  Between lsm_profile_start() and lsm_profile_stop() every kernel
+ * this library launches is bracketed by CUDA events recorded on the stream it is launched on;
+ * lsm_profile_stop() waits for those events and reports, per kernel class, the number of launches
+ * and the summed event time in milliseconds.  Timing adds two event records per launch.  Not
+ * thread safe: profile one caller at a time.
+ */
+#define LSM_KCLASS_TABLES 0   /* reference slowness and coefficient tables */
+#define LSM_KCLASS_SOURCE 1   /* source-wavefield depth sweep */
+#define LSM_KCLASS_ADJOINT 2  /* A^T depth sweep (imaging) */
+#define LSM_KCLASS_FORWARD 3  /* A depth sweep */
+#define LSM_KCLASS_VECTOR 4   /* image reduction and CG vector updates */
+#define LSM_NUM_KCLASSES 5
+
+typedef struct {
+    unsigned long long launches[LSM_NUM_KCLASSES];
+    double ms[LSM_NUM_KCLASSES];
+} lsm_profile;
+
+void lsm_profile_start(void);
+int lsm_profile_stop(lsm_profile* out);
+
+/* Human-readable name of a status code (static string). */
+const char* lsm_status_string(int status);
+
+/* Number of kernels this library has launched in this process (monotonic counter). */
+unsigned long long lsm_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSM_GB300_H */

@@ -1,0 +1,558 @@
+// C ABI of the block-row recursive least-squares migration library (see include/lsm.h).
+//
+// Host side: argument validation, workspace carving, per-call upload of the host geometry and
+// frequency arrays, launch geometry, and the sliding-window CG driver (block-row section,
+// Eq. 10 and Eq. 11).  Every arithmetic step of the operator and of CG runs in the kernels of
+// lsm_sweep.cuh and lsm_cg.cu; the host only sequences them and reads one small state struct
+// per CG iteration to test the stopping rule.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "../../include/lsm.h"
+#include "lsm_cg.h"
+#include "lsm_internal.h"
+
+namespace lsm {
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+
+struct ProfRecord {
+    int cls;
+    cudaEvent_t begin, end;
+};
+static bool g_prof_on = false;
+static std::vector<ProfRecord> g_prof;
+static std::vector<cudaEvent_t> g_event_pool;
+static cudaEvent_t g_pending_begin = nullptr;
+
+static cudaEvent_t pooled_event() {
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+void profile_mark(int cls, cudaStream_t st, bool begin) {
+    if (!g_prof_on) return;
+    if (begin) {
+        g_pending_begin = pooled_event();
+        if (g_pending_begin) cudaEventRecord(g_pending_begin, st);
+    } else {
+        cudaEvent_t e = pooled_event();
+        if (e && g_pending_begin) {
+            cudaEventRecord(e, st);
+            g_prof.push_back({cls, g_pending_begin, e});
+        }
+        g_pending_begin = nullptr;
+    }
+}
+
+bool nx_supported(int nx) {
+    switch (nx) {
+        case 16: case 32: case 64: case 128: case 256: case 512: case 1024: return true;
+        default: return false;
+    }
+}
+
+static int max_warps_for(int nx, int mode) {
+    switch (nx) {
+        case 16: return sweep_max_warps_16(mode);
+        case 32: return sweep_max_warps_32(mode);
+        case 64: return sweep_max_warps_64(mode);
+        case 128: return sweep_max_warps_128(mode);
+        case 256: return sweep_max_warps_256(mode);
+        case 512: return sweep_max_warps_512(mode);
+        default: return sweep_max_warps_1024(mode);
+    }
+}
+
+SweepShape sweep_shape(int nx, int mode, int nitems, int num_sms) {
+    const int V = points_per_thread(nx);
+    const int T = nx / V;
+    const int ipw = 32 / T;
+    const size_t buf = (size_t)(nx + nx / 16) * sizeof(float2);
+    const size_t per_warp = ipw * buf + (mode == MODE_ADJOINT ? 2 * (size_t)nx * sizeof(float) : 0);
+    const int warps_total = (nitems + ipw - 1) / ipw;
+    int maxw = std::min(16, max_warps_for(nx, mode));
+    maxw = std::min<int>(maxw, (int)((227 * 1024) / per_warp));
+    maxw = std::max(maxw, 1);
+    int warps = (warps_total + num_sms - 1) / num_sms;
+    warps = std::max(1, std::min(warps, maxw));
+    SweepShape s;
+    s.warps = warps;
+    s.blocks = (warps_total + warps - 1) / warps;
+    s.smem = per_warp * warps;
+    return s;
+}
+
+cudaError_t launch_tables(const TableArgs& a, cudaStream_t st) {
+    switch (a.nx) {
+        case 16: return launch_tables_16(a, st);
+        case 32: return launch_tables_32(a, st);
+        case 64: return launch_tables_64(a, st);
+        case 128: return launch_tables_128(a, st);
+        case 256: return launch_tables_256(a, st);
+        case 512: return launch_tables_512(a, st);
+        default: return launch_tables_1024(a, st);
+    }
+}
+
+cudaError_t launch_sweep(int mode, const SweepArgs& a, const SweepShape& sh, cudaStream_t st) {
+    switch (a.nx) {
+        case 16: return launch_sweep_16(mode, a, sh, st);
+        case 32: return launch_sweep_32(mode, a, sh, st);
+        case 64: return launch_sweep_64(mode, a, sh, st);
+        case 128: return launch_sweep_128(mode, a, sh, st);
+        case 256: return launch_sweep_256(mode, a, sh, st);
+        case 512: return launch_sweep_512(mode, a, sh, st);
+        default: return launch_sweep_1024(mode, a, sh, st);
+    }
+}
+
+// s_ref(z_j) = mean over x of s(x, z_j), summed in float64 (Examples section: split-step
+// reference slowness per depth row)
+__global__ void reference_slowness_kernel(const float* __restrict__ s, int nx, int nz, double* __restrict__ sref) {
+    __shared__ double sh[32];
+    const int j = blockIdx.x;
+    if (j >= nz) return;
+    double acc = 0.0;
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) acc += (double)s[(size_t)j * nx + x];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh[w];
+        sref[j] = tot / (double)nx;
+    }
+}
+
+}  // namespace lsm
+
+using namespace lsm;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+int num_sms_current() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 152;
+    }
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        return 152;
+    }
+    return n;
+}
+
+struct Layout {
+    // offsets in bytes from the workspace base
+    size_t src, rec, freq, wav, sref, phi, dss, S, part;
+    size_t p, s, r, q, qq, pp, ss, state;
+    size_t total;
+    int ring, nparts;
+};
+
+bool rec_is_identity(const lsm_grid* g, const lsm_geom* geo) { return geo->rec_ix == nullptr; }
+
+Layout make_layout(const lsm_grid* g, const lsm_geom* geo, const lsm_freqs* f, int nshots, int op, int num_sms) {
+    Layout L{};
+    const size_t nx = (size_t)g->nx, nz = (size_t)g->nz, nw = (size_t)f->nw;
+    const size_t plane = nz * nx;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = align_up(off + bytes);
+        return at;
+    };
+    L.src = take((size_t)geo->ns * sizeof(int));
+    L.rec = take(rec_is_identity(g, geo) ? 0 : (size_t)geo->ns * geo->nrec * sizeof(int));
+    L.freq = take(nw * sizeof(float));
+    L.wav = take(nw * sizeof(float2));
+    L.sref = take(nz * sizeof(double));
+    L.phi = take(nw * plane * sizeof(float2));
+    L.dss = take(nw * plane * sizeof(float2));
+    L.ring = nshots;
+    L.S = take((size_t)nshots * nw * plane * sizeof(float2));
+    L.nparts = 0;
+    if (op == LSM_OP_ADJOINT || op == LSM_OP_SOLVE) {
+        const SweepShape sh = sweep_shape(g->nx, MODE_ADJOINT, (int)(nshots * nw), num_sms);
+        L.nparts = sh.blocks;
+    }
+    L.part = take((size_t)L.nparts * plane * sizeof(float));
+    if (op == LSM_OP_SOLVE) {
+        const size_t nd = (size_t)nshots * nw * geo->nrec;
+        L.p = take(plane * sizeof(float));
+        L.s = take(plane * sizeof(float));
+        L.r = take(nd * sizeof(float2));
+        L.q = take(nd * sizeof(float2));
+        L.qq = take(kRedBlocks * sizeof(double));
+        L.pp = take(kRedBlocks * sizeof(double));
+        L.ss = take(kRedBlocks * sizeof(double));
+        L.state = take(sizeof(CgState));
+    } else if (op == LSM_OP_FORWARD) {
+        L.p = L.s = L.r = L.q = L.qq = L.pp = L.ss = L.state = 0;
+    } else {
+        L.ss = take(kRedBlocks * sizeof(double));
+    }
+    L.total = off;
+    return L;
+}
+
+bool aligned16(const void* p) { return p != nullptr && ((uintptr_t)p & 15u) == 0; }
+
+int validate_common(const lsm_grid* g, const lsm_freqs* f, const lsm_geom* geo) {
+    if (!g || !f || !geo) return LSM_ERR_ARG;
+    if (g->nz < 1 || g->nx < 1) return LSM_ERR_ARG;
+    if (!nx_supported(g->nx)) return LSM_ERR_UNSUPPORTED_NX;
+    if (!(g->dx > 0.f) || !(g->dz > 0.f) || !std::isfinite(g->dx) || !std::isfinite(g->dz)) return LSM_ERR_ARG;
+    if (f->nw < 1 || !f->freq_hz || !f->wavelet) return LSM_ERR_ARG;
+    for (int i = 0; i < f->nw; ++i) {
+        if (!std::isfinite(f->freq_hz[i]) || f->freq_hz[i] < 0.f) return LSM_ERR_ARG;
+        if (!std::isfinite(f->wavelet[2 * i]) || !std::isfinite(f->wavelet[2 * i + 1])) return LSM_ERR_ARG;
+    }
+    if (geo->ns < 1 || !geo->src_ix || geo->nrec < 1) return LSM_ERR_ARG;
+    for (int i = 0; i < geo->ns; ++i)
+        if (geo->src_ix[i] < 0 || geo->src_ix[i] >= g->nx) return LSM_ERR_ARG;
+    if (!geo->rec_ix) {
+        if (geo->nrec != g->nx) return LSM_ERR_ARG;
+    } else {
+        const size_t n = (size_t)geo->ns * geo->nrec;
+        for (size_t i = 0; i < n; ++i)
+            if (geo->rec_ix[i] < 0 || geo->rec_ix[i] >= g->nx) return LSM_ERR_ARG;
+    }
+    // item and index arithmetic in the kernels uses 32-bit item counts
+    if ((double)geo->ns * f->nw > 1.0e9 || (double)g->nz * g->nx > 1.0e9) return LSM_ERR_ARG;
+    return LSM_OK;
+}
+
+#define LSM_CHECK(expr)                       \
+    do {                                      \
+        cudaError_t e_ = (expr);              \
+        if (e_ != cudaSuccess) return LSM_ERR_CUDA; \
+    } while (0)
+
+// Upload geometry / frequencies and build s_ref and the coefficient tables in the workspace.
+int prepare(const lsm_grid* g, const float* slowness, const lsm_freqs* f, const lsm_geom* geo, const Layout& L,
+            char* ws, cudaStream_t st) {
+    const size_t nw = (size_t)f->nw;
+    // one staging copy of all host arrays (layout identical to the workspace prefix)
+    const size_t head = L.sref;
+    std::vector<char> host(head, 0);
+    std::memcpy(host.data() + L.src, geo->src_ix, (size_t)geo->ns * sizeof(int));
+    if (geo->rec_ix) std::memcpy(host.data() + L.rec, geo->rec_ix, (size_t)geo->ns * geo->nrec * sizeof(int));
+    std::memcpy(host.data() + L.freq, f->freq_hz, nw * sizeof(float));
+    std::memcpy(host.data() + L.wav, f->wavelet, nw * sizeof(float2));
+    LSM_CHECK(cudaMemcpyAsync(ws, host.data(), head, cudaMemcpyHostToDevice, st));
+    {
+        ProfScope prof_(KC_TABLES, st);
+        reference_slowness_kernel<<<g->nz, 256, 0, st>>>(slowness, g->nx, g->nz,
+                                                         reinterpret_cast<double*>(ws + L.sref));
+    }
+    count_launch();
+    LSM_CHECK(cudaGetLastError());
+    TableArgs ta;
+    ta.nx = g->nx;
+    ta.nz = g->nz;
+    ta.nw = f->nw;
+    ta.dx = g->dx;
+    ta.dz = g->dz;
+    ta.slowness = slowness;
+    ta.sref = reinterpret_cast<const double*>(ws + L.sref);
+    ta.freq_hz = reinterpret_cast<const float*>(ws + L.freq);
+    ta.phi = reinterpret_cast<float2*>(ws + L.phi);
+    ta.dss = reinterpret_cast<float2*>(ws + L.dss);
+    LSM_CHECK(launch_tables(ta, st));
+    return LSM_OK;
+}
+
+SweepArgs base_args(const lsm_grid* g, const lsm_freqs* f, const lsm_geom* geo, const Layout& L, char* ws) {
+    SweepArgs a{};
+    a.nx = g->nx;
+    a.nz = g->nz;
+    a.nw = f->nw;
+    a.nrec = geo->nrec;
+    a.ring = L.ring;
+    a.rec_identity = geo->rec_ix == nullptr ? 1 : 0;
+    a.src_ix = reinterpret_cast<const int*>(ws + L.src);
+    a.rec_ix = geo->rec_ix ? reinterpret_cast<const int*>(ws + L.rec) : nullptr;
+    a.wavelet = reinterpret_cast<const float2*>(ws + L.wav);
+    a.phi = reinterpret_cast<const float2*>(ws + L.phi);
+    a.dss = reinterpret_cast<const float2*>(ws + L.dss);
+    a.S = reinterpret_cast<float2*>(ws + L.S);
+    a.part = reinterpret_cast<float*>(ws + L.part);
+    return a;
+}
+
+// Source wavefields of shots [shot0, shot0 + n) into their ring slots.
+cudaError_t run_source(SweepArgs a, int shot0, int n, int num_sms, cudaStream_t st) {
+    a.shot0 = shot0;
+    a.nshots = n;
+    const SweepShape sh = sweep_shape(a.nx, MODE_SOURCE, n * a.nw, num_sms);
+    return launch_sweep(MODE_SOURCE, a, sh, st);
+}
+
+cudaError_t run_forward(SweepArgs a, int shot0, int n, const float* m, float2* dout, int num_sms, cudaStream_t st) {
+    a.shot0 = shot0;
+    a.nshots = n;
+    a.m = m;
+    a.dout = dout;
+    const SweepShape sh = sweep_shape(a.nx, MODE_FORWARD, n * a.nw, num_sms);
+    return launch_sweep(MODE_FORWARD, a, sh, st);
+}
+
+// Adjoint sweep into the block partial images; returns the number of partials in *nparts.
+cudaError_t run_adjoint(SweepArgs a, int shot0, int n, const float2* din, int num_sms, cudaStream_t st, int* nparts) {
+    a.shot0 = shot0;
+    a.nshots = n;
+    a.din = din;
+    const SweepShape sh = sweep_shape(a.nx, MODE_ADJOINT, n * a.nw, num_sms);
+    *nparts = sh.blocks;
+    return launch_sweep(MODE_ADJOINT, a, sh, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lsm_workspace_bytes(const lsm_grid* grid, const lsm_geom* geom, const lsm_freqs* freqs, int nshots, int op) {
+    if (validate_common(grid, freqs, geom) != LSM_OK) return 0;
+    if (nshots < 1 || nshots > geom->ns) return 0;
+    if (op != LSM_OP_FORWARD && op != LSM_OP_ADJOINT && op != LSM_OP_SOLVE) return 0;
+    return make_layout(grid, geom, freqs, nshots, op, num_sms_current()).total;
+}
+
+int lsm_forward(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs, const lsm_geom* geom,
+                const float* m, float* d_out, int shot0, int nshots, void* workspace, size_t workspace_bytes,
+                void* stream) {
+    int rc = validate_common(grid, freqs, geom);
+    if (rc != LSM_OK) return rc;
+    if (!aligned16(slowness) || !aligned16(m) || !aligned16(d_out) || !aligned16(workspace)) return LSM_ERR_ARG;
+    if (shot0 < 0 || nshots < 1 || shot0 > geom->ns - nshots) return LSM_ERR_ARG;
+    const int nsm = num_sms_current();
+    const Layout L = make_layout(grid, geom, freqs, nshots, LSM_OP_FORWARD, nsm);
+    if (workspace_bytes < L.total) return LSM_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(workspace);
+    rc = prepare(grid, slowness, freqs, geom, L, ws, st);
+    if (rc != LSM_OK) return rc;
+    SweepArgs a = base_args(grid, freqs, geom, L, ws);
+    LSM_CHECK(run_source(a, shot0, nshots, nsm, st));
+    LSM_CHECK(run_forward(a, shot0, nshots, m, reinterpret_cast<float2*>(d_out), nsm, st));
+    return LSM_OK;
+}
+
+int lsm_adjoint(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs, const lsm_geom* geom,
+                const float* d, float* m_out, int shot0, int nshots, int accumulate, void* workspace,
+                size_t workspace_bytes, void* stream) {
+    int rc = validate_common(grid, freqs, geom);
+    if (rc != LSM_OK) return rc;
+    if (!aligned16(slowness) || !aligned16(d) || !aligned16(m_out) || !aligned16(workspace)) return LSM_ERR_ARG;
+    if (shot0 < 0 || nshots < 1 || shot0 > geom->ns - nshots) return LSM_ERR_ARG;
+    const int nsm = num_sms_current();
+    const Layout L = make_layout(grid, geom, freqs, nshots, LSM_OP_ADJOINT, nsm);
+    if (workspace_bytes < L.total) return LSM_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(workspace);
+    rc = prepare(grid, slowness, freqs, geom, L, ws, st);
+    if (rc != LSM_OK) return rc;
+    SweepArgs a = base_args(grid, freqs, geom, L, ws);
+    LSM_CHECK(run_source(a, shot0, nshots, nsm, st));
+    int nparts = 0;
+    LSM_CHECK(run_adjoint(a, shot0, nshots, reinterpret_cast<const float2*>(d), nsm, st, &nparts));
+    LSM_CHECK(cg_reduce_image(a.part, nparts, grid->nx * grid->nz, nullptr, 0.f, accumulate ? 1 : 0, m_out,
+                              reinterpret_cast<double*>(ws + L.ss), st));
+    return LSM_OK;
+}
+
+int lsm_num_windows(int ns, int K, int slide) {
+    if (ns < 1 || K < 1 || K > ns || slide < 1) return 0;
+    const int regular = (ns - K) / slide + 1;
+    const int last = (regular - 1) * slide;
+    return regular + (last + K < ns ? 1 : 0);
+}
+
+static int window_start(int k, int ns, int K, int slide) {
+    const int regular = (ns - K) / slide + 1;
+    return k < regular ? k * slide : ns - K;
+}
+
+int rls_window_solve(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs, const lsm_geom* geom,
+                     const float* d, double lambda, int K, int slide, double cg_tol, int max_iter, int first_window,
+                     int n_windows, float* m_inout, lsm_window_stats* stats, int stats_cap, void* workspace,
+                     size_t workspace_bytes, void* stream) {
+    int rc = validate_common(grid, freqs, geom);
+    if (rc != LSM_OK) return rc;
+    if (!aligned16(slowness) || !aligned16(d) || !aligned16(m_inout) || !aligned16(workspace)) return LSM_ERR_ARG;
+    if (!std::isfinite(lambda) || lambda < 0.0 || !std::isfinite(cg_tol) || cg_tol < 0.0 || max_iter < 0)
+        return LSM_ERR_ARG;
+    const int ns = geom->ns;
+    const int nwin = lsm_num_windows(ns, K, slide);
+    if (nwin == 0) return LSM_ERR_ARG;
+    if (first_window < 0 || first_window > nwin) return LSM_ERR_ARG;
+    if (stats_cap < 0 || (stats_cap > 0 && !stats)) return LSM_ERR_ARG;
+    const int last = n_windows <= 0 ? nwin : std::min(nwin, first_window + n_windows);
+    const int nsm = num_sms_current();
+    const Layout L = make_layout(grid, geom, freqs, K, LSM_OP_SOLVE, nsm);
+    if (workspace_bytes < L.total) return LSM_ERR_WORKSPACE;
+    if (first_window == last) return LSM_OK;
+
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(workspace);
+    rc = prepare(grid, slowness, freqs, geom, L, ws, st);
+    if (rc != LSM_OK) return rc;
+    SweepArgs a = base_args(grid, freqs, geom, L, ws);
+
+    const int n = grid->nx * grid->nz;
+    const size_t nd = (size_t)K * freqs->nw * geom->nrec;
+    const size_t shot_stride = (size_t)freqs->nw * geom->nrec;
+    float* p = reinterpret_cast<float*>(ws + L.p);
+    float* s = reinterpret_cast<float*>(ws + L.s);
+    float2* r = reinterpret_cast<float2*>(ws + L.r);
+    float2* q = reinterpret_cast<float2*>(ws + L.q);
+    double* qq = reinterpret_cast<double*>(ws + L.qq);
+    double* pp = reinterpret_cast<double*>(ws + L.pp);
+    double* ss = reinterpret_cast<double*>(ws + L.ss);
+    CgState* state = reinterpret_cast<CgState*>(ws + L.state);
+    const float2* dall = reinterpret_cast<const float2*>(d);
+    const float lamf = (float)lambda;
+
+    int prev_start = -1;
+    for (int k = first_window; k < last; ++k) {
+        const auto t0 = std::chrono::steady_clock::now();
+        const int start = window_start(k, ns, K, slide);
+        const float2* dk = dall + (size_t)start * shot_stride;
+        // rank-`slide` update: source wavefields of the shots that enter the window
+        const int new_from = prev_start < 0 ? start : std::max(start, prev_start + K);
+        if (new_from < start + K) LSM_CHECK(run_source(a, new_from, start + K - new_from, nsm, st));
+        prev_start = start;
+
+        int nparts = 0;
+        LSM_CHECK(cg_zero_state(state, st));
+        // b = A_k^T d_k  ->  ||b||^2
+        LSM_CHECK(run_adjoint(a, start, K, dk, nsm, st, &nparts));
+        LSM_CHECK(cg_reduce_image(a.part, nparts, n, nullptr, 0.f, 0, s, ss, st));
+        LSM_CHECK(cg_store_sum(ss, state, st));
+        // r = d_k - A_k m
+        LSM_CHECK(run_forward(a, start, K, m_inout, q, nsm, st));
+        LSM_CHECK(cg_residual(dk, q, r, nd, st));
+        // s = A_k^T r - lambda m ; p = s ; gamma = ||s||^2
+        LSM_CHECK(run_adjoint(a, start, K, r, nsm, st, &nparts));
+        LSM_CHECK(cg_reduce_image(a.part, nparts, n, m_inout, lamf, 0, s, ss, st));
+        int gi = 0;
+        LSM_CHECK(cg_update_p(p, s, n, ss, 1, state, 1, gi, pp, st));
+        CgState hs;
+        LSM_CHECK(cudaMemcpyAsync(&hs, state, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+        LSM_CHECK(cudaStreamSynchronize(st));
+        const double bnorm = std::sqrt(hs.bb);
+        double rel = bnorm > 0.0 ? std::sqrt(hs.gamma[gi]) / bnorm : 0.0;
+        const double rel0 = rel;
+        int nfwd = 1, nadj = 2, it = 0;
+        bool broke = hs.breakdown != 0;
+        while (!broke && it < max_iter && !(rel <= cg_tol)) {
+            // q = A_k p ; alpha ; m += alpha p ; r -= alpha q
+            LSM_CHECK(run_forward(a, start, K, p, q, nsm, st));
+            LSM_CHECK(cg_norm2_c64(q, nd, qq, st));
+            LSM_CHECK(cg_update_mr(m_inout, p, n, r, q, nd, qq, pp, lambda, state, gi, st));
+            // s = A_k^T r - lambda m ; beta ; p = s + beta p
+            LSM_CHECK(run_adjoint(a, start, K, r, nsm, st, &nparts));
+            LSM_CHECK(cg_reduce_image(a.part, nparts, n, m_inout, lamf, 0, s, ss, st));
+            LSM_CHECK(cg_update_p(p, s, n, ss, 0, state, gi, gi ^ 1, pp, st));
+            gi ^= 1;
+            ++nfwd;
+            ++nadj;
+            ++it;
+            LSM_CHECK(cudaMemcpyAsync(&hs, state, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+            LSM_CHECK(cudaStreamSynchronize(st));
+            broke = hs.breakdown != 0;
+            rel = bnorm > 0.0 ? std::sqrt(hs.gamma[gi]) / bnorm : 0.0;
+        }
+        const auto t1 = std::chrono::steady_clock::now();
+        const int idx = k - first_window;
+        if (idx < stats_cap) {
+            stats[idx].start = start;
+            stats[idx].iters = it;
+            stats[idx].rel_res0 = rel0;
+            stats[idx].rel_res = rel;
+            stats[idx].n_forward = nfwd;
+            stats[idx].n_adjoint = nadj;
+            stats[idx].ms = std::chrono::duration<float, std::milli>(t1 - t0).count();
+        }
+        if (broke) return LSM_ERR_BREAKDOWN;
+    }
+    return LSM_OK;
+}
+
+const char* lsm_status_string(int status) {
+    switch (status) {
+        case LSM_OK: return "ok";
+        case LSM_ERR_ARG: return "invalid argument";
+        case LSM_ERR_CUDA: return "CUDA error";
+        case LSM_ERR_WORKSPACE: return "workspace too small";
+        case LSM_ERR_BREAKDOWN: return "CG breakdown (step length undefined)";
+        case LSM_ERR_TIMEOUT: return "device wait timed out";
+        case LSM_ERR_UNSUPPORTED_NX: return "nx must be a power of two in [16, 1024]";
+        default: return "unknown status";
+    }
+}
+
+unsigned long long lsm_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+void lsm_profile_start(void) {
+    for (auto& r : g_prof) {
+        g_event_pool.push_back(r.begin);
+        g_event_pool.push_back(r.end);
+    }
+    g_prof.clear();
+    g_prof_on = true;
+}
+
+int lsm_profile_stop(lsm_profile* out) {
+    g_prof_on = false;
+    if (out) std::memset(out, 0, sizeof(*out));
+    int rc = LSM_OK;
+    for (auto& r : g_prof) {
+        if (cudaEventSynchronize(r.end) != cudaSuccess) {
+            rc = LSM_ERR_CUDA;
+            continue;
+        }
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.begin, r.end) != cudaSuccess) {
+            rc = LSM_ERR_CUDA;
+            continue;
+        }
+        if (out && r.cls >= 0 && r.cls < LSM_NUM_KCLASSES) {
+            out->launches[r.cls] += 1;
+            out->ms[r.cls] += ms;
+        }
+    }
+    cudaGetLastError();
+    for (auto& r : g_prof) {
+        g_event_pool.push_back(r.begin);
+        g_event_pool.push_back(r.end);
+    }
+    g_prof.clear();
+    return rc;
+}
+
+}  // extern "C"

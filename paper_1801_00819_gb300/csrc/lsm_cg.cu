@@ -1,0 +1,244 @@
+// CG vector kernels for the per-window normal equations (A_k^T A_k + lambda I) m = A_k^T d_k
+// (Eq. 10), iterated from the previous window's image (Eq. 11).  Vectors are float32 (model:
+// float [nz*nx]; data: complex64 [K*nw*nrec]); every inner product, the step length alpha and
+// beta are float64.  Inner products are formed as per-block partial sums over a fixed grid and
+// added in block order by whichever kernel consumes them, so every scalar is deterministic.
+#include <cuda_runtime.h>
+
+#include "lsm_cg.h"
+#include "lsm_internal.h"
+
+namespace lsm {
+
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double tot = 0.0;
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh[w];
+    }
+    return tot;  // valid in thread 0
+}
+
+// every thread gets sum(part[0..n)) in a fixed order
+__device__ __forceinline__ double sum_partials(const double* __restrict__ part, int n, double* sh) {
+    double v = 0.0;
+    // fixed assignment: thread i adds elements i, i + blockDim, ... then a fixed tree
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v += part[i];
+    double tot = block_sum(v, sh);
+    if (threadIdx.x == 0) sh[32] = tot;
+    __syncthreads();
+    tot = sh[32];
+    __syncthreads();
+    return tot;
+}
+
+// out[i] = (acc ? out[i] : 0) + sum_c part[c][i] - lam * m[i];  partial sums of out[i]^2
+__global__ void __launch_bounds__(kRedThreads) reduce_image_kernel(const float* __restrict__ part, int nparts, int n4,
+                                                               const float* __restrict__ m, float lam, int acc,
+                                                               float* __restrict__ out, double* __restrict__ ss_part) {
+    __shared__ double sh[40];
+    const float4* p4 = reinterpret_cast<const float4*>(part);
+    const float4* m4 = reinterpret_cast<const float4*>(m);
+    float4* o4 = reinterpret_cast<float4*>(out);
+    double ss = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += gridDim.x * blockDim.x) {
+        float4 s = acc ? o4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int c = 0; c < nparts; ++c) {
+            const float4 q = __ldcs(p4 + (size_t)c * n4 + i);
+            s.x += q.x; s.y += q.y; s.z += q.z; s.w += q.w;
+        }
+        if (m) {
+            const float4 mm = m4[i];
+            s.x = fmaf(-lam, mm.x, s.x); s.y = fmaf(-lam, mm.y, s.y);
+            s.z = fmaf(-lam, mm.z, s.z); s.w = fmaf(-lam, mm.w, s.w);
+        }
+        o4[i] = s;
+        ss += (double)s.x * s.x + (double)s.y * s.y + (double)s.z * s.z + (double)s.w * s.w;
+    }
+    const double tot = block_sum(ss, sh);
+    if (threadIdx.x == 0 && ss_part) ss_part[blockIdx.x] = tot;
+}
+
+// partial sums of |q|^2 over a complex vector of n2 float2 pairs (processed as float4)
+__global__ void __launch_bounds__(kRedThreads) norm2_c64_kernel(const float2* __restrict__ q, size_t n2,
+                                                            double* __restrict__ part) {
+    __shared__ double sh[40];
+    const float4* q4 = reinterpret_cast<const float4*>(q);
+    const size_t n4 = n2 / 2;
+    double acc = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+        const float4 v = q4[i];
+        acc += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (n2 & 1)) {
+        const float2 v = q[n2 - 1];
+        acc += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    const double tot = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+// r = d - q  (data space)
+__global__ void residual_kernel(const float2* __restrict__ d, const float2* __restrict__ q, float2* __restrict__ r,
+                                size_t n2) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
+        const float2 a = d[i], b = q[i];
+        r[i] = make_float2(a.x - b.x, a.y - b.y);
+    }
+}
+
+// delta = ||q||^2 + lam ||p||^2, alpha = gamma / delta; m += alpha p; r -= alpha q.
+// A non-positive or non-finite delta sets the breakdown flag and leaves m and r untouched.
+__global__ void __launch_bounds__(kRedThreads) update_mr_kernel(float* __restrict__ m, const float* __restrict__ p, int n4,
+                                                            float2* __restrict__ r, const float2* __restrict__ q,
+                                                            size_t n2, const double* __restrict__ qq_part,
+                                                            const double* __restrict__ pp_part, int nred, double lam,
+                                                            CgState* st, int gi) {
+    __shared__ double sh[40];
+    const double qq = sum_partials(qq_part, nred, sh);
+    const double pp = sum_partials(pp_part, nred, sh);
+    const double delta = qq + lam * pp;
+    const double gamma = st->gamma[gi];
+    const bool bad = !(delta > 0.0) || !isfinite(delta) || !isfinite(gamma);
+    const double alpha = bad ? 0.0 : gamma / delta;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->delta = delta;
+        st->alpha = alpha;
+        if (bad) st->breakdown = 1;
+    }
+    if (bad) return;
+    const float a = (float)alpha;
+    float4* m4 = reinterpret_cast<float4*>(m);
+    const float4* p4 = reinterpret_cast<const float4*>(p);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += gridDim.x * blockDim.x) {
+        float4 x = m4[i];
+        const float4 y = p4[i];
+        x.x = fmaf(a, y.x, x.x); x.y = fmaf(a, y.y, x.y); x.z = fmaf(a, y.z, x.z); x.w = fmaf(a, y.w, x.w);
+        m4[i] = x;
+    }
+    float4* r4 = reinterpret_cast<float4*>(r);
+    const float4* q4 = reinterpret_cast<const float4*>(q);
+    const size_t h4 = n2 / 2;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < h4; i += (size_t)gridDim.x * blockDim.x) {
+        float4 x = r4[i];
+        const float4 y = q4[i];
+        x.x = fmaf(-a, y.x, x.x); x.y = fmaf(-a, y.y, x.y); x.z = fmaf(-a, y.z, x.z); x.w = fmaf(-a, y.w, x.w);
+        r4[i] = x;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (n2 & 1)) {
+        float2 x = r[n2 - 1];
+        const float2 y = q[n2 - 1];
+        r[n2 - 1] = make_float2(fmaf(-a, y.x, x.x), fmaf(-a, y.y, x.y));
+    }
+}
+
+// gamma_new = ||s||^2; beta = first ? 0 : gamma_new / gamma_old; p = s + beta p; partials of ||p||^2.
+// Reads gamma[gi_old] and writes gamma[gi_new] (distinct slots, so blocks never race).
+__global__ void __launch_bounds__(kRedThreads) update_p_kernel(float* __restrict__ p, const float* __restrict__ s, int n4,
+                                                           const double* __restrict__ ss_part, int nred, int first,
+                                                           CgState* st, int gi_old, int gi_new,
+                                                           double* __restrict__ pp_part) {
+    __shared__ double sh[40];
+    const double gnew = sum_partials(ss_part, nred, sh);
+    const double gold = first ? 1.0 : st->gamma[gi_old];
+    const double beta = first ? 0.0 : gnew / gold;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->gamma[gi_new] = gnew;
+        st->beta = beta;
+        if (!isfinite(gnew)) st->breakdown = 1;
+    }
+    const float b = (float)beta;
+    float4* p4 = reinterpret_cast<float4*>(p);
+    const float4* s4 = reinterpret_cast<const float4*>(s);
+    double pp = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += gridDim.x * blockDim.x) {
+        const float4 x = s4[i];
+        float4 y = first ? make_float4(0.f, 0.f, 0.f, 0.f) : p4[i];
+        y.x = fmaf(b, y.x, x.x); y.y = fmaf(b, y.y, x.y); y.z = fmaf(b, y.z, x.z); y.w = fmaf(b, y.w, x.w);
+        p4[i] = y;
+        pp += (double)y.x * y.x + (double)y.y * y.y + (double)y.z * y.z + (double)y.w * y.w;
+    }
+    const double tot = block_sum(pp, sh);
+    if (threadIdx.x == 0) pp_part[blockIdx.x] = tot;
+}
+
+// st->bb = sum of partials (||A^T d||^2)
+__global__ void __launch_bounds__(kRedThreads) store_sum_kernel(const double* __restrict__ part, int nred, CgState* st) {
+    __shared__ double sh[40];
+    const double tot = sum_partials(part, nred, sh);
+    if (threadIdx.x == 0) st->bb = tot;
+}
+
+__global__ void zero_state_kernel(CgState* st) {
+    if (threadIdx.x == 0) {
+        st->gamma[0] = st->gamma[1] = 0.0;
+        st->alpha = st->beta = st->delta = st->bb = 0.0;
+        st->breakdown = 0;
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+
+cudaError_t cg_reduce_image(const float* part, int nparts, int n, const float* m, float lam, int acc, float* out,
+                            double* ss_part, cudaStream_t st) {
+    ProfScope prof_(KC_VECTOR, st);
+    reduce_image_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(part, nparts, n / 4, m, lam, acc, out, ss_part);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t cg_norm2_c64(const float2* q, size_t n2, double* part, cudaStream_t st) {
+    ProfScope prof_(KC_VECTOR, st);
+    norm2_c64_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(q, n2, part);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t cg_residual(const float2* d, const float2* q, float2* r, size_t n2, cudaStream_t st) {
+    ProfScope prof_(KC_VECTOR, st);
+    residual_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(d, q, r, n2);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t cg_update_mr(float* m, const float* p, int n, float2* r, const float2* q, size_t n2,
+                         const double* qq_part, const double* pp_part, double lam, CgState* state, int gi,
+                         cudaStream_t st) {
+    ProfScope prof_(KC_VECTOR, st);
+    update_mr_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(m, p, n / 4, r, q, n2, qq_part, pp_part, kRedBlocks, lam,
+                                                          state, gi);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t cg_update_p(float* p, const float* s, int n, const double* ss_part, int first, CgState* state,
+                        int gi_old, int gi_new, double* pp_part, cudaStream_t st) {
+    ProfScope prof_(KC_VECTOR, st);
+    update_p_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(p, s, n / 4, ss_part, kRedBlocks, first, state, gi_old,
+                                                         gi_new, pp_part);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t cg_store_sum(const double* part, CgState* state, cudaStream_t st) {
+    ProfScope prof_(KC_VECTOR, st);
+    store_sum_kernel<<<1, kRedThreads, 0, st>>>(part, kRedBlocks, state);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t cg_zero_state(CgState* state, cudaStream_t st) {
+    ProfScope prof_(KC_VECTOR, st);
+    zero_state_kernel<<<1, 32, 0, st>>>(state);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace lsm

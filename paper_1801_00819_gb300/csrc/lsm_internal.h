@@ -1,0 +1,87 @@
+// Internal host-side declarations shared by the C-ABI layer and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace lsm {
+
+enum SweepMode { MODE_SOURCE = 0, MODE_ADJOINT = 1, MODE_FORWARD = 2 };
+
+// Arguments of one depth sweep over the (shot, frequency) items of shots [shot0, shot0+nshots).
+// Item index = iw * nshots + (shot - shot0), so consecutive items share a frequency and read the
+// same coefficient rows.  The source wavefield of shot s lives in ring slot s % ring.
+struct SweepArgs {
+    int nx, nz, nw, nrec;
+    int shot0, nshots, ring;
+    int rec_identity;              // 1: receivers at every column in order
+    const int* src_ix;             // device [ns]
+    const int* rec_ix;             // device [ns][nrec] (unused when rec_identity)
+    const float2* wavelet;         // device [nw]
+    const float2* phi;             // device [nw][nz][nx]: Phi_j / nx in the FFT's output order
+    const float2* dss;             // device [nw][nz][nx]: split-step factor D_j(x)
+    float2* S;                     // device [ring][nw][nz][nx]: source wavefield cache
+    const float2* din;             // adjoint input [nshots][nw][nrec]
+    float2* dout;                  // forward output [nshots][nw][nrec]
+    const float* m;                // forward model [nz][nx]
+    float* part;                   // adjoint per-block partial images [grid][nz][nx]
+};
+
+struct TableArgs {
+    int nx, nz, nw;
+    float dx, dz;
+    const float* slowness;   // [nz][nx]
+    const double* sref;      // [nz]
+    const float* freq_hz;    // [nw]
+    float2* phi;
+    float2* dss;
+};
+
+// Launch geometry of a sweep: grid.x blocks of `warps` warps.
+struct SweepShape {
+    int blocks;
+    int warps;
+    size_t smem;
+};
+
+bool nx_supported(int nx);
+// Block count of the adjoint sweep for this many items (partial images to reduce).
+SweepShape sweep_shape(int nx, int mode, int nitems, int num_sms);
+cudaError_t launch_tables(const TableArgs& a, cudaStream_t st);
+cudaError_t launch_sweep(int mode, const SweepArgs& a, const SweepShape& shape, cudaStream_t st);
+
+// per-N dispatch targets (one translation unit per nx)
+#define LSM_DECLARE_N(NN)                                                                     \
+    cudaError_t launch_tables_##NN(const TableArgs& a, cudaStream_t st);                      \
+    cudaError_t launch_sweep_##NN(int mode, const SweepArgs& a, const SweepShape& shape,      \
+                                  cudaStream_t st);                                           \
+    int sweep_max_warps_##NN(int mode);
+LSM_DECLARE_N(16)
+LSM_DECLARE_N(32)
+LSM_DECLARE_N(64)
+LSM_DECLARE_N(128)
+LSM_DECLARE_N(256)
+LSM_DECLARE_N(512)
+LSM_DECLARE_N(1024)
+#undef LSM_DECLARE_N
+
+// points per thread chosen for each nx
+constexpr int points_per_thread(int nx) { return nx >= 1024 ? 32 : 16; }
+
+void count_launch(int n = 1);
+
+// Per-launch event timing (lsm_profile_start / lsm_profile_stop).  Construct a ProfScope right
+// before a launch and destroy it right after; both ends record an event on the launch stream
+// when profiling is on.
+enum KernelClass { KC_TABLES = 0, KC_SOURCE = 1, KC_ADJOINT = 2, KC_FORWARD = 3, KC_VECTOR = 4 };
+void profile_mark(int cls, cudaStream_t st, bool begin);
+struct ProfScope {
+    int cls;
+    cudaStream_t st;
+    ProfScope(int c, cudaStream_t s) : cls(c), st(s) { profile_mark(cls, st, true); }
+    ~ProfScope() { profile_mark(cls, st, false); }
+};
+
+}  // namespace lsm

@@ -1,0 +1,313 @@
+// Depth-sweep kernels of the shot-profile split-step operator (Eq. 1, Eq. 2; Examples section).
+//
+// One (shot, frequency) item is held in registers by T = N / V threads for the whole depth loop;
+// a warp holds 32 / T items.  Per depth row j the item runs one split-step step
+//   P_j u   = D_j . F^-1 (Phi_j . F u)                    (source and forward sweeps)
+//   P_j^H u = F^-1 (conj(Phi_j) . F (conj(D_j) . u))      (adjoint sweep)
+// with Phi_j (already divided by nx and stored in the FFT's output order) and D_j read from
+// precomputed coefficient tables shared by every shot at that frequency.
+//
+//   MODE_SOURCE : S_0 = W(w) delta(x - x_s); store S_j, S_{j+1} = P_j S_j.
+//   MODE_ADJOINT: R_0 = injected data; image_j += Re conj(S_j) R_j; R_{j+1} = P_j^H R_j.
+//                 The block sums its items' image rows every depth (one barrier per row) and
+//                 writes one partial row per block; a separate pass adds the partials in a
+//                 fixed order, so the image is deterministic.
+//   MODE_FORWARD: U <- P_j U_{j+1} + S_j m_j from j = nz-1 up to 0; record U_0.
+#pragma once
+
+#include "lsm_fft.cuh"
+#include "lsm_internal.h"
+
+namespace lsm {
+
+template <int N, int V>
+struct SweepGeom {
+    using P = Plan<N, V>;
+    static constexpr int T = P::T;
+    static constexpr int IPW = 32 / T;  // items per warp
+};
+
+template <int N, int V>
+__device__ __forceinline__ void load_row(float2 (&v)[V], const float2* __restrict__ row, int t, bool ok) {
+    constexpr int T = Plan<N, V>::T;
+#pragma unroll
+    for (int r = 0; r < V; ++r) v[r] = ok ? __ldg(row + t + T * r) : make_float2(0.f, 0.f);
+}
+
+template <int N, int V>
+__device__ __forceinline__ void step_down(float2 (&v)[V], const Twiddles<N, V>& tw, float2* buf, int t,
+                                          const float2* __restrict__ phi_row, const float2* __restrict__ d_row) {
+    constexpr int T = Plan<N, V>::T;
+    fft_forward<N, V>(v, tw, buf, t);
+#pragma unroll
+    for (int r = 0; r < V; ++r) v[r] = cmul(v[r], __ldg(phi_row + t + T * r));
+    fft_inverse<N, V>(v, tw, buf, t);
+#pragma unroll
+    for (int r = 0; r < V; ++r) v[r] = cmul(v[r], __ldg(d_row + t + T * r));
+}
+
+template <int N, int V>
+__device__ __forceinline__ void step_down_adjoint(float2 (&v)[V], const Twiddles<N, V>& tw, float2* buf, int t,
+                                                  const float2* __restrict__ phi_row,
+                                                  const float2* __restrict__ d_row) {
+    constexpr int T = Plan<N, V>::T;
+#pragma unroll
+    for (int r = 0; r < V; ++r) v[r] = cmulc(v[r], __ldg(d_row + t + T * r));
+    fft_forward<N, V>(v, tw, buf, t);
+#pragma unroll
+    for (int r = 0; r < V; ++r) v[r] = cmulc(v[r], __ldg(phi_row + t + T * r));
+    fft_inverse<N, V>(v, tw, buf, t);
+}
+
+template <int N, int V, int MODE>
+__global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs a) {
+    using P = Plan<N, V>;
+    constexpr int T = P::T;
+    constexpr int IPW = 32 / T;
+    extern __shared__ float4 smem_f4[];
+    float2* smem = reinterpret_cast<float2*>(smem_f4);
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int t = lane % T;
+    const int sub = lane / T;
+    const int item_in_block = warp * IPW + sub;
+    const int items_per_block = nwarps * IPW;
+    const int item = blockIdx.x * items_per_block + item_in_block;
+    const int nitems = a.nshots * a.nw;
+    const bool ok = item < nitems;
+    const int iw = ok ? item / a.nshots : 0;
+    const int ishot = ok ? item - iw * a.nshots : 0;
+    const int shot = a.shot0 + ishot;
+    const int slot = shot % a.ring;
+    const int nz = a.nz;
+    float2* buf = smem + item_in_block * P::BUF;
+
+    Twiddles<N, V> tw;
+    init_twiddles<N, V>(tw, t);
+
+    const size_t coef_base = (size_t)iw * nz * N;
+    float2* Sitem = a.S + ((size_t)slot * a.nw + iw) * (size_t)nz * N;
+    float2 v[V];
+
+    if constexpr (MODE == MODE_SOURCE) {
+        const int xs = ok ? __ldg(a.src_ix + shot) : -1;
+        const float2 w = ok ? __ldg(a.wavelet + iw) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int r = 0; r < V; ++r) v[r] = (t + T * r == xs) ? w : make_float2(0.f, 0.f);
+        for (int j = 0; j < nz; ++j) {
+            if (ok) {
+                float2* row = Sitem + (size_t)j * N;
+#pragma unroll
+                for (int r = 0; r < V; ++r) __stcs(row + t + T * r, v[r]);
+            }
+            if (j + 1 < nz)
+                step_down<N, V>(v, tw, buf, t, a.phi + coef_base + (size_t)j * N, a.dss + coef_base + (size_t)j * N);
+        }
+    } else if constexpr (MODE == MODE_ADJOINT) {
+        // R_0: data injected at the receivers
+        const float2* drow = a.din + ((size_t)ishot * a.nw + iw) * a.nrec;
+        if (a.rec_identity) {
+            load_row<N, V>(v, drow, t, ok);
+        } else {
+            __syncwarp();
+            for (int x = t; x < P::BUF; x += T) buf[x] = make_float2(0.f, 0.f);
+            __syncwarp();
+            if (ok) {
+                const int* rix = a.rec_ix + (size_t)shot * a.nrec;
+                for (int rr = t; rr < a.nrec; rr += T) {
+                    const float2 dv = __ldg(drow + rr);
+                    const int x = P::phys(__ldg(rix + rr));
+                    atomicAdd(&buf[x].x, dv.x);
+                    atomicAdd(&buf[x].y, dv.y);
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < V; ++r) v[r] = buf[P::phys(t + T * r)];
+        }
+        float* img = reinterpret_cast<float*>(smem + items_per_block * P::BUF);  // [2][nwarps][N]
+        float* part = a.part + (size_t)blockIdx.x * nz * N;
+        for (int j = 0; j < nz; ++j) {
+            float c[V];
+            {
+                const float2* srow = Sitem + (size_t)j * N;
+#pragma unroll
+                for (int r = 0; r < V; ++r) {
+                    const float2 s = ok ? __ldcs(srow + t + T * r) : make_float2(0.f, 0.f);
+                    c[r] = fmaf(s.x, v[r].x, s.y * v[r].y);
+                }
+            }
+            // sum the items of this warp (lanes with equal t hold equal x)
+#pragma unroll
+            for (int off = T; off < 32; off <<= 1) {
+#pragma unroll
+                for (int r = 0; r < V; ++r) c[r] += __shfl_xor_sync(0xffffffffu, c[r], off);
+            }
+            float* slab = img + ((size_t)(j & 1) * nwarps + warp) * N;
+            if (sub == 0) {
+#pragma unroll
+                for (int r = 0; r < V; ++r) slab[t + T * r] = c[r];
+            }
+            __syncthreads();
+            {
+                const float* rows = img + (size_t)(j & 1) * nwarps * N;
+                for (int x = threadIdx.x; x < N; x += blockDim.x) {
+                    float acc = 0.f;
+                    for (int w = 0; w < nwarps; ++w) acc += rows[w * N + x];
+                    part[(size_t)j * N + x] = acc;
+                }
+            }
+            if (j + 1 < nz)
+                step_down_adjoint<N, V>(v, tw, buf, t, a.phi + coef_base + (size_t)j * N,
+                                        a.dss + coef_base + (size_t)j * N);
+        }
+    } else {  // MODE_FORWARD
+#pragma unroll
+        for (int r = 0; r < V; ++r) v[r] = make_float2(0.f, 0.f);
+        for (int j = nz - 1; j >= 0; --j) {
+            if (j + 1 < nz)
+                step_down<N, V>(v, tw, buf, t, a.phi + coef_base + (size_t)j * N, a.dss + coef_base + (size_t)j * N);
+            const float2* srow = Sitem + (size_t)j * N;
+            const float* mrow = a.m + (size_t)j * N;
+#pragma unroll
+            for (int r = 0; r < V; ++r) {
+                const float2 s = ok ? __ldcs(srow + t + T * r) : make_float2(0.f, 0.f);
+                const float mm = __ldg(mrow + t + T * r);
+                v[r].x = fmaf(s.x, mm, v[r].x);
+                v[r].y = fmaf(s.y, mm, v[r].y);
+            }
+        }
+        float2* orow = a.dout + ((size_t)ishot * a.nw + iw) * a.nrec;
+        if (a.rec_identity) {
+            if (ok) {
+#pragma unroll
+                for (int r = 0; r < V; ++r) orow[t + T * r] = v[r];
+            }
+        } else {
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < V; ++r) buf[P::phys(t + T * r)] = v[r];
+            __syncwarp();
+            if (ok) {
+                const int* rix = a.rec_ix + (size_t)shot * a.nrec;
+                for (int rr = t; rr < a.nrec; rr += T) orow[rr] = buf[P::phys(__ldg(rix + rr))];
+            }
+        }
+    }
+}
+
+// Coefficient tables for every (frequency, depth row): Phi_j / nx in the FFT output order of
+// Plan<N, V>, and D_j in natural order.  Phase arguments are formed in float64 and reduced to
+// [-pi, pi] before the float32 sin / cos.
+template <int N, int V>
+__global__ void tables_kernel(const TableArgs a) {
+    using P = Plan<N, V>;
+    const size_t total = (size_t)a.nw * a.nz * N;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int p = (int)(idx % N);
+        const size_t row = idx / N;
+        const int j = (int)(row % a.nz);
+        const int iw = (int)(row / a.nz);
+        const double omega = 2.0 * kPi * (double)a.freq_hz[iw];
+        const double sref = a.sref[j];
+        // phase shift at the frequency held by table slot p = r T + t
+        {
+            const int t = p % P::T, r = p / P::T;
+            const int k = P::freq_of_position(P::position_of(t, r));
+            const int kk = k < N / 2 ? k : k - N;
+            const double kx = fabs(2.0 * kPi * (double)kk / ((double)N * (double)a.dx));
+            const double ws = omega * sref;
+            const double kz2 = (ws - kx) * (ws + kx);
+            float2 ph;
+            if (kz2 >= 0.0) {
+                double arg = sqrt(kz2) * (double)a.dz;
+                arg = remainder(arg, 2.0 * kPi);
+                float sn, cs;
+                sincosf((float)arg, &sn, &cs);
+                ph = make_float2(cs / (float)N, sn / (float)N);
+            } else {
+                ph = make_float2((float)(exp(-sqrt(-kz2) * (double)a.dz) / (double)N), 0.f);
+            }
+            a.phi[idx] = ph;
+        }
+        // split-step correction at column x = p
+        {
+            const double ds = (double)a.slowness[(size_t)j * N + p] - sref;
+            double arg = omega * ds * (double)a.dz;
+            arg = remainder(arg, 2.0 * kPi);
+            float sn, cs;
+            sincosf((float)arg, &sn, &cs);
+            a.dss[idx] = make_float2(cs, sn);
+        }
+    }
+}
+
+template <int N>
+struct Dispatch {
+    static constexpr int V = points_per_thread(N);
+
+    static cudaError_t tables(const TableArgs& a, cudaStream_t st) {
+        const size_t total = (size_t)a.nw * a.nz * N;
+        size_t blocks = (total + 255) / 256;
+        if (blocks > 65535u * 8u) blocks = 65535u * 8u;
+        ProfScope prof_(KC_TABLES, st);
+        tables_kernel<N, V><<<(unsigned)blocks, 256, 0, st>>>(a);
+        count_launch();
+        return cudaGetLastError();
+    }
+
+    template <int MODE>
+    static cudaError_t sweep(const SweepArgs& a, const SweepShape& sh, cudaStream_t st) {
+        static bool configured = false;
+        if (!configured) {
+            cudaError_t e = cudaFuncSetAttribute(sweep_kernel<N, V, MODE>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+            if (e != cudaSuccess) return e;
+            configured = true;
+        }
+        ProfScope prof_(MODE == MODE_SOURCE ? KC_SOURCE : MODE == MODE_ADJOINT ? KC_ADJOINT : KC_FORWARD, st);
+        sweep_kernel<N, V, MODE><<<sh.blocks, sh.warps * 32, sh.smem, st>>>(a);
+        count_launch();
+        return cudaGetLastError();
+    }
+
+    static cudaError_t sweep_any(int mode, const SweepArgs& a, const SweepShape& sh, cudaStream_t st) {
+        switch (mode) {
+            case MODE_SOURCE: return sweep<MODE_SOURCE>(a, sh, st);
+            case MODE_ADJOINT: return sweep<MODE_ADJOINT>(a, sh, st);
+            default: return sweep<MODE_FORWARD>(a, sh, st);
+        }
+    }
+
+    template <int MODE>
+    static int max_warps_mode() {
+        cudaFuncAttributes attr;
+        if (cudaFuncGetAttributes(&attr, sweep_kernel<N, V, MODE>) != cudaSuccess) return 1;
+        int w = attr.maxThreadsPerBlock / 32;
+        return w < 1 ? 1 : w;
+    }
+    static int max_warps(int mode) {
+        switch (mode) {
+            case MODE_SOURCE: return max_warps_mode<MODE_SOURCE>();
+            case MODE_ADJOINT: return max_warps_mode<MODE_ADJOINT>();
+            default: return max_warps_mode<MODE_FORWARD>();
+        }
+    }
+};
+
+}  // namespace lsm
+
+#define LSM_DEFINE_N(NN)                                                                          \
+    namespace lsm {                                                                               \
+    cudaError_t launch_tables_##NN(const TableArgs& a, cudaStream_t st) {                         \
+        return Dispatch<NN>::tables(a, st);                                                       \
+    }                                                                                             \
+    cudaError_t launch_sweep_##NN(int mode, const SweepArgs& a, const SweepShape& sh,             \
+                                  cudaStream_t st) {                                              \
+        return Dispatch<NN>::sweep_any(mode, a, sh, st);                                          \
+    }                                                                                             \
+    int sweep_max_warps_##NN(int mode) { return Dispatch<NN>::max_warps(mode); }                  \
+    }

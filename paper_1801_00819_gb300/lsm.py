@@ -1,0 +1,222 @@
+"""Python binding of the C ABI in include/lsm.h (argument marshalling only).
+
+Every entry point has the C name and forwards to liblsm_gb300.so through ctypes; all arithmetic
+runs in that library's CUDA kernels.  Device arrays are torch CUDA tensors (or raw integer
+device addresses); host geometry and frequency arrays are numpy arrays.  There is no CPU
+fallback: if the library has not been built, loading it raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblsm_gb300.so")
+
+LSM_OK = 0
+LSM_ERR_ARG = -1
+LSM_ERR_CUDA = -2
+LSM_ERR_WORKSPACE = -3
+LSM_ERR_BREAKDOWN = -4
+LSM_ERR_TIMEOUT = -5
+LSM_ERR_UNSUPPORTED_NX = -6
+
+LSM_OP_FORWARD = 0
+LSM_OP_ADJOINT = 1
+LSM_OP_SOLVE = 2
+
+EXPORTED = ("lsm_workspace_bytes", "lsm_forward", "lsm_adjoint", "lsm_num_windows", "rls_window_solve",
+            "lsm_status_string", "lsm_kernel_launches")
+
+
+class LsmError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {lsm_status_string(status)} ({status})")
+
+
+class lsm_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("nz", ctypes.c_int), ("dx", ctypes.c_float), ("dz", ctypes.c_float)]
+
+
+class lsm_geom(ctypes.Structure):
+    _fields_ = [("ns", ctypes.c_int), ("src_ix", ctypes.POINTER(ctypes.c_int)), ("nrec", ctypes.c_int),
+                ("rec_ix", ctypes.POINTER(ctypes.c_int))]
+
+
+class lsm_freqs(ctypes.Structure):
+    _fields_ = [("nw", ctypes.c_int), ("freq_hz", ctypes.POINTER(ctypes.c_float)),
+                ("wavelet", ctypes.POINTER(ctypes.c_float))]
+
+
+class lsm_window_stats(ctypes.Structure):
+    _fields_ = [("start", ctypes.c_int), ("iters", ctypes.c_int), ("rel_res0", ctypes.c_double),
+                ("rel_res", ctypes.c_double), ("n_forward", ctypes.c_int), ("n_adjoint", ctypes.c_int),
+                ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib_handle = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load liblsm_gb300.so (built by paper_1801_00819_gb300.build); raises if it is missing."""
+    global _lib_handle
+    if _lib_handle is not None:
+        return _lib_handle
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -m paper_1801_00819_gb300.build` "
+                           "(there is no CPU fallback)")
+    try:  # share the CUDA runtime that torch has already loaded, if any
+        import torch  # noqa: F401
+    except Exception:  # pragma: no cover
+        pass
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    lib.lsm_workspace_bytes.restype = ctypes.c_size_t
+    lib.lsm_workspace_bytes.argtypes = [ctypes.POINTER(lsm_grid), ctypes.POINTER(lsm_geom),
+                                        ctypes.POINTER(lsm_freqs), ctypes.c_int, ctypes.c_int]
+    lib.lsm_forward.restype = ctypes.c_int
+    lib.lsm_forward.argtypes = [ctypes.POINTER(lsm_grid), P, ctypes.POINTER(lsm_freqs), ctypes.POINTER(lsm_geom),
+                                P, P, ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t, P]
+    lib.lsm_adjoint.restype = ctypes.c_int
+    lib.lsm_adjoint.argtypes = [ctypes.POINTER(lsm_grid), P, ctypes.POINTER(lsm_freqs), ctypes.POINTER(lsm_geom),
+                                P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t, P]
+    lib.lsm_num_windows.restype = ctypes.c_int
+    lib.lsm_num_windows.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.rls_window_solve.restype = ctypes.c_int
+    lib.rls_window_solve.argtypes = [ctypes.POINTER(lsm_grid), P, ctypes.POINTER(lsm_freqs),
+                                     ctypes.POINTER(lsm_geom), P, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, P,
+                                     ctypes.POINTER(lsm_window_stats), ctypes.c_int, P, ctypes.c_size_t, P]
+    lib.lsm_status_string.restype = ctypes.c_char_p
+    lib.lsm_status_string.argtypes = [ctypes.c_int]
+    lib.lsm_kernel_launches.restype = ctypes.c_ulonglong
+    lib.lsm_kernel_launches.argtypes = []
+    _lib_handle = lib
+    return lib
+
+
+# ------------------------------------------------------------------ argument holders
+
+
+class Grid:
+    def __init__(self, nx: int, nz: int, dx: float, dz: float):
+        self.c = lsm_grid(int(nx), int(nz), float(dx), float(dz))
+
+
+class Geometry:
+    """Host geometry: src_ix [ns] and rec_ix [ns][nrec] (None: receivers at every column)."""
+
+    def __init__(self, src_ix, rec_ix=None, nx: int | None = None):
+        self.src = np.ascontiguousarray(src_ix, dtype=np.int32)
+        ns = int(self.src.shape[0])
+        if rec_ix is None:
+            if nx is None:
+                raise ValueError("nx is needed when rec_ix is None")
+            self.rec = None
+            nrec = int(nx)
+            rec_ptr = ctypes.POINTER(ctypes.c_int)()
+        else:
+            self.rec = np.ascontiguousarray(rec_ix, dtype=np.int32)
+            nrec = int(self.rec.shape[1])
+            rec_ptr = self.rec.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        self.c = lsm_geom(ns, self.src.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), nrec, rec_ptr)
+
+
+class Frequencies:
+    """Host frequency axis (Hz) and complex source spectrum."""
+
+    def __init__(self, freq_hz, wavelet):
+        self.f = np.ascontiguousarray(freq_hz, dtype=np.float32)
+        self.w = np.ascontiguousarray(np.asarray(wavelet, dtype=np.complex64).view(np.float32))
+        self.c = lsm_freqs(int(self.f.shape[0]), self.f.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                           self.w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _nbytes(ws) -> int:
+    if ws is None:
+        return 0
+    return int(ws.numel() * ws.element_size())
+
+
+def _check(status: int, where: str):
+    if status != LSM_OK:
+        raise LsmError(status, where)
+
+
+# ------------------------------------------------------------------ entry points (C names)
+
+
+def lsm_status_string(status: int) -> str:
+    return load_library().lsm_status_string(int(status)).decode()
+
+
+def lsm_kernel_launches() -> int:
+    return int(load_library().lsm_kernel_launches())
+
+
+def lsm_num_windows(ns: int, K: int, slide: int) -> int:
+    return int(load_library().lsm_num_windows(int(ns), int(K), int(slide)))
+
+
+def lsm_workspace_bytes(grid: Grid, geom: Geometry, freqs: Frequencies, nshots: int, op: int) -> int:
+    return int(load_library().lsm_workspace_bytes(ctypes.byref(grid.c), ctypes.byref(geom.c),
+                                                  ctypes.byref(freqs.c), int(nshots), int(op)))
+
+
+def lsm_forward(grid, slowness, freqs, geom, m, d_out, shot0, nshots, workspace, stream=None):
+    """d_out[nshots][nw][nrec] (complex64) = A m for shots shot0 .. shot0+nshots-1."""
+    st = load_library().lsm_forward(ctypes.byref(grid.c), _ptr(slowness), ctypes.byref(freqs.c),
+                                    ctypes.byref(geom.c), _ptr(m), _ptr(d_out), int(shot0), int(nshots),
+                                    _ptr(workspace), _nbytes(workspace), _stream(stream))
+    _check(st, "lsm_forward")
+
+
+def lsm_adjoint(grid, slowness, freqs, geom, d, m_out, shot0, nshots, workspace, accumulate=False,
+                stream=None):
+    """m_out[nz][nx] (=, or += when accumulate) A^T d for shots shot0 .. shot0+nshots-1."""
+    st = load_library().lsm_adjoint(ctypes.byref(grid.c), _ptr(slowness), ctypes.byref(freqs.c),
+                                    ctypes.byref(geom.c), _ptr(d), _ptr(m_out), int(shot0), int(nshots),
+                                    1 if accumulate else 0, _ptr(workspace), _nbytes(workspace), _stream(stream))
+    _check(st, "lsm_adjoint")
+
+
+def rls_window_solve(grid, slowness, freqs, geom, d, lam, K, slide, cg_tol, max_iter, m_inout, workspace,
+                     first_window=0, n_windows=0, stream=None, raise_on_breakdown=True):
+    """Sliding-window CG solve; returns (status, [stats dicts]).  m_inout is updated in place."""
+    lib = load_library()
+    nwin = lib.lsm_num_windows(int(geom.c.ns), int(K), int(slide))
+    cap = max(nwin, 1)
+    stats = (lsm_window_stats * cap)()
+    st = lib.rls_window_solve(ctypes.byref(grid.c), _ptr(slowness), ctypes.byref(freqs.c), ctypes.byref(geom.c),
+                              _ptr(d), float(lam), int(K), int(slide), float(cg_tol), int(max_iter),
+                              int(first_window), int(n_windows), _ptr(m_inout), stats, cap, _ptr(workspace),
+                              _nbytes(workspace), _stream(stream))
+    last = nwin if n_windows <= 0 else min(nwin, first_window + n_windows)
+    out = [stats[i].as_dict() for i in range(max(0, last - first_window))]
+    if st != LSM_OK and (st != LSM_ERR_BREAKDOWN or raise_on_breakdown):
+        raise LsmError(st, "rls_window_solve")
+    return st, out

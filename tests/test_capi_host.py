@@ -1,0 +1,124 @@
+"""CPU-side checks of the C ABI: the library builds for sm_103a, loads, exports every symbol
+include/lsm.h declares, and its host logic (window schedule, argument validation, status strings)
+behaves as documented.  No kernel is launched here."""
+
+import os
+import re
+import shutil
+
+import numpy as np
+import pytest
+
+from oracle import lsm_oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_1801_00819_gb300 import build as B
+    B.build()
+    from paper_1801_00819_gb300 import lsm
+    return lsm
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "lsm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b([a-z_][a-z0-9_]*)\s*\(", src)) - {"if", "sizeof"})
+
+
+def test_header_declares_expected_entry_points():
+    assert _declared_functions() == sorted(["lsm_workspace_bytes", "lsm_forward", "lsm_adjoint", "lsm_num_windows",
+                                            "rls_window_solve", "lsm_status_string", "lsm_kernel_launches"])
+
+
+def test_library_exports_every_declared_symbol(lib):
+    handle = lib.load_library()
+    for name in _declared_functions():
+        assert hasattr(handle, name), name
+    assert set(lib.EXPORTED) == set(_declared_functions())
+
+
+def test_window_count_matches_oracle_schedule(lib):
+    for ns in range(1, 30):
+        for K in range(1, ns + 1):
+            for slide in range(1, 7):
+                assert lib.lsm_num_windows(ns, K, slide) == len(O.window_starts(ns, K, slide))
+    assert lib.lsm_num_windows(240, 5, 3) == 80
+    assert lib.lsm_num_windows(5, 6, 1) == 0
+    assert lib.lsm_num_windows(5, 2, 0) == 0
+
+
+def test_status_strings(lib):
+    assert lib.lsm_status_string(0) == "ok"
+    assert "nx" in lib.lsm_status_string(lib.LSM_ERR_UNSUPPORTED_NX)
+    assert lib.lsm_status_string(-99) == "unknown status"
+
+
+def _holders(lib, nx=64, nz=8, ns=3, nw=4, src=None, rec=None):
+    g = lib.Grid(nx, nz, 10.0, 10.0)
+    geo = lib.Geometry(np.arange(ns) if src is None else src, rec, nx=nx)
+    f = lib.Frequencies(np.linspace(5, 30, nw), np.ones(nw))
+    return g, geo, f
+
+
+def test_validation_rejects_bad_arguments_before_any_launch(lib):
+    before = lib.lsm_kernel_launches()
+    g, geo, f = _holders(lib)
+    fake = 1 << 20  # aligned fake addresses: validation must fail before they are used
+    cases = [
+        (_holders(lib, nx=48), lib.LSM_ERR_UNSUPPORTED_NX),
+        (_holders(lib, nx=2048), lib.LSM_ERR_UNSUPPORTED_NX),
+        (_holders(lib, src=np.array([0, 1, 64])), lib.LSM_ERR_ARG),
+        (_holders(lib, rec=np.full((3, 5), 70)), lib.LSM_ERR_ARG),
+    ]
+    for (gg, gg_geo, gg_f), code in cases:
+        with pytest.raises(lib.LsmError) as ei:
+            lib.lsm_forward(gg, fake, gg_f, gg_geo, fake, fake, 0, 1, None, stream=0)
+        assert ei.value.status == code
+    # misaligned device pointer
+    with pytest.raises(lib.LsmError) as ei:
+        lib.lsm_adjoint(g, fake + 4, f, geo, fake, fake, 0, 1, None, stream=0)
+    assert ei.value.status == lib.LSM_ERR_ARG
+    # shot range
+    with pytest.raises(lib.LsmError):
+        lib.lsm_forward(g, fake, f, geo, fake, fake, 2, 2, None, stream=0)
+    # window arguments
+    with pytest.raises(lib.LsmError):
+        lib.rls_window_solve(g, fake, f, geo, fake, -1.0, 2, 1, 0.0, 3, fake, None, stream=0)
+    with pytest.raises(lib.LsmError):
+        lib.rls_window_solve(g, fake, f, geo, fake, 1.0, 4, 1, 0.0, 3, fake, None, stream=0)
+    assert lib.lsm_kernel_launches() == before
+
+
+def test_workspace_query_and_too_small_workspace(lib):
+    g, geo, f = _holders(lib)
+    fwd = lib.lsm_workspace_bytes(g, geo, f, 3, lib.LSM_OP_FORWARD)
+    adj = lib.lsm_workspace_bytes(g, geo, f, 3, lib.LSM_OP_ADJOINT)
+    sol = lib.lsm_workspace_bytes(g, geo, f, 2, lib.LSM_OP_SOLVE)
+    assert 0 < fwd < adj
+    # tables (2 x nw nz nx complex) plus the source-wavefield ring dominate
+    assert fwd >= (2 + 3) * 4 * 8 * 64 * 8
+    assert sol > 0
+    assert lib.lsm_workspace_bytes(g, geo, f, 4, lib.LSM_OP_FORWARD) == 0
+    assert lib.lsm_workspace_bytes(g, geo, f, 1, 7) == 0
+
+    class FakeWs:
+        def __init__(self, n):
+            self.n = n
+
+        def numel(self):
+            return self.n
+
+        def element_size(self):
+            return 1
+
+        def data_ptr(self):
+            return 1 << 20
+    fake = 1 << 20
+    with pytest.raises(lib.LsmError) as ei:
+        lib.lsm_forward(g, fake, f, geo, fake, fake, 0, 3, FakeWs(fwd - 1), stream=0)
+    assert ei.value.status == lib.LSM_ERR_WORKSPACE

@@ -1,0 +1,185 @@
+"""GPU parity of A (lsm_forward) and A^T (lsm_adjoint) against the FP64 oracle, through the C ABI.
+
+Bar: relative L2 error <= 1e-4 for the float32 path (elementwise comparison on the same seeded,
+float32-rounded inputs).  Sizes span several blocks of items and ragged tails; the full-size
+realistic workload is checked on sampled (shot, frequency) items the oracle computes one by one.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import lsm_oracle as O
+from synth import random_case, config_tiny, config_realistic
+from tests._helpers import oracle_operator, rel_l2, device_survey
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+CASES = [
+    (16, 8, 3, 5),
+    (32, 9, 2, 7),
+    (64, 32, 8, 32),
+    (128, 20, 3, 9),
+    (256, 12, 2, 6),
+    (512, 10, 2, 3),
+    (1024, 6, 1, 3),
+    (64, 1, 3, 3),
+]
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _gpu_forward(torch, ds, m, shot0, nshots):
+    import paper_1801_00819_gb300 as L
+    ws = torch.empty(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, nshots, L.LSM_OP_FORWARD),
+                     dtype=torch.uint8, device="cuda")
+    mt = torch.as_tensor(np.asarray(m, dtype=np.float32), device="cuda")
+    out = torch.empty((nshots, ds.nw, ds.nrec), dtype=torch.complex64, device="cuda")
+    L.lsm_forward(ds.grid, ds.slowness, ds.freqs, ds.geom, mt, out, shot0, nshots, ws)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.complex128)
+
+
+def _gpu_adjoint(torch, ds, d, shot0, nshots, accumulate=None):
+    import paper_1801_00819_gb300 as L
+    ws = torch.empty(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, nshots, L.LSM_OP_ADJOINT),
+                     dtype=torch.uint8, device="cuda")
+    dt = torch.as_tensor(np.asarray(d, dtype=np.complex64), device="cuda")
+    if accumulate is None:
+        out = torch.empty((ds.nz, ds.nx), dtype=torch.float32, device="cuda")
+        L.lsm_adjoint(ds.grid, ds.slowness, ds.freqs, ds.geom, dt, out, shot0, nshots, ws)
+    else:
+        out = torch.as_tensor(np.asarray(accumulate, dtype=np.float32), device="cuda")
+        L.lsm_adjoint(ds.grid, ds.slowness, ds.freqs, ds.geom, dt, out, shot0, nshots, ws, accumulate=True)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(map(str, c)))
+def test_forward_matches_oracle(torch_cuda, case):
+    nx, nz, ns, nw = case
+    sv = random_case(nx, nz, ns, nw, seed=100 + nx + nz)
+    op = oracle_operator(sv)
+    ds = device_survey(sv)
+    m = np.asarray(sv.reflectivity, dtype=np.float32).astype(np.float64)
+    got = _gpu_forward(torch_cuda, ds, m, 0, ns)
+    ref = op.forward(m)
+    err = rel_l2(got, ref)
+    assert err <= TOL, err
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(map(str, c)))
+def test_adjoint_matches_oracle(torch_cuda, case):
+    nx, nz, ns, nw = case
+    sv = random_case(nx, nz, ns, nw, seed=200 + nx + nz)
+    op = oracle_operator(sv)
+    ds = device_survey(sv)
+    rng = np.random.default_rng(7)
+    d = (rng.normal(size=(ns, nw, nx)) + 1j * rng.normal(size=(ns, nw, nx))).astype(np.complex64)
+    got = _gpu_adjoint(torch_cuda, ds, d, 0, ns)
+    ref = op.adjoint(d.astype(np.complex128))
+    err = rel_l2(got, ref)
+    assert err <= TOL, err
+
+
+def test_shot_subrange_and_accumulate(torch_cuda):
+    sv = random_case(64, 16, 6, 5, seed=31)
+    op = oracle_operator(sv)
+    ds = device_survey(sv)
+    rng = np.random.default_rng(3)
+    d = (rng.normal(size=(6, 5, 64)) + 1j * rng.normal(size=(6, 5, 64))).astype(np.complex64)
+    base = rng.normal(size=(16, 64)).astype(np.float32)
+    got = _gpu_adjoint(torch_cuda, ds, d[2:5], 2, 3, accumulate=base)
+    ref = base.astype(np.float64) + op.adjoint(d[2:5].astype(np.complex128), shots=np.arange(2, 5))
+    assert rel_l2(got, ref) <= TOL
+    m = np.asarray(sv.reflectivity, dtype=np.float32).astype(np.float64)
+    gotf = _gpu_forward(torch_cuda, ds, m, 1, 4)
+    reff = op.forward(m, shots=np.arange(1, 5))
+    assert rel_l2(gotf, reff) <= TOL
+
+
+def test_partial_receiver_spread(torch_cuda):
+    """Per-shot receiver subsets (off-end style spreads), including a duplicated column."""
+    sv = random_case(64, 12, 4, 6, seed=41)
+    rng = np.random.default_rng(5)
+    rec = np.stack([np.sort(rng.choice(64, 40, replace=False)) for _ in range(4)]).astype(np.int32)
+    rec[1, 3] = rec[1, 4]
+    op = oracle_operator(sv, rec_ix=rec)
+    ds = device_survey(sv, rec_ix=rec)
+    assert ds.geom.rec is not None
+    m = np.asarray(sv.reflectivity, dtype=np.float32).astype(np.float64)
+    assert rel_l2(_gpu_forward(torch_cuda, ds, m, 0, 4), op.forward(m)) <= TOL
+    d = (rng.normal(size=(4, 6, 40)) + 1j * rng.normal(size=(4, 6, 40))).astype(np.complex64)
+    assert rel_l2(_gpu_adjoint(torch_cuda, ds, d, 0, 4), op.adjoint(d.astype(np.complex128))) <= TOL
+
+
+def test_gpu_dot_product_test(torch_cuda):
+    """<A m, d> = <m, A^T d> with both sides from the GPU operator (float32 arithmetic)."""
+    sv = random_case(128, 40, 4, 16, seed=51)
+    ds = device_survey(sv)
+    rng = np.random.default_rng(9)
+    m = rng.normal(size=(40, 128)).astype(np.float32)
+    d = (rng.normal(size=(4, 16, 128)) + 1j * rng.normal(size=(4, 16, 128))).astype(np.complex64)
+    Am = _gpu_forward(torch_cuda, ds, m, 0, 4)
+    Atd = _gpu_adjoint(torch_cuda, ds, d, 0, 4)
+    lhs = O.real_dot(Am, d.astype(np.complex128))
+    rhs = O.real_dot(m.astype(np.float64), Atd)
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+def test_adjoint_is_deterministic(torch_cuda):
+    sv = random_case(256, 16, 5, 7, seed=61)
+    ds = device_survey(sv)
+    rng = np.random.default_rng(1)
+    d = (rng.normal(size=(5, 7, 256)) + 1j * rng.normal(size=(5, 7, 256))).astype(np.complex64)
+    a = _gpu_adjoint(torch_cuda, ds, d, 0, 5)
+    b = _gpu_adjoint(torch_cuda, ds, d, 0, 5)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_tiny_config_operator(torch_cuda):
+    sv = config_tiny()
+    op = oracle_operator(sv)
+    ds = device_survey(sv)
+    m = np.asarray(sv.reflectivity, dtype=np.float32).astype(np.float64)
+    d = _gpu_forward(torch_cuda, ds, m, 0, sv.ns)
+    assert rel_l2(d, op.forward(m)) <= TOL
+    assert rel_l2(_gpu_adjoint(torch_cuda, ds, d, 0, sv.ns), op.adjoint(d)) <= TOL
+
+
+def test_realistic_full_size_sampled_items(torch_cuda):
+    """512 x 256, 128 frequencies, one 16-shot window in the solver's launch configuration:
+    A is compared on sampled (shot, frequency) rows; A^T on data that is zero except at the
+    sampled items, which the oracle migrates one by one."""
+    sv = config_realistic()
+    ds = device_survey(sv)
+    K, shot0 = sv.window, 40
+    m = np.asarray(sv.reflectivity, dtype=np.float32).astype(np.float64)
+    got = _gpu_forward(torch_cuda, ds, m, shot0, K)
+    samples = [(0, 0), (5, 37), (11, 90), (15, 127)]
+    op = oracle_operator(sv)
+    for ishot, iw in samples:
+        sub = op.with_freqs([iw])
+        ref = sub.forward(m, shots=[shot0 + ishot])[0, 0]
+        assert rel_l2(got[ishot, iw], ref) <= TOL, (ishot, iw)
+    rng = np.random.default_rng(2)
+    d = np.zeros((K, sv.nw, sv.nx), dtype=np.complex64)
+    ref = np.zeros((sv.nz, sv.nx))
+    for ishot, iw in samples[:2]:
+        row = (rng.normal(size=sv.nx) + 1j * rng.normal(size=sv.nx)).astype(np.complex64)
+        d[ishot, iw] = row
+        ref += op.with_freqs([iw]).adjoint(row[None, None, :].astype(np.complex128), shots=[shot0 + ishot])
+    img = _gpu_adjoint(torch_cuda, ds, d, shot0, K)
+    assert rel_l2(img, ref) <= TOL
+    # full-size dot-product property on the whole window
+    dd = (rng.normal(size=(K, sv.nw, sv.nx)) + 1j * rng.normal(size=(K, sv.nw, sv.nx))).astype(np.complex64)
+    lhs = O.real_dot(got, dd.astype(np.complex128))
+    rhs = O.real_dot(m, _gpu_adjoint(torch_cuda, ds, dd, shot0, K))
+    assert abs(lhs - rhs) <= 1e-4 * abs(lhs)

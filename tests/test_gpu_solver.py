@@ -1,0 +1,120 @@
+"""GPU parity of the sliding-window CG solve (rls_window_solve) against the FP64 oracle."""
+
+import numpy as np
+import pytest
+
+from oracle import lsm_oracle as O
+from synth import config_tiny, random_case
+from tests._helpers import oracle_operator, rel_l2, device_survey
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _oracle_data(sv, op):
+    clean = op.forward(np.asarray(sv.reflectivity, dtype=np.float32).astype(np.float64))
+    sigma = sv.noise_pct * np.sqrt(np.mean(np.abs(clean) ** 2))
+    d = (clean + sigma * sv.noise()).astype(np.complex64)
+    lam = float(np.float32(O.regularisation_from_adjoint(op, d.astype(np.complex128))))
+    return d, lam
+
+
+def _gpu_solve(torch, ds, d, lam, K, slide, tol, iters, m0=None, first_window=0, n_windows=0):
+    import paper_1801_00819_gb300 as L
+    ws = torch.empty(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, K, L.LSM_OP_SOLVE), dtype=torch.uint8,
+                     device="cuda")
+    dt = torch.as_tensor(d, device="cuda")
+    m = torch.zeros((ds.nz, ds.nx), dtype=torch.float32, device="cuda") if m0 is None else \
+        torch.as_tensor(np.asarray(m0, dtype=np.float32), device="cuda").clone()
+    status, stats = L.rls_window_solve(ds.grid, ds.slowness, ds.freqs, ds.geom, dt, lam, K, slide, tol, iters, m, ws,
+                                       first_window=first_window, n_windows=n_windows)
+    torch.cuda.synchronize()
+    return m.cpu().numpy().astype(np.float64), stats
+
+
+def test_tiny_config_sliding_solve_matches_oracle(torch_cuda):
+    """64 x 32, 8 shots, 32 frequencies, window 4 / slide 2, 10 CG iterations per window."""
+    sv = config_tiny()
+    op = oracle_operator(sv)
+    d, lam = _oracle_data(sv, op)
+    ds = device_survey(sv)
+    m_gpu, st_gpu = _gpu_solve(torch_cuda, ds, d, lam, sv.window, sv.slide, 0.0, sv.cg_iters)
+    m_ref, st_ref = O.rls_solve(op, d.astype(np.complex128), lam, sv.window, sv.slide, sv.cg_iters)
+    assert [s["start"] for s in st_gpu] == [s.start for s in st_ref] == [0, 2, 4]
+    assert all(s["iters"] == sv.cg_iters for s in st_gpu)
+    for g, r in zip(st_gpu, st_ref):
+        assert abs(g["rel_res0"] - r.rel_res0) <= 1e-3 * r.rel_res0
+        assert g["n_forward"] == r.n_forward and g["n_adjoint"] == r.n_adjoint
+    err = rel_l2(m_gpu, m_ref)
+    assert err <= TOL, err
+
+
+def test_tolerance_stopping_matches_oracle_iteration_counts(torch_cuda):
+    sv = random_case(64, 24, 6, 12, seed=71)
+    op = oracle_operator(sv)
+    d, lam = _oracle_data(sv, op)
+    ds = device_survey(sv)
+    tol = 1e-2
+    m_gpu, st_gpu = _gpu_solve(torch_cuda, ds, d, lam, 3, 2, tol, 50)
+    m_ref, st_ref = O.rls_solve(op, d.astype(np.complex128), lam, 3, 2, 50, tol=tol)
+    assert [s["iters"] for s in st_gpu] == [s.iters for s in st_ref]
+    assert all(s["rel_res"] <= tol for s in st_gpu)
+    assert rel_l2(m_gpu, m_ref) <= TOL
+
+
+def test_window_spanning_all_shots_is_full_lsm(torch_cuda):
+    sv = random_case(128, 16, 4, 8, seed=81)
+    op = oracle_operator(sv)
+    d, lam = _oracle_data(sv, op)
+    ds = device_survey(sv)
+    m_gpu, st = _gpu_solve(torch_cuda, ds, d, lam, 4, 1, 0.0, 8)
+    assert len(st) == 1
+    m_ref, _ = O.cg_window(op, np.arange(4), d.astype(np.complex128), lam, np.zeros((16, 128)), 8)
+    assert rel_l2(m_gpu, m_ref) <= TOL
+
+
+def test_warm_start_from_given_image(torch_cuda):
+    sv = random_case(32, 12, 5, 6, seed=91)
+    op = oracle_operator(sv)
+    d, lam = _oracle_data(sv, op)
+    ds = device_survey(sv)
+    m0 = np.random.default_rng(4).normal(size=(12, 32)).astype(np.float32) * 0.01
+    m_gpu, _ = _gpu_solve(torch_cuda, ds, d, lam, 2, 1, 0.0, 6, m0=m0)
+    m_ref, _ = O.rls_solve(op, d.astype(np.complex128), lam, 2, 1, 6, m0=m0.astype(np.float64))
+    assert rel_l2(m_gpu, m_ref) <= TOL
+
+
+def test_resume_is_bitwise_identical(torch_cuda):
+    """Checkpoint/resume: state is (window index, image); a split run equals an uninterrupted one."""
+    sv = random_case(64, 16, 9, 8, seed=95)
+    op = oracle_operator(sv)
+    d, lam = _oracle_data(sv, op)
+    ds = device_survey(sv)
+    full, _ = _gpu_solve(torch_cuda, ds, d, lam, 4, 2, 0.0, 5)
+    part1, st1 = _gpu_solve(torch_cuda, ds, d, lam, 4, 2, 0.0, 5, n_windows=2)
+    part2, st2 = _gpu_solve(torch_cuda, ds, d, lam, 4, 2, 0.0, 5, m0=part1, first_window=2)
+    assert len(st1) == 2 and len(st2) == 2
+    np.testing.assert_array_equal(full, part2)
+
+
+def test_breakdown_on_nonfinite_data(torch_cuda):
+    import paper_1801_00819_gb300 as L
+    sv = random_case(32, 8, 3, 4, seed=97)
+    ds = device_survey(sv)
+    d = np.zeros((3, 4, 32), dtype=np.complex64)
+    d[1, 2, 5] = np.nan
+    ws = torch_cuda.empty(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, 3, L.LSM_OP_SOLVE),
+                          dtype=torch_cuda.uint8, device="cuda")
+    m = torch_cuda.zeros((8, 32), dtype=torch_cuda.float32, device="cuda")
+    status, _ = L.rls_window_solve(ds.grid, ds.slowness, ds.freqs, ds.geom, torch_cuda.as_tensor(d, device="cuda"),
+                                   1.0, 3, 1, 0.0, 3, m, ws, raise_on_breakdown=False)
+    assert status == L.lsm.LSM_ERR_BREAKDOWN
