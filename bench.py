@@ -1,0 +1,441 @@
+#!/usr/bin/env python
+"""Benchmark of the block-row recursive least-squares migration solve on one GB300.
+
+One step = one complete sliding-window solve of the realistic synthetic survey (512 x 256 grid at
+8 m, 96 shots, 128 frequencies 3-40 Hz, window K = 16 shots, slide 8, every window's CG run to a
+relative normal-equation residual of 1e-3), warm-started window to window, through the C ABI
+(rls_window_solve) with the survey data already resident in HBM.
+
+Metric: shot*omega*depth units per second through A + A^T: each window contributes
+(applications of A + applications of A^T) / 2 * K * nw * nz units; value = units of all ranks /
+(max over ranks of the timed wall time).  ms_per_step is the time to solve the whole survey to
+1e-3 (the time-to-residual half of the metric).
+
+Also reported: the dominant sweep kernel against its roofline (per-launch CUDA-event times taken
+live on the library's stream), the end-to-end number with host buffers (pinned host -> device
+copies of the data and slowness and the device -> host copy of the image inside the timed
+region), SM clocks sampled during the timed region, and the FP64 oracle timed on the host cores
+on a bounded sample (cpu_baseline).
+
+`--impl reference` times the FP64 oracle (test infrastructure, pure numpy) on the host cores as
+the reference arm: each step is one A + A^T application on one shot and 16 frequencies of
+the same workload.
+
+Launch: `python bench.py --gpus 1 --steps K --warmup W`; for N > 1 under torchrun each rank
+solves its own independent survey line (weak scaling, no collective on the data path).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+FP32_LANES_PER_SM = 128     # FP32 FMA lanes per Blackwell SM
+FALLBACK_HBM_GBS = 6800.0   # profiling recipe's fallback copy bandwidth
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sweep_adjoint_realistic_512x256.md")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("gb300", "reference"), default="gb300")
+    ap.add_argument("--workload", choices=("realistic", "tiny"), default="realistic")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample-freqs", type=int, default=128,
+                    help="frequencies in the GPU arm's cpu_baseline sample (about 10-30 s of oracle work)")
+    ap.add_argument("--ref-sample-freqs", type=int, default=16,
+                    help="frequencies per step of the reference arm's sample")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(name, rank=0):
+    from synth import config_realistic, config_tiny
+
+    sv = config_realistic() if name == "realistic" else config_tiny()
+    if name == "tiny":
+        sv.cg_tol, sv.cg_iters = 1e-3, 200
+    sv.noise_seed = sv.noise_seed + rank  # independent line per rank
+    return sv
+
+
+def workload_config(sv, l2_note=True):
+    cfg = {"workload": f"{sv.name} {sv.nx}x{sv.nz} grid, {sv.ns} shots, {sv.nw} freqs "
+                       f"{sv.freqs[0]:g}-{sv.freqs[-1]:g} Hz, window {sv.window}, slide {sv.slide}, "
+                       f"CG to {sv.cg_tol:g}",
+           "nx": sv.nx, "nz": sv.nz, "dx_m": sv.dx, "shots": sv.ns, "freqs": sv.nw, "window_K": sv.window,
+           "slide": sv.slide, "cg_tol": sv.cg_tol, "noise_pct": sv.noise_pct * 100}
+    if l2_note:
+        cfg["l2"] = "inputs larger than L2: each step streams the source-wavefield ring (K*nw*nz*nx c64) " \
+                    "and coefficient tables from HBM"
+    return cfg
+
+
+# ------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ roofline helpers
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+def flops_per_unit(nx):
+    """One split-step depth step of one wavefield: forward + inverse nx-point FFT at the nominal
+    5 n log2 n each, the phase-shift and split-step complex multiplies (6 nx each), and the imaging
+    (adjoint) or scatter-add (forward) term (4 nx)."""
+    return 10 * nx * math.log2(nx) + 16 * nx
+
+
+def bytes_per_unit(nx, nrec, nz, K):
+    """Algorithmic HBM bytes of one unit of an A or A^T sweep: the cached source-wavefield row
+    (8 nx), the Phi and D coefficient rows shared by the K shots of the window (16 nx / K), and the
+    item's data row read or written once over the depth loop (8 nrec / nz)."""
+    return 8 * nx + 16 * nx / K + 8 * nrec / nz
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1801_00819_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(name.encode())
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kclass):
+    """DRAM bytes per launch recorded in the committed ncu summary, if it was taken on the current
+    kernel sources (null otherwise)."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    text = open(PROFILE_SUMMARY).read()
+    m_hash = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
+    m_val = re.search(rf"{kclass}_dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_val or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_val.group(1))
+
+
+# ------------------------------------------------------------------ GPU arm
+
+
+def gpu_arm(args):
+    import numpy as np
+    import torch
+
+    import paper_1801_00819_gb300 as L
+    from paper_1801_00819_gb300.device import to_device, workspace
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1801_00819_gb300 import build as B
+    B.build()
+
+    sv = workload(args.workload, rank)
+    s32 = np.asarray(sv.slowness, dtype=np.float32)
+    ds = to_device(sv.nx, sv.nz, sv.dx, sv.dz, s32, sv.src_ix, sv.rec_ix, sv.freqs, sv.wavelet)
+    K, nw, nz, nx, ns = sv.window, sv.nw, sv.nz, sv.nx, sv.ns
+
+    # synthetic data d = A m + noise, modelled with the library itself in chunks of K shots
+    m_true = torch.as_tensor(np.asarray(sv.reflectivity, dtype=np.float32), device="cuda")
+    d = torch.empty((ns, nw, ds.nrec), dtype=torch.complex64, device="cuda")
+    ws_f = workspace(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, K, L.LSM_OP_ADJOINT))
+    for s0 in range(0, ns, K):
+        n = min(K, ns - s0)
+        L.lsm_forward(ds.grid, ds.slowness, ds.freqs, ds.geom, m_true, d[s0:s0 + n], s0, n, ws_f)
+    rms = float(torch.sqrt(torch.mean(torch.abs(d) ** 2)))
+    noise = torch.as_tensor(sv.noise().astype(np.complex64), device="cuda")
+    d += sv.noise_pct * rms * noise
+    del noise
+    adj = torch.zeros((nz, nx), dtype=torch.float32, device="cuda")
+    for s0 in range(0, ns, K):
+        n = min(K, ns - s0)
+        L.lsm_adjoint(ds.grid, ds.slowness, ds.freqs, ds.geom, d[s0:s0 + n], adj, s0, n, ws_f, accumulate=True)
+    lam = 1e-3 * float(adj.abs().max())
+    del ws_f
+    torch.cuda.synchronize()
+
+    ws = workspace(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, K, L.LSM_OP_SOLVE))
+    m = torch.zeros((nz, nx), dtype=torch.float32, device="cuda")
+
+    def step():
+        m.zero_()
+        _, st = L.rls_window_solve(ds.grid, ds.slowness, ds.freqs, ds.geom, d, lam, K, sv.slide, sv.cg_tol,
+                                   sv.cg_iters, m, ws)
+        return st
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = L.lsm_kernel_launches()
+    L.lsm_profile_start()
+    ev0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        stats.append(step())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    prof = L.lsm_profile_stop()
+    launches = L.lsm_kernel_launches() - launches0
+    barrier()
+    clk = clocks.stop()
+    t_ms = ev0.elapsed_time(ev1)
+    t_max = t_ms
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+
+    units_per_pass = K * nw * nz
+    units = sum((w["n_forward"] + w["n_adjoint"]) / 2 * units_per_pass for st in stats for w in st)
+    value = units * world / (t_max / 1e3)
+    iters = [w["iters"] for w in stats[-1]]
+    final_res = [w["rel_res"] for w in stats[-1]]
+
+    # dominant sweep kernel vs its roofline
+    dom = max(("adjoint", "forward"), key=lambda k: prof[k]["ms"])
+    avg_ms = prof[dom]["ms"] / max(prof[dom]["launches"], 1)
+    fl = flops_per_unit(nx) * units_per_pass
+    by = bytes_per_unit(nx, ds.nrec, nz, K) * units_per_pass
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    alu_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    peaks, peak_src = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    alu_ach = fl / (avg_ms / 1e3) / 1e12
+    hbm_ach = by / (avg_ms / 1e3) / 1e9
+    traffic = profiled_traffic(dom)
+    alu = {"bound": "alu", "achieved": round(alu_ach, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
+           "frac": round(alu_ach / alu_peak, 4),
+           "peak_source": f"derived: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                          f"{sm_max:g} MHz"}
+    hbm = {"bound": "hbm", "achieved": round(hbm_ach, 1), "peak": hbm_peak, "unit": "GB/s",
+           "frac": round(hbm_ach / hbm_peak, 4), "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"
+           if peak_src == "measured" else "fallback 6.8 TB/s (MEASURED_PEAKS.json absent)"}
+    primary, secondary = (alu, hbm) if alu["frac"] >= hbm["frac"] else (hbm, alu)
+    roofline = dict(primary)
+    roofline["traffic"] = traffic
+    roofline["kernel"] = f"{dom} sweep (sweep_kernel MODE_{dom.upper()}, nx={nx})"
+    roofline["launch_ms"] = round(avg_ms, 4)
+    roofline["algorithmic_per_unit"] = {"flop": flops_per_unit(nx), "bytes": bytes_per_unit(nx, ds.nrec, nz, K)}
+    roofline["units_per_launch"] = units_per_pass
+    roofline["secondary"] = secondary
+
+    out = {"metric": "shot*omega*depth steps/s for A+A^T (window-RLS solve to 1e-3 residual)",
+           "value": round(value, 1), "unit": "units/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+           "config": workload_config(sv), "roofline": roofline, "clocks": clk, "gpu_launches": int(launches),
+           "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items()},
+           "kernel_launches": {k: v["launches"] for k, v in prof.items()},
+           "cg": {"windows": len(stats[-1]), "iters_per_window": iters, "total_iters": int(sum(iters)),
+                  "max_final_rel_res": max(final_res), "time_to_tol_ms": round(t_max / args.steps, 3)}}
+
+    # end to end through the public API with host buffers
+    if not args.no_e2e:
+        d_host = d.cpu().pin_memory()
+        s_host = torch.as_tensor(s32).pin_memory()
+        img_host = torch.empty((nz, nx), dtype=torch.float32).pin_memory()
+        d_dev = torch.empty_like(d)
+        s_dev = torch.empty_like(ds.slowness)
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats_e = []
+        for _ in range(args.steps):
+            d_dev.copy_(d_host, non_blocking=True)
+            s_dev.copy_(s_host, non_blocking=True)
+            m.zero_()
+            _, st = L.rls_window_solve(ds.grid, s_dev, ds.freqs, ds.geom, d_dev, lam, K, sv.slide, sv.cg_tol,
+                                       sv.cg_iters, m, ws)
+            img_host.copy_(m, non_blocking=True)
+            stats_e.append(st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        te = e0.elapsed_time(e1)
+        if world > 1:
+            import torch.distributed as dist
+            tt = torch.tensor([te], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        units_e = sum((w["n_forward"] + w["n_adjoint"]) / 2 * units_per_pass for st in stats_e for w in st)
+        out["e2e"] = {"value": round(units_e * world / (te / 1e3), 1), "unit": "units/s",
+                      "h2d_bytes_per_step": int(d_host.numel() * 8 + s_host.numel() * 4),
+                      "d2h_bytes_per_step": int(img_host.numel() * 4), "ms_per_step": round(te / args.steps, 3)}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(sv, args.cpu_sample_freqs)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ oracle (CPU) arm
+
+
+def oracle_sample(sv, n_freqs, n_shots=1):
+    """One A + A^T of the FP64 oracle on n_shots shots from shot 40 (or the middle shot) and the
+    first n_freqs frequencies, at the workload's full grid; returns (units, seconds)."""
+    import numpy as np
+
+    from oracle import lsm_oracle as O
+
+    op = O.SplitStepOperator(sv.slowness, sv.dx, sv.dz, sv.freqs, sv.wavelet, sv.src_ix, sv.rec_ix)
+    sub = op.with_freqs(np.arange(min(n_freqs, sv.nw)))
+    shot = min(40, sv.ns // 2)
+    shots = list(range(shot, min(sv.ns, shot + n_shots)))
+    t0 = time.perf_counter()
+    dd = sub.forward(sv.reflectivity, shots=shots)
+    sub.adjoint(dd, shots=shots)
+    dt = time.perf_counter() - t0
+    return len(shots) * sub.nw * sv.nz, dt
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count()
+
+
+def cpu_baseline(sv, n_freqs, n_shots=3):
+    units, dt = oracle_sample(sv, n_freqs, n_shots)
+    return {"value": round(units / dt, 2), "unit": "units/s", "cores": host_cores(), "kind": "oracle",
+            "sample": f"FP64 oracle (numpy, naive DFT matrices), one A + A^T on {n_shots} shots x "
+                      f"{min(n_freqs, sv.nw)} frequencies x {sv.nz} depths at {sv.nx} columns = {units} units "
+                      f"in {dt:.2f} s"}
+
+
+def reference_arm(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    sv = workload(args.workload, 0)
+    for _ in range(args.warmup):
+        oracle_sample(sv, min(4, args.ref_sample_freqs))
+    units_total, t_total, per = 0, 0.0, []
+    for _ in range(args.steps):
+        u, dt = oracle_sample(sv, args.ref_sample_freqs)
+        units_total += u
+        t_total += dt
+        per.append(dt)
+    value = units_total / t_total
+    base = {"value": round(value, 2), "unit": "units/s", "cores": host_cores(), "kind": "oracle",
+            "sample": f"each step: one A + A^T on 1 shot x {min(args.ref_sample_freqs, sv.nw)} frequencies of the "
+                      f"workload (FP64 numpy oracle)"}
+    out = {"impl": "reference", "metric": "shot*omega*depth steps/s for A+A^T (window-RLS solve to 1e-3 residual)",
+           "value": round(value, 2), "unit": "units/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(1e3 * t_total / args.steps, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+           "config": workload_config(sv, l2_note=False), "cpu_baseline": base,
+           "e2e": {"value": round(value, 2), "unit": "units/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

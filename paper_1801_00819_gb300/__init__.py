@@ -14,6 +14,8 @@ from .lsm import (  # noqa: F401
     lsm_forward,
     lsm_kernel_launches,
     lsm_num_windows,
+    lsm_profile_start,
+    lsm_profile_stop,
     lsm_status_string,
     lsm_workspace_bytes,
     rls_window_solve,

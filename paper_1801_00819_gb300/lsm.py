@@ -29,7 +29,9 @@ LSM_OP_ADJOINT = 1
 LSM_OP_SOLVE = 2
 
 EXPORTED = ("lsm_workspace_bytes", "lsm_forward", "lsm_adjoint", "lsm_num_windows", "rls_window_solve",
-            "lsm_status_string", "lsm_kernel_launches")
+            "lsm_status_string", "lsm_kernel_launches", "lsm_profile_start", "lsm_profile_stop")
+
+KERNEL_CLASSES = ("tables", "source", "adjoint", "forward", "vector")
 
 
 class LsmError(RuntimeError):
@@ -59,6 +61,10 @@ class lsm_window_stats(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class lsm_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_ulonglong * 5), ("ms", ctypes.c_double * 5)]
 
 
 _lib_handle = None
@@ -98,6 +104,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lsm_status_string.argtypes = [ctypes.c_int]
     lib.lsm_kernel_launches.restype = ctypes.c_ulonglong
     lib.lsm_kernel_launches.argtypes = []
+    lib.lsm_profile_start.restype = None
+    lib.lsm_profile_start.argtypes = []
+    lib.lsm_profile_stop.restype = ctypes.c_int
+    lib.lsm_profile_stop.argtypes = [ctypes.POINTER(lsm_profile)]
     _lib_handle = lib
     return lib
 
@@ -176,6 +186,19 @@ def lsm_status_string(status: int) -> str:
 
 def lsm_kernel_launches() -> int:
     return int(load_library().lsm_kernel_launches())
+
+
+def lsm_profile_start() -> None:
+    """Start per-launch CUDA-event timing of every kernel the library launches."""
+    load_library().lsm_profile_start()
+
+
+def lsm_profile_stop() -> dict:
+    """Stop timing; returns {class: {"launches": n, "ms": total}} for each kernel class."""
+    prof = lsm_profile()
+    _check(load_library().lsm_profile_stop(ctypes.byref(prof)), "lsm_profile_stop")
+    return {name: {"launches": int(prof.launches[i]), "ms": float(prof.ms[i])}
+            for i, name in enumerate(KERNEL_CLASSES)}
 
 
 def lsm_num_windows(ns: int, K: int, slide: int) -> int:

@@ -1,0 +1,61 @@
+"""Run one window of A and A^T on a synthetic survey, for timing and profiling the sweep kernels.
+
+    python -m paper_1801_00819_gb300.sweep_case [--workload realistic|tiny] [--reps N]
+
+Prepares the workload's grid, velocity, geometry and frequencies on the device, random data for
+one window of K shots, then calls lsm_forward and lsm_adjoint through the C ABI `reps` times each
+(each call builds the coefficient tables, computes the window's source wavefields and runs one
+sweep).  Prints per-class kernel times from the library's event timing.  The inputs are random,
+so no modelling pass precedes the timed calls.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="realistic", choices=("realistic", "tiny", "precision"))
+    ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--shots", type=int, default=0, help="shots per call (default: the window length)")
+    args = ap.parse_args()
+
+    import torch
+
+    import paper_1801_00819_gb300 as L
+    from paper_1801_00819_gb300.device import to_device, workspace
+    from synth import config_precision, config_realistic, config_tiny
+
+    sv = {"realistic": config_realistic, "tiny": config_tiny, "precision": config_precision}[args.workload]()
+    K = args.shots or sv.window
+    ds = to_device(sv.nx, sv.nz, sv.dx, sv.dz, sv.slowness, sv.src_ix, sv.rec_ix, sv.freqs, sv.wavelet)
+    rng = np.random.default_rng(0)
+    d = torch.as_tensor((rng.normal(size=(K, sv.nw, sv.nx)) + 1j * rng.normal(size=(K, sv.nw, sv.nx)))
+                        .astype(np.complex64), device="cuda")
+    m = torch.as_tensor(np.asarray(sv.reflectivity, dtype=np.float32), device="cuda")
+    img = torch.empty_like(m)
+    out = torch.empty_like(d)
+    ws = workspace(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, K, L.LSM_OP_ADJOINT))
+    L.lsm_profile_start()
+    for _ in range(args.reps):
+        L.lsm_forward(ds.grid, ds.slowness, ds.freqs, ds.geom, m, out, 0, K, ws)
+        L.lsm_adjoint(ds.grid, ds.slowness, ds.freqs, ds.geom, d, img, 0, K, ws)
+    torch.cuda.synchronize()
+    prof = L.lsm_profile_stop()
+    print(json.dumps({"workload": sv.name, "K": K, "nw": sv.nw, "nz": sv.nz, "nx": sv.nx,
+                      "per_launch_ms": {k: (v["ms"] / v["launches"] if v["launches"] else 0.0)
+                                        for k, v in prof.items()}}))
+
+
+if __name__ == "__main__":
+    main()

@@ -32,7 +32,8 @@ def _declared_functions():
 
 def test_header_declares_expected_entry_points():
     assert _declared_functions() == sorted(["lsm_workspace_bytes", "lsm_forward", "lsm_adjoint", "lsm_num_windows",
-                                            "rls_window_solve", "lsm_status_string", "lsm_kernel_launches"])
+                                            "rls_window_solve", "lsm_status_string", "lsm_kernel_launches",
+                                            "lsm_profile_start", "lsm_profile_stop"])
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -50,6 +51,13 @@ def test_window_count_matches_oracle_schedule(lib):
     assert lib.lsm_num_windows(240, 5, 3) == 80
     assert lib.lsm_num_windows(5, 6, 1) == 0
     assert lib.lsm_num_windows(5, 2, 0) == 0
+
+
+def test_profile_without_launches_is_empty(lib):
+    lib.lsm_profile_start()
+    prof = lib.lsm_profile_stop()
+    assert set(prof) == set(lib.KERNEL_CLASSES)
+    assert all(v["launches"] == 0 and v["ms"] == 0.0 for v in prof.values())
 
 
 def test_status_strings(lib):
