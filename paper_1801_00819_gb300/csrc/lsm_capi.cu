@@ -81,22 +81,28 @@ static int max_warps_for(int nx, int mode) {
     }
 }
 
-SweepShape sweep_shape(int nx, int mode, int nitems, int num_sms) {
+SweepShape sweep_shape(int nx, int mode, int nshots, int nw, int num_sms) {
     const int V = points_per_thread(nx);
     const int T = nx / V;
     const int ipw = 32 / T;
+    const int nitems = nshots * nw;
     const size_t buf = (size_t)(nx + nx / 16) * sizeof(float2);
-    const size_t per_warp = ipw * buf + (mode == MODE_ADJOINT ? 2 * (size_t)nx * sizeof(float) : 0);
     const int warps_total = (nitems + ipw - 1) / ipw;
-    int maxw = std::min(16, max_warps_for(nx, mode));
-    maxw = std::min<int>(maxw, (int)((227 * 1024) / per_warp));
-    maxw = std::max(maxw, 1);
+    // shared memory of a block of w warps (must match sweep_smem_bytes in lsm_sweep.cuh)
+    auto wslots_of = [&](int w) { return std::min(nw, (w * ipw + nshots - 1) / nshots + 1); };
+    auto smem_of = [&](int w) {
+        return (size_t)w * ipw * buf + 2 * ((size_t)wslots_of(w) * 2 * nx * sizeof(float2) + (size_t)nx * sizeof(float)) +
+               (mode == MODE_ADJOINT ? (size_t)2 * w * nx * sizeof(float) : 0);
+    };
+    int maxw = std::min(V >= 32 ? 8 : 16, max_warps_for(nx, mode));
+    while (maxw > 1 && smem_of(maxw) > 227 * 1024) --maxw;
     int warps = (warps_total + num_sms - 1) / num_sms;
     warps = std::max(1, std::min(warps, maxw));
     SweepShape s;
     s.warps = warps;
     s.blocks = (warps_total + warps - 1) / warps;
-    s.smem = per_warp * warps;
+    s.wslots = wslots_of(warps);
+    s.smem = smem_of(warps);
     return s;
 }
 
@@ -196,7 +202,7 @@ Layout make_layout(const lsm_grid* g, const lsm_geom* geo, const lsm_freqs* f, i
     L.S = take((size_t)nshots * nw * plane * sizeof(float2));
     L.nparts = 0;
     if (op == LSM_OP_ADJOINT || op == LSM_OP_SOLVE) {
-        const SweepShape sh = sweep_shape(g->nx, MODE_ADJOINT, (int)(nshots * nw), num_sms);
+        const SweepShape sh = sweep_shape(g->nx, MODE_ADJOINT, nshots, (int)nw, num_sms);
         L.nparts = sh.blocks;
     }
     L.part = take((size_t)L.nparts * plane * sizeof(float));
@@ -308,7 +314,8 @@ SweepArgs base_args(const lsm_grid* g, const lsm_freqs* f, const lsm_geom* geo, 
 cudaError_t run_source(SweepArgs a, int shot0, int n, int num_sms, cudaStream_t st) {
     a.shot0 = shot0;
     a.nshots = n;
-    const SweepShape sh = sweep_shape(a.nx, MODE_SOURCE, n * a.nw, num_sms);
+    const SweepShape sh = sweep_shape(a.nx, MODE_SOURCE, n, a.nw, num_sms);
+    a.wslots = sh.wslots;
     return launch_sweep(MODE_SOURCE, a, sh, st);
 }
 
@@ -317,7 +324,8 @@ cudaError_t run_forward(SweepArgs a, int shot0, int n, const float* m, float2* d
     a.nshots = n;
     a.m = m;
     a.dout = dout;
-    const SweepShape sh = sweep_shape(a.nx, MODE_FORWARD, n * a.nw, num_sms);
+    const SweepShape sh = sweep_shape(a.nx, MODE_FORWARD, n, a.nw, num_sms);
+    a.wslots = sh.wslots;
     return launch_sweep(MODE_FORWARD, a, sh, st);
 }
 
@@ -326,7 +334,8 @@ cudaError_t run_adjoint(SweepArgs a, int shot0, int n, const float2* din, int nu
     a.shot0 = shot0;
     a.nshots = n;
     a.din = din;
-    const SweepShape sh = sweep_shape(a.nx, MODE_ADJOINT, n * a.nw, num_sms);
+    const SweepShape sh = sweep_shape(a.nx, MODE_ADJOINT, n, a.nw, num_sms);
+    a.wslots = sh.wslots;
     *nparts = sh.blocks;
     return launch_sweep(MODE_ADJOINT, a, sh, st);
 }

@@ -17,6 +17,7 @@ struct SweepArgs {
     int nx, nz, nw, nrec;
     int shot0, nshots, ring;
     int rec_identity;              // 1: receivers at every column in order
+    int wslots;                    // staging slots: most frequencies any block's items span
     const int* src_ix;             // device [ns]
     const int* rec_ix;             // device [ns][nrec] (unused when rec_identity)
     const float2* wavelet;         // device [nw]
@@ -39,16 +40,18 @@ struct TableArgs {
     float2* dss;
 };
 
-// Launch geometry of a sweep: grid.x blocks of `warps` warps.
+// Launch geometry of a sweep: grid.x blocks of `warps` warps whose items span at most `wslots`
+// frequencies, with `smem` bytes of dynamic shared memory.
 struct SweepShape {
     int blocks;
     int warps;
+    int wslots;
     size_t smem;
 };
 
 bool nx_supported(int nx);
 // Block count of the adjoint sweep for this many items (partial images to reduce).
-SweepShape sweep_shape(int nx, int mode, int nitems, int num_sms);
+SweepShape sweep_shape(int nx, int mode, int nshots, int nw, int num_sms);
 cudaError_t launch_tables(const TableArgs& a, cudaStream_t st);
 cudaError_t launch_sweep(int mode, const SweepArgs& a, const SweepShape& shape, cudaStream_t st);
 
@@ -68,7 +71,7 @@ LSM_DECLARE_N(1024)
 #undef LSM_DECLARE_N
 
 // points per thread chosen for each nx
-constexpr int points_per_thread(int nx) { return nx >= 1024 ? 32 : 16; }
+constexpr int points_per_thread(int nx) { return nx >= 512 ? 32 : 16; }
 
 void count_launch(int n = 1);
 

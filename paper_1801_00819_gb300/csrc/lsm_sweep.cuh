@@ -1,17 +1,23 @@
 // Depth-sweep kernels of the shot-profile split-step operator (Eq. 1, Eq. 2; Examples section).
 //
 // One (shot, frequency) item is held in registers by T = N / V threads for the whole depth loop;
-// a warp holds 32 / T items.  Per depth row j the item runs one split-step step
+// a warp holds 32 / T items and a block `ipb` consecutive items in frequency-major order, so a
+// block's items span only a few frequencies.  Per depth row j every item runs one step
 //   P_j u   = D_j . F^-1 (Phi_j . F u)                    (source and forward sweeps)
 //   P_j^H u = F^-1 (conj(Phi_j) . F (conj(D_j) . u))      (adjoint sweep)
-// with Phi_j (already divided by nx and stored in the FFT's output order) and D_j read from
-// precomputed coefficient tables shared by every shot at that frequency.
+// with Phi_j (already divided by nx and stored in the FFT's output order) and D_j taken from
+// precomputed coefficient tables shared by every shot at that frequency.  The block stages the
+// Phi and D rows of its frequencies for the next depth (and, in the forward sweep, the model row)
+// into double-buffered shared memory with cp.async while it computes the current depth, and each
+// item requests its next source-wavefield row into registers one step early, so no global-memory
+// latency sits on the critical path of a step.  One block barrier per depth hands the staged
+// buffers over.
 //
 //   MODE_SOURCE : S_0 = W(w) delta(x - x_s); store S_j, S_{j+1} = P_j S_j.
 //   MODE_ADJOINT: R_0 = injected data; image_j += Re conj(S_j) R_j; R_{j+1} = P_j^H R_j.
-//                 The block sums its items' image rows every depth (one barrier per row) and
-//                 writes one partial row per block; a separate pass adds the partials in a
-//                 fixed order, so the image is deterministic.
+//                 The block sums its items' image rows every depth and writes one partial row
+//                 per block; a separate pass adds the partials in a fixed order, so the image is
+//                 deterministic.
 //   MODE_FORWARD: U <- P_j U_{j+1} + S_j m_j from j = nz-1 up to 0; record U_0.
 #pragma once
 
@@ -20,47 +26,69 @@
 
 namespace lsm {
 
-template <int N, int V>
-struct SweepGeom {
-    using P = Plan<N, V>;
-    static constexpr int T = P::T;
-    static constexpr int IPW = 32 / T;  // items per warp
-};
+// ------------------------------------------------------------------ cp.async helpers
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// ------------------------------------------------------------------ one depth step
 
 template <int N, int V>
 __device__ __forceinline__ void load_row(float2 (&v)[V], const float2* __restrict__ row, int t, bool ok) {
     constexpr int T = Plan<N, V>::T;
 #pragma unroll
-    for (int r = 0; r < V; ++r) v[r] = ok ? __ldg(row + t + T * r) : make_float2(0.f, 0.f);
+    for (int r = 0; r < V; ++r) v[r] = ok ? __ldcs(row + t + T * r) : make_float2(0.f, 0.f);
 }
 
+// phi, dss: this depth's rows staged in shared memory
 template <int N, int V>
 __device__ __forceinline__ void step_down(float2 (&v)[V], const Twiddles<N, V>& tw, float2* buf, int t,
-                                          const float2* __restrict__ phi_row, const float2* __restrict__ d_row) {
+                                          const float2* phi, const float2* dss) {
     constexpr int T = Plan<N, V>::T;
     fft_forward<N, V>(v, tw, buf, t);
 #pragma unroll
-    for (int r = 0; r < V; ++r) v[r] = cmul(v[r], __ldg(phi_row + t + T * r));
+    for (int r = 0; r < V; ++r) v[r] = cmul(v[r], phi[t + T * r]);
     fft_inverse<N, V>(v, tw, buf, t);
 #pragma unroll
-    for (int r = 0; r < V; ++r) v[r] = cmul(v[r], __ldg(d_row + t + T * r));
+    for (int r = 0; r < V; ++r) v[r] = cmul(v[r], dss[t + T * r]);
 }
 
 template <int N, int V>
 __device__ __forceinline__ void step_down_adjoint(float2 (&v)[V], const Twiddles<N, V>& tw, float2* buf, int t,
-                                                  const float2* __restrict__ phi_row,
-                                                  const float2* __restrict__ d_row) {
+                                                  const float2* phi, const float2* dss) {
     constexpr int T = Plan<N, V>::T;
 #pragma unroll
-    for (int r = 0; r < V; ++r) v[r] = cmulc(v[r], __ldg(d_row + t + T * r));
+    for (int r = 0; r < V; ++r) v[r] = cmulc(v[r], dss[t + T * r]);
     fft_forward<N, V>(v, tw, buf, t);
 #pragma unroll
-    for (int r = 0; r < V; ++r) v[r] = cmulc(v[r], __ldg(phi_row + t + T * r));
+    for (int r = 0; r < V; ++r) v[r] = cmulc(v[r], phi[t + T * r]);
     fft_inverse<N, V>(v, tw, buf, t);
 }
 
+// ------------------------------------------------------------------ shared-memory layout
+
+// Threads per block the kernel is compiled for: 32 points per thread need up to ~250 registers,
+// which leaves room for 8 warps per SM; 16 points per thread fit 16 warps at 128 registers.
+template <int V>
+constexpr int sweep_max_threads() { return V >= 32 ? 256 : 512; }
+
+// Bytes of dynamic shared memory for a block of `warps` warps whose items span at most `wslots`
+// frequencies (mirrored on the host by sweep_shape): per-item exchange buffers, the block's
+// double-buffered staging of [wslots][Phi row, D row] plus one model row, and the adjoint's
+// double-buffered per-warp image rows.
+template <int N, int V>
+constexpr size_t sweep_smem_bytes(int warps, int wslots, bool adjoint) {
+    return (size_t)warps * (32 / Plan<N, V>::T) * Plan<N, V>::BUF * sizeof(float2) +
+           2 * ((size_t)wslots * 2 * N * sizeof(float2) + (size_t)N * sizeof(float)) +
+           (adjoint ? (size_t)2 * warps * N * sizeof(float) : 0);
+}
+
 template <int N, int V, int MODE>
-__global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs a) {
+__global__ void __launch_bounds__(sweep_max_threads<V>()) sweep_kernel(const SweepArgs a) {
     using P = Plan<N, V>;
     constexpr int T = P::T;
     constexpr int IPW = 32 / T;
@@ -72,40 +100,78 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs a) {
     const int nwarps = blockDim.x >> 5;
     const int t = lane % T;
     const int sub = lane / T;
-    const int item_in_block = warp * IPW + sub;
-    const int items_per_block = nwarps * IPW;
-    const int item = blockIdx.x * items_per_block + item_in_block;
+    const int ipb = nwarps * IPW;
     const int nitems = a.nshots * a.nw;
+    // items are frequency-major: item = iw * nshots + ishot
+    const int item = blockIdx.x * ipb + warp * IPW + sub;
     const bool ok = item < nitems;
-    const int iw = ok ? item / a.nshots : 0;
+    const int w_first = min(blockIdx.x * ipb, nitems - 1) / a.nshots;
+    const int w_last = (min((blockIdx.x + 1) * ipb, nitems) - 1) / a.nshots;
+    const int nslots = w_last - w_first + 1;  // <= a.wslots
+    const int iw = ok ? item / a.nshots : w_first;
     const int ishot = ok ? item - iw * a.nshots : 0;
     const int shot = a.shot0 + ishot;
     const int slot = shot % a.ring;
+    const int wslot = iw - w_first;
     const int nz = a.nz;
-    float2* buf = smem + item_in_block * P::BUF;
+
+    // shared memory: exchange buffers | staging [2][wslots][2][N] float2 + [2][N] float | images
+    float2* buf = smem + (warp * IPW + sub) * P::BUF;
+    float2* stage = smem + ipb * P::BUF;
+    const int stage_buf = a.wslots * 2 * N;  // float2 per staging buffer (coefficients)
+    float* mstage = reinterpret_cast<float*>(stage + 2 * stage_buf);  // [2][N]
+    float* img = mstage + 2 * N;                                        // [2][nwarps][N]
 
     Twiddles<N, V> tw;
     init_twiddles<N, V>(tw, t);
 
-    const size_t coef_base = (size_t)iw * nz * N;
     float2* Sitem = a.S + ((size_t)slot * a.nw + iw) * (size_t)nz * N;
     float2 v[V];
+
+    // the whole block stages the Phi and D rows of depth `row` for its frequencies into
+    // buffer b (and the model row when asked), as one cp.async group per thread
+    auto stage_rows = [&](int row, int b, bool with_model) {
+        constexpr int CH = N / 2;  // 16-byte chunks per complex row
+        float2* dst = stage + b * stage_buf;
+        const int total = nslots * 2 * CH;
+        for (int c = threadIdx.x; c < total; c += blockDim.x) {
+            const int sl = c / (2 * CH);
+            const int rem = c - sl * 2 * CH;
+            const int which = rem / CH;
+            const int ch = rem - which * CH;
+            const float2* src = (which ? a.dss : a.phi) + ((size_t)(w_first + sl) * nz + row) * N + 2 * ch;
+            cp_async16(dst + (sl * 2 + which) * N + 2 * ch, src);
+        }
+        if (with_model) {
+            for (int c = threadIdx.x; c < N / 4; c += blockDim.x)
+                cp_async16(mstage + b * N + 4 * c, a.m + (size_t)row * N + 4 * c);
+        }
+        cp_async_commit();
+    };
+    auto phi_of = [&](int b) -> const float2* { return stage + b * stage_buf + (wslot * 2) * N; };
+    auto dss_of = [&](int b) -> const float2* { return stage + b * stage_buf + (wslot * 2 + 1) * N; };
 
     if constexpr (MODE == MODE_SOURCE) {
         const int xs = ok ? __ldg(a.src_ix + shot) : -1;
         const float2 w = ok ? __ldg(a.wavelet + iw) : make_float2(0.f, 0.f);
 #pragma unroll
         for (int r = 0; r < V; ++r) v[r] = (t + T * r == xs) ? w : make_float2(0.f, 0.f);
+        if (nz > 1) stage_rows(0, 0, false);
         for (int j = 0; j < nz; ++j) {
             if (ok) {
                 float2* row = Sitem + (size_t)j * N;
 #pragma unroll
                 for (int r = 0; r < V; ++r) __stcs(row + t + T * r, v[r]);
             }
-            if (j + 1 < nz)
-                step_down<N, V>(v, tw, buf, t, a.phi + coef_base + (size_t)j * N, a.dss + coef_base + (size_t)j * N);
+            if (j + 1 < nz) {
+                cp_async_wait_all();
+                __syncthreads();
+                if (j + 2 < nz) stage_rows(j + 1, (j + 1) & 1, false);
+                step_down<N, V>(v, tw, buf, t, phi_of(j & 1), dss_of(j & 1));
+            }
         }
     } else if constexpr (MODE == MODE_ADJOINT) {
+        if (nz > 1) stage_rows(0, 0, false);
         // R_0: data injected at the receivers
         const float2* drow = a.din + ((size_t)ishot * a.nw + iw) * a.nrec;
         if (a.rec_identity) {
@@ -127,18 +193,16 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs a) {
 #pragma unroll
             for (int r = 0; r < V; ++r) v[r] = buf[P::phys(t + T * r)];
         }
-        float* img = reinterpret_cast<float*>(smem + items_per_block * P::BUF);  // [2][nwarps][N]
         float* part = a.part + (size_t)blockIdx.x * nz * N;
+        // s holds S_j; the row of depth j+1 is requested right after imaging depth j so that
+        // its HBM latency hides behind the propagation step
+        float2 s[V];
+        load_row<N, V>(s, Sitem, t, ok);
         for (int j = 0; j < nz; ++j) {
             float c[V];
-            {
-                const float2* srow = Sitem + (size_t)j * N;
 #pragma unroll
-                for (int r = 0; r < V; ++r) {
-                    const float2 s = ok ? __ldcs(srow + t + T * r) : make_float2(0.f, 0.f);
-                    c[r] = fmaf(s.x, v[r].x, s.y * v[r].y);
-                }
-            }
+            for (int r = 0; r < V; ++r) c[r] = fmaf(s[r].x, v[r].x, s[r].y * v[r].y);
+            if (j + 1 < nz) load_row<N, V>(s, Sitem + (size_t)(j + 1) * N, t, ok);
             // sum the items of this warp (lanes with equal t hold equal x)
 #pragma unroll
             for (int off = T; off < 32; off <<= 1) {
@@ -150,7 +214,9 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs a) {
 #pragma unroll
                 for (int r = 0; r < V; ++r) slab[t + T * r] = c[r];
             }
-            __syncthreads();
+            if (j + 1 < nz) cp_async_wait_all();
+            __syncthreads();  // image rows of depth j and staged rows of depth j are visible
+            if (j + 2 < nz) stage_rows(j + 1, (j + 1) & 1, false);
             {
                 const float* rows = img + (size_t)(j & 1) * nwarps * N;
                 for (int x = threadIdx.x; x < N; x += blockDim.x) {
@@ -159,24 +225,37 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs a) {
                     part[(size_t)j * N + x] = acc;
                 }
             }
-            if (j + 1 < nz)
-                step_down_adjoint<N, V>(v, tw, buf, t, a.phi + coef_base + (size_t)j * N,
-                                        a.dss + coef_base + (size_t)j * N);
+            if (j + 1 < nz) step_down_adjoint<N, V>(v, tw, buf, t, phi_of(j & 1), dss_of(j & 1));
         }
     } else {  // MODE_FORWARD
 #pragma unroll
         for (int r = 0; r < V; ++r) v[r] = make_float2(0.f, 0.f);
+        // step k (k = 0 .. nz-2) propagates with row j = nz-2-k and then adds model row j, both
+        // from buffer k & 1; the deepest model row is staged on its own into buffer 1 first
+        for (int c = threadIdx.x; c < N / 4; c += blockDim.x)
+            cp_async16(mstage + N + 4 * c, a.m + (size_t)(nz - 1) * N + 4 * c);
+        cp_async_commit();
+        if (nz > 1) stage_rows(nz - 2, 0, true);
         for (int j = nz - 1; j >= 0; --j) {
-            if (j + 1 < nz)
-                step_down<N, V>(v, tw, buf, t, a.phi + coef_base + (size_t)j * N, a.dss + coef_base + (size_t)j * N);
-            const float2* srow = Sitem + (size_t)j * N;
-            const float* mrow = a.m + (size_t)j * N;
+            // request S_j before propagating U_{j+1} so the load overlaps the step
+            float2 s[V];
+            load_row<N, V>(s, Sitem + (size_t)j * N, t, ok);
+            cp_async_wait_all();
+            __syncthreads();
+            const float* mrow;
+            if (j + 1 < nz) {
+                const int k = nz - 2 - j;
+                if (j >= 1) stage_rows(j - 1, (k + 1) & 1, true);
+                step_down<N, V>(v, tw, buf, t, phi_of(k & 1), dss_of(k & 1));
+                mrow = mstage + (k & 1) * N;
+            } else {
+                mrow = mstage + N;
+            }
 #pragma unroll
             for (int r = 0; r < V; ++r) {
-                const float2 s = ok ? __ldcs(srow + t + T * r) : make_float2(0.f, 0.f);
-                const float mm = __ldg(mrow + t + T * r);
-                v[r].x = fmaf(s.x, mm, v[r].x);
-                v[r].y = fmaf(s.y, mm, v[r].y);
+                const float mm = mrow[t + T * r];
+                v[r].x = fmaf(s[r].x, mm, v[r].x);
+                v[r].y = fmaf(s[r].y, mm, v[r].y);
             }
         }
         float2* orow = a.dout + ((size_t)ishot * a.nw + iw) * a.nrec;
@@ -268,6 +347,7 @@ struct Dispatch {
             if (e != cudaSuccess) return e;
             configured = true;
         }
+        if (sh.smem != sweep_smem_bytes<N, V>(sh.warps, a.wslots, MODE == MODE_ADJOINT)) return cudaErrorInvalidValue;
         ProfScope prof_(MODE == MODE_SOURCE ? KC_SOURCE : MODE == MODE_ADJOINT ? KC_ADJOINT : KC_FORWARD, st);
         sweep_kernel<N, V, MODE><<<sh.blocks, sh.warps * 32, sh.smem, st>>>(a);
         count_launch();
@@ -285,7 +365,10 @@ struct Dispatch {
     template <int MODE>
     static int max_warps_mode() {
         cudaFuncAttributes attr;
-        if (cudaFuncGetAttributes(&attr, sweep_kernel<N, V, MODE>) != cudaSuccess) return 1;
+        if (cudaFuncGetAttributes(&attr, sweep_kernel<N, V, MODE>) != cudaSuccess) {
+            cudaGetLastError();
+            return sweep_max_threads<V>() / 32;
+        }
         int w = attr.maxThreadsPerBlock / 32;
         return w < 1 ? 1 : w;
     }
