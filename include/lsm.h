@@ -160,6 +160,28 @@ int rls_window_solve(const lsm_grid* grid, const float* slowness, const lsm_freq
                      void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * Migration m = A^T d for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is a packaging variant of lsm_adjoint for code that must not
+ * call cudaMalloc or any allocating routine (for example a plug-in running inside a host process
+ * that owns every device allocation, or a step that must not allocate once it is set up).  It takes
+ * the same arguments as lsm_adjoint minus the workspace: its scratch (coefficient tables, source
+ * wavefields, partial images) lives in one fixed static device array of LSM_STATIC_SCRATCH_BYTES,
+ * which every GPU that loads the library keeps until the process exits.
+ *  - The caller still owns and passes d and m_out; nothing is allocated, freed or resized.
+ *  - Problems whose scratch (lsm_workspace_bytes(..., LSM_OP_ADJOINT)) exceeds
+ *    LSM_STATIC_SCRATCH_BYTES are rejected with LSM_ERR_WORKSPACE before anything is launched.
+ *  - The first call on each device looks up the array's device address (cudaGetSymbolAddress) and
+ *    caches it; make that first call before any stream capture on that device.
+ *  - All calls share the one array and it keeps the last call's contents; every region is fully
+ *    rewritten before it is read, so results do not depend on earlier calls.  Calls that overlap
+ *    on the GPU (other streams, other host threads) race on the array: serialise them.
+ */
+#define LSM_STATIC_SCRATCH_BYTES (64u << 20)
+int lsm_adjoint_static(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs,
+                       const lsm_geom* geom, const float* d, float* m_out, int shot0, int nshots,
+                       int accumulate, void* stream);
+
+/*
  * Kernel timing for benchmarks.  Between lsm_profile_start() and lsm_profile_stop() every kernel
  * this library launches is bracketed by CUDA events recorded on the stream it is launched on;
  * lsm_profile_stop() waits for those events and reports, per kernel class, the number of launches

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "../../include/lsm.h"
@@ -385,6 +386,94 @@ int lsm_adjoint(const lsm_grid* grid, const float* slowness, const lsm_freqs* fr
     char* ws = static_cast<char*>(workspace);
     rc = prepare(grid, slowness, freqs, geom, L, ws, st);
     if (rc != LSM_OK) return rc;
+    SweepArgs a = base_args(grid, freqs, geom, L, ws);
+    LSM_CHECK(run_source(a, shot0, nshots, nsm, st));
+    int nparts = 0;
+    LSM_CHECK(run_adjoint(a, shot0, nshots, reinterpret_cast<const float2*>(d), nsm, st, &nparts));
+    LSM_CHECK(cg_reduce_image(a.part, nparts, grid->nx * grid->nz, nullptr, 0.f, accumulate ? 1 : 0, m_out,
+                              reinterpret_cast<double*>(ws + L.ss), st));
+    return LSM_OK;
+}
+
+// ------------------------------------------------------------------ allocation-free adjoint
+//
+// Scratch for lsm_adjoint_static: a fixed file-scope device array instead of a caller-provided
+// workspace.  Every GPU that loads this library holds these LSM_STATIC_SCRATCH_BYTES until the
+// process exits.  Host code must not hand `g_static_scratch` itself to a kernel (on the host it
+// names a stand-in, not device memory): each device's address is looked up once with
+// cudaGetSymbolAddress and cached.
+static __device__ __align__(256) unsigned char g_static_scratch[LSM_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_ptr[kMaxDevices] = {};
+
+// Device address of the static scratch on the current device (looked up on first use).
+int static_scratch_address(void** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return LSM_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || p == nullptr) {
+            cudaGetLastError();
+            return LSM_ERR_CUDA;
+        }
+        g_static_ptr[dev] = p;
+    }
+    *out = g_static_ptr[dev];
+    return LSM_OK;
+}
+
+}  // namespace
+
+int lsm_adjoint_static(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs, const lsm_geom* geom,
+                       const float* d, float* m_out, int shot0, int nshots, int accumulate, void* stream) {
+    int rc = validate_common(grid, freqs, geom);
+    if (rc != LSM_OK) return rc;
+    if (!aligned16(slowness) || !aligned16(d) || !aligned16(m_out)) return LSM_ERR_ARG;
+    if (shot0 < 0 || nshots < 1 || shot0 > geom->ns - nshots) return LSM_ERR_ARG;
+    const int nsm = num_sms_current();
+    const Layout L = make_layout(grid, geom, freqs, nshots, LSM_OP_ADJOINT, nsm);
+    if (L.total > (size_t)LSM_STATIC_SCRATCH_BYTES) return LSM_ERR_WORKSPACE;
+    void* base = nullptr;
+    rc = static_scratch_address(&base);
+    if (rc != LSM_OK) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(base);
+    // host arrays go straight from the caller's memory to the scratch (no staging buffer)
+    const size_t nw = (size_t)freqs->nw;
+    LSM_CHECK(cudaMemcpyAsync(ws + L.src, geom->src_ix, (size_t)geom->ns * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (geom->rec_ix)
+        LSM_CHECK(cudaMemcpyAsync(ws + L.rec, geom->rec_ix, (size_t)geom->ns * geom->nrec * sizeof(int),
+                                  cudaMemcpyHostToDevice, st));
+    LSM_CHECK(cudaMemcpyAsync(ws + L.freq, freqs->freq_hz, nw * sizeof(float), cudaMemcpyHostToDevice, st));
+    LSM_CHECK(cudaMemcpyAsync(ws + L.wav, freqs->wavelet, nw * sizeof(float2), cudaMemcpyHostToDevice, st));
+    {
+        ProfScope prof_(KC_TABLES, st);
+        reference_slowness_kernel<<<grid->nz, 256, 0, st>>>(slowness, grid->nx, grid->nz,
+                                                            reinterpret_cast<double*>(ws + L.sref));
+    }
+    count_launch();
+    LSM_CHECK(cudaGetLastError());
+    TableArgs ta;
+    ta.nx = grid->nx;
+    ta.nz = grid->nz;
+    ta.nw = freqs->nw;
+    ta.dx = grid->dx;
+    ta.dz = grid->dz;
+    ta.slowness = slowness;
+    ta.sref = reinterpret_cast<const double*>(ws + L.sref);
+    ta.freq_hz = reinterpret_cast<const float*>(ws + L.freq);
+    ta.phi = reinterpret_cast<float2*>(ws + L.phi);
+    ta.dss = reinterpret_cast<float2*>(ws + L.dss);
+    LSM_CHECK(launch_tables(ta, st));
+    // every scratch region below is fully written before it is read: nothing needs clearing
     SweepArgs a = base_args(grid, freqs, geom, L, ws);
     LSM_CHECK(run_source(a, shot0, nshots, nsm, st));
     int nparts = 0;

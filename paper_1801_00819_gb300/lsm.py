@@ -29,7 +29,10 @@ LSM_OP_ADJOINT = 1
 LSM_OP_SOLVE = 2
 
 EXPORTED = ("lsm_workspace_bytes", "lsm_forward", "lsm_adjoint", "lsm_num_windows", "rls_window_solve",
-            "lsm_status_string", "lsm_kernel_launches", "lsm_profile_start", "lsm_profile_stop")
+            "lsm_status_string", "lsm_kernel_launches", "lsm_profile_start", "lsm_profile_stop",
+            "lsm_adjoint_static")
+
+LSM_STATIC_SCRATCH_BYTES = 64 << 20
 
 KERNEL_CLASSES = ("tables", "source", "adjoint", "forward", "vector")
 
@@ -93,6 +96,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lsm_adjoint.restype = ctypes.c_int
     lib.lsm_adjoint.argtypes = [ctypes.POINTER(lsm_grid), P, ctypes.POINTER(lsm_freqs), ctypes.POINTER(lsm_geom),
                                 P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t, P]
+    lib.lsm_adjoint_static.restype = ctypes.c_int
+    lib.lsm_adjoint_static.argtypes = [ctypes.POINTER(lsm_grid), P, ctypes.POINTER(lsm_freqs),
+                                       ctypes.POINTER(lsm_geom), P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
     lib.lsm_num_windows.restype = ctypes.c_int
     lib.lsm_num_windows.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.rls_window_solve.restype = ctypes.c_int
@@ -225,6 +231,15 @@ def lsm_adjoint(grid, slowness, freqs, geom, d, m_out, shot0, nshots, workspace,
                                     ctypes.byref(geom.c), _ptr(d), _ptr(m_out), int(shot0), int(nshots),
                                     1 if accumulate else 0, _ptr(workspace), _nbytes(workspace), _stream(stream))
     _check(st, "lsm_adjoint")
+
+
+def lsm_adjoint_static(grid, slowness, freqs, geom, d, m_out, shot0, nshots, accumulate=False, stream=None):
+    """A^T d like lsm_adjoint, but with the library's fixed static device scratch instead of a
+    workspace, for callers that cannot allocate device memory (see include/lsm.h)."""
+    st = load_library().lsm_adjoint_static(ctypes.byref(grid.c), _ptr(slowness), ctypes.byref(freqs.c),
+                                           ctypes.byref(geom.c), _ptr(d), _ptr(m_out), int(shot0), int(nshots),
+                                           1 if accumulate else 0, _stream(stream))
+    _check(st, "lsm_adjoint_static")
 
 
 def rls_window_solve(grid, slowness, freqs, geom, d, lam, K, slide, cg_tol, max_iter, m_inout, workspace,

@@ -33,7 +33,7 @@ def _declared_functions():
 def test_header_declares_expected_entry_points():
     assert _declared_functions() == sorted(["lsm_workspace_bytes", "lsm_forward", "lsm_adjoint", "lsm_num_windows",
                                             "rls_window_solve", "lsm_status_string", "lsm_kernel_launches",
-                                            "lsm_profile_start", "lsm_profile_stop"])
+                                            "lsm_profile_start", "lsm_profile_stop", "lsm_adjoint_static"])
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -99,6 +99,19 @@ def test_validation_rejects_bad_arguments_before_any_launch(lib):
         lib.rls_window_solve(g, fake, f, geo, fake, -1.0, 2, 1, 0.0, 3, fake, None, stream=0)
     with pytest.raises(lib.LsmError):
         lib.rls_window_solve(g, fake, f, geo, fake, 1.0, 4, 1, 0.0, 3, fake, None, stream=0)
+    assert lib.lsm_kernel_launches() == before
+
+
+def test_static_scratch_variant_rejects_oversize_problems_before_launch(lib):
+    before = lib.lsm_kernel_launches()
+    g = lib.Grid(512, 256, 8.0, 8.0)
+    geo = lib.Geometry(np.arange(16) * 32, None, nx=512)
+    f = lib.Frequencies(np.linspace(3, 40, 128), np.ones(128))
+    assert lib.lsm_workspace_bytes(g, geo, f, 16, lib.LSM_OP_ADJOINT) > lib.LSM_STATIC_SCRATCH_BYTES
+    fake = 1 << 20
+    with pytest.raises(lib.LsmError) as ei:
+        lib.lsm_adjoint_static(g, fake, f, geo, fake, fake, 0, 16, stream=0)
+    assert ei.value.status == lib.LSM_ERR_WORKSPACE
     assert lib.lsm_kernel_launches() == before
 
 
