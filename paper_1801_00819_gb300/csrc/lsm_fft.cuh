@@ -317,4 +317,48 @@ __device__ __forceinline__ void fft_inverse(float2 (&v)[V], const Twiddles<N, V>
     inverse_stages<N, V, Plan<N, V>::NS - 1>(v, tw, buf, t);
 }
 
+// One phase-shift step in the transform domain for two-stage plans, F^-1 (phi . F v): forward
+// first stage in registers, then, per last-stage butterfly (a runtime loop, so its code exists
+// once), forward last stage -> multiply by phi (or conj(phi)) -> inverse last stage in place in
+// the exchange buffer, then the inverse first stage in registers.  Equivalent to fft_forward, a
+// pointwise multiply in the digit-reversed register order, and fft_inverse; the smaller code
+// footprint keeps more of the depth loop in the instruction cache.  phi is indexed like the
+// register layout: phi[r * T + t] multiplies register r of thread t.
+template <int N, int V, bool CONJ>
+__device__ __forceinline__ void phase_shift_two_stage(float2 (&v)[V], const Twiddles<N, V>& tw, float2* buf, int t,
+                                                      const float2* phi) {
+    using P = Plan<N, V>;
+    static_assert(P::NS == 2, "two-stage plans only");
+    constexpr int R0 = P::R(0), R1 = P::R(1), M1 = P::M(1), L1 = P::L(1), T = P::T;
+    static_assert(M1 == 1 && R0 == V, "one first-stage butterfly per thread, unit-stride last stage");
+    small_dft<R0, false>(v);
+#pragma unroll
+    for (int k2 = 1; k2 < R0; ++k2) v[k2] = cmul(v[k2], tw.w[P::tw_offset(0) + (k2 - 1)]);
+    __syncwarp();
+    store_outputs<N, V, 0>(v, buf, t);
+    __syncwarp();
+#pragma unroll 1
+    for (int i = 0; i < P::NB(1); ++i) {
+        float2* blk = buf + (t + T * i) * L1;  // last-stage block, unit stride
+        const int a0 = (t + T * i) * L1;
+        float2 u[R1];
+#pragma unroll
+        for (int n2 = 0; n2 < R1; ++n2) u[n2] = blk[P::phys(a0 + n2) - a0];
+        small_dft<R1, false>(u);
+#pragma unroll
+        for (int k2 = 0; k2 < R1; ++k2) {
+            const float2 ph = phi[(i * R1 + k2) * T + t];
+            u[k2] = CONJ ? cmulc(u[k2], ph) : cmul(u[k2], ph);
+        }
+        small_dft<R1, true>(u);
+#pragma unroll
+        for (int n2 = 0; n2 < R1; ++n2) blk[P::phys(a0 + n2) - a0] = u[n2];
+    }
+    __syncwarp();
+    load_outputs<N, V, 0>(v, buf, t);
+#pragma unroll
+    for (int k2 = 1; k2 < R0; ++k2) v[k2] = cmulc(v[k2], tw.w[P::tw_offset(0) + (k2 - 1)]);
+    small_dft<R0, true>(v);
+}
+
 }  // namespace lsm

@@ -49,10 +49,14 @@ template <int N, int V>
 __device__ __forceinline__ void step_down(float2 (&v)[V], const Twiddles<N, V>& tw, float2* buf, int t,
                                           const float2* phi, const float2* dss) {
     constexpr int T = Plan<N, V>::T;
-    fft_forward<N, V>(v, tw, buf, t);
+    if constexpr (Plan<N, V>::NS == 2 && Plan<N, V>::NB(0) == 1) {
+        phase_shift_two_stage<N, V, false>(v, tw, buf, t, phi);
+    } else {
+        fft_forward<N, V>(v, tw, buf, t);
 #pragma unroll
-    for (int r = 0; r < V; ++r) v[r] = cmul(v[r], phi[t + T * r]);
-    fft_inverse<N, V>(v, tw, buf, t);
+        for (int r = 0; r < V; ++r) v[r] = cmul(v[r], phi[t + T * r]);
+        fft_inverse<N, V>(v, tw, buf, t);
+    }
 #pragma unroll
     for (int r = 0; r < V; ++r) v[r] = cmul(v[r], dss[t + T * r]);
 }
@@ -63,10 +67,14 @@ __device__ __forceinline__ void step_down_adjoint(float2 (&v)[V], const Twiddles
     constexpr int T = Plan<N, V>::T;
 #pragma unroll
     for (int r = 0; r < V; ++r) v[r] = cmulc(v[r], dss[t + T * r]);
-    fft_forward<N, V>(v, tw, buf, t);
+    if constexpr (Plan<N, V>::NS == 2 && Plan<N, V>::NB(0) == 1) {
+        phase_shift_two_stage<N, V, true>(v, tw, buf, t, phi);
+    } else {
+        fft_forward<N, V>(v, tw, buf, t);
 #pragma unroll
-    for (int r = 0; r < V; ++r) v[r] = cmulc(v[r], phi[t + T * r]);
-    fft_inverse<N, V>(v, tw, buf, t);
+        for (int r = 0; r < V; ++r) v[r] = cmulc(v[r], phi[t + T * r]);
+        fft_inverse<N, V>(v, tw, buf, t);
+    }
 }
 
 // ------------------------------------------------------------------ shared-memory layout
