@@ -77,11 +77,13 @@ __device__ __forceinline__ float2 twiddle_const(float2 v) {
 // Radix-2 decimation-in-frequency passes (natural in, bit-reversed out) followed by a
 // compile-time renaming to natural order.  INV selects the +i sign (unnormalised inverse).
 
+// The sum and difference use the paired-FP32 instructions of sm_100-class GPUs (one instruction
+// for both components); a - b is formed exactly as fma(b, -1, a).
 template <bool INV, int H, int K>
 __device__ __forceinline__ void r2_butterfly(float2* v) {
     const float2 a = v[K], b = v[K + H];
-    v[K] = cadd(a, b);
-    v[K + H] = twiddle_const<2 * H, K, INV>(csub(a, b));
+    v[K] = __fadd2_rn(a, b);
+    v[K + H] = twiddle_const<2 * H, K, INV>(__ffma2_rn(b, make_float2(-1.f, -1.f), a));
 }
 
 template <int R, bool INV, int H, int... Ks>
