@@ -398,7 +398,7 @@ def host_cores():
         return os.cpu_count()
 
 
-def cpu_baseline(sv, n_freqs, n_shots=3):
+def cpu_baseline(sv, n_freqs, n_shots=5):
     units, dt = oracle_sample(sv, n_freqs, n_shots)
     return {"value": round(units / dt, 2), "unit": "units/s", "cores": host_cores(), "kind": "oracle",
             "sample": f"FP64 oracle (numpy, naive DFT matrices), one A + A^T on {n_shots} shots x "
