@@ -35,6 +35,8 @@ What it computes, with the passage each part follows:
   ns - K when the last one does not end at ns.  The result is the last window's image.
 * Stopping rule ("threshold for the normal equation", Examples section) read as
   ||A_k^T (d_k - A_k m) - lambda m|| / ||A_k^T d_k|| <= tol.
+* Gradients of a real loss of d = A(s) m with respect to m (= A^T g, Eq. 2) and to the slowness
+  with the reference slowness held fixed (adjoint-state recursion, `born_gradients`).
 
 Parity pins for every function live in tests/test_oracle_pins.py.  The operator conventions
 above are readings (the paper prints no numbers or figures for them); they are pinned by
@@ -109,7 +111,7 @@ class SplitStepOperator:
     src_ix: [ns]; rec_ix: [ns][nrec].
     """
 
-    def __init__(self, slowness, dx, dz, freqs_hz, wavelet, src_ix, rec_ix):
+    def __init__(self, slowness, dx, dz, freqs_hz, wavelet, src_ix, rec_ix, sref=None):
         self.s = np.asarray(slowness, dtype=np.float64)
         self.nz, self.nx = self.s.shape
         self.dx, self.dz = float(dx), float(dz)
@@ -121,7 +123,8 @@ class SplitStepOperator:
         self.F = dft_matrix(self.nx)
         self.Finv = idft_matrix(self.nx)
         self.kx = kx_axis(self.nx, self.dx)
-        self.sref = reference_slowness(self.s)
+        # the reference slowness may be held fixed at a background model's (for slowness gradients)
+        self.sref = reference_slowness(self.s) if sref is None else np.asarray(sref, dtype=np.float64)
 
     @property
     def ns(self):
@@ -139,7 +142,7 @@ class SplitStepOperator:
         """The same operator restricted to a subset of the frequency axis."""
         idx = np.asarray(idx)
         return SplitStepOperator(self.s, self.dx, self.dz, self.freqs[idx], self.wavelet[idx],
-                                 self.geom.src_ix, self.geom.rec_ix)
+                                 self.geom.src_ix, self.geom.rec_ix, sref=self.sref)
 
     # lateral transforms on the last axis
     def _fft(self, u):
@@ -216,6 +219,51 @@ class SplitStepOperator:
             if j + 1 < self.nz:
                 R = self.propagate_adjoint(R, j)
         return m
+
+
+# --------------------------------------------------------------------------------------------
+# Gradients of a real loss L(d), d = A(s) m, with respect to m and to the slowness s
+# --------------------------------------------------------------------------------------------
+
+def born_gradients(op, m, g, shots=None):
+    """(dL/dm, dL/ds) for d = A(s) m given g = dL/dRe(d) + i dL/dIm(d) at the receivers.
+
+    The reference slowness s_ref is held fixed (only the split-step factor D_j depends on s), so
+    dD_j(x)/ds_j(x) = i w dz D_j(x) and dP_j u = i w dz ds_j . (P_j u).  Adjoint-state recursion:
+      R_0 = injected g, R_{j+1} = P_j^H R_j;
+      U_{nz-1} = S_{nz-1} m_{nz-1}, U_j = S_j m_j + P_j U_{j+1};
+      mu_{nz} = 0, mu_j = m_j R_j + P_j^H mu_{j+1};
+      dL/dm_j = Re sum conj(S_j) R_j                      (= A^T g, Eq. 2);
+      dL/ds_j = Re sum i w dz [conj(R_j) (U_j - S_j m_j) + conj(mu_{j+1}) S_{j+1}]
+    summed over shots and frequencies.  Pinned by central finite differences of the oracle's
+    forward operator with the same fixed s_ref.
+    """
+    shots = np.arange(op.ns) if shots is None else np.asarray(shots)
+    m = np.asarray(m, dtype=np.float64)
+    S = op.source_wavefield(shots)
+    nz = op.nz
+    R = np.empty_like(S)
+    cur = op.inject(np.asarray(g, dtype=np.complex128), shots)
+    for j in range(nz):
+        R[j] = cur
+        if j + 1 < nz:
+            cur = op.propagate_adjoint(cur, j)
+    U = np.empty_like(S)
+    U[nz - 1] = S[nz - 1] * m[nz - 1]
+    for j in range(nz - 2, -1, -1):
+        U[j] = S[j] * m[j] + op.propagate(U[j + 1], j)
+    w = op.omega[None, :, None]
+    grad_m = np.zeros((nz, op.nx))
+    grad_s = np.zeros((nz, op.nx))
+    mu = np.zeros_like(S[0])
+    for j in range(nz - 1, -1, -1):
+        grad_m[j] = np.real(np.conj(S[j]) * R[j]).sum(axis=(0, 1))
+        if j + 1 < nz:
+            term = np.conj(R[j]) * (U[j] - S[j] * m[j]) + np.conj(mu) * S[j + 1]
+            grad_s[j] = np.real(1j * w * op.dz * term).sum(axis=(0, 1))
+        mu_next = mu
+        mu = m[j] * R[j] + (op.propagate_adjoint(mu_next, j) if j + 1 < nz else 0.0)
+    return grad_m, grad_s
 
 
 # --------------------------------------------------------------------------------------------

@@ -390,3 +390,69 @@ def test_planted_unconjugated_inner_product_fails_cholesky_pin(monkeypatch):
     monkeypatch.setattr(O, "real_dot", lambda u, v: float(np.real(np.sum(u * v))))
     with pytest.raises(AssertionError):
         test_cg_matches_explicit_cholesky_solution()
+
+
+# ---------------------------------------------------------------- gradients (autograd row)
+
+
+def _gradient_problem(seed=3, nx=64, nz=32, ns=2, nw=6):
+    """64 x 32 crop with a smooth slowness perturbation direction (Gaussian-smoothed N(0, 1e-5))."""
+    sv = random_case(nx, nz, ns, nw, seed=seed)
+    op = _op(sv)
+    m = sv.reflectivity
+    dobs = op.forward(m) + 0.1 * sv.noise()
+    rng = np.random.default_rng(seed)
+    from scipy.ndimage import gaussian_filter
+    ds = gaussian_filter(rng.normal(0.0, 1e-5, size=m.shape), 2.0)
+    return sv, op, m, dobs, ds
+
+
+def _misfit(sv, sref, s, m, dobs):
+    o = O.SplitStepOperator(s, sv.dx, sv.dz, sv.freqs, sv.wavelet, sv.src_ix, sv.rec_ix, sref=sref)
+    return float(np.sum(np.abs(o.forward(m) - dobs) ** 2))
+
+
+def test_slowness_gradient_matches_central_differences():
+    """dL/ds (s_ref held fixed) against central differences of L = ||A(s) m - d||^2, h = 1e-3."""
+    sv, op, m, dobs, ds = _gradient_problem()
+    _, gs = O.born_gradients(op, m, 2.0 * (op.forward(m) - dobs))
+    analytic = float(np.sum(gs * ds))
+    for h, tol in ((1e-1, 1e-3), (1e-3, 1e-6)):
+        fd = (_misfit(sv, op.sref, op.s + h * ds, m, dobs) - _misfit(sv, op.sref, op.s - h * ds, m, dobs)) / (2 * h)
+        assert abs(fd - analytic) <= tol * abs(analytic), (h, fd, analytic)
+
+
+def test_model_gradient_is_adjoint_and_matches_differences():
+    sv, op, m, dobs, _ = _gradient_problem(seed=5, nx=32, nz=12)
+    g = 2.0 * (op.forward(m) - dobs)
+    gm, _ = O.born_gradients(op, m, g)
+    np.testing.assert_allclose(gm, op.adjoint(g), rtol=0, atol=1e-12 * np.abs(gm).max())
+    dm = np.random.default_rng(1).normal(size=m.shape)
+    h = 1e-3
+    fd = (np.sum(np.abs(op.forward(m + h * dm) - dobs) ** 2) - np.sum(np.abs(op.forward(m - h * dm) - dobs) ** 2)) / (2 * h)
+    assert abs(fd - np.sum(gm * dm)) <= 1e-8 * abs(fd)
+
+
+def test_planted_missing_source_adjoint_term_fails_gradient_pin(monkeypatch):
+    """Dropping the mu (source-side) term of the slowness gradient is caught by the FD pin."""
+    good = O.born_gradients
+
+    def without_mu(op, m, g, shots=None):
+        gm, gs = good(op, m, g, shots)
+        shots = np.arange(op.ns) if shots is None else shots
+        S = op.source_wavefield(shots)
+        R = [op.inject(np.asarray(g, dtype=complex), shots)]
+        for j in range(op.nz - 1):
+            R.append(op.propagate_adjoint(R[-1], j))
+        U = [None] * op.nz
+        U[-1] = S[-1] * m[-1]
+        for j in range(op.nz - 2, -1, -1):
+            U[j] = S[j] * m[j] + op.propagate(U[j + 1], j)
+        w = op.omega[None, :, None]
+        gs2 = np.zeros_like(gs)
+        for j in range(op.nz - 1):
+            gs2[j] = np.real(1j * w * op.dz * np.conj(R[j]) * (U[j] - S[j] * m[j])).sum(axis=(0, 1))
+        return gm, gs2
+    monkeypatch.setattr(O, "born_gradients", without_mu)
+    with pytest.raises(AssertionError):
+        test_slowness_gradient_matches_central_differences()
