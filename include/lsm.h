@@ -65,6 +65,10 @@ extern "C" {
 #define LSM_OP_FORWARD 0
 #define LSM_OP_ADJOINT 1
 #define LSM_OP_SOLVE 2
+#define LSM_OP_GRADIENT 3
+
+/* depth stride of the source / adjoint wavefield checkpoints kept by lsm_born_gradient */
+#define LSM_CHECKPOINT_EVERY 16
 
 typedef struct {
     int nx, nz;     /* lateral cells, depth rows */
@@ -98,6 +102,7 @@ typedef struct {
  * Workspace size in bytes for one call.
  *   op = LSM_OP_FORWARD / LSM_OP_ADJOINT: nshots = shots processed per call.
  *   op = LSM_OP_SOLVE: nshots = the window length K.
+ *   op = LSM_OP_GRADIENT: nshots = shots per lsm_born_gradient call.
  * The size depends on the current device's multiprocessor count (152 is assumed when no
  * device is visible), so query it with the device that will run the call current.
  * Returns 0 for invalid arguments.
@@ -127,6 +132,31 @@ int lsm_forward(const lsm_grid* grid, const float* slowness, const lsm_freqs* fr
 int lsm_adjoint(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs,
                 const lsm_geom* geom, const float* d, float* m_out, int shot0, int nshots,
                 int accumulate, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Modelling and gradients for differentiable use of d = A(s) m (Eq. 1), e.g. behind an autograd
+ * function whose backward is the adjoint.  The reference slowness of the split-step operator is held
+ * fixed: `sref` is a device float64 [nz] array (for example the row means of a background model),
+ * or NULL for the row means of `slowness`.  Only the split-step factor D_j then depends on s, and
+ * the derivatives follow the adjoint-state recursion
+ *   R_0 = injected g, R_{j+1} = P_j^H R_j;  U_j = S_j m_j + P_j U_{j+1};
+ *   mu_nz = 0, mu_j = m_j R_j + P_j^H mu_{j+1};
+ *   grad_m_j = Re sum conj(S_j) R_j   (= A^T g, Eq. 2),
+ *   grad_s_j = Re sum i w dz [conj(R_j) P_j U_{j+1} + conj(mu_{j+1}) S_{j+1}],
+ * summed over the shots and frequencies.  S and R are swept down once keeping only every
+ * LSM_CHECKPOINT_EVERY-th depth, and recomputed segment by segment while U and mu run up.
+ *   m: device float32 [nz][nx];
+ *   g: device complex64 [nshots][nw][nrec], dL/dRe(d) + i dL/dIm(d) (the convention of PyTorch
+ *      complex gradients), or NULL to only model d;
+ *   d_out: device complex64 [nshots][nw][nrec] or NULL (required when g is NULL);
+ *   grad_m, grad_s: device float32 [nz][nx] or NULL; overwritten.
+ * Workspace: lsm_workspace_bytes(..., nshots, LSM_OP_GRADIENT).  Gradients need nx <= 512
+ * (LSM_ERR_UNSUPPORTED_NX otherwise); modelling supports every nx of lsm_forward.
+ */
+int lsm_born_gradient(const lsm_grid* grid, const float* slowness, const double* sref,
+                      const lsm_freqs* freqs, const lsm_geom* geom, const float* m,
+                      const float* g, float* d_out, float* grad_m, float* grad_s, int shot0,
+                      int nshots, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * Number of sliding windows of K shots with the given slide over ns shots: starts are
@@ -193,7 +223,8 @@ int lsm_adjoint_static(const lsm_grid* grid, const float* slowness, const lsm_fr
 #define LSM_KCLASS_ADJOINT 2  /* A^T depth sweep (imaging) */
 #define LSM_KCLASS_FORWARD 3  /* A depth sweep */
 #define LSM_KCLASS_VECTOR 4   /* image reduction and CG vector updates */
-#define LSM_NUM_KCLASSES 5
+#define LSM_KCLASS_GRADIENT 5 /* lsm_born_gradient's checkpointed gradient sweep */
+#define LSM_NUM_KCLASSES 6
 
 typedef struct {
     unsigned long long launches[LSM_NUM_KCLASSES];

@@ -11,6 +11,7 @@ from .lsm import (  # noqa: F401
     Grid,
     LsmError,
     lsm_adjoint,
+    lsm_born_gradient,
     lsm_forward,
     lsm_kernel_launches,
     lsm_num_windows,
@@ -22,4 +23,5 @@ from .lsm import (  # noqa: F401
     LSM_OP_FORWARD,
     LSM_OP_ADJOINT,
     LSM_OP_SOLVE,
+    LSM_OP_GRADIENT,
 )

@@ -107,6 +107,64 @@ SweepShape sweep_shape(int nx, int mode, int nshots, int nw, int num_sms) {
     return s;
 }
 
+bool gradient_nx_supported(int nx) { return nx_supported(nx) && nx <= 16 * 32; }
+
+static int gradient_max_warps_for(int nx) {
+    switch (nx) {
+        case 16: return gradient_max_warps_16();
+        case 32: return gradient_max_warps_32();
+        case 64: return gradient_max_warps_64();
+        case 128: return gradient_max_warps_128();
+        case 256: return gradient_max_warps_256();
+        default: return gradient_max_warps_512();
+    }
+}
+
+SweepShape gradient_shape(int nx, int nshots, int nw, int num_sms) {
+    const int V = gradient_points_per_thread();
+    const int T = nx / V;
+    const int ipw = 32 / T;
+    const int nitems = nshots * nw;
+    const int warps_total = (nitems + ipw - 1) / ipw;
+    auto smem_of = [&](int w) {
+        return (size_t)w * ipw * (size_t)(nx + nx / 16) * sizeof(float2) + (size_t)4 * w * nx * sizeof(float);
+    };
+    int maxw = std::min(8, gradient_max_warps_for(nx));
+    while (maxw > 1 && smem_of(maxw) > 227 * 1024) --maxw;
+    int warps = (warps_total + num_sms - 1) / num_sms;
+    warps = std::max(1, std::min(warps, maxw));
+    SweepShape s;
+    s.warps = warps;
+    s.blocks = (warps_total + warps - 1) / warps;
+    s.wslots = 0;
+    s.smem = smem_of(warps);
+    return s;
+}
+
+cudaError_t launch_tables_grad(const TableArgs& a, cudaStream_t st) {
+    switch (a.nx) {
+        case 16: return launch_tables_grad_16(a, st);
+        case 32: return launch_tables_grad_32(a, st);
+        case 64: return launch_tables_grad_64(a, st);
+        case 128: return launch_tables_grad_128(a, st);
+        case 256: return launch_tables_grad_256(a, st);
+        case 512: return launch_tables_grad_512(a, st);
+        default: return cudaErrorNotSupported;
+    }
+}
+
+cudaError_t launch_gradient(const GradArgs& a, const SweepShape& sh, cudaStream_t st) {
+    switch (a.nx) {
+        case 16: return launch_gradient_16(a, sh, st);
+        case 32: return launch_gradient_32(a, sh, st);
+        case 64: return launch_gradient_64(a, sh, st);
+        case 128: return launch_gradient_128(a, sh, st);
+        case 256: return launch_gradient_256(a, sh, st);
+        case 512: return launch_gradient_512(a, sh, st);
+        default: return cudaErrorNotSupported;
+    }
+}
+
 cudaError_t launch_tables(const TableArgs& a, cudaStream_t st) {
     switch (a.nx) {
         case 16: return launch_tables_16(a, st);
@@ -176,6 +234,7 @@ struct Layout {
     // offsets in bytes from the workspace base
     size_t src, rec, freq, wav, sref, phi, dss, S, part;
     size_t p, s, r, q, qq, pp, ss, state;
+    size_t ckpt, seg, part_s;  // gradient op
     size_t total;
     int ring, nparts;
 };
@@ -205,8 +264,19 @@ Layout make_layout(const lsm_grid* g, const lsm_geom* geo, const lsm_freqs* f, i
     if (op == LSM_OP_ADJOINT || op == LSM_OP_SOLVE) {
         const SweepShape sh = sweep_shape(g->nx, MODE_ADJOINT, nshots, (int)nw, num_sms);
         L.nparts = sh.blocks;
+    } else if (op == LSM_OP_GRADIENT) {
+        L.nparts = gradient_shape(g->nx, nshots, (int)nw, num_sms).blocks;
     }
     L.part = take((size_t)L.nparts * plane * sizeof(float));
+    if (op == LSM_OP_GRADIENT) {
+        const size_t items = (size_t)nshots * nw;
+        const size_t c = LSM_CHECKPOINT_EVERY;
+        const size_t ncp = (nz + c - 1) / c;
+        L.part_s = take((size_t)L.nparts * plane * sizeof(float));
+        L.ckpt = take(items * 2 * ncp * nx * sizeof(float2));
+        L.seg = take(items * (2 * c + 1) * nx * sizeof(float2));
+        L.ss = take(kRedBlocks * sizeof(double));
+    }
     if (op == LSM_OP_SOLVE) {
         const size_t nd = (size_t)nshots * nw * geo->nrec;
         L.p = take(plane * sizeof(float));
@@ -217,9 +287,7 @@ Layout make_layout(const lsm_grid* g, const lsm_geom* geo, const lsm_freqs* f, i
         L.pp = take(kRedBlocks * sizeof(double));
         L.ss = take(kRedBlocks * sizeof(double));
         L.state = take(sizeof(CgState));
-    } else if (op == LSM_OP_FORWARD) {
-        L.p = L.s = L.r = L.q = L.qq = L.pp = L.ss = L.state = 0;
-    } else {
+    } else if (op == LSM_OP_ADJOINT) {
         L.ss = take(kRedBlocks * sizeof(double));
     }
     L.total = off;
@@ -261,7 +329,7 @@ int validate_common(const lsm_grid* g, const lsm_freqs* f, const lsm_geom* geo) 
 
 // Upload geometry / frequencies and build s_ref and the coefficient tables in the workspace.
 int prepare(const lsm_grid* g, const float* slowness, const lsm_freqs* f, const lsm_geom* geo, const Layout& L,
-            char* ws, cudaStream_t st) {
+            char* ws, cudaStream_t st, const double* sref_override = nullptr, bool gradient_tables = false) {
     const size_t nw = (size_t)f->nw;
     // one staging copy of all host arrays (layout identical to the workspace prefix)
     const size_t head = L.sref;
@@ -271,13 +339,18 @@ int prepare(const lsm_grid* g, const float* slowness, const lsm_freqs* f, const 
     std::memcpy(host.data() + L.freq, f->freq_hz, nw * sizeof(float));
     std::memcpy(host.data() + L.wav, f->wavelet, nw * sizeof(float2));
     LSM_CHECK(cudaMemcpyAsync(ws, host.data(), head, cudaMemcpyHostToDevice, st));
-    {
-        ProfScope prof_(KC_TABLES, st);
-        reference_slowness_kernel<<<g->nz, 256, 0, st>>>(slowness, g->nx, g->nz,
-                                                         reinterpret_cast<double*>(ws + L.sref));
+    if (sref_override) {
+        LSM_CHECK(cudaMemcpyAsync(ws + L.sref, sref_override, (size_t)g->nz * sizeof(double), cudaMemcpyDeviceToDevice,
+                                  st));
+    } else {
+        {
+            ProfScope prof_(KC_TABLES, st);
+            reference_slowness_kernel<<<g->nz, 256, 0, st>>>(slowness, g->nx, g->nz,
+                                                             reinterpret_cast<double*>(ws + L.sref));
+        }
+        count_launch();
+        LSM_CHECK(cudaGetLastError());
     }
-    count_launch();
-    LSM_CHECK(cudaGetLastError());
     TableArgs ta;
     ta.nx = g->nx;
     ta.nz = g->nz;
@@ -289,7 +362,7 @@ int prepare(const lsm_grid* g, const float* slowness, const lsm_freqs* f, const 
     ta.freq_hz = reinterpret_cast<const float*>(ws + L.freq);
     ta.phi = reinterpret_cast<float2*>(ws + L.phi);
     ta.dss = reinterpret_cast<float2*>(ws + L.dss);
-    LSM_CHECK(launch_tables(ta, st));
+    LSM_CHECK(gradient_tables ? launch_tables_grad(ta, st) : launch_tables(ta, st));
     return LSM_OK;
 }
 
@@ -348,7 +421,7 @@ extern "C" {
 size_t lsm_workspace_bytes(const lsm_grid* grid, const lsm_geom* geom, const lsm_freqs* freqs, int nshots, int op) {
     if (validate_common(grid, freqs, geom) != LSM_OK) return 0;
     if (nshots < 1 || nshots > geom->ns) return 0;
-    if (op != LSM_OP_FORWARD && op != LSM_OP_ADJOINT && op != LSM_OP_SOLVE) return 0;
+    if (op != LSM_OP_FORWARD && op != LSM_OP_ADJOINT && op != LSM_OP_SOLVE && op != LSM_OP_GRADIENT) return 0;
     return make_layout(grid, geom, freqs, nshots, op, num_sms_current()).total;
 }
 
@@ -480,6 +553,68 @@ int lsm_adjoint_static(const lsm_grid* grid, const float* slowness, const lsm_fr
     LSM_CHECK(run_adjoint(a, shot0, nshots, reinterpret_cast<const float2*>(d), nsm, st, &nparts));
     LSM_CHECK(cg_reduce_image(a.part, nparts, grid->nx * grid->nz, nullptr, 0.f, accumulate ? 1 : 0, m_out,
                               reinterpret_cast<double*>(ws + L.ss), st));
+    return LSM_OK;
+}
+
+int lsm_born_gradient(const lsm_grid* grid, const float* slowness, const double* sref, const lsm_freqs* freqs,
+                      const lsm_geom* geom, const float* m, const float* g, float* d_out, float* grad_m, float* grad_s,
+                      int shot0, int nshots, void* workspace, size_t workspace_bytes, void* stream) {
+    int rc = validate_common(grid, freqs, geom);
+    if (rc != LSM_OK) return rc;
+    if (!aligned16(slowness) || !aligned16(m) || !aligned16(workspace)) return LSM_ERR_ARG;
+    if (sref && ((uintptr_t)sref & 7u)) return LSM_ERR_ARG;
+    if (g && !aligned16(g)) return LSM_ERR_ARG;
+    if (d_out && !aligned16(d_out)) return LSM_ERR_ARG;
+    if (grad_m && !aligned16(grad_m)) return LSM_ERR_ARG;
+    if (grad_s && !aligned16(grad_s)) return LSM_ERR_ARG;
+    if (!g && !d_out) return LSM_ERR_ARG;
+    if (shot0 < 0 || nshots < 1 || shot0 > geom->ns - nshots) return LSM_ERR_ARG;
+    if (g && !gradient_nx_supported(grid->nx)) return LSM_ERR_UNSUPPORTED_NX;
+    const int nsm = num_sms_current();
+    const Layout L = make_layout(grid, geom, freqs, nshots, LSM_OP_GRADIENT, nsm);
+    if (workspace_bytes < L.total) return LSM_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(workspace);
+    if (!g) {
+        // modelling only: the sweep kernels with the given reference slowness
+        rc = prepare(grid, slowness, freqs, geom, L, ws, st, sref, false);
+        if (rc != LSM_OK) return rc;
+        SweepArgs a = base_args(grid, freqs, geom, L, ws);
+        LSM_CHECK(run_source(a, shot0, nshots, nsm, st));
+        LSM_CHECK(run_forward(a, shot0, nshots, m, reinterpret_cast<float2*>(d_out), nsm, st));
+        return LSM_OK;
+    }
+    rc = prepare(grid, slowness, freqs, geom, L, ws, st, sref, true);
+    if (rc != LSM_OK) return rc;
+    GradArgs ga{};
+    ga.nx = grid->nx;
+    ga.nz = grid->nz;
+    ga.nw = freqs->nw;
+    ga.nrec = geom->nrec;
+    ga.shot0 = shot0;
+    ga.nshots = nshots;
+    ga.rec_identity = geom->rec_ix == nullptr ? 1 : 0;
+    ga.ckpt_every = LSM_CHECKPOINT_EVERY;
+    ga.dz = grid->dz;
+    ga.src_ix = reinterpret_cast<const int*>(ws + L.src);
+    ga.rec_ix = geom->rec_ix ? reinterpret_cast<const int*>(ws + L.rec) : nullptr;
+    ga.wavelet = reinterpret_cast<const float2*>(ws + L.wav);
+    ga.freq_hz = reinterpret_cast<const float*>(ws + L.freq);
+    ga.phi = reinterpret_cast<const float2*>(ws + L.phi);
+    ga.dss = reinterpret_cast<const float2*>(ws + L.dss);
+    ga.m = m;
+    ga.g = reinterpret_cast<const float2*>(g);
+    ga.ckpt = reinterpret_cast<float2*>(ws + L.ckpt);
+    ga.seg = reinterpret_cast<float2*>(ws + L.seg);
+    ga.part_m = reinterpret_cast<float*>(ws + L.part);
+    ga.part_s = reinterpret_cast<float*>(ws + L.part_s);
+    ga.dout = reinterpret_cast<float2*>(d_out);
+    const SweepShape sh = gradient_shape(grid->nx, nshots, freqs->nw, nsm);
+    LSM_CHECK(launch_gradient(ga, sh, st));
+    const int n = grid->nx * grid->nz;
+    double* ssp = reinterpret_cast<double*>(ws + L.ss);
+    if (grad_m) LSM_CHECK(cg_reduce_image(ga.part_m, sh.blocks, n, nullptr, 0.f, 0, grad_m, ssp, st));
+    if (grad_s) LSM_CHECK(cg_reduce_image(ga.part_s, sh.blocks, n, nullptr, 0.f, 0, grad_s, ssp, st));
     return LSM_OK;
 }
 

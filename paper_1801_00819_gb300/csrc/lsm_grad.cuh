@@ -1,0 +1,261 @@
+// Gradients of a real loss L(d), d = A(s) m, with respect to the model m and the slowness s, for
+// the shot-profile split-step operator (Eq. 1) with the reference slowness held fixed.  Given
+// g = dL/dRe(d) + i dL/dIm(d) at the receivers, per (shot, w) item:
+//   R_0 = injected g, R_{j+1} = P_j^H R_j                      (adjoint wavefield, top-down)
+//   U_{nz-1} = S_{nz-1} m_{nz-1}, U_j = S_j m_j + P_j U_{j+1}  (scattered field, bottom-up)
+//   mu_{nz} = 0, mu_j = m_j R_j + P_j^H mu_{j+1}               (source-side adjoint, bottom-up)
+//   dL/dm_j += Re conj(S_j) R_j
+//   dL/ds_j += Re i w dz [conj(R_j) P_j U_{j+1} + conj(mu_{j+1}) S_{j+1}]
+// The source and adjoint wavefields run top-down but are needed bottom-up, so phase 1 sweeps them
+// down once and keeps only every `c`-th depth (checkpoints); phase 2 walks the depth segments from
+// the bottom, recomputes each segment's S and R rows from their checkpoints into a small per-item
+// buffer, and runs the U and mu recursions in registers.  Per-depth gradient rows are summed over
+// the block's items and written as block partials (reduced later in a fixed order).
+#pragma once
+
+#include "lsm_fft.cuh"
+#include "lsm_internal.h"
+
+namespace lsm {
+
+// generic one-step propagation in registers with coefficients read from the global tables
+template <int N, int V, bool ADJ>
+__device__ __forceinline__ void grad_step(float2 (&v)[V], const Twiddles<N, V>& tw, float2* buf, int t,
+                                          const float2* __restrict__ phi, const float2* __restrict__ dss) {
+    constexpr int T = Plan<N, V>::T;
+    if (ADJ) {
+#pragma unroll
+        for (int r = 0; r < V; ++r) v[r] = cmulc(v[r], __ldg(dss + t + T * r));
+    }
+    fft_forward<N, V>(v, tw, buf, t);
+#pragma unroll
+    for (int r = 0; r < V; ++r) v[r] = ADJ ? cmulc(v[r], __ldg(phi + t + T * r)) : cmul(v[r], __ldg(phi + t + T * r));
+    fft_inverse<N, V>(v, tw, buf, t);
+    if (!ADJ) {
+#pragma unroll
+        for (int r = 0; r < V; ++r) v[r] = cmul(v[r], __ldg(dss + t + T * r));
+    }
+}
+
+template <int N, int V>
+__device__ __forceinline__ void grad_store(float2* __restrict__ row, const float2 (&v)[V], int t, bool ok) {
+    constexpr int T = Plan<N, V>::T;
+    if (ok) {
+#pragma unroll
+        for (int r = 0; r < V; ++r) row[t + T * r] = v[r];
+    }
+}
+
+template <int N, int V>
+__device__ __forceinline__ void grad_load(float2 (&v)[V], const float2* __restrict__ row, int t, bool ok) {
+    constexpr int T = Plan<N, V>::T;
+#pragma unroll
+    for (int r = 0; r < V; ++r) v[r] = ok ? row[t + T * r] : make_float2(0.f, 0.f);
+}
+
+// dynamic shared memory: exchange buffers + [2 buffers][2 images][warps][N] floats
+template <int N, int V>
+constexpr size_t gradient_smem_bytes(int warps) {
+    return (size_t)warps * (32 / Plan<N, V>::T) * Plan<N, V>::BUF * sizeof(float2) +
+           (size_t)2 * 2 * warps * N * sizeof(float);
+}
+
+template <int N, int V>
+__global__ void __launch_bounds__(256) gradient_kernel(const GradArgs a) {
+    using P = Plan<N, V>;
+    constexpr int T = P::T;
+    constexpr int IPW = 32 / T;
+    extern __shared__ float4 smem_f4[];
+    float2* smem = reinterpret_cast<float2*>(smem_f4);
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int t = lane % T;
+    const int sub = lane / T;
+    const int ipb = nwarps * IPW;
+    const int nitems = a.nshots * a.nw;
+    const int item = blockIdx.x * ipb + warp * IPW + sub;
+    const bool ok = item < nitems;
+    const int iw = ok ? item / a.nshots : 0;
+    const int ishot = ok ? item - iw * a.nshots : 0;
+    const int shot = a.shot0 + ishot;
+    const int nz = a.nz;
+    const int c = a.ckpt_every;
+    const int ncp = (nz + c - 1) / c;
+    float2* buf = smem + (warp * IPW + sub) * P::BUF;
+    float* img = reinterpret_cast<float*>(smem + ipb * P::BUF);  // [2][2][nwarps][N]
+
+    Twiddles<N, V> tw;
+    init_twiddles<N, V>(tw, t);
+
+    const float2* phi_w = a.phi + (size_t)iw * nz * N;
+    const float2* dss_w = a.dss + (size_t)iw * nz * N;
+    const size_t slot = ok ? (size_t)item : 0;
+    float2* Sck = a.ckpt + slot * 2 * ncp * N;
+    float2* Rck = Sck + (size_t)ncp * N;
+    float2* Sseg = a.seg + slot * (2 * c + 1) * N;
+    float2* Rseg = Sseg + (size_t)(c + 1) * N;
+    const float wdz = 2.0f * (float)kPi * (ok ? __ldg(a.freq_hz + iw) : 0.f) * a.dz;
+
+    // ---------------- phase 1: S and R down, checkpoints every c depths
+    {
+        float2 S[V], R[V];
+        const int xs = ok ? __ldg(a.src_ix + shot) : -1;
+        const float2 w = ok ? __ldg(a.wavelet + iw) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int r = 0; r < V; ++r) S[r] = (t + T * r == xs) ? w : make_float2(0.f, 0.f);
+        const float2* grow = a.g + ((size_t)ishot * a.nw + iw) * a.nrec;
+        if (a.rec_identity) {
+            grad_load<N, V>(R, grow, t, ok);
+        } else {
+            __syncwarp();
+            for (int x = t; x < P::BUF; x += T) buf[x] = make_float2(0.f, 0.f);
+            __syncwarp();
+            if (ok) {
+                const int* rix = a.rec_ix + (size_t)shot * a.nrec;
+                for (int rr = t; rr < a.nrec; rr += T) {
+                    const float2 dv = __ldg(grow + rr);
+                    const int x = P::phys(__ldg(rix + rr));
+                    atomicAdd(&buf[x].x, dv.x);
+                    atomicAdd(&buf[x].y, dv.y);
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < V; ++r) R[r] = buf[P::phys(t + T * r)];
+        }
+        for (int j = 0; j < nz; ++j) {
+            if (j % c == 0) {
+                grad_store<N, V>(Sck + (size_t)(j / c) * N, S, t, ok);
+                grad_store<N, V>(Rck + (size_t)(j / c) * N, R, t, ok);
+            }
+            if (j + 1 < nz) {
+                grad_step<N, V, false>(S, tw, buf, t, phi_w + (size_t)j * N, dss_w + (size_t)j * N);
+                grad_step<N, V, true>(R, tw, buf, t, phi_w + (size_t)j * N, dss_w + (size_t)j * N);
+            }
+        }
+    }
+
+    // ---------------- phase 2: segments bottom-up
+    float2 U[V], mu[V];
+#pragma unroll
+    for (int r = 0; r < V; ++r) U[r] = mu[r] = make_float2(0.f, 0.f);
+    int depth_count = 0;  // barrier parity
+    for (int seg = ncp - 1; seg >= 0; --seg) {
+        const int j0 = seg * c;
+        const int j1 = min(j0 + c, nz);
+        {
+            // S rows j0 .. jmax (jmax = j1 when a deeper row exists, for S_{j+1} at j = j1 - 1)
+            const int jmax = j1 < nz ? j1 : nz - 1;
+            float2 S[V];
+            grad_load<N, V>(S, Sck + (size_t)seg * N, t, ok);
+            for (int j = j0; j <= jmax; ++j) {
+                grad_store<N, V>(Sseg + (size_t)(j - j0) * N, S, t, ok);
+                if (j < jmax) grad_step<N, V, false>(S, tw, buf, t, phi_w + (size_t)j * N, dss_w + (size_t)j * N);
+            }
+        }
+        {
+            float2 R[V];
+            grad_load<N, V>(R, Rck + (size_t)seg * N, t, ok);
+            for (int j = j0; j < j1; ++j) {
+                grad_store<N, V>(Rseg + (size_t)(j - j0) * N, R, t, ok);
+                if (j + 1 < j1) grad_step<N, V, true>(R, tw, buf, t, phi_w + (size_t)j * N, dss_w + (size_t)j * N);
+            }
+        }
+        for (int j = j1 - 1; j >= j0; --j, ++depth_count) {
+            const float* mrow = a.m + (size_t)j * N;
+            // P_j U_{j+1} (zero at the deepest row)
+            if (j + 1 < nz) grad_step<N, V, false>(U, tw, buf, t, phi_w + (size_t)j * N, dss_w + (size_t)j * N);
+            float2 Rj[V];
+            grad_load<N, V>(Rj, Rseg + (size_t)(j - j0) * N, t, ok);
+            float gs[V], gm[V];
+#pragma unroll
+            for (int r = 0; r < V; ++r) gs[r] = fmaf(Rj[r].x, U[r].y, -Rj[r].y * U[r].x);  // Im conj(R) PU
+            if (j + 1 < nz) {
+                float2 S1[V];
+                grad_load<N, V>(S1, Sseg + (size_t)(j + 1 - j0) * N, t, ok);
+#pragma unroll
+                for (int r = 0; r < V; ++r) gs[r] += fmaf(mu[r].x, S1[r].y, -mu[r].y * S1[r].x);  // Im conj(mu) S1
+            }
+            {
+                float2 Sj[V];
+                grad_load<N, V>(Sj, Sseg + (size_t)(j - j0) * N, t, ok);
+#pragma unroll
+                for (int r = 0; r < V; ++r) {
+                    const float mm = __ldg(mrow + t + T * r);
+                    gm[r] = fmaf(Sj[r].x, Rj[r].x, Sj[r].y * Rj[r].y);
+                    U[r].x = fmaf(Sj[r].x, mm, U[r].x);
+                    U[r].y = fmaf(Sj[r].y, mm, U[r].y);
+                }
+            }
+            // Re(i z) = -Im(z)
+#pragma unroll
+            for (int r = 0; r < V; ++r) gs[r] = -wdz * gs[r];
+            // mu_j = m_j R_j + P_j^H mu_{j+1}
+            if (j + 1 < nz) {
+                grad_step<N, V, true>(mu, tw, buf, t, phi_w + (size_t)j * N, dss_w + (size_t)j * N);
+            } else {
+#pragma unroll
+                for (int r = 0; r < V; ++r) mu[r] = make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int r = 0; r < V; ++r) {
+                const float mm = __ldg(mrow + t + T * r);
+                mu[r].x = fmaf(mm, Rj[r].x, mu[r].x);
+                mu[r].y = fmaf(mm, Rj[r].y, mu[r].y);
+            }
+            // sum both gradient rows over the block's items
+#pragma unroll
+            for (int off = T; off < 32; off <<= 1) {
+#pragma unroll
+                for (int r = 0; r < V; ++r) {
+                    gm[r] += __shfl_xor_sync(0xffffffffu, gm[r], off);
+                    gs[r] += __shfl_xor_sync(0xffffffffu, gs[r], off);
+                }
+            }
+            const int b = depth_count & 1;
+            float* slab_m = img + ((size_t)(b * 2 + 0) * nwarps + warp) * N;
+            float* slab_s = img + ((size_t)(b * 2 + 1) * nwarps + warp) * N;
+            if (sub == 0) {
+#pragma unroll
+                for (int r = 0; r < V; ++r) {
+                    slab_m[t + T * r] = ok ? gm[r] : 0.f;
+                    slab_s[t + T * r] = ok ? gs[r] : 0.f;
+                }
+            }
+            __syncthreads();
+            {
+                const float* rows_m = img + (size_t)(b * 2 + 0) * nwarps * N;
+                const float* rows_s = img + (size_t)(b * 2 + 1) * nwarps * N;
+                for (int x = threadIdx.x; x < N; x += blockDim.x) {
+                    float am = 0.f, as = 0.f;
+                    for (int w2 = 0; w2 < nwarps; ++w2) {
+                        am += rows_m[w2 * N + x];
+                        as += rows_s[w2 * N + x];
+                    }
+                    a.part_m[((size_t)blockIdx.x * nz + j) * N + x] = am;
+                    a.part_s[((size_t)blockIdx.x * nz + j) * N + x] = as;
+                }
+            }
+        }
+    }
+    // U now holds U_0: the modelled data of this item
+    if (a.dout) {
+        float2* orow = a.dout + ((size_t)ishot * a.nw + iw) * a.nrec;
+        if (a.rec_identity) {
+            grad_store<N, V>(orow, U, t, ok);
+        } else {
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < V; ++r) buf[P::phys(t + T * r)] = U[r];
+            __syncwarp();
+            if (ok) {
+                const int* rix = a.rec_ix + (size_t)shot * a.nrec;
+                for (int rr = t; rr < a.nrec; rr += T) orow[rr] = buf[P::phys(__ldg(rix + rr))];
+            }
+        }
+    }
+}
+
+}  // namespace lsm

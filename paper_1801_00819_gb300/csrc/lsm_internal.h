@@ -30,6 +30,28 @@ struct SweepArgs {
     float* part;                   // adjoint per-block partial images [grid][nz][nx]
 };
 
+// Arguments of the gradient kernel (lsm_grad.cuh) over the items of shots [shot0, shot0+nshots).
+struct GradArgs {
+    int nx, nz, nw, nrec;
+    int shot0, nshots;
+    int rec_identity;
+    int ckpt_every;                // depth checkpoint stride of S and R
+    float dz;
+    const int* src_ix;
+    const int* rec_ix;
+    const float2* wavelet;
+    const float* freq_hz;          // device [nw]
+    const float2* phi;             // coefficient tables in the order of Plan<nx, 16>
+    const float2* dss;
+    const float* m;                // [nz][nx]
+    const float2* g;               // dL/dRe d + i dL/dIm d, [nshots][nw][nrec]
+    float2* ckpt;                  // [items][2][ceil(nz/c)][nx]
+    float2* seg;                   // [items][2c+1][nx]
+    float* part_m;                 // [blocks][nz][nx]
+    float* part_s;                 // [blocks][nz][nx]
+    float2* dout;                  // optional modelled data [nshots][nw][nrec]
+};
+
 struct TableArgs {
     int nx, nz, nw;
     float dx, dz;
@@ -60,7 +82,10 @@ cudaError_t launch_sweep(int mode, const SweepArgs& a, const SweepShape& shape, 
     cudaError_t launch_tables_##NN(const TableArgs& a, cudaStream_t st);                      \
     cudaError_t launch_sweep_##NN(int mode, const SweepArgs& a, const SweepShape& shape,      \
                                   cudaStream_t st);                                           \
-    int sweep_max_warps_##NN(int mode);
+    int sweep_max_warps_##NN(int mode);                                                       \
+    cudaError_t launch_tables_grad_##NN(const TableArgs& a, cudaStream_t st);                 \
+    cudaError_t launch_gradient_##NN(const GradArgs& a, const SweepShape& shape, cudaStream_t st); \
+    int gradient_max_warps_##NN();
 LSM_DECLARE_N(16)
 LSM_DECLARE_N(32)
 LSM_DECLARE_N(64)
@@ -73,12 +98,19 @@ LSM_DECLARE_N(1024)
 // points per thread chosen for each nx
 constexpr int points_per_thread(int nx) { return nx >= 512 ? 32 : 16; }
 
+// Points per thread of the gradient kernel (it carries three wavefields in registers).
+constexpr int gradient_points_per_thread() { return 16; }
+bool gradient_nx_supported(int nx);
+SweepShape gradient_shape(int nx, int nshots, int nw, int num_sms);
+cudaError_t launch_tables_grad(const TableArgs& a, cudaStream_t st);
+cudaError_t launch_gradient(const GradArgs& a, const SweepShape& shape, cudaStream_t st);
+
 void count_launch(int n = 1);
 
 // Per-launch event timing (lsm_profile_start / lsm_profile_stop).  Construct a ProfScope right
 // before a launch and destroy it right after; both ends record an event on the launch stream
 // when profiling is on.
-enum KernelClass { KC_TABLES = 0, KC_SOURCE = 1, KC_ADJOINT = 2, KC_FORWARD = 3, KC_VECTOR = 4 };
+enum KernelClass { KC_TABLES = 0, KC_SOURCE = 1, KC_ADJOINT = 2, KC_FORWARD = 3, KC_VECTOR = 4, KC_GRADIENT = 5 };
 void profile_mark(int cls, cudaStream_t st, bool begin);
 struct ProfScope {
     int cls;

@@ -22,6 +22,7 @@
 #pragma once
 
 #include "lsm_fft.cuh"
+#include "lsm_grad.cuh"
 #include "lsm_internal.h"
 
 namespace lsm {
@@ -387,6 +388,57 @@ struct Dispatch {
             default: return max_warps_mode<MODE_FORWARD>();
         }
     }
+
+    // gradient kernel: 16 points per thread, so nx <= 512
+    static constexpr int VG = gradient_points_per_thread();
+    static constexpr bool kGrad = N / VG <= 32;
+
+    static cudaError_t tables_grad(const TableArgs& a, cudaStream_t st) {
+        if constexpr (kGrad) {
+            const size_t total = (size_t)a.nw * a.nz * N;
+            size_t blocks = (total + 255) / 256;
+            if (blocks > 65535u * 8u) blocks = 65535u * 8u;
+            ProfScope prof_(KC_TABLES, st);
+            tables_kernel<N, VG><<<(unsigned)blocks, 256, 0, st>>>(a);
+            count_launch();
+            return cudaGetLastError();
+        } else {
+            return cudaErrorNotSupported;
+        }
+    }
+
+    static cudaError_t gradient(const GradArgs& a, const SweepShape& sh, cudaStream_t st) {
+        if constexpr (kGrad) {
+            static bool configured = false;
+            if (!configured) {
+                cudaError_t e = cudaFuncSetAttribute(gradient_kernel<N, VG>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+                if (e != cudaSuccess) return e;
+                configured = true;
+            }
+            if (sh.smem != gradient_smem_bytes<N, VG>(sh.warps)) return cudaErrorInvalidValue;
+            ProfScope prof_(KC_GRADIENT, st);
+            gradient_kernel<N, VG><<<sh.blocks, sh.warps * 32, sh.smem, st>>>(a);
+            count_launch();
+            return cudaGetLastError();
+        } else {
+            return cudaErrorNotSupported;
+        }
+    }
+
+    static int gradient_max_warps() {
+        if constexpr (kGrad) {
+            cudaFuncAttributes attr;
+            if (cudaFuncGetAttributes(&attr, gradient_kernel<N, VG>) != cudaSuccess) {
+                cudaGetLastError();
+                return 8;
+            }
+            const int w = attr.maxThreadsPerBlock / 32;
+            return w < 1 ? 1 : (w > 8 ? 8 : w);
+        } else {
+            return 1;
+        }
+    }
 };
 
 }  // namespace lsm
@@ -401,4 +453,11 @@ struct Dispatch {
         return Dispatch<NN>::sweep_any(mode, a, sh, st);                                          \
     }                                                                                             \
     int sweep_max_warps_##NN(int mode) { return Dispatch<NN>::max_warps(mode); }                  \
+    cudaError_t launch_tables_grad_##NN(const TableArgs& a, cudaStream_t st) {                    \
+        return Dispatch<NN>::tables_grad(a, st);                                                  \
+    }                                                                                             \
+    cudaError_t launch_gradient_##NN(const GradArgs& a, const SweepShape& sh, cudaStream_t st) {  \
+        return Dispatch<NN>::gradient(a, sh, st);                                                 \
+    }                                                                                             \
+    int gradient_max_warps_##NN() { return Dispatch<NN>::gradient_max_warps(); }                  \
     }

@@ -27,14 +27,16 @@ LSM_ERR_UNSUPPORTED_NX = -6
 LSM_OP_FORWARD = 0
 LSM_OP_ADJOINT = 1
 LSM_OP_SOLVE = 2
+LSM_OP_GRADIENT = 3
+LSM_CHECKPOINT_EVERY = 16
 
 EXPORTED = ("lsm_workspace_bytes", "lsm_forward", "lsm_adjoint", "lsm_num_windows", "rls_window_solve",
             "lsm_status_string", "lsm_kernel_launches", "lsm_profile_start", "lsm_profile_stop",
-            "lsm_adjoint_static")
+            "lsm_adjoint_static", "lsm_born_gradient")
 
 LSM_STATIC_SCRATCH_BYTES = 64 << 20
 
-KERNEL_CLASSES = ("tables", "source", "adjoint", "forward", "vector")
+KERNEL_CLASSES = ("tables", "source", "adjoint", "forward", "vector", "gradient")
 
 
 class LsmError(RuntimeError):
@@ -67,7 +69,7 @@ class lsm_window_stats(ctypes.Structure):
 
 
 class lsm_profile(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_ulonglong * 5), ("ms", ctypes.c_double * 5)]
+    _fields_ = [("launches", ctypes.c_ulonglong * 6), ("ms", ctypes.c_double * 6)]
 
 
 _lib_handle = None
@@ -99,6 +101,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lsm_adjoint_static.restype = ctypes.c_int
     lib.lsm_adjoint_static.argtypes = [ctypes.POINTER(lsm_grid), P, ctypes.POINTER(lsm_freqs),
                                        ctypes.POINTER(lsm_geom), P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
+    lib.lsm_born_gradient.restype = ctypes.c_int
+    lib.lsm_born_gradient.argtypes = [ctypes.POINTER(lsm_grid), P, P, ctypes.POINTER(lsm_freqs),
+                                      ctypes.POINTER(lsm_geom), P, P, P, P, P, ctypes.c_int, ctypes.c_int, P,
+                                      ctypes.c_size_t, P]
     lib.lsm_num_windows.restype = ctypes.c_int
     lib.lsm_num_windows.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.rls_window_solve.restype = ctypes.c_int
@@ -240,6 +246,16 @@ def lsm_adjoint_static(grid, slowness, freqs, geom, d, m_out, shot0, nshots, acc
                                            ctypes.byref(geom.c), _ptr(d), _ptr(m_out), int(shot0), int(nshots),
                                            1 if accumulate else 0, _stream(stream))
     _check(st, "lsm_adjoint_static")
+
+
+def lsm_born_gradient(grid, slowness, sref, freqs, geom, m, g, d_out, grad_m, grad_s, shot0, nshots, workspace,
+                      stream=None):
+    """Model d = A(s) m (g None) or the gradients dL/dm, dL/ds with s_ref held fixed (see include/lsm.h)."""
+    st = load_library().lsm_born_gradient(ctypes.byref(grid.c), _ptr(slowness), _ptr(sref), ctypes.byref(freqs.c),
+                                          ctypes.byref(geom.c), _ptr(m), _ptr(g), _ptr(d_out), _ptr(grad_m),
+                                          _ptr(grad_s), int(shot0), int(nshots), _ptr(workspace), _nbytes(workspace),
+                                          _stream(stream))
+    _check(st, "lsm_born_gradient")
 
 
 def rls_window_solve(grid, slowness, freqs, geom, d, lam, K, slide, cg_tol, max_iter, m_inout, workspace,
