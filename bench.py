@@ -317,11 +317,18 @@ def gpu_arm(args):
     roofline["units_per_launch"] = units_per_pass
     roofline["secondary"] = secondary
 
+    fwd_ms = prof["forward"]["ms"] / max(prof["forward"]["launches"], 1)
+    adj_ms = prof["adjoint"]["ms"] / max(prof["adjoint"]["launches"], 1)
+    operator = {"definition": "K*nw*nz / (t_A + t_AT) for one window application, mean event times in the "
+                              "timed region",
+                "value": round(units_per_pass / ((fwd_ms + adj_ms) / 1e3), 1), "unit": "units/s",
+                "t_A_ms": round(fwd_ms, 4), "t_AT_ms": round(adj_ms, 4)}
     out = {"metric": "shot*omega*depth steps/s for A+A^T (window-RLS solve to 1e-3 residual)",
            "value": round(value, 1), "unit": "units/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
-           "config": workload_config(sv), "roofline": roofline, "clocks": clk, "gpu_launches": int(launches),
+           "config": workload_config(sv), "roofline": roofline, "operator": operator, "clocks": clk,
+           "gpu_launches": int(launches),
            "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items()},
            "kernel_launches": {k: v["launches"] for k, v in prof.items()},
            "cg": {"windows": len(stats[-1]), "iters_per_window": iters, "total_iters": int(sum(iters)),
