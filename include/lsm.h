@@ -234,6 +234,31 @@ typedef struct {
 void lsm_profile_start(void);
 int lsm_profile_stop(lsm_profile* out);
 
+/*
+ * Solver options for rls_window_solve_ex.
+ *   preconditioner: LSM_PRECOND_NONE, or LSM_PRECOND_ILLUMINATION for preconditioned CG with the
+ *     diagonal source-illumination preconditioner of each window,
+ *     M = sum_{shots in window, w} |S_j(x)|^2 + precond_eps * max (M^-1 applied to the model
+ *     residual).  The paper asks for preconditioners that cluster the spectrum of each windowed
+ *     Hessian (block-row section) without naming one; this is the reading.  The stopping rule stays
+ *     the unpreconditioned ||A_k^T (d_k - A_k m) - lambda m|| / ||A_k^T d_k||.
+ *   precond_eps: > 0, relative stabiliser (1e-2 is a good default).
+ */
+#define LSM_PRECOND_NONE 0
+#define LSM_PRECOND_ILLUMINATION 1
+typedef struct {
+    int preconditioner;
+    double precond_eps;
+} lsm_solve_options;
+
+/* rls_window_solve with options (options == NULL: plain CG, identical to rls_window_solve). */
+int rls_window_solve_ex(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs,
+                        const lsm_geom* geom, const float* d, double lambda, int K, int slide,
+                        double cg_tol, int max_iter, int first_window, int n_windows,
+                        float* m_inout, lsm_window_stats* stats, int stats_cap,
+                        void* workspace, size_t workspace_bytes, void* stream,
+                        const lsm_solve_options* options);
+
 /* Human-readable name of a status code (static string). */
 const char* lsm_status_string(int status);
 

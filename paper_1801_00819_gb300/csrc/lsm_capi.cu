@@ -235,6 +235,7 @@ struct Layout {
     size_t src, rec, freq, wav, sref, phi, dss, S, part;
     size_t p, s, r, q, qq, pp, ss, state;
     size_t ckpt, seg, part_s;  // gradient op
+    size_t illum, minv, bmax, sz;  // preconditioned solve
     size_t total;
     int ring, nparts;
 };
@@ -287,6 +288,10 @@ Layout make_layout(const lsm_grid* g, const lsm_geom* geo, const lsm_freqs* f, i
         L.pp = take(kRedBlocks * sizeof(double));
         L.ss = take(kRedBlocks * sizeof(double));
         L.state = take(sizeof(CgState));
+        L.illum = take(plane * sizeof(float));
+        L.minv = take(plane * sizeof(float));
+        L.bmax = take(kIllumBlocks * sizeof(float));
+        L.sz = take(kRedBlocks * sizeof(double));
     } else if (op == LSM_OP_ADJOINT) {
         L.ss = take(kRedBlocks * sizeof(double));
     }
@@ -630,15 +635,19 @@ static int window_start(int k, int ns, int K, int slide) {
     return k < regular ? k * slide : ns - K;
 }
 
-int rls_window_solve(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs, const lsm_geom* geom,
-                     const float* d, double lambda, int K, int slide, double cg_tol, int max_iter, int first_window,
-                     int n_windows, float* m_inout, lsm_window_stats* stats, int stats_cap, void* workspace,
-                     size_t workspace_bytes, void* stream) {
+int rls_window_solve_ex(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs, const lsm_geom* geom,
+                        const float* d, double lambda, int K, int slide, double cg_tol, int max_iter,
+                        int first_window, int n_windows, float* m_inout, lsm_window_stats* stats, int stats_cap,
+                        void* workspace, size_t workspace_bytes, void* stream, const lsm_solve_options* options) {
     int rc = validate_common(grid, freqs, geom);
     if (rc != LSM_OK) return rc;
     if (!aligned16(slowness) || !aligned16(d) || !aligned16(m_inout) || !aligned16(workspace)) return LSM_ERR_ARG;
     if (!std::isfinite(lambda) || lambda < 0.0 || !std::isfinite(cg_tol) || cg_tol < 0.0 || max_iter < 0)
         return LSM_ERR_ARG;
+    const int precond = options ? options->preconditioner : LSM_PRECOND_NONE;
+    const double precond_eps = options ? options->precond_eps : 0.0;
+    if (precond != LSM_PRECOND_NONE && precond != LSM_PRECOND_ILLUMINATION) return LSM_ERR_ARG;
+    if (precond == LSM_PRECOND_ILLUMINATION && !(precond_eps > 0.0 && std::isfinite(precond_eps))) return LSM_ERR_ARG;
     const int ns = geom->ns;
     const int nwin = lsm_num_windows(ns, K, slide);
     if (nwin == 0) return LSM_ERR_ARG;
@@ -667,6 +676,8 @@ int rls_window_solve(const lsm_grid* grid, const float* slowness, const lsm_freq
     double* pp = reinterpret_cast<double*>(ws + L.pp);
     double* ss = reinterpret_cast<double*>(ws + L.ss);
     CgState* state = reinterpret_cast<CgState*>(ws + L.state);
+    float* minv = precond == LSM_PRECOND_ILLUMINATION ? reinterpret_cast<float*>(ws + L.minv) : nullptr;
+    double* sz = minv ? reinterpret_cast<double*>(ws + L.sz) : nullptr;
     const float2* dall = reinterpret_cast<const float2*>(d);
     const float lamf = (float)lambda;
 
@@ -679,6 +690,13 @@ int rls_window_solve(const lsm_grid* grid, const float* slowness, const lsm_freq
         const int new_from = prev_start < 0 ? start : std::max(start, prev_start + K);
         if (new_from < start + K) LSM_CHECK(run_source(a, new_from, start + K - new_from, nsm, st));
         prev_start = start;
+        if (minv) {
+            // the ring now holds exactly this window's source wavefields
+            LSM_CHECK(cg_illumination(a.S, K * freqs->nw, n, reinterpret_cast<float*>(ws + L.illum),
+                                      reinterpret_cast<float*>(ws + L.bmax), st));
+            LSM_CHECK(cg_precond_finalize(reinterpret_cast<const float*>(ws + L.illum), n,
+                                          reinterpret_cast<const float*>(ws + L.bmax), precond_eps, minv, st));
+        }
 
         int nparts = 0;
         LSM_CHECK(cg_zero_state(state, st));
@@ -691,14 +709,14 @@ int rls_window_solve(const lsm_grid* grid, const float* slowness, const lsm_freq
         LSM_CHECK(cg_residual(dk, q, r, nd, st));
         // s = A_k^T r - lambda m ; p = s ; gamma = ||s||^2
         LSM_CHECK(run_adjoint(a, start, K, r, nsm, st, &nparts));
-        LSM_CHECK(cg_reduce_image(a.part, nparts, n, m_inout, lamf, 0, s, ss, st));
+        LSM_CHECK(cg_reduce_image(a.part, nparts, n, m_inout, lamf, 0, s, ss, st, minv, sz));
         int gi = 0;
-        LSM_CHECK(cg_update_p(p, s, n, ss, 1, state, 1, gi, pp, st));
+        LSM_CHECK(cg_update_p(p, s, n, ss, 1, state, 1, gi, pp, st, minv, sz));
         CgState hs;
         LSM_CHECK(cudaMemcpyAsync(&hs, state, sizeof(CgState), cudaMemcpyDeviceToHost, st));
         LSM_CHECK(cudaStreamSynchronize(st));
         const double bnorm = std::sqrt(hs.bb);
-        double rel = bnorm > 0.0 ? std::sqrt(hs.gamma[gi]) / bnorm : 0.0;
+        double rel = bnorm > 0.0 ? std::sqrt(hs.ss[gi]) / bnorm : 0.0;
         const double rel0 = rel;
         int nfwd = 1, nadj = 2, it = 0;
         bool broke = hs.breakdown != 0;
@@ -709,8 +727,8 @@ int rls_window_solve(const lsm_grid* grid, const float* slowness, const lsm_freq
             LSM_CHECK(cg_update_mr(m_inout, p, n, r, q, nd, qq, pp, lambda, state, gi, st));
             // s = A_k^T r - lambda m ; beta ; p = s + beta p
             LSM_CHECK(run_adjoint(a, start, K, r, nsm, st, &nparts));
-            LSM_CHECK(cg_reduce_image(a.part, nparts, n, m_inout, lamf, 0, s, ss, st));
-            LSM_CHECK(cg_update_p(p, s, n, ss, 0, state, gi, gi ^ 1, pp, st));
+            LSM_CHECK(cg_reduce_image(a.part, nparts, n, m_inout, lamf, 0, s, ss, st, minv, sz));
+            LSM_CHECK(cg_update_p(p, s, n, ss, 0, state, gi, gi ^ 1, pp, st, minv, sz));
             gi ^= 1;
             ++nfwd;
             ++nadj;
@@ -718,7 +736,7 @@ int rls_window_solve(const lsm_grid* grid, const float* slowness, const lsm_freq
             LSM_CHECK(cudaMemcpyAsync(&hs, state, sizeof(CgState), cudaMemcpyDeviceToHost, st));
             LSM_CHECK(cudaStreamSynchronize(st));
             broke = hs.breakdown != 0;
-            rel = bnorm > 0.0 ? std::sqrt(hs.gamma[gi]) / bnorm : 0.0;
+            rel = bnorm > 0.0 ? std::sqrt(hs.ss[gi]) / bnorm : 0.0;
         }
         const auto t1 = std::chrono::steady_clock::now();
         const int idx = k - first_window;
@@ -734,6 +752,14 @@ int rls_window_solve(const lsm_grid* grid, const float* slowness, const lsm_freq
         if (broke) return LSM_ERR_BREAKDOWN;
     }
     return LSM_OK;
+}
+
+int rls_window_solve(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs, const lsm_geom* geom,
+                     const float* d, double lambda, int K, int slide, double cg_tol, int max_iter, int first_window,
+                     int n_windows, float* m_inout, lsm_window_stats* stats, int stats_cap, void* workspace,
+                     size_t workspace_bytes, void* stream) {
+    return rls_window_solve_ex(grid, slowness, freqs, geom, d, lambda, K, slide, cg_tol, max_iter, first_window,
+                               n_windows, m_inout, stats, stats_cap, workspace, workspace_bytes, stream, nullptr);
 }
 
 const char* lsm_status_string(int status) {

@@ -39,15 +39,19 @@ __device__ __forceinline__ double sum_partials(const double* __restrict__ part, 
     return tot;
 }
 
-// out[i] = (acc ? out[i] : 0) + sum_c part[c][i] - lam * m[i];  partial sums of out[i]^2
+// out[i] = (acc ? out[i] : 0) + sum_c part[c][i] - lam * m[i];  partial sums of out[i]^2 and,
+// when minv is given, of out[i]^2 minv[i] (s.z for preconditioned CG)
 __global__ void __launch_bounds__(kRedThreads) reduce_image_kernel(const float* __restrict__ part, int nparts, int n4,
                                                                const float* __restrict__ m, float lam, int acc,
-                                                               float* __restrict__ out, double* __restrict__ ss_part) {
+                                                               float* __restrict__ out, double* __restrict__ ss_part,
+                                                               const float* __restrict__ minv,
+                                                               double* __restrict__ sz_part) {
     __shared__ double sh[40];
     const float4* p4 = reinterpret_cast<const float4*>(part);
     const float4* m4 = reinterpret_cast<const float4*>(m);
+    const float4* w4 = reinterpret_cast<const float4*>(minv);
     float4* o4 = reinterpret_cast<float4*>(out);
-    double ss = 0.0;
+    double ss = 0.0, sz = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += gridDim.x * blockDim.x) {
         float4 s = acc ? o4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         for (int c = 0; c < nparts; ++c) {
@@ -61,9 +65,17 @@ __global__ void __launch_bounds__(kRedThreads) reduce_image_kernel(const float* 
         }
         o4[i] = s;
         ss += (double)s.x * s.x + (double)s.y * s.y + (double)s.z * s.z + (double)s.w * s.w;
+        if (minv) {
+            const float4 w = w4[i];
+            sz += (double)s.x * s.x * w.x + (double)s.y * s.y * w.y + (double)s.z * s.z * w.z + (double)s.w * s.w * w.w;
+        }
     }
     const double tot = block_sum(ss, sh);
     if (threadIdx.x == 0 && ss_part) ss_part[blockIdx.x] = tot;
+    if (minv) {
+        const double tz = block_sum(sz, sh);
+        if (threadIdx.x == 0 && sz_part) sz_part[blockIdx.x] = tz;
+    }
 }
 
 // partial sums of |q|^2 over a complex vector of n2 float2 pairs (processed as float4)
@@ -139,27 +151,36 @@ __global__ void __launch_bounds__(kRedThreads) update_mr_kernel(float* __restric
     }
 }
 
-// gamma_new = ||s||^2; beta = first ? 0 : gamma_new / gamma_old; p = s + beta p; partials of ||p||^2.
-// Reads gamma[gi_old] and writes gamma[gi_new] (distinct slots, so blocks never race).
+// gamma_new = s.z (z = minv s, or z = s); beta = first ? 0 : gamma_new / gamma_old; p = z + beta p;
+// partials of ||p||^2.  Reads gamma[gi_old] and writes gamma[gi_new] and ss[gi_new] (distinct
+// slots, so blocks never race).
 __global__ void __launch_bounds__(kRedThreads) update_p_kernel(float* __restrict__ p, const float* __restrict__ s, int n4,
                                                            const double* __restrict__ ss_part, int nred, int first,
                                                            CgState* st, int gi_old, int gi_new,
-                                                           double* __restrict__ pp_part) {
+                                                           double* __restrict__ pp_part, const float* __restrict__ minv,
+                                                           const double* __restrict__ sz_part) {
     __shared__ double sh[40];
-    const double gnew = sum_partials(ss_part, nred, sh);
+    const double ssum = sum_partials(ss_part, nred, sh);
+    const double gnew = minv ? sum_partials(sz_part, nred, sh) : ssum;
     const double gold = first ? 1.0 : st->gamma[gi_old];
     const double beta = first ? 0.0 : gnew / gold;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->gamma[gi_new] = gnew;
+        st->ss[gi_new] = ssum;
         st->beta = beta;
-        if (!isfinite(gnew)) st->breakdown = 1;
+        if (!isfinite(gnew) || !isfinite(ssum)) st->breakdown = 1;
     }
     const float b = (float)beta;
     float4* p4 = reinterpret_cast<float4*>(p);
     const float4* s4 = reinterpret_cast<const float4*>(s);
+    const float4* w4 = reinterpret_cast<const float4*>(minv);
     double pp = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += gridDim.x * blockDim.x) {
-        const float4 x = s4[i];
+        float4 x = s4[i];
+        if (minv) {
+            const float4 w = w4[i];
+            x.x *= w.x; x.y *= w.y; x.z *= w.z; x.w *= w.w;
+        }
         float4 y = first ? make_float4(0.f, 0.f, 0.f, 0.f) : p4[i];
         y.x = fmaf(b, y.x, x.x); y.y = fmaf(b, y.y, x.y); y.z = fmaf(b, y.z, x.z); y.w = fmaf(b, y.w, x.w);
         p4[i] = y;
@@ -167,6 +188,60 @@ __global__ void __launch_bounds__(kRedThreads) update_p_kernel(float* __restrict
     }
     const double tot = block_sum(pp, sh);
     if (threadIdx.x == 0) pp_part[blockIdx.x] = tot;
+}
+
+// illum[i] = sum over rows r of |S[r * n + i]|^2 (rows = ring slots x frequencies, each row one
+// [nz][nx] plane); per-block maxima of illum
+__global__ void __launch_bounds__(256) illumination_kernel(const float2* __restrict__ S, int rows, int n,
+                                                           float* __restrict__ illum, float* __restrict__ block_max) {
+    __shared__ float shm[8];
+    float mx = 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+        int r = 0;
+        for (; r + 4 <= rows; r += 4) {
+            const float2 a = __ldcs(S + (size_t)r * n + i), b = __ldcs(S + (size_t)(r + 1) * n + i);
+            const float2 c = __ldcs(S + (size_t)(r + 2) * n + i), d = __ldcs(S + (size_t)(r + 3) * n + i);
+            acc0 = fmaf(a.x, a.x, fmaf(a.y, a.y, acc0));
+            acc1 = fmaf(b.x, b.x, fmaf(b.y, b.y, acc1));
+            acc2 = fmaf(c.x, c.x, fmaf(c.y, c.y, acc2));
+            acc3 = fmaf(d.x, d.x, fmaf(d.y, d.y, acc3));
+        }
+        for (; r < rows; ++r) {
+            const float2 a = __ldcs(S + (size_t)r * n + i);
+            acc0 = fmaf(a.x, a.x, fmaf(a.y, a.y, acc0));
+        }
+        const float v = (acc0 + acc1) + (acc2 + acc3);
+        illum[i] = v;
+        mx = fmaxf(mx, v);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m2 = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m2 = fmaxf(m2, shm[w]);
+        block_max[blockIdx.x] = m2;
+    }
+}
+
+// minv = 1 / (illum + eps max illum); every block takes the maximum of the block maxima itself
+__global__ void __launch_bounds__(256) precond_finalize_kernel(const float* __restrict__ illum, int n,
+                                                               const float* __restrict__ block_max, int nblocks,
+                                                               float eps, float* __restrict__ minv) {
+    __shared__ float shm[8];
+    float mx = 0.f;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) mx = fmaxf(mx, block_max[b]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    float gmax = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) gmax = fmaxf(gmax, shm[w]);
+    const float stab = gmax > 0.f ? eps * gmax : 1.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        minv[i] = 1.f / (illum[i] + stab);
 }
 
 // st->bb = sum of partials (||A^T d||^2)
@@ -180,6 +255,7 @@ __global__ void zero_state_kernel(CgState* st) {
     if (threadIdx.x == 0) {
         st->gamma[0] = st->gamma[1] = 0.0;
         st->alpha = st->beta = st->delta = st->bb = 0.0;
+        st->ss[0] = st->ss[1] = 0.0;
         st->breakdown = 0;
     }
 }
@@ -187,9 +263,10 @@ __global__ void zero_state_kernel(CgState* st) {
 // ------------------------------------------------------------------ launchers
 
 cudaError_t cg_reduce_image(const float* part, int nparts, int n, const float* m, float lam, int acc, float* out,
-                            double* ss_part, cudaStream_t st) {
+                            double* ss_part, cudaStream_t st, const float* minv, double* sz_part) {
     ProfScope prof_(KC_VECTOR, st);
-    reduce_image_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(part, nparts, n / 4, m, lam, acc, out, ss_part);
+    reduce_image_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(part, nparts, n / 4, m, lam, acc, out, ss_part, minv,
+                                                            sz_part);
     count_launch();
     return cudaGetLastError();
 }
@@ -219,10 +296,11 @@ cudaError_t cg_update_mr(float* m, const float* p, int n, float2* r, const float
 }
 
 cudaError_t cg_update_p(float* p, const float* s, int n, const double* ss_part, int first, CgState* state,
-                        int gi_old, int gi_new, double* pp_part, cudaStream_t st) {
+                        int gi_old, int gi_new, double* pp_part, cudaStream_t st, const float* minv,
+                        const double* sz_part) {
     ProfScope prof_(KC_VECTOR, st);
     update_p_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(p, s, n / 4, ss_part, kRedBlocks, first, state, gi_old,
-                                                         gi_new, pp_part);
+                                                         gi_new, pp_part, minv, sz_part);
     count_launch();
     return cudaGetLastError();
 }
@@ -237,6 +315,21 @@ cudaError_t cg_store_sum(const double* part, CgState* state, cudaStream_t st) {
 cudaError_t cg_zero_state(CgState* state, cudaStream_t st) {
     ProfScope prof_(KC_VECTOR, st);
     zero_state_kernel<<<1, 32, 0, st>>>(state);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t cg_illumination(const float2* S, int rows, int n, float* illum, float* block_max, cudaStream_t st) {
+    ProfScope prof_(KC_VECTOR, st);
+    illumination_kernel<<<kIllumBlocks, 256, 0, st>>>(S, rows, n, illum, block_max);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t cg_precond_finalize(const float* illum, int n, const float* block_max, double eps, float* minv,
+                                cudaStream_t st) {
+    ProfScope prof_(KC_VECTOR, st);
+    precond_finalize_kernel<<<kRedBlocks, 256, 0, st>>>(illum, n, block_max, kIllumBlocks, (float)eps, minv);
     count_launch();
     return cudaGetLastError();
 }

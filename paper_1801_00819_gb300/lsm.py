@@ -32,7 +32,10 @@ LSM_CHECKPOINT_EVERY = 16
 
 EXPORTED = ("lsm_workspace_bytes", "lsm_forward", "lsm_adjoint", "lsm_num_windows", "rls_window_solve",
             "lsm_status_string", "lsm_kernel_launches", "lsm_profile_start", "lsm_profile_stop",
-            "lsm_adjoint_static", "lsm_born_gradient")
+            "lsm_adjoint_static", "lsm_born_gradient", "rls_window_solve_ex")
+
+LSM_PRECOND_NONE = 0
+LSM_PRECOND_ILLUMINATION = 1
 
 LSM_STATIC_SCRATCH_BYTES = 64 << 20
 
@@ -57,6 +60,10 @@ class lsm_geom(ctypes.Structure):
 class lsm_freqs(ctypes.Structure):
     _fields_ = [("nw", ctypes.c_int), ("freq_hz", ctypes.POINTER(ctypes.c_float)),
                 ("wavelet", ctypes.POINTER(ctypes.c_float))]
+
+
+class lsm_solve_options(ctypes.Structure):
+    _fields_ = [("preconditioner", ctypes.c_int), ("precond_eps", ctypes.c_double)]
 
 
 class lsm_window_stats(ctypes.Structure):
@@ -112,6 +119,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                      ctypes.POINTER(lsm_geom), P, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, P,
                                      ctypes.POINTER(lsm_window_stats), ctypes.c_int, P, ctypes.c_size_t, P]
+    lib.rls_window_solve_ex.restype = ctypes.c_int
+    lib.rls_window_solve_ex.argtypes = list(lib.rls_window_solve.argtypes) + [ctypes.POINTER(lsm_solve_options)]
     lib.lsm_status_string.restype = ctypes.c_char_p
     lib.lsm_status_string.argtypes = [ctypes.c_int]
     lib.lsm_kernel_launches.restype = ctypes.c_ulonglong
@@ -259,16 +268,27 @@ def lsm_born_gradient(grid, slowness, sref, freqs, geom, m, g, d_out, grad_m, gr
 
 
 def rls_window_solve(grid, slowness, freqs, geom, d, lam, K, slide, cg_tol, max_iter, m_inout, workspace,
-                     first_window=0, n_windows=0, stream=None, raise_on_breakdown=True):
-    """Sliding-window CG solve; returns (status, [stats dicts]).  m_inout is updated in place."""
+                     first_window=0, n_windows=0, stream=None, raise_on_breakdown=True, preconditioner=None,
+                     precond_eps=1e-2):
+    """Sliding-window CG solve; returns (status, [stats dicts]).  m_inout is updated in place.
+
+    preconditioner=None calls rls_window_solve; "illumination" calls rls_window_solve_ex with the
+    diagonal source-illumination preconditioner (stabiliser precond_eps times its maximum).
+    """
     lib = load_library()
     nwin = lib.lsm_num_windows(int(geom.c.ns), int(K), int(slide))
     cap = max(nwin, 1)
     stats = (lsm_window_stats * cap)()
-    st = lib.rls_window_solve(ctypes.byref(grid.c), _ptr(slowness), ctypes.byref(freqs.c), ctypes.byref(geom.c),
-                              _ptr(d), float(lam), int(K), int(slide), float(cg_tol), int(max_iter),
-                              int(first_window), int(n_windows), _ptr(m_inout), stats, cap, _ptr(workspace),
-                              _nbytes(workspace), _stream(stream))
+    args = (ctypes.byref(grid.c), _ptr(slowness), ctypes.byref(freqs.c), ctypes.byref(geom.c), _ptr(d), float(lam),
+            int(K), int(slide), float(cg_tol), int(max_iter), int(first_window), int(n_windows), _ptr(m_inout), stats,
+            cap, _ptr(workspace), _nbytes(workspace), _stream(stream))
+    if preconditioner is None:
+        st = lib.rls_window_solve(*args)
+    elif preconditioner == "illumination":
+        opts = lsm_solve_options(LSM_PRECOND_ILLUMINATION, float(precond_eps))
+        st = lib.rls_window_solve_ex(*args, ctypes.byref(opts))
+    else:
+        raise ValueError(f"unknown preconditioner {preconditioner!r}")
     last = nwin if n_windows <= 0 else min(nwin, first_window + n_windows)
     out = [stats[i].as_dict() for i in range(max(0, last - first_window))]
     if st != LSM_OK and (st != LSM_ERR_BREAKDOWN or raise_on_breakdown):

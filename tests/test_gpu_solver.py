@@ -118,3 +118,39 @@ def test_breakdown_on_nonfinite_data(torch_cuda):
     status, _ = L.rls_window_solve(ds.grid, ds.slowness, ds.freqs, ds.geom, torch_cuda.as_tensor(d, device="cuda"),
                                    1.0, 3, 1, 0.0, 3, m, ws, raise_on_breakdown=False)
     assert status == L.lsm.LSM_ERR_BREAKDOWN
+
+
+def _gpu_solve_pc(torch, ds, d, lam, K, slide, tol, iters):
+    import paper_1801_00819_gb300 as L
+    ws = torch.empty(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, K, L.LSM_OP_SOLVE), dtype=torch.uint8,
+                     device="cuda")
+    m = torch.zeros((ds.nz, ds.nx), dtype=torch.float32, device="cuda")
+    _, stats = L.rls_window_solve(ds.grid, ds.slowness, ds.freqs, ds.geom, torch.as_tensor(d, device="cuda"), lam,
+                                  K, slide, tol, iters, m, ws, preconditioner="illumination", precond_eps=1e-2)
+    torch.cuda.synchronize()
+    return m.cpu().numpy().astype(np.float64), stats
+
+
+def test_illumination_preconditioned_solve_matches_oracle(torch_cuda):
+    """Preconditioned variant on the tiny workload: window 4 / slide 2, 10 PCG iterations."""
+    sv = config_tiny()
+    op = oracle_operator(sv)
+    d, lam = _oracle_data(sv, op)
+    ds = device_survey(sv)
+    m_gpu, st_gpu = _gpu_solve_pc(torch_cuda, ds, d, lam, sv.window, sv.slide, 0.0, sv.cg_iters)
+    m_ref, st_ref = O.rls_solve(op, d.astype(np.complex128), lam, sv.window, sv.slide, sv.cg_iters, precond_eps=1e-2)
+    for g, r in zip(st_gpu, st_ref):
+        assert abs(g["rel_res0"] - r.rel_res0) <= 1e-3 * r.rel_res0
+    assert rel_l2(m_gpu, m_ref) <= TOL
+
+
+def test_preconditioned_tolerance_stopping_matches_oracle(torch_cuda):
+    sv = random_case(64, 24, 6, 12, seed=72)
+    op = oracle_operator(sv)
+    d, lam = _oracle_data(sv, op)
+    ds = device_survey(sv)
+    m_gpu, st_gpu = _gpu_solve_pc(torch_cuda, ds, d, lam, 3, 2, 1e-2, 50)
+    m_ref, st_ref = O.rls_solve(op, d.astype(np.complex128), lam, 3, 2, 50, tol=1e-2, precond_eps=1e-2)
+    assert [s["iters"] for s in st_gpu] == [s.iters for s in st_ref]
+    assert all(s["rel_res"] <= 1e-2 for s in st_gpu)
+    assert rel_l2(m_gpu, m_ref) <= TOL

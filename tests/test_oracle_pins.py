@@ -456,3 +456,58 @@ def test_planted_missing_source_adjoint_term_fails_gradient_pin(monkeypatch):
     monkeypatch.setattr(O, "born_gradients", without_mu)
     with pytest.raises(AssertionError):
         test_slowness_gradient_matches_central_differences()
+
+
+# ---------------------------------------------------------------- preconditioned variant
+
+
+def test_pcg_converges_to_cholesky_solution():
+    op, d = _tiny_problem(seed=7)
+    A = O.explicit_matrix(op)
+    lam = 1e-2 * np.linalg.norm(np.real(A.conj().T @ A), 2)
+    m_chol = O.closed_form_solution(A, d, lam).reshape(op.nz, op.nx)
+    m_pcg, st = O.pcg_window(op, np.arange(op.ns), d, lam, np.zeros((op.nz, op.nx)), 300, tol=1e-13)
+    assert st.rel_res <= 1e-13
+    assert np.linalg.norm(m_pcg - m_chol) <= 1e-9 * np.linalg.norm(m_chol)
+
+
+def test_pcg_iterates_equal_textbook_pcg_on_explicit_matrix():
+    op, d = _tiny_problem(seed=8)
+    A = O.explicit_matrix(op)
+    H = np.real(A.conj().T @ A)
+    lam = 0.05 * np.linalg.norm(H, 2)
+    H = H + lam * np.eye(H.shape[0])
+    shots = np.arange(op.ns)
+    illum = O.illumination(op, shots).ravel()
+    # the illumination is the diagonal of the source-side part, cross-checked by brute force
+    S = op.source_wavefield(shots)
+    assert np.allclose(illum, sum(np.abs(S[:, i, w, :].ravel()) ** 2 for i in range(op.ns) for w in range(op.nw)))
+    minv = 1.0 / (illum + 1e-2 * illum.max())
+    hist = []
+    O.pcg_window(op, shots, d, lam, np.zeros((op.nz, op.nx)), 6, tol=0.0, precond_eps=1e-2, history=hist)
+    b = np.real(A.conj().T @ d.ravel())
+    x = np.zeros_like(b)
+    r = b.copy()
+    z = minv * r
+    p = z.copy()
+    for it in range(1, 7):
+        Hp = H @ p
+        a = (r @ z) / (p @ Hp)
+        x = x + a * p
+        r_new = r - a * Hp
+        z_new = minv * r_new
+        p = z_new + (r_new @ z_new) / (r @ z) * p
+        r, z = r_new, z_new
+        np.testing.assert_allclose(hist[it].ravel(), x, rtol=0, atol=1e-9 * np.linalg.norm(x))
+
+
+def test_illumination_preconditioner_cuts_iterations_on_tiny_config():
+    sv = config_tiny()
+    op = _op(sv)
+    clean = op.forward(sv.reflectivity)
+    d = clean + sv.noise_pct * np.sqrt(np.mean(np.abs(clean) ** 2)) * sv.noise()
+    lam = O.regularisation_from_adjoint(op, d)
+    shots = np.arange(sv.window)
+    _, plain = O.cg_window(op, shots, d[shots], lam, np.zeros((op.nz, op.nx)), 200, tol=1e-3)
+    _, pre = O.pcg_window(op, shots, d[shots], lam, np.zeros((op.nz, op.nx)), 200, tol=1e-3)
+    assert pre.iters < plain.iters
