@@ -57,6 +57,7 @@ def parse_args():
     ap.add_argument("--workload", choices=("realistic", "tiny"), default="realistic")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--cpu-sample-freqs", type=int, default=128,
                     help="frequencies in the GPU arm's cpu_baseline sample (about 10-30 s of oracle work)")
     ap.add_argument("--ref-sample-freqs", type=int, default=16,
@@ -366,6 +367,22 @@ def gpu_arm(args):
         out["e2e"] = {"value": round(units_e * world / (te / 1e3), 1), "unit": "units/s",
                       "h2d_bytes_per_step": int(d_host.numel() * 8 + s_host.numel() * 4),
                       "d2h_bytes_per_step": int(img_host.numel() * 4), "ms_per_step": round(te / args.steps, 3)}
+
+    # the paper's preconditioned variant (illumination preconditioner), one untimed-by-contract solve
+    if not args.no_variants:
+        torch.cuda.synchronize()
+        v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        m.zero_()
+        v0.record(stream)
+        _, stv = L.rls_window_solve(ds.grid, ds.slowness, ds.freqs, ds.geom, d, lam, K, sv.slide, sv.cg_tol,
+                                    sv.cg_iters, m, ws, preconditioner="illumination", precond_eps=1e-2)
+        v1.record(stream)
+        torch.cuda.synchronize()
+        tv = v0.elapsed_time(v1)
+        out["variants"] = {"illumination_preconditioned": {
+            "time_to_tol_ms": round(tv, 3), "total_iters": int(sum(w["iters"] for w in stv)),
+            "iters_per_window": [w["iters"] for w in stv],
+            "time_to_tol_vs_plain": round((t_max / args.steps) / tv, 3)}}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sv, args.cpu_sample_freqs)
