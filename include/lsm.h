@@ -11,8 +11,10 @@
  *
  * Conventions shared by every entry point
  * ---------------------------------------
- *  - Grid: nx lateral cells (a power of two, 16 <= nx <= 1024) by nz depth rows, spacing
- *    dx, dz in metres.  Depth row j sits at z = j dz; sources and receivers are at row 0.
+ *  - Grid: nx lateral cells by nz depth rows, spacing dx, dz in metres.  nx is a power of two
+ *    from 16 to 1024 or one of 48, 96, 192, 384, 768 (3 * 2^a), 80, 160, 320, 640 (5 * 2^a),
+ *    112, 224, 448, 896 (7 * 2^a); the lateral transforms are exact mixed-radix FFTs of that
+ *    length (no padding, the boundary stays periodic).  Depth row j sits at z = j dz; sources and receivers are at row 0.
  *  - Slowness: device float32 [nz][nx] in s/m (row j contiguous).  Model / image: device
  *    float32 [nz][nx].
  *  - Frequencies: host float32 freq_hz[nw] (Hz; w = 2 pi f) and host float32 wavelet[nw][2]
@@ -60,7 +62,7 @@ extern "C" {
 #define LSM_ERR_BREAKDOWN (-4)      /* CG step length undefined: q^T q + lambda p^T p <= 0 or
                                        not finite (e.g. non-finite input data) */
 #define LSM_ERR_TIMEOUT (-5)        /* reserved: a bounded device wait expired */
-#define LSM_ERR_UNSUPPORTED_NX (-6) /* nx is not a power of two in [16, 1024] */
+#define LSM_ERR_UNSUPPORTED_NX (-6) /* nx is not one of the supported widths (see Grid) */
 
 #define LSM_OP_FORWARD 0
 #define LSM_OP_ADJOINT 1

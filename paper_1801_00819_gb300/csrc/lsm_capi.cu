@@ -63,39 +63,33 @@ void profile_mark(int cls, cudaStream_t st, bool begin) {
     }
 }
 
-bool nx_supported(int nx) {
-    switch (nx) {
-        case 16: case 32: case 64: case 128: case 256: case 512: case 1024: return true;
-        default: return false;
-    }
+#define LSM_NX_LIST(X)                                                                       \
+    X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(48) X(96) X(192) X(384) X(768) X(80) X(160) \
+    X(320) X(640) X(112) X(224) X(448) X(896)
+#define LSM_DECLARE_OPS(NN) extern const NxOps kNxOps_##NN;
+LSM_NX_LIST(LSM_DECLARE_OPS)
+#undef LSM_DECLARE_OPS
+
+const NxOps* nx_ops(int nx) {
+#define LSM_MATCH_OPS(NN) \
+    if (nx == NN) return &kNxOps_##NN;
+    LSM_NX_LIST(LSM_MATCH_OPS)
+#undef LSM_MATCH_OPS
+    return nullptr;
 }
 
-static int max_warps_for(int nx, int mode) {
-    switch (nx) {
-        case 16: return sweep_max_warps_16(mode);
-        case 32: return sweep_max_warps_32(mode);
-        case 64: return sweep_max_warps_64(mode);
-        case 128: return sweep_max_warps_128(mode);
-        case 256: return sweep_max_warps_256(mode);
-        case 512: return sweep_max_warps_512(mode);
-        default: return sweep_max_warps_1024(mode);
-    }
-}
+bool nx_supported(int nx) { return nx_ops(nx) != nullptr; }
 
 SweepShape sweep_shape(int nx, int mode, int nshots, int nw, int num_sms) {
-    const int V = points_per_thread(nx);
+    const NxOps* ops = nx_ops(nx);
+    const int V = ops->points_per_thread;
     const int T = nx / V;
     const int ipw = 32 / T;
     const int nitems = nshots * nw;
-    const size_t buf = (size_t)(nx + nx / 16) * sizeof(float2);
     const int warps_total = (nitems + ipw - 1) / ipw;
-    // shared memory of a block of w warps (must match sweep_smem_bytes in lsm_sweep.cuh)
     auto wslots_of = [&](int w) { return std::min(nw, (w * ipw + nshots - 1) / nshots + 1); };
-    auto smem_of = [&](int w) {
-        return (size_t)w * ipw * buf + 2 * ((size_t)wslots_of(w) * 2 * nx * sizeof(float2) + (size_t)nx * sizeof(float)) +
-               (mode == MODE_ADJOINT ? (size_t)2 * w * nx * sizeof(float) : 0);
-    };
-    int maxw = std::min(V >= 32 ? 8 : 16, max_warps_for(nx, mode));
+    auto smem_of = [&](int w) { return ops->smem(mode, w, wslots_of(w)); };
+    int maxw = std::min(V >= 24 ? 8 : 16, ops->max_warps(mode));
     while (maxw > 1 && smem_of(maxw) > 227 * 1024) --maxw;
     int warps = (warps_total + num_sms - 1) / num_sms;
     warps = std::max(1, std::min(warps, maxw));
@@ -107,20 +101,13 @@ SweepShape sweep_shape(int nx, int mode, int nshots, int nw, int num_sms) {
     return s;
 }
 
-bool gradient_nx_supported(int nx) { return nx_supported(nx) && nx <= 16 * 32; }
-
-static int gradient_max_warps_for(int nx) {
-    switch (nx) {
-        case 16: return gradient_max_warps_16();
-        case 32: return gradient_max_warps_32();
-        case 64: return gradient_max_warps_64();
-        case 128: return gradient_max_warps_128();
-        case 256: return gradient_max_warps_256();
-        default: return gradient_max_warps_512();
-    }
+bool gradient_nx_supported(int nx) {
+    const NxOps* ops = nx_ops(nx);
+    return ops && ops->has_gradient;
 }
 
 SweepShape gradient_shape(int nx, int nshots, int nw, int num_sms) {
+    const NxOps* ops = nx_ops(nx);
     const int V = gradient_points_per_thread();
     const int T = nx / V;
     const int ipw = 32 / T;
@@ -129,7 +116,7 @@ SweepShape gradient_shape(int nx, int nshots, int nw, int num_sms) {
     auto smem_of = [&](int w) {
         return (size_t)w * ipw * (size_t)(nx + nx / 16) * sizeof(float2) + (size_t)4 * w * nx * sizeof(float);
     };
-    int maxw = std::min(8, gradient_max_warps_for(nx));
+    int maxw = std::min(8, ops->gradient_max_warps());
     while (maxw > 1 && smem_of(maxw) > 227 * 1024) --maxw;
     int warps = (warps_total + num_sms - 1) / num_sms;
     warps = std::max(1, std::min(warps, maxw));
@@ -141,52 +128,13 @@ SweepShape gradient_shape(int nx, int nshots, int nw, int num_sms) {
     return s;
 }
 
-cudaError_t launch_tables_grad(const TableArgs& a, cudaStream_t st) {
-    switch (a.nx) {
-        case 16: return launch_tables_grad_16(a, st);
-        case 32: return launch_tables_grad_32(a, st);
-        case 64: return launch_tables_grad_64(a, st);
-        case 128: return launch_tables_grad_128(a, st);
-        case 256: return launch_tables_grad_256(a, st);
-        case 512: return launch_tables_grad_512(a, st);
-        default: return cudaErrorNotSupported;
-    }
-}
-
+cudaError_t launch_tables_grad(const TableArgs& a, cudaStream_t st) { return nx_ops(a.nx)->tables_grad(a, st); }
 cudaError_t launch_gradient(const GradArgs& a, const SweepShape& sh, cudaStream_t st) {
-    switch (a.nx) {
-        case 16: return launch_gradient_16(a, sh, st);
-        case 32: return launch_gradient_32(a, sh, st);
-        case 64: return launch_gradient_64(a, sh, st);
-        case 128: return launch_gradient_128(a, sh, st);
-        case 256: return launch_gradient_256(a, sh, st);
-        case 512: return launch_gradient_512(a, sh, st);
-        default: return cudaErrorNotSupported;
-    }
+    return nx_ops(a.nx)->gradient(a, sh, st);
 }
-
-cudaError_t launch_tables(const TableArgs& a, cudaStream_t st) {
-    switch (a.nx) {
-        case 16: return launch_tables_16(a, st);
-        case 32: return launch_tables_32(a, st);
-        case 64: return launch_tables_64(a, st);
-        case 128: return launch_tables_128(a, st);
-        case 256: return launch_tables_256(a, st);
-        case 512: return launch_tables_512(a, st);
-        default: return launch_tables_1024(a, st);
-    }
-}
-
+cudaError_t launch_tables(const TableArgs& a, cudaStream_t st) { return nx_ops(a.nx)->tables(a, st); }
 cudaError_t launch_sweep(int mode, const SweepArgs& a, const SweepShape& sh, cudaStream_t st) {
-    switch (a.nx) {
-        case 16: return launch_sweep_16(mode, a, sh, st);
-        case 32: return launch_sweep_32(mode, a, sh, st);
-        case 64: return launch_sweep_64(mode, a, sh, st);
-        case 128: return launch_sweep_128(mode, a, sh, st);
-        case 256: return launch_sweep_256(mode, a, sh, st);
-        case 512: return launch_sweep_512(mode, a, sh, st);
-        default: return launch_sweep_1024(mode, a, sh, st);
-    }
+    return nx_ops(a.nx)->sweep(mode, a, sh, st);
 }
 
 // s_ref(z_j) = mean over x of s(x, z_j), summed in float64 (Examples section: split-step
@@ -770,7 +718,9 @@ const char* lsm_status_string(int status) {
         case LSM_ERR_WORKSPACE: return "workspace too small";
         case LSM_ERR_BREAKDOWN: return "CG breakdown (step length undefined)";
         case LSM_ERR_TIMEOUT: return "device wait timed out";
-        case LSM_ERR_UNSUPPORTED_NX: return "nx must be a power of two in [16, 1024]";
+        case LSM_ERR_UNSUPPORTED_NX:
+            return "unsupported nx: 16, 32, 64, 128, 256, 512, 1024, 48, 96, 192, 384, 768, 80, 160, 320, 640, "
+                   "112, 224, 448, 896 (gradients: powers of two up to 512)";
         default: return "unknown status";
     }
 }

@@ -109,9 +109,52 @@ constexpr int bit_reverse(int k, int n) {
     return r;
 }
 
+// Odd prime R (3, 5, 7): direct DFT using the symmetry of its constants.  With a_n = x_n + x_{R-n}
+// and b_n = x_n - x_{R-n} (n = 1 .. (R-1)/2), re_k = x_0 + sum a_n cos(2 pi n k / R) and
+// im_k = sum b_n sin(2 pi n k / R); the forward DFT is y_k = re_k - i im_k, y_{R-k} = re_k + i im_k
+// (the inverse swaps the two).
+template <int R, int K, int NN>
+struct OddConst {
+    static constexpr float c = (float)series_cos(turn_angle(NN * K, R));
+    static constexpr float s = (float)series_sin(turn_angle(NN * K, R));
+};
+
+template <int R, bool INV, int K, int... Ns>
+__device__ __forceinline__ void odd_output(float2* y, float2 x0, const float2* a, const float2* b,
+                                           std::integer_sequence<int, Ns...>) {
+    float2 re = x0, im = make_float2(0.f, 0.f);
+    ((re.x = fmaf(a[Ns + 1].x, OddConst<R, K, Ns + 1>::c, re.x),
+      re.y = fmaf(a[Ns + 1].y, OddConst<R, K, Ns + 1>::c, re.y),
+      im.x = fmaf(b[Ns + 1].x, OddConst<R, K, Ns + 1>::s, im.x),
+      im.y = fmaf(b[Ns + 1].y, OddConst<R, K, Ns + 1>::s, im.y)), ...);
+    const float2 mi = make_float2(im.y, -im.x);  // -i * im
+    y[K] = INV ? csub(re, mi) : cadd(re, mi);
+    y[R - K] = INV ? cadd(re, mi) : csub(re, mi);
+}
+
+template <int R, bool INV, int... Ks>
+__device__ __forceinline__ void odd_dft(float2* v, std::integer_sequence<int, Ks...>) {
+    constexpr int H = (R - 1) / 2;
+    float2 a[H + 1], b[H + 1], y[R];
+    float2 y0 = v[0];
+#pragma unroll
+    for (int n = 1; n <= H; ++n) {
+        a[n] = cadd(v[n], v[R - n]);
+        b[n] = csub(v[n], v[R - n]);
+        y0 = cadd(y0, a[n]);
+    }
+    y[0] = y0;
+    (odd_output<R, INV, Ks + 1>(y, v[0], a, b, std::make_integer_sequence<int, H>{}), ...);
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = y[k];
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void small_dft(float2* v) {
-    if constexpr (R > 1) {
+    if constexpr (R == 3 || R == 5 || R == 7) {
+        odd_dft<R, INV>(v, std::make_integer_sequence<int, (R - 1) / 2>{});
+    } else if constexpr (R > 1) {
+        static_assert((R & (R - 1)) == 0, "power-of-two or odd prime radix");
         r2_passes<R, INV, R / 2>(v);
         float2 t[R];
 #pragma unroll
@@ -125,23 +168,37 @@ __device__ __forceinline__ void small_dft(float2* v) {
 // Stage s works on blocks of length L(s) = N / (R(0)...R(s-1)); each block is split into R(s)
 // interleaved sub-sequences of length M(s) = L(s) / R(s).  Butterfly beta = t + T i (i < NB(s))
 // takes block b = beta / M, offset n1 = beta % M, inputs b L + n1 + M n2 (n2 < R), and writes
-// output k2, twiddled by exp(-2 pi i n1 k2 / L), to position b L + k2 M + n1.  Radices are
-// greedy: R(s) = min(V, L(s)).  After the last stage (M = 1) thread t's register
-// r = i R_last + k2 holds position (t + T i) R_last + k2; the position's mixed-radix digits,
-// read in reverse, give the frequency index.
+// output k2, twiddled by exp(-2 pi i n1 k2 / L), to position b L + k2 M + n1.  Radices: for a
+// power-of-two N, R(s) = min(V, L(s)); for N = q 2^a with q in {3, 5, 7}, the first stage has
+// radix q and the others min(power-of-two part of V, L(s)).  Every radix divides V.  So thread t
+// holds input x = t + T (r / R0) + M0 (r % R0) in register r (x = t + T r when R0 = V), and after
+// the last stage (M = 1) register r = i R_last + k2 holds position (t + T i) R_last + k2; the
+// position's mixed-radix digits, read in reverse, give the frequency index.
+
+constexpr int odd_part(int n) {
+    while (n > 1 && n % 2 == 0) n /= 2;
+    return n;
+}
 
 template <int N, int V>
 struct Plan {
-    static_assert((N & (N - 1)) == 0 && (V & (V - 1)) == 0, "powers of two");
-    static_assert(N >= V && V >= 2, "V points per thread");
+    static constexpr int Q = odd_part(N);
+    static_assert(Q == 1 || Q == 3 || Q == 5 || Q == 7, "N = 2^a times 1, 3, 5 or 7");
+    static_assert(N % V == 0 && V % Q == 0 && V / Q >= 2 && V >= 2, "V points per thread");
     static constexpr int T = N / V;
-    static_assert(T <= 32, "one transform per warp at most");
+    static_assert(T <= 32 && (T & (T - 1)) == 0, "a power-of-two number of threads, one warp at most");
+    static constexpr int VP2 = V / odd_part(V);  // power-of-two part of V
+    static constexpr int R(int s) {
+        int len = N;
+        for (int i = 0; i < s; ++i) len /= R(i);
+        if (s == 0) return Q > 1 ? Q : (len < V ? len : V);
+        return len < VP2 ? len : VP2;
+    }
     static constexpr int L(int s) {
         int len = N;
-        for (int i = 0; i < s; ++i) len /= (len < V ? len : V);
+        for (int i = 0; i < s; ++i) len /= R(i);
         return len;
     }
-    static constexpr int R(int s) { return L(s) < V ? L(s) : V; }
     static constexpr int M(int s) { return L(s) / R(s); }
     static constexpr int NB(int s) { return V / R(s); }
     static constexpr int count_stages() {
@@ -151,18 +208,31 @@ struct Plan {
     }
     static constexpr int NS = count_stages();
     static constexpr int RLAST = R(NS - 1);
-    // registers of precomputed twiddles: stages with M > 1
+    static constexpr int R0 = R(0);
+    static constexpr int M0 = M(0);
+    // twiddles live in registers for power-of-two plans and in a shared table otherwise
+    static constexpr bool TW_SMEM = Q > 1;
     static constexpr int tw_offset(int s) {
         int off = 0;
         for (int i = 0; i < s; ++i)
             if (M(i) > 1) off += NB(i) * (R(i) - 1);
         return off;
     }
-    static constexpr int NTW = tw_offset(NS) > 0 ? tw_offset(NS) : 1;
+    static constexpr int NTW = (!TW_SMEM && tw_offset(NS) > 0) ? tw_offset(NS) : 1;
+    // shared twiddle table: exp(-2 pi i e / L(s)) for e < L(s), per stage with M(s) > 1
+    static constexpr int tab_offset(int s) {
+        int off = 0;
+        for (int i = 0; i < s; ++i)
+            if (M(i) > 1) off += L(i);
+        return off;
+    }
+    static constexpr int TAB = TW_SMEM ? tab_offset(NS) : 0;
     // padded shared-memory index: one float2 of padding every 16 removes bank conflicts of the
     // strided stage exchanges
     static __device__ __forceinline__ int phys(int a) { return a + (a >> 4); }
     static constexpr int BUF = N + N / 16;
+    // natural-order column held in register r of thread t
+    static __host__ __device__ constexpr int xpos(int t, int r) { return t + T * (r / R0) + M0 * (r % R0); }
     // frequency index held at final position pos
     static __host__ __device__ constexpr int freq_of_position(int pos) {
         int k = 0, weight = 1;
@@ -181,29 +251,63 @@ struct Plan {
 
 template <int N, int V>
 struct Twiddles {
-    float2 w[Plan<N, V>::NTW];
+    using P = Plan<N, V>;
+    float2 w[P::NTW];
+    const float2* table;  // shared table (TW_SMEM plans)
+    int t;
+    // twiddle exp(-2 pi i n1 k2 / L(S)) of butterfly i of this thread, k2 >= 1 (plan quantities are
+    // bound to constexpr locals so that register indices fold at compile time)
+    template <int S>
+    __device__ __forceinline__ float2 at(int i, int k2) const {
+        constexpr int M = P::M(S), L = P::L(S), R = P::R(S);
+        if constexpr (P::TW_SMEM) {
+            constexpr int TOFF = P::tab_offset(S);
+            const int n1 = (t + P::T * i) % M;
+            return table[TOFF + (n1 * k2) % L];
+        } else {
+            constexpr int OFF = P::tw_offset(S);
+            return w[OFF + i * (R - 1) + (k2 - 1)];
+        }
+    }
 };
 
-template <int N, int V>
-__device__ __forceinline__ void init_twiddles(Twiddles<N, V>& tw, int t) {
+template <int N, int V, int S>
+__device__ __forceinline__ void init_twiddles_stage(Twiddles<N, V>& tw, int t, float2* table) {
     using P = Plan<N, V>;
+    constexpr int M = P::M(S), L = P::L(S), R = P::R(S), NB = P::NB(S);
+    if constexpr (M > 1) {
+        if constexpr (P::TW_SMEM) {
+            constexpr int TOFF = P::tab_offset(S);
+            for (int e = threadIdx.x; e < L; e += blockDim.x) {
+                float sn, cs;
+                sincospif(-2.0f * (float)e / (float)L, &sn, &cs);
+                table[TOFF + e] = make_float2(cs, sn);
+            }
+        } else {
+            constexpr int OFF = P::tw_offset(S);
 #pragma unroll
-    for (int s = 0; s < P::NS; ++s) {
-        if (P::M(s) > 1) {
+            for (int i = 0; i < NB; ++i) {
+                const int n1 = (t + P::T * i) % M;
 #pragma unroll
-            for (int i = 0; i < P::NB(s); ++i) {
-                const int beta = t + P::T * i;
-                const int n1 = beta % P::M(s);
-#pragma unroll
-                for (int k2 = 1; k2 < P::R(s); ++k2) {
-                    const int e = (n1 * k2) % P::L(s);
+                for (int k2 = 1; k2 < R; ++k2) {
+                    const int e = (n1 * k2) % L;
                     float sn, cs;
-                    sincospif(-2.0f * (float)e / (float)P::L(s), &sn, &cs);
-                    tw.w[P::tw_offset(s) + i * (P::R(s) - 1) + (k2 - 1)] = make_float2(cs, sn);
+                    sincospif(-2.0f * (float)e / (float)L, &sn, &cs);
+                    tw.w[OFF + i * (R - 1) + (k2 - 1)] = make_float2(cs, sn);
                 }
             }
         }
     }
+    if constexpr (S + 1 < P::NS) init_twiddles_stage<N, V, S + 1>(tw, t, table);
+}
+
+// Registers: every thread computes its own twiddles.  Shared table (mixed-radix plans): the whole
+// block fills it, so every thread must call this and the block must synchronise before first use.
+template <int N, int V>
+__device__ __forceinline__ void init_twiddles(Twiddles<N, V>& tw, int t, float2* table = nullptr) {
+    tw.t = t;
+    tw.table = table;
+    init_twiddles_stage<N, V, 0>(tw, t, table);
 }
 
 // ------------------------------------------------------------------ exchanges
@@ -273,7 +377,7 @@ __device__ __forceinline__ void forward_stages(float2 (&v)[V], const Twiddles<N,
         if constexpr (P::M(S) > 1) {
 #pragma unroll
             for (int k2 = 1; k2 < R; ++k2)
-                v[i * R + k2] = cmul(v[i * R + k2], tw.w[P::tw_offset(S) + i * (R - 1) + (k2 - 1)]);
+                v[i * R + k2] = cmul(v[i * R + k2], tw.template at<S>(i, k2));
         }
     }
     if constexpr (S + 1 < P::NS) {
@@ -294,7 +398,7 @@ __device__ __forceinline__ void inverse_stages(float2 (&v)[V], const Twiddles<N,
         if constexpr (P::M(S) > 1) {
 #pragma unroll
             for (int k2 = 1; k2 < R; ++k2)
-                v[i * R + k2] = cmulc(v[i * R + k2], tw.w[P::tw_offset(S) + i * (R - 1) + (k2 - 1)]);
+                v[i * R + k2] = cmulc(v[i * R + k2], tw.template at<S>(i, k2));
         }
         small_dft<R, true>(&v[i * R]);
     }
@@ -335,7 +439,7 @@ __device__ __forceinline__ void phase_shift_two_stage(float2 (&v)[V], const Twid
     static_assert(M1 == 1 && R0 == V, "one first-stage butterfly per thread, unit-stride last stage");
     small_dft<R0, false>(v);
 #pragma unroll
-    for (int k2 = 1; k2 < R0; ++k2) v[k2] = cmul(v[k2], tw.w[P::tw_offset(0) + (k2 - 1)]);
+    for (int k2 = 1; k2 < R0; ++k2) v[k2] = cmul(v[k2], tw.template at<0>(0, k2));
     __syncwarp();
     store_outputs<N, V, 0>(v, buf, t);
     __syncwarp();
@@ -359,7 +463,7 @@ __device__ __forceinline__ void phase_shift_two_stage(float2 (&v)[V], const Twid
     __syncwarp();
     load_outputs<N, V, 0>(v, buf, t);
 #pragma unroll
-    for (int k2 = 1; k2 < R0; ++k2) v[k2] = cmulc(v[k2], tw.w[P::tw_offset(0) + (k2 - 1)]);
+    for (int k2 = 1; k2 < R0; ++k2) v[k2] = cmulc(v[k2], tw.template at<0>(0, k2));
     small_dft<R0, true>(v);
 }
 

@@ -25,7 +25,7 @@ __device__ __forceinline__ void grad_step(float2 (&v)[V], const Twiddles<N, V>& 
     constexpr int T = Plan<N, V>::T;
     if (ADJ) {
 #pragma unroll
-        for (int r = 0; r < V; ++r) v[r] = cmulc(v[r], __ldg(dss + t + T * r));
+        for (int r = 0; r < V; ++r) v[r] = cmulc(v[r], __ldg(dss + Plan<N, V>::xpos(t, r)));
     }
     fft_forward<N, V>(v, tw, buf, t);
 #pragma unroll
@@ -33,7 +33,7 @@ __device__ __forceinline__ void grad_step(float2 (&v)[V], const Twiddles<N, V>& 
     fft_inverse<N, V>(v, tw, buf, t);
     if (!ADJ) {
 #pragma unroll
-        for (int r = 0; r < V; ++r) v[r] = cmul(v[r], __ldg(dss + t + T * r));
+        for (int r = 0; r < V; ++r) v[r] = cmul(v[r], __ldg(dss + Plan<N, V>::xpos(t, r)));
     }
 }
 
@@ -63,6 +63,7 @@ constexpr size_t gradient_smem_bytes(int warps) {
 template <int N, int V>
 __global__ void __launch_bounds__(256) gradient_kernel(const GradArgs a) {
     using P = Plan<N, V>;
+    static_assert(P::R0 == V && !P::TW_SMEM, "power-of-two plans: register r holds column t + T r");
     constexpr int T = P::T;
     constexpr int IPW = 32 / T;
     extern __shared__ float4 smem_f4[];

@@ -77,26 +77,35 @@ SweepShape sweep_shape(int nx, int mode, int nshots, int nw, int num_sms);
 cudaError_t launch_tables(const TableArgs& a, cudaStream_t st);
 cudaError_t launch_sweep(int mode, const SweepArgs& a, const SweepShape& shape, cudaStream_t st);
 
-// per-N dispatch targets (one translation unit per nx)
-#define LSM_DECLARE_N(NN)                                                                     \
-    cudaError_t launch_tables_##NN(const TableArgs& a, cudaStream_t st);                      \
-    cudaError_t launch_sweep_##NN(int mode, const SweepArgs& a, const SweepShape& shape,      \
-                                  cudaStream_t st);                                           \
-    int sweep_max_warps_##NN(int mode);                                                       \
-    cudaError_t launch_tables_grad_##NN(const TableArgs& a, cudaStream_t st);                 \
-    cudaError_t launch_gradient_##NN(const GradArgs& a, const SweepShape& shape, cudaStream_t st); \
-    int gradient_max_warps_##NN();
-LSM_DECLARE_N(16)
-LSM_DECLARE_N(32)
-LSM_DECLARE_N(64)
-LSM_DECLARE_N(128)
-LSM_DECLARE_N(256)
-LSM_DECLARE_N(512)
-LSM_DECLARE_N(1024)
-#undef LSM_DECLARE_N
+// Per-nx entry points, one translation unit (sweep_n<nx>.cu) per supported nx.
+struct NxOps {
+    int nx;
+    int points_per_thread;        // V of the sweep kernels
+    bool has_gradient;            // lsm_born_gradient's kernel exists for this nx
+    cudaError_t (*tables)(const TableArgs& a, cudaStream_t st);
+    cudaError_t (*sweep)(int mode, const SweepArgs& a, const SweepShape& shape, cudaStream_t st);
+    int (*max_warps)(int mode);
+    size_t (*smem)(int mode, int warps, int wslots);
+    cudaError_t (*tables_grad)(const TableArgs& a, cudaStream_t st);
+    cudaError_t (*gradient)(const GradArgs& a, const SweepShape& shape, cudaStream_t st);
+    int (*gradient_max_warps)();
+};
+// The operations for nx, or nullptr when nx is not supported.
+const NxOps* nx_ops(int nx);
 
-// points per thread chosen for each nx
-constexpr int points_per_thread(int nx) { return nx >= 512 ? 32 : 16; }
+// Points per thread of the sweep kernels: 16 for power-of-two nx below 512 and 32 from 512; for
+// nx = q 2^a (q = 3, 5, 7), 8 q (4 q when q = 7), doubled until at most 32 threads share a line.
+constexpr int odd_factor(int n) {
+    while (n > 1 && n % 2 == 0) n /= 2;
+    return n;
+}
+constexpr int points_per_thread(int nx) {
+    const int q = odd_factor(nx);
+    if (q == 1) return nx >= 512 ? 32 : 16;
+    int v = q == 7 ? 4 * q : 8 * q;
+    while (nx / v > 32) v *= 2;
+    return v;
+}
 
 // Points per thread of the gradient kernel (it carries three wavefields in registers).
 constexpr int gradient_points_per_thread() { return 16; }

@@ -38,11 +38,12 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // ------------------------------------------------------------------ one depth step
 
+// a natural-order row (S, data) into the register layout
 template <int N, int V>
 __device__ __forceinline__ void load_row(float2 (&v)[V], const float2* __restrict__ row, int t, bool ok) {
-    constexpr int T = Plan<N, V>::T;
+    using P = Plan<N, V>;
 #pragma unroll
-    for (int r = 0; r < V; ++r) v[r] = ok ? __ldcs(row + t + T * r) : make_float2(0.f, 0.f);
+    for (int r = 0; r < V; ++r) v[r] = ok ? __ldcs(row + P::xpos(t, r)) : make_float2(0.f, 0.f);
 }
 
 // phi, dss: this depth's rows staged in shared memory
@@ -59,7 +60,7 @@ __device__ __forceinline__ void step_down(float2 (&v)[V], const Twiddles<N, V>& 
         fft_inverse<N, V>(v, tw, buf, t);
     }
 #pragma unroll
-    for (int r = 0; r < V; ++r) v[r] = cmul(v[r], dss[t + T * r]);
+    for (int r = 0; r < V; ++r) v[r] = cmul(v[r], dss[Plan<N, V>::xpos(t, r)]);
 }
 
 template <int N, int V>
@@ -67,7 +68,7 @@ __device__ __forceinline__ void step_down_adjoint(float2 (&v)[V], const Twiddles
                                                   const float2* phi, const float2* dss) {
     constexpr int T = Plan<N, V>::T;
 #pragma unroll
-    for (int r = 0; r < V; ++r) v[r] = cmulc(v[r], dss[t + T * r]);
+    for (int r = 0; r < V; ++r) v[r] = cmulc(v[r], dss[Plan<N, V>::xpos(t, r)]);
     if constexpr (Plan<N, V>::NS == 2 && Plan<N, V>::NB(0) == 1) {
         phase_shift_two_stage<N, V, true>(v, tw, buf, t, phi);
     } else {
@@ -83,7 +84,7 @@ __device__ __forceinline__ void step_down_adjoint(float2 (&v)[V], const Twiddles
 // Threads per block the kernel is compiled for: 32 points per thread need up to ~250 registers,
 // which leaves room for 8 warps per SM; 16 points per thread fit 16 warps at 128 registers.
 template <int V>
-constexpr int sweep_max_threads() { return V >= 32 ? 256 : 512; }
+constexpr int sweep_max_threads() { return V >= 24 ? 256 : 512; }
 
 // Bytes of dynamic shared memory for a block of `warps` warps whose items span at most `wslots`
 // frequencies (mirrored on the host by sweep_shape): per-item exchange buffers, the block's
@@ -91,7 +92,8 @@ constexpr int sweep_max_threads() { return V >= 32 ? 256 : 512; }
 // double-buffered per-warp image rows.
 template <int N, int V>
 constexpr size_t sweep_smem_bytes(int warps, int wslots, bool adjoint) {
-    return (size_t)warps * (32 / Plan<N, V>::T) * Plan<N, V>::BUF * sizeof(float2) +
+    return (size_t)Plan<N, V>::TAB * sizeof(float2) +
+           (size_t)warps * (32 / Plan<N, V>::T) * Plan<N, V>::BUF * sizeof(float2) +
            2 * ((size_t)wslots * 2 * N * sizeof(float2) + (size_t)N * sizeof(float)) +
            (adjoint ? (size_t)2 * warps * N * sizeof(float) : 0);
 }
@@ -102,7 +104,8 @@ __global__ void __launch_bounds__(sweep_max_threads<V>()) sweep_kernel(const Swe
     constexpr int T = P::T;
     constexpr int IPW = 32 / T;
     extern __shared__ float4 smem_f4[];
-    float2* smem = reinterpret_cast<float2*>(smem_f4);
+    float2* const tab = reinterpret_cast<float2*>(smem_f4);  // twiddle table (mixed-radix plans)
+    float2* smem = tab + P::TAB;
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -132,7 +135,8 @@ __global__ void __launch_bounds__(sweep_max_threads<V>()) sweep_kernel(const Swe
     float* img = mstage + 2 * N;                                        // [2][nwarps][N]
 
     Twiddles<N, V> tw;
-    init_twiddles<N, V>(tw, t);
+    init_twiddles<N, V>(tw, t, tab);
+    if constexpr (P::TW_SMEM) __syncthreads();
 
     float2* Sitem = a.S + ((size_t)slot * a.nw + iw) * (size_t)nz * N;
     float2 v[V];
@@ -164,13 +168,13 @@ __global__ void __launch_bounds__(sweep_max_threads<V>()) sweep_kernel(const Swe
         const int xs = ok ? __ldg(a.src_ix + shot) : -1;
         const float2 w = ok ? __ldg(a.wavelet + iw) : make_float2(0.f, 0.f);
 #pragma unroll
-        for (int r = 0; r < V; ++r) v[r] = (t + T * r == xs) ? w : make_float2(0.f, 0.f);
+        for (int r = 0; r < V; ++r) v[r] = (P::xpos(t, r) == xs) ? w : make_float2(0.f, 0.f);
         if (nz > 1) stage_rows(0, 0, false);
         for (int j = 0; j < nz; ++j) {
             if (ok) {
                 float2* row = Sitem + (size_t)j * N;
 #pragma unroll
-                for (int r = 0; r < V; ++r) __stcs(row + t + T * r, v[r]);
+                for (int r = 0; r < V; ++r) __stcs(row + P::xpos(t, r), v[r]);
             }
             if (j + 1 < nz) {
                 cp_async_wait_all();
@@ -200,7 +204,7 @@ __global__ void __launch_bounds__(sweep_max_threads<V>()) sweep_kernel(const Swe
             }
             __syncwarp();
 #pragma unroll
-            for (int r = 0; r < V; ++r) v[r] = buf[P::phys(t + T * r)];
+            for (int r = 0; r < V; ++r) v[r] = buf[P::phys(P::xpos(t, r))];
         }
         float* part = a.part + (size_t)blockIdx.x * nz * N;
         // s holds S_j; the row of depth j+1 is requested right after imaging depth j so that
@@ -221,7 +225,7 @@ __global__ void __launch_bounds__(sweep_max_threads<V>()) sweep_kernel(const Swe
             float* slab = img + ((size_t)(j & 1) * nwarps + warp) * N;
             if (sub == 0) {
 #pragma unroll
-                for (int r = 0; r < V; ++r) slab[t + T * r] = c[r];
+                for (int r = 0; r < V; ++r) slab[P::xpos(t, r)] = c[r];
             }
             if (j + 1 < nz) cp_async_wait_all();
             __syncthreads();  // image rows of depth j and staged rows of depth j are visible
@@ -262,7 +266,7 @@ __global__ void __launch_bounds__(sweep_max_threads<V>()) sweep_kernel(const Swe
             }
 #pragma unroll
             for (int r = 0; r < V; ++r) {
-                const float mm = mrow[t + T * r];
+                const float mm = mrow[P::xpos(t, r)];
                 v[r].x = fmaf(s[r].x, mm, v[r].x);
                 v[r].y = fmaf(s[r].y, mm, v[r].y);
             }
@@ -271,12 +275,12 @@ __global__ void __launch_bounds__(sweep_max_threads<V>()) sweep_kernel(const Swe
         if (a.rec_identity) {
             if (ok) {
 #pragma unroll
-                for (int r = 0; r < V; ++r) orow[t + T * r] = v[r];
+                for (int r = 0; r < V; ++r) orow[P::xpos(t, r)] = v[r];
             }
         } else {
             __syncwarp();
 #pragma unroll
-            for (int r = 0; r < V; ++r) buf[P::phys(t + T * r)] = v[r];
+            for (int r = 0; r < V; ++r) buf[P::phys(P::xpos(t, r))] = v[r];
             __syncwarp();
             if (ok) {
                 const int* rix = a.rec_ix + (size_t)shot * a.nrec;
@@ -391,7 +395,7 @@ struct Dispatch {
 
     // gradient kernel: 16 points per thread, so nx <= 512
     static constexpr int VG = gradient_points_per_thread();
-    static constexpr bool kGrad = N / VG <= 32;
+    static constexpr bool kGrad = (N & (N - 1)) == 0 && N >= VG && N / VG <= 32;
 
     static cudaError_t tables_grad(const TableArgs& a, cudaStream_t st) {
         if constexpr (kGrad) {
@@ -445,19 +449,22 @@ struct Dispatch {
 
 #define LSM_DEFINE_N(NN)                                                                          \
     namespace lsm {                                                                               \
-    cudaError_t launch_tables_##NN(const TableArgs& a, cudaStream_t st) {                         \
-        return Dispatch<NN>::tables(a, st);                                                       \
-    }                                                                                             \
-    cudaError_t launch_sweep_##NN(int mode, const SweepArgs& a, const SweepShape& sh,             \
-                                  cudaStream_t st) {                                              \
+    static cudaError_t tables_##NN(const TableArgs& a, cudaStream_t st) { return Dispatch<NN>::tables(a, st); } \
+    static cudaError_t sweep_##NN(int mode, const SweepArgs& a, const SweepShape& sh, cudaStream_t st) {      \
         return Dispatch<NN>::sweep_any(mode, a, sh, st);                                          \
     }                                                                                             \
-    int sweep_max_warps_##NN(int mode) { return Dispatch<NN>::max_warps(mode); }                  \
-    cudaError_t launch_tables_grad_##NN(const TableArgs& a, cudaStream_t st) {                    \
+    static int max_warps_##NN(int mode) { return Dispatch<NN>::max_warps(mode); }                 \
+    static size_t smem_##NN(int mode, int warps, int wslots) {                                    \
+        return sweep_smem_bytes<NN, Dispatch<NN>::V>(warps, wslots, mode == MODE_ADJOINT);        \
+    }                                                                                             \
+    static cudaError_t tables_grad_##NN(const TableArgs& a, cudaStream_t st) {                    \
         return Dispatch<NN>::tables_grad(a, st);                                                  \
     }                                                                                             \
-    cudaError_t launch_gradient_##NN(const GradArgs& a, const SweepShape& sh, cudaStream_t st) {  \
+    static cudaError_t gradient_##NN(const GradArgs& a, const SweepShape& sh, cudaStream_t st) {  \
         return Dispatch<NN>::gradient(a, sh, st);                                                 \
     }                                                                                             \
-    int gradient_max_warps_##NN() { return Dispatch<NN>::gradient_max_warps(); }                  \
+    static int gradient_max_warps_##NN() { return Dispatch<NN>::gradient_max_warps(); }           \
+    extern const NxOps kNxOps_##NN = {NN, Dispatch<NN>::V, Dispatch<NN>::kGrad, tables_##NN, sweep_##NN,        \
+                                      max_warps_##NN, smem_##NN, tables_grad_##NN, gradient_##NN,  \
+                                      gradient_max_warps_##NN};                                   \
     }

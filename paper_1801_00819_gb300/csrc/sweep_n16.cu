@@ -1,3 +1,3 @@
-// Sweep and coefficient-table kernels instantiated for nx = 16.
+// Sweep, gradient and coefficient-table kernels instantiated for nx = 16.
 #include "lsm_sweep.cuh"
 LSM_DEFINE_N(16)

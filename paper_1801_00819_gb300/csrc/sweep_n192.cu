@@ -1,0 +1,3 @@
+// Sweep, gradient and coefficient-table kernels instantiated for nx = 192.
+#include "lsm_sweep.cuh"
+LSM_DEFINE_N(192)

@@ -1,3 +1,3 @@
-// Sweep and coefficient-table kernels instantiated for nx = 32.
+// Sweep, gradient and coefficient-table kernels instantiated for nx = 32.
 #include "lsm_sweep.cuh"
 LSM_DEFINE_N(32)

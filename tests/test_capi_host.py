@@ -64,6 +64,7 @@ def test_profile_without_launches_is_empty(lib):
 def test_status_strings(lib):
     assert lib.lsm_status_string(0) == "ok"
     assert "nx" in lib.lsm_status_string(lib.LSM_ERR_UNSUPPORTED_NX)
+    assert "896" in lib.lsm_status_string(lib.LSM_ERR_UNSUPPORTED_NX)
     assert lib.lsm_status_string(-99) == "unknown status"
 
 
@@ -79,7 +80,8 @@ def test_validation_rejects_bad_arguments_before_any_launch(lib):
     g, geo, f = _holders(lib)
     fake = 1 << 20  # aligned fake addresses: validation must fail before they are used
     cases = [
-        (_holders(lib, nx=48), lib.LSM_ERR_UNSUPPORTED_NX),
+        (_holders(lib, nx=40), lib.LSM_ERR_UNSUPPORTED_NX),
+        (_holders(lib, nx=1536), lib.LSM_ERR_UNSUPPORTED_NX),
         (_holders(lib, nx=2048), lib.LSM_ERR_UNSUPPORTED_NX),
         (_holders(lib, src=np.array([0, 1, 64])), lib.LSM_ERR_ARG),
         (_holders(lib, rec=np.full((3, 5), 70)), lib.LSM_ERR_ARG),

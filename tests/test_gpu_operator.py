@@ -25,6 +25,15 @@ CASES = [
     (512, 10, 2, 3),
     (1024, 6, 1, 3),
     (64, 1, 3, 3),
+    # mixed-radix widths nx = q 2^a, q = 3, 5, 7
+    (48, 10, 2, 3),
+    (96, 8, 3, 4),
+    (112, 9, 3, 5),
+    (160, 7, 2, 3),
+    (384, 12, 2, 3),
+    (640, 8, 1, 2),
+    (768, 6, 1, 2),
+    (896, 6, 1, 2),
 ]
 
 

@@ -71,6 +71,17 @@ def test_tolerance_stopping_matches_oracle_iteration_counts(torch_cuda):
     assert rel_l2(m_gpu, m_ref) <= TOL
 
 
+@pytest.mark.parametrize("nx", [96, 224])
+def test_mixed_radix_width_sliding_solve(torch_cuda, nx):
+    sv = random_case(nx, 14, 5, 6, seed=nx)
+    op = oracle_operator(sv)
+    d, lam = _oracle_data(sv, op)
+    ds = device_survey(sv)
+    m_gpu, _ = _gpu_solve(torch_cuda, ds, d, lam, 3, 1, 0.0, 4)
+    m_ref, _ = O.rls_solve(op, d.astype(np.complex128), lam, 3, 1, 4)
+    assert rel_l2(m_gpu, m_ref) <= TOL
+
+
 def test_window_spanning_all_shots_is_full_lsm(torch_cuda):
     sv = random_case(128, 16, 4, 8, seed=81)
     op = oracle_operator(sv)
