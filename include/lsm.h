@@ -261,6 +261,38 @@ int rls_window_solve_ex(const lsm_grid* grid, const float* slowness, const lsm_f
                         void* workspace, size_t workspace_bytes, void* stream,
                         const lsm_solve_options* options);
 
+/*
+ * Several independent survey lines solved together (batching): each line is a complete
+ * rls_window_solve_ex problem with its own grid (any supported nx), data, window length K, slide,
+ * tolerance, image, statistics, workspace and stream.  The lines run concurrently, one host worker
+ * thread per line issuing that line's kernels on that line's stream, so small lines overlap on the
+ * GPU instead of running one after another.  Every line's result is bitwise identical to solving it
+ * alone with rls_window_solve_ex.  Streams must be distinct (and not the legacy default stream) for
+ * the lines to overlap.  Fields are the arguments of rls_window_solve_ex; `status` receives the
+ * line's return code.  Returns LSM_OK when every line succeeded, else the first failing line's
+ * code.  The calling thread's current device is used for every line.
+ */
+typedef struct {
+    lsm_grid grid;
+    const float* slowness;
+    lsm_freqs freqs;
+    lsm_geom geom;
+    const float* d;
+    double lambda;
+    int K, slide;
+    double cg_tol;
+    int max_iter;
+    float* m_inout;
+    lsm_window_stats* stats;
+    int stats_cap;
+    void* workspace;
+    size_t workspace_bytes;
+    void* stream;
+    int status;
+} lsm_line;
+
+int rls_multi_line_solve(lsm_line* lines, int nlines, const lsm_solve_options* options);
+
 /* Human-readable name of a status code (static string). */
 const char* lsm_status_string(int status);
 

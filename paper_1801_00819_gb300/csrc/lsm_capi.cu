@@ -14,6 +14,7 @@
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "../../include/lsm.h"
@@ -29,12 +30,14 @@ struct ProfRecord {
     int cls;
     cudaEvent_t begin, end;
 };
-static bool g_prof_on = false;
+static std::atomic<bool> g_prof_on{false};
+static std::mutex g_prof_mu;  // guards g_prof and g_event_pool
 static std::vector<ProfRecord> g_prof;
 static std::vector<cudaEvent_t> g_event_pool;
-static cudaEvent_t g_pending_begin = nullptr;
+static thread_local cudaEvent_t g_pending_begin = nullptr;
 
 static cudaEvent_t pooled_event() {
+    std::lock_guard<std::mutex> lock(g_prof_mu);
     if (!g_event_pool.empty()) {
         cudaEvent_t e = g_event_pool.back();
         g_event_pool.pop_back();
@@ -57,6 +60,7 @@ void profile_mark(int cls, cudaStream_t st, bool begin) {
         cudaEvent_t e = pooled_event();
         if (e && g_pending_begin) {
             cudaEventRecord(e, st);
+            std::lock_guard<std::mutex> lock(g_prof_mu);
             g_prof.push_back({cls, g_pending_begin, e});
         }
         g_pending_begin = nullptr;
@@ -710,6 +714,34 @@ int rls_window_solve(const lsm_grid* grid, const float* slowness, const lsm_freq
                                n_windows, m_inout, stats, stats_cap, workspace, workspace_bytes, stream, nullptr);
 }
 
+int rls_multi_line_solve(lsm_line* lines, int nlines, const lsm_solve_options* options) {
+    if (!lines || nlines < 1) return LSM_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return LSM_ERR_CUDA;
+    }
+    auto solve_line = [&](int i) {
+        lsm_line& l = lines[i];
+        if (cudaSetDevice(dev) != cudaSuccess) {
+            cudaGetLastError();
+            l.status = LSM_ERR_CUDA;
+            return;
+        }
+        l.status = rls_window_solve_ex(&l.grid, l.slowness, &l.freqs, &l.geom, l.d, l.lambda, l.K, l.slide,
+                                       l.cg_tol, l.max_iter, 0, 0, l.m_inout, l.stats, l.stats_cap, l.workspace,
+                                       l.workspace_bytes, l.stream, options);
+    };
+    std::vector<std::thread> workers;
+    workers.reserve((size_t)nlines);
+    for (int i = 1; i < nlines; ++i) workers.emplace_back(solve_line, i);
+    solve_line(0);
+    for (auto& w : workers) w.join();
+    for (int i = 0; i < nlines; ++i)
+        if (lines[i].status != LSM_OK) return lines[i].status;
+    return LSM_OK;
+}
+
 const char* lsm_status_string(int status) {
     switch (status) {
         case LSM_OK: return "ok";
@@ -728,6 +760,7 @@ const char* lsm_status_string(int status) {
 unsigned long long lsm_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 void lsm_profile_start(void) {
+    std::lock_guard<std::mutex> lock(g_prof_mu);
     for (auto& r : g_prof) {
         g_event_pool.push_back(r.begin);
         g_event_pool.push_back(r.end);
@@ -738,6 +771,7 @@ void lsm_profile_start(void) {
 
 int lsm_profile_stop(lsm_profile* out) {
     g_prof_on = false;
+    std::lock_guard<std::mutex> lock(g_prof_mu);
     if (out) std::memset(out, 0, sizeof(*out));
     int rc = LSM_OK;
     for (auto& r : g_prof) {

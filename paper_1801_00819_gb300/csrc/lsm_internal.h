@@ -3,8 +3,10 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 
 namespace lsm {
 
@@ -115,6 +117,24 @@ cudaError_t launch_tables_grad(const TableArgs& a, cudaStream_t st);
 cudaError_t launch_gradient(const GradArgs& a, const SweepShape& shape, cudaStream_t st);
 
 void count_launch(int n = 1);
+
+// Runs a set-up call once per device (thread safe): kernel attributes are per device.
+struct DeviceOnce {
+    std::mutex mu;
+    uint64_t done = 0;
+    template <class F>
+    cudaError_t run(F&& f) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        const uint64_t bit = dev < 64 ? (uint64_t)1 << dev : 0;
+        std::lock_guard<std::mutex> lock(mu);
+        if (bit && (done & bit)) return cudaSuccess;
+        e = f();
+        if (e == cudaSuccess) done |= bit;
+        return e;
+    }
+};
 
 // Per-launch event timing (lsm_profile_start / lsm_profile_stop).  Construct a ProfScope right
 // before a launch and destroy it right after; both ends record an event on the launch stream

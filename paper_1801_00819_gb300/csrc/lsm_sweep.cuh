@@ -353,13 +353,12 @@ struct Dispatch {
 
     template <int MODE>
     static cudaError_t sweep(const SweepArgs& a, const SweepShape& sh, cudaStream_t st) {
-        static bool configured = false;
-        if (!configured) {
-            cudaError_t e = cudaFuncSetAttribute(sweep_kernel<N, V, MODE>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-            if (e != cudaSuccess) return e;
-            configured = true;
-        }
+        static DeviceOnce configured;
+        cudaError_t e = configured.run([] {
+            return cudaFuncSetAttribute(sweep_kernel<N, V, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        227 * 1024);
+        });
+        if (e != cudaSuccess) return e;
         if (sh.smem != sweep_smem_bytes<N, V>(sh.warps, a.wslots, MODE == MODE_ADJOINT)) return cudaErrorInvalidValue;
         ProfScope prof_(MODE == MODE_SOURCE ? KC_SOURCE : MODE == MODE_ADJOINT ? KC_ADJOINT : KC_FORWARD, st);
         sweep_kernel<N, V, MODE><<<sh.blocks, sh.warps * 32, sh.smem, st>>>(a);
@@ -413,13 +412,12 @@ struct Dispatch {
 
     static cudaError_t gradient(const GradArgs& a, const SweepShape& sh, cudaStream_t st) {
         if constexpr (kGrad) {
-            static bool configured = false;
-            if (!configured) {
-                cudaError_t e = cudaFuncSetAttribute(gradient_kernel<N, VG>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-                if (e != cudaSuccess) return e;
-                configured = true;
-            }
+            static DeviceOnce configured;
+            cudaError_t e = configured.run([] {
+                return cudaFuncSetAttribute(gradient_kernel<N, VG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            227 * 1024);
+            });
+            if (e != cudaSuccess) return e;
             if (sh.smem != gradient_smem_bytes<N, VG>(sh.warps)) return cudaErrorInvalidValue;
             ProfScope prof_(KC_GRADIENT, st);
             gradient_kernel<N, VG><<<sh.blocks, sh.warps * 32, sh.smem, st>>>(a);

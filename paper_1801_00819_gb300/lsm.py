@@ -32,7 +32,7 @@ LSM_CHECKPOINT_EVERY = 16
 
 EXPORTED = ("lsm_workspace_bytes", "lsm_forward", "lsm_adjoint", "lsm_num_windows", "rls_window_solve",
             "lsm_status_string", "lsm_kernel_launches", "lsm_profile_start", "lsm_profile_stop",
-            "lsm_adjoint_static", "lsm_born_gradient", "rls_window_solve_ex")
+            "lsm_adjoint_static", "lsm_born_gradient", "rls_window_solve_ex", "rls_multi_line_solve")
 
 LSM_PRECOND_NONE = 0
 LSM_PRECOND_ILLUMINATION = 1
@@ -66,6 +66,10 @@ class lsm_solve_options(ctypes.Structure):
     _fields_ = [("preconditioner", ctypes.c_int), ("precond_eps", ctypes.c_double)]
 
 
+class lsm_line(ctypes.Structure):
+    pass  # fields assigned after lsm_window_stats
+
+
 class lsm_window_stats(ctypes.Structure):
     _fields_ = [("start", ctypes.c_int), ("iters", ctypes.c_int), ("rel_res0", ctypes.c_double),
                 ("rel_res", ctypes.c_double), ("n_forward", ctypes.c_int), ("n_adjoint", ctypes.c_int),
@@ -73,6 +77,14 @@ class lsm_window_stats(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+lsm_line._fields_ = [("grid", lsm_grid), ("slowness", ctypes.c_void_p), ("freqs", lsm_freqs), ("geom", lsm_geom),
+                     ("d", ctypes.c_void_p), ("lambda_", ctypes.c_double), ("K", ctypes.c_int),
+                     ("slide", ctypes.c_int), ("cg_tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                     ("m_inout", ctypes.c_void_p), ("stats", ctypes.POINTER(lsm_window_stats)),
+                     ("stats_cap", ctypes.c_int), ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
+                     ("stream", ctypes.c_void_p), ("status", ctypes.c_int)]
 
 
 class lsm_profile(ctypes.Structure):
@@ -121,6 +133,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                      ctypes.POINTER(lsm_window_stats), ctypes.c_int, P, ctypes.c_size_t, P]
     lib.rls_window_solve_ex.restype = ctypes.c_int
     lib.rls_window_solve_ex.argtypes = list(lib.rls_window_solve.argtypes) + [ctypes.POINTER(lsm_solve_options)]
+    lib.rls_multi_line_solve.restype = ctypes.c_int
+    lib.rls_multi_line_solve.argtypes = [ctypes.POINTER(lsm_line), ctypes.c_int, ctypes.POINTER(lsm_solve_options)]
     lib.lsm_status_string.restype = ctypes.c_char_p
     lib.lsm_status_string.argtypes = [ctypes.c_int]
     lib.lsm_kernel_launches.restype = ctypes.c_ulonglong
@@ -294,3 +308,39 @@ def rls_window_solve(grid, slowness, freqs, geom, d, lam, K, slide, cg_tol, max_
     if st != LSM_OK and (st != LSM_ERR_BREAKDOWN or raise_on_breakdown):
         raise LsmError(st, "rls_window_solve")
     return st, out
+
+
+class LineProblem:
+    """One survey line for rls_multi_line_solve: argument holders, device tensors and a stream."""
+
+    def __init__(self, grid, slowness, freqs, geom, d, lam, K, slide, cg_tol, max_iter, m_inout, workspace, stream):
+        self.grid, self.slowness, self.freqs, self.geom = grid, slowness, freqs, geom
+        self.d, self.lam, self.K, self.slide = d, lam, K, slide
+        self.cg_tol, self.max_iter, self.m_inout, self.workspace, self.stream = cg_tol, max_iter, m_inout, workspace, stream
+
+
+def rls_multi_line_solve(problems, preconditioner=None, precond_eps=1e-2, raise_on_error=True):
+    """Solve several LineProblems concurrently; returns ([status], [[stats dicts]])."""
+    lib = load_library()
+    n = len(problems)
+    arr = (lsm_line * n)()
+    keep = []
+    for i, pr in enumerate(problems):
+        nwin = max(lib.lsm_num_windows(int(pr.geom.c.ns), int(pr.K), int(pr.slide)), 1)
+        stats = (lsm_window_stats * nwin)()
+        keep.append((stats, nwin))
+        arr[i] = lsm_line(pr.grid.c, _ptr(pr.slowness), pr.freqs.c, pr.geom.c, _ptr(pr.d), float(pr.lam), int(pr.K),
+                          int(pr.slide), float(pr.cg_tol), int(pr.max_iter), _ptr(pr.m_inout),
+                          ctypes.cast(stats, ctypes.POINTER(lsm_window_stats)), nwin, _ptr(pr.workspace),
+                          _nbytes(pr.workspace), _stream(pr.stream), 0)
+    opts = None
+    if preconditioner == "illumination":
+        opts = ctypes.byref(lsm_solve_options(LSM_PRECOND_ILLUMINATION, float(precond_eps)))
+    elif preconditioner is not None:
+        raise ValueError(f"unknown preconditioner {preconditioner!r}")
+    st = lib.rls_multi_line_solve(arr, n, opts)
+    statuses = [int(arr[i].status) for i in range(n)]
+    out = [[keep[i][0][k].as_dict() for k in range(keep[i][1])] for i in range(n)]
+    if st != LSM_OK and raise_on_error:
+        raise LsmError(st, "rls_multi_line_solve")
+    return statuses, out

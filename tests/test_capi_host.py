@@ -34,7 +34,7 @@ def test_header_declares_expected_entry_points():
     assert _declared_functions() == sorted(["lsm_workspace_bytes", "lsm_forward", "lsm_adjoint", "lsm_num_windows",
                                             "rls_window_solve", "lsm_status_string", "lsm_kernel_launches",
                                             "lsm_profile_start", "lsm_profile_stop", "lsm_adjoint_static",
-                                            "lsm_born_gradient", "rls_window_solve_ex"])
+                                            "lsm_born_gradient", "rls_window_solve_ex", "rls_multi_line_solve"])
 
 
 def test_library_exports_every_declared_symbol(lib):
