@@ -54,7 +54,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("gb300", "reference"), default="gb300")
-    ap.add_argument("--workload", choices=("realistic", "tiny"), default="realistic")
+    ap.add_argument("--workload", choices=("realistic", "tiny", "batching"), default="realistic",
+                    help="batching: eight survey lines of mixed widths solved concurrently vs one after another")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
@@ -456,10 +457,102 @@ def reference_arm(args):
     print(json.dumps(out), flush=True)
 
 
+def batching_arm(args):
+    """Eight independent survey lines (nx 256..1024 incl. 384, 640, 768, 896; K 4..32), every window
+    to 1e-3: one step solves all lines concurrently (rls_multi_line_solve, a stream per line); the
+    comparison loops the plain per-line solve over the same lines."""
+    import numpy as np
+    import torch
+
+    import paper_1801_00819_gb300 as L
+    from paper_1801_00819_gb300 import build as B
+    from paper_1801_00819_gb300 import lsm
+    from paper_1801_00819_gb300.device import to_device, workspace
+    from synth import config_batching_lines
+
+    torch.cuda.set_device(0)
+    B.build()
+    lines = []
+    for sv in config_batching_lines():
+        ds = to_device(sv.nx, sv.nz, sv.dx, sv.dz, sv.slowness, sv.src_ix, sv.rec_ix, sv.freqs, sv.wavelet)
+        K = sv.window
+        m_true = torch.as_tensor(np.asarray(sv.reflectivity, dtype=np.float32), device="cuda")
+        d = torch.empty((sv.ns, sv.nw, ds.nrec), dtype=torch.complex64, device="cuda")
+        ws_f = workspace(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, K, L.LSM_OP_ADJOINT))
+        for s0 in range(0, sv.ns, K):
+            n = min(K, sv.ns - s0)
+            L.lsm_forward(ds.grid, ds.slowness, ds.freqs, ds.geom, m_true, d[s0:s0 + n], s0, n, ws_f)
+        rms = float(torch.sqrt(torch.mean(torch.abs(d) ** 2)))
+        d += sv.noise_pct * rms * torch.as_tensor(sv.noise().astype(np.complex64), device="cuda")
+        adj = torch.zeros((sv.nz, sv.nx), dtype=torch.float32, device="cuda")
+        for s0 in range(0, sv.ns, K):
+            n = min(K, sv.ns - s0)
+            L.lsm_adjoint(ds.grid, ds.slowness, ds.freqs, ds.geom, d[s0:s0 + n], adj, s0, n, ws_f, accumulate=True)
+        lam = 1e-3 * float(adj.abs().max())
+        del ws_f
+        ws = workspace(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, K, L.LSM_OP_SOLVE))
+        m = torch.zeros((sv.nz, sv.nx), dtype=torch.float32, device="cuda")
+        lines.append(lsm.LineProblem(ds.grid, ds.slowness, ds.freqs, ds.geom, d, lam, K, sv.slide, sv.cg_tol,
+                                     sv.cg_iters, m, ws, torch.cuda.Stream()))
+    torch.cuda.synchronize()
+
+    def units_of(stats_per_line):
+        total = 0
+        for pr, st in zip(lines, stats_per_line):
+            per_pass = pr.K * pr.freqs.c.nw * pr.grid.c.nz
+            total += sum((w["n_forward"] + w["n_adjoint"]) / 2 * per_pass for w in st)
+        return total
+
+    def sequential():
+        out = []
+        for pr in lines:
+            pr.m_inout.zero_()
+            _, st = L.rls_window_solve(pr.grid, pr.slowness, pr.freqs, pr.geom, pr.d, pr.lam, pr.K, pr.slide,
+                                       pr.cg_tol, pr.max_iter, pr.m_inout, pr.workspace)
+            out.append(st)
+        return out
+
+    def concurrent():
+        for pr in lines:
+            pr.m_inout.zero_()
+        torch.cuda.synchronize()
+        _, st = lsm.rls_multi_line_solve(lines)
+        return st
+
+    for _ in range(max(args.warmup, 1)):
+        concurrent()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st_conc = [concurrent() for _ in range(args.steps)][-1]
+    torch.cuda.synchronize()
+    t_conc = (time.perf_counter() - t0) / args.steps
+    t0 = time.perf_counter()
+    st_seq = sequential()
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    units = units_of(st_conc)
+    out = {"metric": "shot*omega*depth steps/s for A+A^T (eight-line batched window-RLS solve to 1e-3)",
+           "value": round(units / t_conc, 1), "unit": "units/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(1e3 * t_conc, 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+           "config": {"workload": "batching: 8 lines nx 256-1024 (incl. 384, 640, 768, 896), nz = nx/2, shots 64-200, "
+                                  "freqs 96-192, K 4-32, slide ceil(K/2), CG to 1e-3",
+                      "lines": [{"nx": pr.grid.c.nx, "shots": pr.geom.c.ns, "freqs": pr.freqs.c.nw, "K": pr.K,
+                                 "slide": pr.slide,
+                                 "iters": int(sum(w["iters"] for w in st))} for pr, st in zip(lines, st_conc)]},
+           "timing": "host wall clock around each whole solve, GPU synchronised on both sides",
+           "sequential_ms": round(1e3 * t_seq, 1), "concurrent_ms": round(1e3 * t_conc, 1),
+           "speedup_concurrent_vs_sequential": round(t_seq / t_conc, 3),
+           "sequential_units_per_s": round(units_of(st_seq) / t_seq, 1)}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload == "batching":
+        batching_arm(args)
     else:
         gpu_arm(args)
 
