@@ -248,10 +248,35 @@ int lsm_profile_stop(lsm_profile* out);
  */
 #define LSM_PRECOND_NONE 0
 #define LSM_PRECOND_ILLUMINATION 1
+/*
+ *   transform: the lateral transforms of every depth step.
+ *     LSM_TRANSFORM_FFT (0): register-resident FP32 FFTs (every supported nx).
+ *     LSM_TRANSFORM_DFT_BF16X3, _FP16X3, _BF16X1: the transforms as DFT-matrix products on the
+ *     tensor cores (four-step 16 x nx/16 factorisation, mma.sync with FP32 accumulation), with every
+ *     FP32 operand split as hi + lo in bf16 (three products), in fp16 with the lo part scaled by
+ *     2^11 (three products), or bf16 hi only (one product).  These are precision variants for
+ *     nx = 128, 256, 512 with receivers at every column (rec_ix NULL); LSM_ERR_UNSUPPORTED_NX or
+ *     LSM_ERR_ARG otherwise.
+ */
+#define LSM_TRANSFORM_FFT 0
+#define LSM_TRANSFORM_DFT_BF16X3 1
+#define LSM_TRANSFORM_DFT_FP16X3 2
+#define LSM_TRANSFORM_DFT_BF16X1 3
 typedef struct {
     int preconditioner;
     double precond_eps;
+    int transform;
 } lsm_solve_options;
+
+/* lsm_forward / lsm_adjoint with solver options (only `transform` applies; NULL: FP32 FFTs). */
+int lsm_forward_ex(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs,
+                   const lsm_geom* geom, const float* m, float* d_out, int shot0, int nshots,
+                   void* workspace, size_t workspace_bytes, void* stream,
+                   const lsm_solve_options* options);
+int lsm_adjoint_ex(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs,
+                   const lsm_geom* geom, const float* d, float* m_out, int shot0, int nshots,
+                   int accumulate, void* workspace, size_t workspace_bytes, void* stream,
+                   const lsm_solve_options* options);
 
 /* rls_window_solve with options (options == NULL: plain CG, identical to rls_window_solve). */
 int rls_window_solve_ex(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs,

@@ -132,6 +132,20 @@ SweepShape gradient_shape(int nx, int nshots, int nw, int num_sms) {
     return s;
 }
 
+// tensor-core variants: one item per warp, up to 8 warps per block
+SweepShape tc_shape(int nx, int mode, int nshots, int nw, int num_sms) {
+    const NxOps* ops = nx_ops(nx);
+    const int nitems = nshots * nw;
+    int warps = (nitems + num_sms - 1) / num_sms;
+    warps = std::max(1, std::min(warps, 8));
+    SweepShape s;
+    s.warps = warps;
+    s.blocks = (nitems + warps - 1) / warps;
+    s.wslots = 0;
+    s.smem = ops->tc_smem(mode, warps);
+    return s;
+}
+
 cudaError_t launch_tables_grad(const TableArgs& a, cudaStream_t st) { return nx_ops(a.nx)->tables_grad(a, st); }
 cudaError_t launch_gradient(const GradArgs& a, const SweepShape& sh, cudaStream_t st) {
     return nx_ops(a.nx)->gradient(a, sh, st);
@@ -217,6 +231,8 @@ Layout make_layout(const lsm_grid* g, const lsm_geom* geo, const lsm_freqs* f, i
     if (op == LSM_OP_ADJOINT || op == LSM_OP_SOLVE) {
         const SweepShape sh = sweep_shape(g->nx, MODE_ADJOINT, nshots, (int)nw, num_sms);
         L.nparts = sh.blocks;
+        if (nx_ops(g->nx)->has_tc)
+            L.nparts = std::max(L.nparts, tc_shape(g->nx, MODE_ADJOINT, nshots, (int)nw, num_sms).blocks);
     } else if (op == LSM_OP_GRADIENT) {
         L.nparts = gradient_shape(g->nx, nshots, (int)nw, num_sms).blocks;
     }
@@ -285,8 +301,10 @@ int validate_common(const lsm_grid* g, const lsm_freqs* f, const lsm_geom* geo) 
     } while (0)
 
 // Upload geometry / frequencies and build s_ref and the coefficient tables in the workspace.
+enum TableOrder { TABLES_SWEEP = 0, TABLES_GRADIENT = 1, TABLES_NATURAL = 2 };
+
 int prepare(const lsm_grid* g, const float* slowness, const lsm_freqs* f, const lsm_geom* geo, const Layout& L,
-            char* ws, cudaStream_t st, const double* sref_override = nullptr, bool gradient_tables = false) {
+            char* ws, cudaStream_t st, const double* sref_override = nullptr, int table_order = TABLES_SWEEP) {
     const size_t nw = (size_t)f->nw;
     // one staging copy of all host arrays (layout identical to the workspace prefix)
     const size_t head = L.sref;
@@ -319,7 +337,12 @@ int prepare(const lsm_grid* g, const float* slowness, const lsm_freqs* f, const 
     ta.freq_hz = reinterpret_cast<const float*>(ws + L.freq);
     ta.phi = reinterpret_cast<float2*>(ws + L.phi);
     ta.dss = reinterpret_cast<float2*>(ws + L.dss);
-    LSM_CHECK(gradient_tables ? launch_tables_grad(ta, st) : launch_tables(ta, st));
+    if (table_order == TABLES_GRADIENT)
+        LSM_CHECK(launch_tables_grad(ta, st));
+    else if (table_order == TABLES_NATURAL)
+        LSM_CHECK(nx_ops(g->nx)->tables_natural(ta, st));
+    else
+        LSM_CHECK(launch_tables(ta, st));
     return LSM_OK;
 }
 
@@ -341,34 +364,54 @@ SweepArgs base_args(const lsm_grid* g, const lsm_freqs* f, const lsm_geom* geo, 
     return a;
 }
 
-// Source wavefields of shots [shot0, shot0 + n) into their ring slots.
-cudaError_t run_source(SweepArgs a, int shot0, int n, int num_sms, cudaStream_t st) {
-    a.shot0 = shot0;
-    a.nshots = n;
-    const SweepShape sh = sweep_shape(a.nx, MODE_SOURCE, n, a.nw, num_sms);
-    a.wslots = sh.wslots;
-    return launch_sweep(MODE_SOURCE, a, sh, st);
+// transform: 0 = register FFT (FP32); otherwise the tensor-core precision variant (TcPrecision)
+cudaError_t launch_any(int mode, int transform, SweepArgs& a, int n, int num_sms, cudaStream_t st, int* blocks) {
+    if (transform == 0) {
+        const SweepShape sh = sweep_shape(a.nx, mode, n, a.nw, num_sms);
+        a.wslots = sh.wslots;
+        if (blocks) *blocks = sh.blocks;
+        return launch_sweep(mode, a, sh, st);
+    }
+    const SweepShape sh = tc_shape(a.nx, mode, n, a.nw, num_sms);
+    if (blocks) *blocks = sh.blocks;
+    return nx_ops(a.nx)->tc_sweep(mode, transform, a, sh, st);
 }
 
-cudaError_t run_forward(SweepArgs a, int shot0, int n, const float* m, float2* dout, int num_sms, cudaStream_t st) {
+// Source wavefields of shots [shot0, shot0 + n) into their ring slots.
+cudaError_t run_source(SweepArgs a, int shot0, int n, int num_sms, cudaStream_t st, int transform = 0) {
+    a.shot0 = shot0;
+    a.nshots = n;
+    return launch_any(MODE_SOURCE, transform, a, n, num_sms, st, nullptr);
+}
+
+cudaError_t run_forward(SweepArgs a, int shot0, int n, const float* m, float2* dout, int num_sms, cudaStream_t st,
+                        int transform = 0) {
     a.shot0 = shot0;
     a.nshots = n;
     a.m = m;
     a.dout = dout;
-    const SweepShape sh = sweep_shape(a.nx, MODE_FORWARD, n, a.nw, num_sms);
-    a.wslots = sh.wslots;
-    return launch_sweep(MODE_FORWARD, a, sh, st);
+    return launch_any(MODE_FORWARD, transform, a, n, num_sms, st, nullptr);
 }
 
 // Adjoint sweep into the block partial images; returns the number of partials in *nparts.
-cudaError_t run_adjoint(SweepArgs a, int shot0, int n, const float2* din, int num_sms, cudaStream_t st, int* nparts) {
+cudaError_t run_adjoint(SweepArgs a, int shot0, int n, const float2* din, int num_sms, cudaStream_t st, int* nparts,
+                        int transform = 0) {
     a.shot0 = shot0;
     a.nshots = n;
     a.din = din;
-    const SweepShape sh = sweep_shape(a.nx, MODE_ADJOINT, n, a.nw, num_sms);
-    a.wslots = sh.wslots;
-    *nparts = sh.blocks;
-    return launch_sweep(MODE_ADJOINT, a, sh, st);
+    return launch_any(MODE_ADJOINT, transform, a, n, num_sms, st, nparts);
+}
+
+// The lateral transform selected by the options of an _ex entry point, and its requirements.
+int transform_of(const lsm_solve_options* o, const lsm_grid* g, const lsm_geom* geo, int* transform) {
+    *transform = o ? o->transform : LSM_TRANSFORM_FFT;
+    if (*transform == LSM_TRANSFORM_FFT) return LSM_OK;
+    if (*transform != LSM_TRANSFORM_DFT_BF16X3 && *transform != LSM_TRANSFORM_DFT_FP16X3 &&
+        *transform != LSM_TRANSFORM_DFT_BF16X1)
+        return LSM_ERR_ARG;
+    if (!nx_ops(g->nx)->has_tc) return LSM_ERR_UNSUPPORTED_NX;
+    if (geo->rec_ix) return LSM_ERR_ARG;  // the tensor-core variants take receivers at every column
+    return LSM_OK;
 }
 
 }  // namespace
@@ -385,7 +428,17 @@ size_t lsm_workspace_bytes(const lsm_grid* grid, const lsm_geom* geom, const lsm
 int lsm_forward(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs, const lsm_geom* geom,
                 const float* m, float* d_out, int shot0, int nshots, void* workspace, size_t workspace_bytes,
                 void* stream) {
+    return lsm_forward_ex(grid, slowness, freqs, geom, m, d_out, shot0, nshots, workspace, workspace_bytes, stream,
+                          nullptr);
+}
+
+int lsm_forward_ex(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs, const lsm_geom* geom,
+                   const float* m, float* d_out, int shot0, int nshots, void* workspace, size_t workspace_bytes,
+                   void* stream, const lsm_solve_options* options) {
     int rc = validate_common(grid, freqs, geom);
+    if (rc != LSM_OK) return rc;
+    int transform = 0;
+    rc = transform_of(options, grid, geom, &transform);
     if (rc != LSM_OK) return rc;
     if (!aligned16(slowness) || !aligned16(m) || !aligned16(d_out) || !aligned16(workspace)) return LSM_ERR_ARG;
     if (shot0 < 0 || nshots < 1 || shot0 > geom->ns - nshots) return LSM_ERR_ARG;
@@ -394,18 +447,28 @@ int lsm_forward(const lsm_grid* grid, const float* slowness, const lsm_freqs* fr
     if (workspace_bytes < L.total) return LSM_ERR_WORKSPACE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     char* ws = static_cast<char*>(workspace);
-    rc = prepare(grid, slowness, freqs, geom, L, ws, st);
+    rc = prepare(grid, slowness, freqs, geom, L, ws, st, nullptr, transform ? TABLES_NATURAL : TABLES_SWEEP);
     if (rc != LSM_OK) return rc;
     SweepArgs a = base_args(grid, freqs, geom, L, ws);
-    LSM_CHECK(run_source(a, shot0, nshots, nsm, st));
-    LSM_CHECK(run_forward(a, shot0, nshots, m, reinterpret_cast<float2*>(d_out), nsm, st));
+    LSM_CHECK(run_source(a, shot0, nshots, nsm, st, transform));
+    LSM_CHECK(run_forward(a, shot0, nshots, m, reinterpret_cast<float2*>(d_out), nsm, st, transform));
     return LSM_OK;
 }
 
 int lsm_adjoint(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs, const lsm_geom* geom,
                 const float* d, float* m_out, int shot0, int nshots, int accumulate, void* workspace,
                 size_t workspace_bytes, void* stream) {
+    return lsm_adjoint_ex(grid, slowness, freqs, geom, d, m_out, shot0, nshots, accumulate, workspace,
+                          workspace_bytes, stream, nullptr);
+}
+
+int lsm_adjoint_ex(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs, const lsm_geom* geom,
+                   const float* d, float* m_out, int shot0, int nshots, int accumulate, void* workspace,
+                   size_t workspace_bytes, void* stream, const lsm_solve_options* options) {
     int rc = validate_common(grid, freqs, geom);
+    if (rc != LSM_OK) return rc;
+    int transform = 0;
+    rc = transform_of(options, grid, geom, &transform);
     if (rc != LSM_OK) return rc;
     if (!aligned16(slowness) || !aligned16(d) || !aligned16(m_out) || !aligned16(workspace)) return LSM_ERR_ARG;
     if (shot0 < 0 || nshots < 1 || shot0 > geom->ns - nshots) return LSM_ERR_ARG;
@@ -414,12 +477,12 @@ int lsm_adjoint(const lsm_grid* grid, const float* slowness, const lsm_freqs* fr
     if (workspace_bytes < L.total) return LSM_ERR_WORKSPACE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     char* ws = static_cast<char*>(workspace);
-    rc = prepare(grid, slowness, freqs, geom, L, ws, st);
+    rc = prepare(grid, slowness, freqs, geom, L, ws, st, nullptr, transform ? TABLES_NATURAL : TABLES_SWEEP);
     if (rc != LSM_OK) return rc;
     SweepArgs a = base_args(grid, freqs, geom, L, ws);
-    LSM_CHECK(run_source(a, shot0, nshots, nsm, st));
+    LSM_CHECK(run_source(a, shot0, nshots, nsm, st, transform));
     int nparts = 0;
-    LSM_CHECK(run_adjoint(a, shot0, nshots, reinterpret_cast<const float2*>(d), nsm, st, &nparts));
+    LSM_CHECK(run_adjoint(a, shot0, nshots, reinterpret_cast<const float2*>(d), nsm, st, &nparts, transform));
     LSM_CHECK(cg_reduce_image(a.part, nparts, grid->nx * grid->nz, nullptr, 0.f, accumulate ? 1 : 0, m_out,
                               reinterpret_cast<double*>(ws + L.ss), st));
     return LSM_OK;
@@ -534,14 +597,14 @@ int lsm_born_gradient(const lsm_grid* grid, const float* slowness, const double*
     char* ws = static_cast<char*>(workspace);
     if (!g) {
         // modelling only: the sweep kernels with the given reference slowness
-        rc = prepare(grid, slowness, freqs, geom, L, ws, st, sref, false);
+        rc = prepare(grid, slowness, freqs, geom, L, ws, st, sref, TABLES_SWEEP);
         if (rc != LSM_OK) return rc;
         SweepArgs a = base_args(grid, freqs, geom, L, ws);
         LSM_CHECK(run_source(a, shot0, nshots, nsm, st));
         LSM_CHECK(run_forward(a, shot0, nshots, m, reinterpret_cast<float2*>(d_out), nsm, st));
         return LSM_OK;
     }
-    rc = prepare(grid, slowness, freqs, geom, L, ws, st, sref, true);
+    rc = prepare(grid, slowness, freqs, geom, L, ws, st, sref, TABLES_GRADIENT);
     if (rc != LSM_OK) return rc;
     GradArgs ga{};
     ga.nx = grid->nx;
@@ -600,6 +663,9 @@ int rls_window_solve_ex(const lsm_grid* grid, const float* slowness, const lsm_f
     const double precond_eps = options ? options->precond_eps : 0.0;
     if (precond != LSM_PRECOND_NONE && precond != LSM_PRECOND_ILLUMINATION) return LSM_ERR_ARG;
     if (precond == LSM_PRECOND_ILLUMINATION && !(precond_eps > 0.0 && std::isfinite(precond_eps))) return LSM_ERR_ARG;
+    int transform = 0;
+    rc = transform_of(options, grid, geom, &transform);
+    if (rc != LSM_OK) return rc;
     const int ns = geom->ns;
     const int nwin = lsm_num_windows(ns, K, slide);
     if (nwin == 0) return LSM_ERR_ARG;
@@ -613,7 +679,7 @@ int rls_window_solve_ex(const lsm_grid* grid, const float* slowness, const lsm_f
 
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     char* ws = static_cast<char*>(workspace);
-    rc = prepare(grid, slowness, freqs, geom, L, ws, st);
+    rc = prepare(grid, slowness, freqs, geom, L, ws, st, nullptr, transform ? TABLES_NATURAL : TABLES_SWEEP);
     if (rc != LSM_OK) return rc;
     SweepArgs a = base_args(grid, freqs, geom, L, ws);
 
@@ -640,7 +706,7 @@ int rls_window_solve_ex(const lsm_grid* grid, const float* slowness, const lsm_f
         const float2* dk = dall + (size_t)start * shot_stride;
         // rank-`slide` update: source wavefields of the shots that enter the window
         const int new_from = prev_start < 0 ? start : std::max(start, prev_start + K);
-        if (new_from < start + K) LSM_CHECK(run_source(a, new_from, start + K - new_from, nsm, st));
+        if (new_from < start + K) LSM_CHECK(run_source(a, new_from, start + K - new_from, nsm, st, transform));
         prev_start = start;
         if (minv) {
             // the ring now holds exactly this window's source wavefields
@@ -653,14 +719,14 @@ int rls_window_solve_ex(const lsm_grid* grid, const float* slowness, const lsm_f
         int nparts = 0;
         LSM_CHECK(cg_zero_state(state, st));
         // b = A_k^T d_k  ->  ||b||^2
-        LSM_CHECK(run_adjoint(a, start, K, dk, nsm, st, &nparts));
+        LSM_CHECK(run_adjoint(a, start, K, dk, nsm, st, &nparts, transform));
         LSM_CHECK(cg_reduce_image(a.part, nparts, n, nullptr, 0.f, 0, s, ss, st));
         LSM_CHECK(cg_store_sum(ss, state, st));
         // r = d_k - A_k m
-        LSM_CHECK(run_forward(a, start, K, m_inout, q, nsm, st));
+        LSM_CHECK(run_forward(a, start, K, m_inout, q, nsm, st, transform));
         LSM_CHECK(cg_residual(dk, q, r, nd, st));
         // s = A_k^T r - lambda m ; p = s ; gamma = ||s||^2
-        LSM_CHECK(run_adjoint(a, start, K, r, nsm, st, &nparts));
+        LSM_CHECK(run_adjoint(a, start, K, r, nsm, st, &nparts, transform));
         LSM_CHECK(cg_reduce_image(a.part, nparts, n, m_inout, lamf, 0, s, ss, st, minv, sz));
         int gi = 0;
         LSM_CHECK(cg_update_p(p, s, n, ss, 1, state, 1, gi, pp, st, minv, sz));
@@ -674,11 +740,11 @@ int rls_window_solve_ex(const lsm_grid* grid, const float* slowness, const lsm_f
         bool broke = hs.breakdown != 0;
         while (!broke && it < max_iter && !(rel <= cg_tol)) {
             // q = A_k p ; alpha ; m += alpha p ; r -= alpha q
-            LSM_CHECK(run_forward(a, start, K, p, q, nsm, st));
+            LSM_CHECK(run_forward(a, start, K, p, q, nsm, st, transform));
             LSM_CHECK(cg_norm2_c64(q, nd, qq, st));
             LSM_CHECK(cg_update_mr(m_inout, p, n, r, q, nd, qq, pp, lambda, state, gi, st));
             // s = A_k^T r - lambda m ; beta ; p = s + beta p
-            LSM_CHECK(run_adjoint(a, start, K, r, nsm, st, &nparts));
+            LSM_CHECK(run_adjoint(a, start, K, r, nsm, st, &nparts, transform));
             LSM_CHECK(cg_reduce_image(a.part, nparts, n, m_inout, lamf, 0, s, ss, st, minv, sz));
             LSM_CHECK(cg_update_p(p, s, n, ss, 0, state, gi, gi ^ 1, pp, st, minv, sz));
             gi ^= 1;

@@ -91,6 +91,10 @@ struct NxOps {
     cudaError_t (*tables_grad)(const TableArgs& a, cudaStream_t st);
     cudaError_t (*gradient)(const GradArgs& a, const SweepShape& shape, cudaStream_t st);
     int (*gradient_max_warps)();
+    bool has_tc;                  // tensor-core transform variants exist for this nx
+    cudaError_t (*tables_natural)(const TableArgs& a, cudaStream_t st);
+    cudaError_t (*tc_sweep)(int mode, int prec, const SweepArgs& a, const SweepShape& shape, cudaStream_t st);
+    size_t (*tc_smem)(int mode, int warps);
 };
 // The operations for nx, or nullptr when nx is not supported.
 const NxOps* nx_ops(int nx);

@@ -24,6 +24,7 @@
 #include "lsm_fft.cuh"
 #include "lsm_grad.cuh"
 #include "lsm_internal.h"
+#include "lsm_tc.cuh"
 
 namespace lsm {
 
@@ -293,7 +294,7 @@ __global__ void __launch_bounds__(sweep_max_threads<V>()) sweep_kernel(const Swe
 // Coefficient tables for every (frequency, depth row): Phi_j / nx in the FFT output order of
 // Plan<N, V>, and D_j in natural order.  Phase arguments are formed in float64 and reduced to
 // [-pi, pi] before the float32 sin / cos.
-template <int N, int V>
+template <int N, int V, bool NATURAL = false>
 __global__ void tables_kernel(const TableArgs a) {
     using P = Plan<N, V>;
     const size_t total = (size_t)a.nw * a.nz * N;
@@ -308,7 +309,7 @@ __global__ void tables_kernel(const TableArgs a) {
         // phase shift at the frequency held by table slot p = r T + t
         {
             const int t = p % P::T, r = p / P::T;
-            const int k = P::freq_of_position(P::position_of(t, r));
+            const int k = NATURAL ? p : P::freq_of_position(P::position_of(t, r));
             const int kk = k < N / 2 ? k : k - N;
             const double kx = fabs(2.0 * kPi * (double)kk / ((double)N * (double)a.dx));
             const double ws = omega * sref;
@@ -392,6 +393,61 @@ struct Dispatch {
         }
     }
 
+    // tensor-core transform variants (nx = 128, 256, 512)
+    static constexpr bool kTc = N == 128 || N == 256 || N == 512;
+
+    static cudaError_t tables_natural(const TableArgs& a, cudaStream_t st) {
+        const size_t total = (size_t)a.nw * a.nz * N;
+        size_t blocks = (total + 255) / 256;
+        if (blocks > 65535u * 8u) blocks = 65535u * 8u;
+        ProfScope prof_(KC_TABLES, st);
+        tables_kernel<N, V, true><<<(unsigned)blocks, 256, 0, st>>>(a);
+        count_launch();
+        return cudaGetLastError();
+    }
+
+    template <int PREC, int MODE>
+    static cudaError_t tc_launch(const SweepArgs& a, const SweepShape& sh, cudaStream_t st) {
+        if constexpr (kTc) {
+            static DeviceOnce configured;
+            cudaError_t e = configured.run([] {
+                return cudaFuncSetAttribute(tc_sweep_kernel<N, PREC, MODE>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+            });
+            if (e != cudaSuccess) return e;
+            if (sh.smem != tc_smem_bytes<N>(sh.warps, MODE == MODE_ADJOINT)) return cudaErrorInvalidValue;
+            ProfScope prof_(MODE == MODE_SOURCE ? KC_SOURCE : MODE == MODE_ADJOINT ? KC_ADJOINT : KC_FORWARD, st);
+            tc_sweep_kernel<N, PREC, MODE><<<sh.blocks, sh.warps * 32, sh.smem, st>>>(a);
+            count_launch();
+            return cudaGetLastError();
+        } else {
+            return cudaErrorNotSupported;
+        }
+    }
+
+    template <int PREC>
+    static cudaError_t tc_mode(int mode, const SweepArgs& a, const SweepShape& sh, cudaStream_t st) {
+        switch (mode) {
+            case MODE_SOURCE: return tc_launch<PREC, MODE_SOURCE>(a, sh, st);
+            case MODE_ADJOINT: return tc_launch<PREC, MODE_ADJOINT>(a, sh, st);
+            default: return tc_launch<PREC, MODE_FORWARD>(a, sh, st);
+        }
+    }
+
+    static cudaError_t tc_sweep(int mode, int prec, const SweepArgs& a, const SweepShape& sh, cudaStream_t st) {
+        switch (prec) {
+            case PREC_BF16X3: return tc_mode<PREC_BF16X3>(mode, a, sh, st);
+            case PREC_FP16X3: return tc_mode<PREC_FP16X3>(mode, a, sh, st);
+            case PREC_BF16X1: return tc_mode<PREC_BF16X1>(mode, a, sh, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+
+    static size_t tc_smem(int mode, int warps) {
+        if constexpr (kTc) return tc_smem_bytes<N>(warps, mode == MODE_ADJOINT);
+        return 0;
+    }
+
     // gradient kernel: 16 points per thread, so nx <= 512
     static constexpr int VG = gradient_points_per_thread();
     static constexpr bool kGrad = (N & (N - 1)) == 0 && N >= VG && N / VG <= 32;
@@ -462,7 +518,16 @@ struct Dispatch {
         return Dispatch<NN>::gradient(a, sh, st);                                                 \
     }                                                                                             \
     static int gradient_max_warps_##NN() { return Dispatch<NN>::gradient_max_warps(); }           \
+    static cudaError_t tables_natural_##NN(const TableArgs& a, cudaStream_t st) {                 \
+        return Dispatch<NN>::tables_natural(a, st);                                               \
+    }                                                                                             \
+    static cudaError_t tc_sweep_##NN(int mode, int prec, const SweepArgs& a, const SweepShape& sh,  \
+                                     cudaStream_t st) {                                           \
+        return Dispatch<NN>::tc_sweep(mode, prec, a, sh, st);                                     \
+    }                                                                                             \
+    static size_t tc_smem_##NN(int mode, int warps) { return Dispatch<NN>::tc_smem(mode, warps); } \
     extern const NxOps kNxOps_##NN = {NN, Dispatch<NN>::V, Dispatch<NN>::kGrad, tables_##NN, sweep_##NN,        \
                                       max_warps_##NN, smem_##NN, tables_grad_##NN, gradient_##NN,  \
-                                      gradient_max_warps_##NN};                                   \
+                                      gradient_max_warps_##NN, Dispatch<NN>::kTc, tables_natural_##NN, \
+                                      tc_sweep_##NN, tc_smem_##NN};                               \
     }

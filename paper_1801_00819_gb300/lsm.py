@@ -32,7 +32,10 @@ LSM_CHECKPOINT_EVERY = 16
 
 EXPORTED = ("lsm_workspace_bytes", "lsm_forward", "lsm_adjoint", "lsm_num_windows", "rls_window_solve",
             "lsm_status_string", "lsm_kernel_launches", "lsm_profile_start", "lsm_profile_stop",
-            "lsm_adjoint_static", "lsm_born_gradient", "rls_window_solve_ex", "rls_multi_line_solve")
+            "lsm_adjoint_static", "lsm_born_gradient", "rls_window_solve_ex", "rls_multi_line_solve",
+            "lsm_forward_ex", "lsm_adjoint_ex")
+
+TRANSFORMS = {"fft": 0, "dft_bf16x3": 1, "dft_fp16x3": 2, "dft_bf16x1": 3}
 
 LSM_PRECOND_NONE = 0
 LSM_PRECOND_ILLUMINATION = 1
@@ -63,7 +66,19 @@ class lsm_freqs(ctypes.Structure):
 
 
 class lsm_solve_options(ctypes.Structure):
-    _fields_ = [("preconditioner", ctypes.c_int), ("precond_eps", ctypes.c_double)]
+    _fields_ = [("preconditioner", ctypes.c_int), ("precond_eps", ctypes.c_double), ("transform", ctypes.c_int)]
+
+
+def _options(preconditioner=None, precond_eps=1e-2, transform="fft"):
+    if transform not in TRANSFORMS:
+        raise ValueError(f"unknown transform {transform!r}")
+    if preconditioner is None:
+        pc = LSM_PRECOND_NONE
+    elif preconditioner == "illumination":
+        pc = LSM_PRECOND_ILLUMINATION
+    else:
+        raise ValueError(f"unknown preconditioner {preconditioner!r}")
+    return lsm_solve_options(pc, float(precond_eps), TRANSFORMS[transform])
 
 
 class lsm_line(ctypes.Structure):
@@ -124,6 +139,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lsm_born_gradient.argtypes = [ctypes.POINTER(lsm_grid), P, P, ctypes.POINTER(lsm_freqs),
                                       ctypes.POINTER(lsm_geom), P, P, P, P, P, ctypes.c_int, ctypes.c_int, P,
                                       ctypes.c_size_t, P]
+    lib.lsm_forward_ex.restype = ctypes.c_int
+    lib.lsm_forward_ex.argtypes = list(lib.lsm_forward.argtypes) + [ctypes.POINTER(lsm_solve_options)]
+    lib.lsm_adjoint_ex.restype = ctypes.c_int
+    lib.lsm_adjoint_ex.argtypes = list(lib.lsm_adjoint.argtypes) + [ctypes.POINTER(lsm_solve_options)]
     lib.lsm_num_windows.restype = ctypes.c_int
     lib.lsm_num_windows.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.rls_window_solve.restype = ctypes.c_int
@@ -245,20 +264,31 @@ def lsm_workspace_bytes(grid: Grid, geom: Geometry, freqs: Frequencies, nshots: 
                                                   ctypes.byref(freqs.c), int(nshots), int(op)))
 
 
-def lsm_forward(grid, slowness, freqs, geom, m, d_out, shot0, nshots, workspace, stream=None):
-    """d_out[nshots][nw][nrec] (complex64) = A m for shots shot0 .. shot0+nshots-1."""
-    st = load_library().lsm_forward(ctypes.byref(grid.c), _ptr(slowness), ctypes.byref(freqs.c),
-                                    ctypes.byref(geom.c), _ptr(m), _ptr(d_out), int(shot0), int(nshots),
-                                    _ptr(workspace), _nbytes(workspace), _stream(stream))
+def lsm_forward(grid, slowness, freqs, geom, m, d_out, shot0, nshots, workspace, stream=None, transform="fft"):
+    """d_out[nshots][nw][nrec] (complex64) = A m for shots shot0 .. shot0+nshots-1.
+
+    transform: "fft" (FP32 register FFTs) or a tensor-core precision variant ("dft_bf16x3",
+    "dft_fp16x3", "dft_bf16x1"; nx = 128, 256, 512, receivers at every column)."""
+    lib = load_library()
+    args = (ctypes.byref(grid.c), _ptr(slowness), ctypes.byref(freqs.c), ctypes.byref(geom.c), _ptr(m), _ptr(d_out),
+            int(shot0), int(nshots), _ptr(workspace), _nbytes(workspace), _stream(stream))
+    if transform == "fft":
+        st = lib.lsm_forward(*args)
+    else:
+        st = lib.lsm_forward_ex(*args, ctypes.byref(_options(transform=transform)))
     _check(st, "lsm_forward")
 
 
 def lsm_adjoint(grid, slowness, freqs, geom, d, m_out, shot0, nshots, workspace, accumulate=False,
-                stream=None):
+                stream=None, transform="fft"):
     """m_out[nz][nx] (=, or += when accumulate) A^T d for shots shot0 .. shot0+nshots-1."""
-    st = load_library().lsm_adjoint(ctypes.byref(grid.c), _ptr(slowness), ctypes.byref(freqs.c),
-                                    ctypes.byref(geom.c), _ptr(d), _ptr(m_out), int(shot0), int(nshots),
-                                    1 if accumulate else 0, _ptr(workspace), _nbytes(workspace), _stream(stream))
+    lib = load_library()
+    args = (ctypes.byref(grid.c), _ptr(slowness), ctypes.byref(freqs.c), ctypes.byref(geom.c), _ptr(d), _ptr(m_out),
+            int(shot0), int(nshots), 1 if accumulate else 0, _ptr(workspace), _nbytes(workspace), _stream(stream))
+    if transform == "fft":
+        st = lib.lsm_adjoint(*args)
+    else:
+        st = lib.lsm_adjoint_ex(*args, ctypes.byref(_options(transform=transform)))
     _check(st, "lsm_adjoint")
 
 
@@ -283,7 +313,7 @@ def lsm_born_gradient(grid, slowness, sref, freqs, geom, m, g, d_out, grad_m, gr
 
 def rls_window_solve(grid, slowness, freqs, geom, d, lam, K, slide, cg_tol, max_iter, m_inout, workspace,
                      first_window=0, n_windows=0, stream=None, raise_on_breakdown=True, preconditioner=None,
-                     precond_eps=1e-2):
+                     precond_eps=1e-2, transform="fft"):
     """Sliding-window CG solve; returns (status, [stats dicts]).  m_inout is updated in place.
 
     preconditioner=None calls rls_window_solve; "illumination" calls rls_window_solve_ex with the
@@ -296,13 +326,11 @@ def rls_window_solve(grid, slowness, freqs, geom, d, lam, K, slide, cg_tol, max_
     args = (ctypes.byref(grid.c), _ptr(slowness), ctypes.byref(freqs.c), ctypes.byref(geom.c), _ptr(d), float(lam),
             int(K), int(slide), float(cg_tol), int(max_iter), int(first_window), int(n_windows), _ptr(m_inout), stats,
             cap, _ptr(workspace), _nbytes(workspace), _stream(stream))
-    if preconditioner is None:
+    if preconditioner is None and transform == "fft":
         st = lib.rls_window_solve(*args)
-    elif preconditioner == "illumination":
-        opts = lsm_solve_options(LSM_PRECOND_ILLUMINATION, float(precond_eps))
-        st = lib.rls_window_solve_ex(*args, ctypes.byref(opts))
     else:
-        raise ValueError(f"unknown preconditioner {preconditioner!r}")
+        opts = _options(preconditioner, precond_eps, transform)
+        st = lib.rls_window_solve_ex(*args, ctypes.byref(opts))
     last = nwin if n_windows <= 0 else min(nwin, first_window + n_windows)
     out = [stats[i].as_dict() for i in range(max(0, last - first_window))]
     if st != LSM_OK and (st != LSM_ERR_BREAKDOWN or raise_on_breakdown):
@@ -319,7 +347,7 @@ class LineProblem:
         self.cg_tol, self.max_iter, self.m_inout, self.workspace, self.stream = cg_tol, max_iter, m_inout, workspace, stream
 
 
-def rls_multi_line_solve(problems, preconditioner=None, precond_eps=1e-2, raise_on_error=True):
+def rls_multi_line_solve(problems, preconditioner=None, precond_eps=1e-2, raise_on_error=True, transform="fft"):
     """Solve several LineProblems concurrently; returns ([status], [[stats dicts]])."""
     lib = load_library()
     n = len(problems)
@@ -333,11 +361,7 @@ def rls_multi_line_solve(problems, preconditioner=None, precond_eps=1e-2, raise_
                           int(pr.slide), float(pr.cg_tol), int(pr.max_iter), _ptr(pr.m_inout),
                           ctypes.cast(stats, ctypes.POINTER(lsm_window_stats)), nwin, _ptr(pr.workspace),
                           _nbytes(pr.workspace), _stream(pr.stream), 0)
-    opts = None
-    if preconditioner == "illumination":
-        opts = ctypes.byref(lsm_solve_options(LSM_PRECOND_ILLUMINATION, float(precond_eps)))
-    elif preconditioner is not None:
-        raise ValueError(f"unknown preconditioner {preconditioner!r}")
+    opts = ctypes.byref(_options(preconditioner, precond_eps, transform))
     st = lib.rls_multi_line_solve(arr, n, opts)
     statuses = [int(arr[i].status) for i in range(n)]
     out = [[keep[i][0][k].as_dict() for k in range(keep[i][1])] for i in range(n)]

@@ -28,6 +28,7 @@ def main():
     ap.add_argument("--workload", default="realistic", choices=("realistic", "tiny", "precision"))
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--shots", type=int, default=0, help="shots per call (default: the window length)")
+    ap.add_argument("--transform", default="fft", help="fft, dft_bf16x3, dft_fp16x3 or dft_bf16x1")
     args = ap.parse_args()
 
     import torch
@@ -48,11 +49,11 @@ def main():
     ws = workspace(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, K, L.LSM_OP_ADJOINT))
     L.lsm_profile_start()
     for _ in range(args.reps):
-        L.lsm_forward(ds.grid, ds.slowness, ds.freqs, ds.geom, m, out, 0, K, ws)
-        L.lsm_adjoint(ds.grid, ds.slowness, ds.freqs, ds.geom, d, img, 0, K, ws)
+        L.lsm_forward(ds.grid, ds.slowness, ds.freqs, ds.geom, m, out, 0, K, ws, transform=args.transform)
+        L.lsm_adjoint(ds.grid, ds.slowness, ds.freqs, ds.geom, d, img, 0, K, ws, transform=args.transform)
     torch.cuda.synchronize()
     prof = L.lsm_profile_stop()
-    print(json.dumps({"workload": sv.name, "K": K, "nw": sv.nw, "nz": sv.nz, "nx": sv.nx,
+    print(json.dumps({"workload": sv.name, "transform": args.transform, "K": K, "nw": sv.nw, "nz": sv.nz, "nx": sv.nx,
                       "per_launch_ms": {k: (v["ms"] / v["launches"] if v["launches"] else 0.0)
                                         for k, v in prof.items()}}))
 

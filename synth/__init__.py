@@ -11,6 +11,7 @@ from .survey import (  # noqa: F401
     config_tiny,
     config_realistic,
     config_precision,
+    config_precision_subsample,
     config_batching_lines,
     random_case,
     ricker_spectrum,

@@ -204,6 +204,12 @@ def config_precision() -> Survey:
     return _realistic_like("precision", 1024, 512, 6.0, 6.0, 192, 3.0, 60.0, 256, 16, 8)
 
 
+def config_precision_subsample(nx: int = 128) -> Survey:
+    """The precision workload's construction (6 m grid, 3-60 Hz) subsampled to nx x 64, 6 shots,
+    10 frequencies: small enough for the FP64 oracle, used to compare the transform precisions."""
+    return _realistic_like("precision-subsample", nx, 64, 6.0, 6.0, 6, 3.0, 60.0, 10, 3, 2)
+
+
 def config_batching_lines():
     """Eight independent lines of the batching workload (seed 3)."""
     rng = np.random.default_rng(3)

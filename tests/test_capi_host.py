@@ -34,7 +34,8 @@ def test_header_declares_expected_entry_points():
     assert _declared_functions() == sorted(["lsm_workspace_bytes", "lsm_forward", "lsm_adjoint", "lsm_num_windows",
                                             "rls_window_solve", "lsm_status_string", "lsm_kernel_launches",
                                             "lsm_profile_start", "lsm_profile_stop", "lsm_adjoint_static",
-                                            "lsm_born_gradient", "rls_window_solve_ex", "rls_multi_line_solve"])
+                                            "lsm_born_gradient", "rls_window_solve_ex", "rls_multi_line_solve",
+                                            "lsm_forward_ex", "lsm_adjoint_ex"])
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -115,6 +116,22 @@ def test_static_scratch_variant_rejects_oversize_problems_before_launch(lib):
     with pytest.raises(lib.LsmError) as ei:
         lib.lsm_adjoint_static(g, fake, f, geo, fake, fake, 0, 16, stream=0)
     assert ei.value.status == lib.LSM_ERR_WORKSPACE
+    assert lib.lsm_kernel_launches() == before
+
+
+def test_tensor_core_transform_validation(lib):
+    before = lib.lsm_kernel_launches()
+    fake = 1 << 20
+    g, geo, f = _holders(lib, nx=64)
+    with pytest.raises(lib.LsmError) as ei:  # nx 64 has no tensor-core variant
+        lib.lsm_forward(g, fake, f, geo, fake, fake, 0, 1, None, stream=0, transform="dft_bf16x3")
+    assert ei.value.status == lib.LSM_ERR_UNSUPPORTED_NX
+    g, geo, f = _holders(lib, nx=128, rec=np.tile(np.arange(64), (3, 1)))
+    with pytest.raises(lib.LsmError) as ei:  # receiver lists are not taken by the variants
+        lib.lsm_adjoint(g, fake, f, geo, fake, fake, 0, 1, None, stream=0, transform="dft_fp16x3")
+    assert ei.value.status == lib.LSM_ERR_ARG
+    with pytest.raises(ValueError):
+        lib._options(transform="fp8")
     assert lib.lsm_kernel_launches() == before
 
 
