@@ -136,8 +136,9 @@ SweepShape gradient_shape(int nx, int nshots, int nw, int num_sms) {
 SweepShape tc_shape(int nx, int mode, int nshots, int nw, int num_sms) {
     const NxOps* ops = nx_ops(nx);
     const int nitems = nshots * nw;
-    int warps = (nitems + num_sms - 1) / num_sms;
-    warps = std::max(1, std::min(warps, 8));
+    // one item per warp, up to 7 warps per block, two blocks per SM
+    int warps = (nitems + 2 * num_sms - 1) / (2 * num_sms);
+    warps = std::max(1, std::min(warps, 7));
     SweepShape s;
     s.warps = warps;
     s.blocks = (nitems + warps - 1) / warps;

@@ -8,7 +8,8 @@
 // format:
 //   PREC_BF16X3: hi = bf16(x), lo = bf16(x - hi); a b ~ ah bh + ah bl + al bh;
 //   PREC_FP16X3: hi = fp16(x), lo = fp16((x - hi) 2^11); the two lo terms accumulate separately
-//                and are scaled back by 2^-11 (keeps lo out of the fp16 subnormal range);
+//                and are scaled back by 2^-11 (keeps lo out of the fp16 subnormal range); each
+//                item is block-scaled by a power of two per depth step (FP16's exponent range);
 //   PREC_BF16X1: hi only (one product; shows the error of a plain bf16 transform).
 // One warp holds one (shot, w) item for the whole depth loop, in the mma accumulator layout: lane
 // (g = lane / 4, c = lane % 4) holds, for n-tile j and element e, row g + 8 (e / 2) and column
@@ -79,7 +80,7 @@ __device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4], 
 template <int PREC>
 struct CTile {
     float re[4], im[4];
-    float re2[PREC == PREC_FP16X3 ? 4 : 1], im2[PREC == PREC_FP16X3 ? 4 : 1];
+    float re2[4], im2[4];  // used by FP16X3 only
     __device__ __forceinline__ void zero() {
 #pragma unroll
         for (int e = 0; e < 4; ++e) re[e] = im[e] = 0.f;
@@ -96,35 +97,40 @@ struct CTile {
     }
 };
 
-// the eight cross-term products (hi x lo and lo x hi) of one complex tile into (cr, ci)
+// C += sum of two real products into each of C.re and C.im, as split fragments (index 0 hi, 1 lo):
+//   C.re += A1 B1 + A2 B2,  C.im += A3 B3 + A4 B4,
+// each real product as hi hi (+ hi lo + lo hi; for FP16X3 the cross terms go to re2/im2, which hold
+// them scaled by 2^11).  A complex product takes (A1, B1, A2, B2, A3, B3, A4, B4) =
+// (Ar, Br, -Ai, Bi, Ar, Bi, Ai, Br).
 template <int PREC>
-__device__ __forceinline__ void cgemm_cross(float (&cr)[4], float (&ci)[4], const uint32_t (&Ar)[2][4],
-                                            const uint32_t (&Ai)[2][4], const uint32_t (&Anim)[2][4],
-                                            const uint32_t (&Br)[2][2], const uint32_t (&Bi)[2][2]) {
-    mma16816<PREC>(cr, Ar[0], Br[1][0], Br[1][1]);
-    mma16816<PREC>(cr, Anim[0], Bi[1][0], Bi[1][1]);
-    mma16816<PREC>(ci, Ar[0], Bi[1][0], Bi[1][1]);
-    mma16816<PREC>(ci, Ai[0], Br[1][0], Br[1][1]);
-    mma16816<PREC>(cr, Ar[1], Br[0][0], Br[0][1]);
-    mma16816<PREC>(cr, Anim[1], Bi[0][0], Bi[0][1]);
-    mma16816<PREC>(ci, Ar[1], Bi[0][0], Bi[0][1]);
-    mma16816<PREC>(ci, Ai[1], Br[0][0], Br[0][1]);
+__device__ __forceinline__ void cross_terms(float (&cr)[4], float (&ci)[4], const uint32_t (&A1)[2][4],
+                                            const uint32_t (&B1)[2][2], const uint32_t (&A2)[2][4],
+                                            const uint32_t (&B2)[2][2], const uint32_t (&A3)[2][4],
+                                            const uint32_t (&B3)[2][2], const uint32_t (&A4)[2][4],
+                                            const uint32_t (&B4)[2][2]) {
+    mma16816<PREC>(cr, A1[0], B1[1][0], B1[1][1]);
+    mma16816<PREC>(cr, A2[0], B2[1][0], B2[1][1]);
+    mma16816<PREC>(ci, A3[0], B3[1][0], B3[1][1]);
+    mma16816<PREC>(ci, A4[0], B4[1][0], B4[1][1]);
+    mma16816<PREC>(cr, A1[1], B1[0][0], B1[0][1]);
+    mma16816<PREC>(cr, A2[1], B2[0][0], B2[0][1]);
+    mma16816<PREC>(ci, A3[1], B3[0][0], B3[0][1]);
+    mma16816<PREC>(ci, A4[1], B4[0][0], B4[0][1]);
 }
 
-// C += A B for complex A, B given as split fragments: A {re, im, -im} x {hi, lo}, B {re, im} x {hi, lo};
-// Cr += Ar Br + (-Ai) Bi, Ci += Ar Bi + Ai Br, each real product as hi hi (+ hi lo + lo hi)
 template <int PREC>
-__device__ __forceinline__ void cgemm_tile(CTile<PREC>& C, const uint32_t (&Ar)[2][4], const uint32_t (&Ai)[2][4],
-                                           const uint32_t (&Anim)[2][4], const uint32_t (&Br)[2][2],
-                                           const uint32_t (&Bi)[2][2]) {
-    mma16816<PREC>(C.re, Ar[0], Br[0][0], Br[0][1]);
-    mma16816<PREC>(C.re, Anim[0], Bi[0][0], Bi[0][1]);
-    mma16816<PREC>(C.im, Ar[0], Bi[0][0], Bi[0][1]);
-    mma16816<PREC>(C.im, Ai[0], Br[0][0], Br[0][1]);
+__device__ __forceinline__ void cgemm4(CTile<PREC>& C, const uint32_t (&A1)[2][4], const uint32_t (&B1)[2][2],
+                                       const uint32_t (&A2)[2][4], const uint32_t (&B2)[2][2],
+                                       const uint32_t (&A3)[2][4], const uint32_t (&B3)[2][2],
+                                       const uint32_t (&A4)[2][4], const uint32_t (&B4)[2][2]) {
+    mma16816<PREC>(C.re, A1[0], B1[0][0], B1[0][1]);
+    mma16816<PREC>(C.re, A2[0], B2[0][0], B2[0][1]);
+    mma16816<PREC>(C.im, A3[0], B3[0][0], B3[0][1]);
+    mma16816<PREC>(C.im, A4[0], B4[0][0], B4[0][1]);
     if constexpr (PREC == PREC_FP16X3) {
-        cgemm_cross<PREC>(C.re2, C.im2, Ar, Ai, Anim, Br, Bi);
+        cross_terms<PREC>(C.re2, C.im2, A1, B1, A2, B2, A3, B3, A4, B4);
     } else if constexpr (PREC == PREC_BF16X3) {
-        cgemm_cross<PREC>(C.re, C.im, Ar, Ai, Anim, Br, Bi);
+        cross_terms<PREC>(C.re, C.im, A1, B1, A2, B2, A3, B3, A4, B4);
     }
 }
 
@@ -226,13 +232,14 @@ __device__ __forceinline__ void tc_left(TcItem<N>& out, const float2* buf, const
         }
         CTile<PREC> C;
         C.zero();
-        cgemm_tile<PREC>(C, Ar, Ai, An, Br, Bi);
+        cgemm4<PREC>(C, Ar, Br, An, Bi, Ar, Bi, Ai, Br);
 #pragma unroll
         for (int e = 0; e < 4; ++e) out.x[j][e] = C.get(e);
     }
 }
 
-// right product: out = M . F_R2 (CONJ: conj(F_R2)), M in accumulator layout (chained as operand A)
+// right product: out = M . F_R2 (CONJ: conj(F_R2)), M in accumulator layout (chained as operand A:
+// A word w of k-step kk holds elements 2 (w % 2) + {0, 1} of accumulator tile 2 kk + w / 2).
 template <int N, int PREC, bool CONJ>
 __device__ __forceinline__ void tc_right(TcItem<N>& out, const TcItem<N>& in, const uint32_t* Bfr, int lane) {
     using S = TcShape<N>;
@@ -242,7 +249,6 @@ __device__ __forceinline__ void tc_right(TcItem<N>& out, const TcItem<N>& in, co
         C.zero();
 #pragma unroll
         for (int kk = 0; kk < S::KS; ++kk) {
-            // A word w (elements 2w, 2w + 1) = tile 2 kk + (w >> 1), elements 2 (w & 1) + {0, 1}
             uint32_t Ar[2][4], Ai[2][4], An[2][4];
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
@@ -266,7 +272,7 @@ __device__ __forceinline__ void tc_right(TcItem<N>& out, const TcItem<N>& in, co
                 Bi[0][w] = base[((CONJ ? 2 : 1) * 32 + lane) * 2 + w];
                 Bi[1][w] = base[((CONJ ? 5 : 4) * 32 + lane) * 2 + w];
             }
-            cgemm_tile<PREC>(C, Ar, Ai, An, Br, Bi);
+            cgemm4<PREC>(C, Ar, Br, An, Bi, Ar, Bi, Ai, Br);
         }
 #pragma unroll
         for (int e = 0; e < 4; ++e) out.x[jj][e] = C.get(e);
@@ -300,9 +306,29 @@ __device__ __forceinline__ int tc_kpos(int lane, int j, int e) {
 // u <- F^-1 (phi . F u) with phi (already divided by N, natural frequency order) or conj(phi)
 template <int N, int PREC, bool CONJ_PHI>
 __device__ __forceinline__ void tc_phase_step(TcItem<N>& u, float2* buf, const uint32_t* Afr, const uint32_t* Bfr,
-                                              const float2 (&tw)[TcShape<N>::NT][4], const float2* __restrict__ phi,
-                                              int lane) {
+                                              const float2* tws, const float2* __restrict__ phi, int lane) {
     using S = TcShape<N>;
+    // FP16 has a 5-bit exponent: the item is brought to a largest component in [1/2, 1) by an exact
+    // power-of-two scale before the split and scaled back after the step (the products are linear),
+    // so wavefields of any magnitude stay inside the FP16 normal range at every stage (at most
+    // 16 R2 after the two forward factors).  BF16 keeps the FP32 exponent range and needs no scale.
+    int ex = 0;
+    if constexpr (PREC == PREC_FP16X3) {
+        float mx = 0.f;
+#pragma unroll
+        for (int j = 0; j < S::NT; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) mx = fmaxf(mx, fmaxf(fabsf(u.x[j][e].x), fabsf(u.x[j][e].y)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (mx > 0.f && mx <= 3.0e38f) frexpf(mx, &ex);
+        ex = max(-100, min(ex, 100));  // both 2^ex and 2^-ex stay normal FP32 numbers
+        const float down = ldexpf(1.f, -ex);
+#pragma unroll
+        for (int j = 0; j < S::NT; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) u.x[j][e] = make_float2(u.x[j][e].x * down, u.x[j][e].y * down);
+    }
     TcItem<N> y;
     __syncwarp();
     tc_store<N>(u, buf, lane);
@@ -311,7 +337,7 @@ __device__ __forceinline__ void tc_phase_step(TcItem<N>& u, float2* buf, const u
 #pragma unroll
     for (int j = 0; j < S::NT; ++j)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) y.x[j][e] = cmul(y.x[j][e], tw[j][e]);
+        for (int e = 0; e < 4; ++e) y.x[j][e] = cmul(y.x[j][e], tws[(j * 4 + e) * 32 + lane]);
     TcItem<N> z;
     tc_right<N, PREC, false>(z, y, Bfr, lane);
 #pragma unroll
@@ -325,30 +351,40 @@ __device__ __forceinline__ void tc_phase_step(TcItem<N>& u, float2* buf, const u
 #pragma unroll
     for (int j = 0; j < S::NT; ++j)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) y.x[j][e] = cmulc(y.x[j][e], tw[j][e]);
+        for (int e = 0; e < 4; ++e) y.x[j][e] = cmulc(y.x[j][e], tws[(j * 4 + e) * 32 + lane]);
     __syncwarp();
     tc_store<N>(y, buf, lane);
     __syncwarp();
     tc_left<N, PREC, true>(u, buf, Afr, lane);
+    if constexpr (PREC == PREC_FP16X3) {
+        const float up = ldexpf(1.f, ex);
+#pragma unroll
+        for (int j = 0; j < S::NT; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) u.x[j][e] = make_float2(u.x[j][e].x * up, u.x[j][e].y * up);
+    }
 }
 
 template <int N>
 constexpr size_t tc_smem_bytes(int warps, bool adjoint) {
     using S = TcShape<N>;
-    return (size_t)(S::A_WORDS + S::B_WORDS) * 4 + (size_t)warps * S::BUF * sizeof(float2) +
-           (adjoint ? (size_t)2 * warps * N * sizeof(float) : 0);
+    return (size_t)(S::A_WORDS + S::B_WORDS) * 4 + (size_t)S::NT * 4 * 32 * sizeof(float2) +
+           (size_t)warps * S::BUF * sizeof(float2) + (adjoint ? (size_t)2 * warps * N * sizeof(float) : 0);
 }
 
 // Depth sweeps with the tensor-core transforms; same modes, inputs and outputs as sweep_kernel,
 // one item per warp, coefficients read straight from the tables (Phi in natural frequency order).
 template <int N, int PREC, int MODE>
-__global__ void __launch_bounds__(256) tc_sweep_kernel(const SweepArgs a) {
+// Up to 7 warps per block and two blocks per SM (at most 146 registers a thread): the 2,048 items of a
+// 512-wide window of 16 shots x 128 frequencies then run in a single wave on 152 SMs.
+__global__ void __launch_bounds__(224, 2) tc_sweep_kernel(const SweepArgs a) {
     using S = TcShape<N>;
     constexpr int NT = S::NT;
     extern __shared__ float4 smem_f4[];
     uint32_t* Afr = reinterpret_cast<uint32_t*>(smem_f4);
     uint32_t* Bfr = Afr + S::A_WORDS;
-    float2* bufs = reinterpret_cast<float2*>(Bfr + S::B_WORDS);
+    float2* tws = reinterpret_cast<float2*>(Bfr + S::B_WORDS);  // twiddles W, [element][lane]
+    float2* bufs = tws + NT * 4 * 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     float* img = reinterpret_cast<float*>(bufs + nwarps * S::BUF);  // [2][nwarps][N]
     float2* buf = bufs + warp * S::BUF;
@@ -362,18 +398,13 @@ __global__ void __launch_bounds__(256) tc_sweep_kernel(const SweepArgs a) {
     const int nz = a.nz;
 
     tc_build_constants<N, PREC>(Afr, Bfr);
-    float2 tw[NT][4];
-    {
-        const int g = lane >> 2, tig = lane & 3;
-#pragma unroll
-        for (int j = 0; j < NT; ++j)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int k1 = g + 8 * (e >> 1), n2 = 8 * j + 2 * tig + (e & 1);
-                float sn, cs;
-                sincospif(-2.0f * (float)((k1 * n2) % N) / (float)N, &sn, &cs);
-                tw[j][e] = make_float2(cs, sn);
-            }
+    // W[k1][n2] for element (j, e) of lane l: k1 = g + 8 (e / 2), n2 = 8 j + 2 c + (e % 2)
+    for (int idx = threadIdx.x; idx < NT * 4 * 32; idx += blockDim.x) {
+        const int l = idx & 31, je = idx >> 5, j = je >> 2, e = je & 3;
+        const int k1 = (l >> 2) + 8 * (e >> 1), n2 = 8 * j + 2 * (l & 3) + (e & 1);
+        float sn, cs;
+        sincospif(-2.0f * (float)((k1 * n2) % N) / (float)N, &sn, &cs);
+        tws[idx] = make_float2(cs, sn);
     }
     __syncthreads();
 
@@ -415,7 +446,7 @@ __global__ void __launch_bounds__(256) tc_sweep_kernel(const SweepArgs a) {
                     for (int e = 0; e < 4; ++e) __stcs(row + tc_xpos<N>(lane, j, e), u.x[j][e]);
             }
             if (jz + 1 < nz) {
-                tc_phase_step<N, PREC, false>(u, buf, Afr, Bfr, tw, phi_w + (size_t)jz * N, lane);
+                tc_phase_step<N, PREC, false>(u, buf, Afr, Bfr, tws, phi_w + (size_t)jz * N, lane);
                 mul_d(u, dss_w + (size_t)jz * N, false);
             }
         }
@@ -443,7 +474,7 @@ __global__ void __launch_bounds__(256) tc_sweep_kernel(const SweepArgs a) {
             }
             if (jz + 1 < nz) {
                 mul_d(u, dss_w + (size_t)jz * N, true);
-                tc_phase_step<N, PREC, true>(u, buf, Afr, Bfr, tw, phi_w + (size_t)jz * N, lane);
+                tc_phase_step<N, PREC, true>(u, buf, Afr, Bfr, tws, phi_w + (size_t)jz * N, lane);
             }
         }
     } else {  // MODE_FORWARD
@@ -453,7 +484,7 @@ __global__ void __launch_bounds__(256) tc_sweep_kernel(const SweepArgs a) {
             for (int e = 0; e < 4; ++e) u.x[j][e] = make_float2(0.f, 0.f);
         for (int jz = nz - 1; jz >= 0; --jz) {
             if (jz + 1 < nz) {
-                tc_phase_step<N, PREC, false>(u, buf, Afr, Bfr, tw, phi_w + (size_t)jz * N, lane);
+                tc_phase_step<N, PREC, false>(u, buf, Afr, Bfr, tws, phi_w + (size_t)jz * N, lane);
                 mul_d(u, dss_w + (size_t)jz * N, false);
             }
             TcItem<N> s;

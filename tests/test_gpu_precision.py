@@ -106,3 +106,37 @@ def test_tensor_core_transform_rejects_receiver_subsets():
     out = torch.empty((2, sv.nw, 64), dtype=torch.complex64, device="cuda")
     with pytest.raises(L.LsmError):
         L.lsm_forward(ds.grid, ds.slowness, ds.freqs, ds.geom, m, out, 0, 2, ws, transform="dft_fp16x3")
+
+
+@pytest.mark.parametrize("transform", ["dft_fp16x3", "dft_bf16x3"])
+def test_tensor_core_transforms_are_scale_invariant(transform):
+    """A is linear: A(c m) = c A(m) for any c.  Wavefields of 1e-6 or 1e4 times the natural size (the
+    CG direction vectors take such scales) must keep the precision's relative error; a 16-bit split
+    without a block scale loses FP16's narrow exponent range here."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1801_00819_gb300 as L
+    sv = _subsampled_problem(128)
+    op = oracle_operator(sv)
+    ds = device_survey(sv)
+    ns = sv.ns
+    m = np.asarray(sv.reflectivity, dtype=np.float32)
+    ws = torch.empty(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, ns, L.LSM_OP_ADJOINT), dtype=torch.uint8,
+                     device="cuda")
+    ref_f = op.forward(m.astype(np.float64))
+    rng = np.random.default_rng(1)
+    d = (rng.normal(size=(ns, sv.nw, sv.nx)) + 1j * rng.normal(size=(ns, sv.nw, sv.nx))).astype(np.complex64)
+    ref_a = op.adjoint(d.astype(np.complex128))
+    bound = BOUNDS[transform]
+    for c in (1e-6, 1.0, 1e4):
+        out = torch.empty((ns, sv.nw, sv.nx), dtype=torch.complex64, device="cuda")
+        L.lsm_forward(ds.grid, ds.slowness, ds.freqs, ds.geom, torch.as_tensor(m * np.float32(c), device="cuda"), out,
+                      0, ns, ws, transform=transform)
+        img = torch.empty((sv.nz, sv.nx), dtype=torch.float32, device="cuda")
+        L.lsm_adjoint(ds.grid, ds.slowness, ds.freqs, ds.geom, torch.as_tensor(d * np.complex64(c), device="cuda"),
+                      img, 0, ns, ws, transform=transform)
+        torch.cuda.synchronize()
+        ef = rel_l2(out.cpu().numpy() / c, ref_f)
+        ea = rel_l2(img.cpu().numpy() / c, ref_a)
+        assert ef <= bound and ea <= bound, (c, ef, ea)
