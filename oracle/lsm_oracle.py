@@ -33,7 +33,7 @@ What it computes, with the passage each part follows:
   shots and adding the next `slide` (the rank-K downdate/update of the block-row section).
   Window starts are 0, slide, 2 slide, ... while start + K <= ns, plus a final window at
   ns - K when the last one does not end at ns.  The result is the last window's image.
-* Stopping rule ("threshold for the normal equation", Examples section) read as
+* Stopping rule (a threshold on the normal equation, Examples section) read as
   ||A_k^T (d_k - A_k m) - lambda m|| / ||A_k^T d_k|| <= tol.
 * Preconditioned variant (`pcg_window`): the paper asks for preconditioners in each windowed
   setup without naming one; the reading is the diagonal source-illumination preconditioner.
