@@ -45,7 +45,7 @@ if ROOT not in sys.path:
 
 FP32_LANES_PER_SM = 128     # FP32 FMA lanes per Blackwell SM
 FALLBACK_HBM_GBS = 6800.0   # profiling recipe's fallback copy bandwidth
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sweep_adjoint_realistic_512x256.md")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sweep_kernels_realistic_512x256.md")
 
 
 def parse_args():
