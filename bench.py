@@ -384,6 +384,23 @@ def gpu_arm(args):
             "time_to_tol_ms": round(tv, 3), "total_iters": int(sum(w["iters"] for w in stv)),
             "iters_per_window": [w["iters"] for w in stv],
             "time_to_tol_vs_plain": round((t_max / args.steps) / tv, 3)}}
+        # the plain solve with each window's CG iterations replayed as one CUDA graph (conditional
+        # WHILE node, stopping test on the device): same kernels, one host wait per window
+        tg = []
+        for rep in range(2):  # the first call also builds and instantiates its graph; both are timed
+            m.zero_()
+            torch.cuda.synchronize()
+            v0.record(stream)
+            _, stg = L.rls_window_solve(ds.grid, ds.slowness, ds.freqs, ds.geom, d, lam, K, sv.slide, sv.cg_tol,
+                                        sv.cg_iters, m, ws, cuda_graph=True)
+            v1.record(stream)
+            torch.cuda.synchronize()
+            tg.append(v0.elapsed_time(v1))
+        out["variants"]["cuda_graph"] = {
+            "time_to_tol_ms": round(tg[-1], 3), "time_to_tol_ms_per_call": [round(x, 3) for x in tg],
+            "total_iters": int(sum(w["iters"] for w in stg)),
+            "same_iterations_as_plain": [w["iters"] for w in stg] == iters,
+            "time_to_tol_vs_plain": round((t_max / args.steps) / tg[-1], 3)}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sv, args.cpu_sample_freqs)

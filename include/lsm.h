@@ -262,10 +262,19 @@ int lsm_profile_stop(lsm_profile* out);
 #define LSM_TRANSFORM_DFT_BF16X3 1
 #define LSM_TRANSFORM_DFT_FP16X3 2
 #define LSM_TRANSFORM_DFT_BF16X1 3
+/*
+ *   cuda_graph: nonzero runs each window's CG iterations as one CUDA graph -- a conditional WHILE
+ *     node whose body is one iteration (A, the vector updates, A^T, the stopping test evaluated on
+ *     the device) -- so the host waits once per window instead of once per iteration.  The kernels
+ *     and their order are those of the host-driven loop, so results and iteration counts are
+ *     identical.  The graph is built once per call on a private stream; kernels inside it are not
+ *     seen by lsm_profile_start / lsm_profile_stop.
+ */
 typedef struct {
     int preconditioner;
     double precond_eps;
     int transform;
+    int cuda_graph;
 } lsm_solve_options;
 
 /* lsm_forward / lsm_adjoint with solver options (only `transform` applies; NULL: FP32 FFTs). */

@@ -9,6 +9,7 @@ from .lsm import (  # noqa: F401
     Frequencies,
     Geometry,
     Grid,
+    LineProblem,
     LsmError,
     lsm_adjoint,
     lsm_born_gradient,
@@ -19,6 +20,7 @@ from .lsm import (  # noqa: F401
     lsm_profile_stop,
     lsm_status_string,
     lsm_workspace_bytes,
+    rls_multi_line_solve,
     rls_window_solve,
     LSM_OP_FORWARD,
     LSM_OP_ADJOINT,

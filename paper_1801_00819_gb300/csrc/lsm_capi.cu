@@ -24,7 +24,18 @@
 namespace lsm {
 
 static std::atomic<unsigned long long> g_launches{0};
-void count_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+// While this thread captures a CG iteration into a graph, launches are counted per replay (the
+// captured count times the iterations run) and no profiling events are recorded (a conditional
+// node's body may hold kernels only).
+static thread_local bool g_capturing = false;
+static thread_local int g_captured_launches = 0;
+void count_launch(int n) {
+    if (g_capturing) {
+        g_captured_launches += n;
+        return;
+    }
+    g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed);
+}
 
 struct ProfRecord {
     int cls;
@@ -52,7 +63,7 @@ static cudaEvent_t pooled_event() {
 }
 
 void profile_mark(int cls, cudaStream_t st, bool begin) {
-    if (!g_prof_on) return;
+    if (!g_prof_on || g_capturing) return;
     if (begin) {
         g_pending_begin = pooled_event();
         if (g_pending_begin) cudaEventRecord(g_pending_begin, st);
@@ -203,6 +214,7 @@ struct Layout {
     size_t p, s, r, q, qq, pp, ss, state;
     size_t ckpt, seg, part_s;  // gradient op
     size_t illum, minv, bmax, sz;  // preconditioned solve
+    size_t ctrl;                   // solve: window start read by graph-replayed sweeps
     size_t total;
     int ring, nparts;
 };
@@ -257,6 +269,7 @@ Layout make_layout(const lsm_grid* g, const lsm_geom* geo, const lsm_freqs* f, i
         L.pp = take(kRedBlocks * sizeof(double));
         L.ss = take(kRedBlocks * sizeof(double));
         L.state = take(sizeof(CgState));
+        L.ctrl = take(sizeof(int));
         L.illum = take(plane * sizeof(float));
         L.minv = take(plane * sizeof(float));
         L.bmax = take(kIllumBlocks * sizeof(float));
@@ -651,6 +664,85 @@ static int window_start(int k, int ns, int K, int slide) {
     return k < regular ? k * slide : ns - K;
 }
 
+// The CG iterations of a window as one CUDA graph: a test node (cg_loop_test without advance)
+// followed by a conditional WHILE node whose body is one iteration -- q = A p, ||q||^2, the m and r
+// updates, s = A^T r - lambda m, the p update -- and the advancing test.  The sweeps read the
+// window start from the workspace (shot0_dev), so one instantiation serves every window of a call.
+struct CgGraph {
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int body_launches = 0;
+    bool capturing = false;
+    CgGraph() = default;
+    CgGraph(const CgGraph&) = delete;
+    CgGraph& operator=(const CgGraph&) = delete;
+    ~CgGraph() {
+        if (capturing) {
+            cudaGraph_t body = nullptr;  // owned by the conditional node
+            cudaStreamEndCapture(cs, &body);
+            g_capturing = false;
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cs) cudaStreamDestroy(cs);
+    }
+};
+
+struct CgVectors {
+    float *m, *p, *s;
+    float2 *r, *q;
+    double *qq, *pp, *ss, *sz;
+    const float* minv;
+    CgState* state;
+    size_t nd;
+    int n;
+    double lambda;
+};
+
+static int build_cg_graph(CgGraph& G, SweepArgs a, int K, int nsm, int transform, const CgVectors& v) {
+    LSM_CHECK(cudaStreamCreateWithFlags(&G.cs, cudaStreamNonBlocking));
+    LSM_CHECK(cudaGraphCreate(&G.graph, 0));
+    cudaGraphConditionalHandle handle = 0;
+    LSM_CHECK(cudaGraphConditionalHandleCreate(&handle, G.graph, 0, cudaGraphCondAssignDefault));
+    CgState* state = v.state;
+    int no_advance = 0;
+    void* test_args[] = {&state, &handle, &no_advance};
+    cudaKernelNodeParams kp;
+    cg_loop_test_node_params(&kp, test_args);
+    cudaGraphNode_t test0 = nullptr, loop = nullptr;
+    LSM_CHECK(cudaGraphAddKernelNode(&test0, G.graph, nullptr, 0, &kp));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    LSM_CHECK(cudaGraphAddNode(&loop, G.graph, &test0, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+
+    LSM_CHECK(cudaStreamBeginCaptureToGraph(G.cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    G.capturing = true;
+    g_capturing = true;
+    g_captured_launches = 0;
+    int nparts = 0;
+    cudaError_t e = run_forward(a, 0, K, v.p, v.q, nsm, G.cs, transform);
+    if (e == cudaSuccess) e = cg_norm2_c64(v.q, v.nd, v.qq, G.cs);
+    if (e == cudaSuccess) e = cg_update_mr(v.m, v.p, v.n, v.r, v.q, v.nd, v.qq, v.pp, v.lambda, v.state, -1, G.cs);
+    if (e == cudaSuccess) e = run_adjoint(a, 0, K, v.r, nsm, G.cs, &nparts, transform);
+    if (e == cudaSuccess)
+        e = cg_reduce_image(a.part, nparts, v.n, v.m, (float)v.lambda, 0, v.s, v.ss, G.cs, v.minv, v.sz);
+    if (e == cudaSuccess) e = cg_update_p(v.p, v.s, v.n, v.ss, 0, v.state, -1, -1, v.pp, G.cs, v.minv, v.sz);
+    if (e == cudaSuccess) e = cg_loop_test(v.state, handle, 1, G.cs);
+    g_capturing = false;
+    G.body_launches = g_captured_launches;
+    cudaGraph_t out = nullptr;
+    const cudaError_t e_end = cudaStreamEndCapture(G.cs, &out);
+    G.capturing = false;
+    if (e != cudaSuccess || e_end != cudaSuccess) return LSM_ERR_CUDA;
+    LSM_CHECK(cudaGraphInstantiate(&G.exec, G.graph, 0));
+    return LSM_OK;
+}
+
 int rls_window_solve_ex(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs, const lsm_geom* geom,
                         const float* d, double lambda, int K, int slide, double cg_tol, int max_iter,
                         int first_window, int n_windows, float* m_inout, lsm_window_stats* stats, int stats_cap,
@@ -695,6 +787,9 @@ int rls_window_solve_ex(const lsm_grid* grid, const float* slowness, const lsm_f
     double* pp = reinterpret_cast<double*>(ws + L.pp);
     double* ss = reinterpret_cast<double*>(ws + L.ss);
     CgState* state = reinterpret_cast<CgState*>(ws + L.state);
+    int* shot0_dev = reinterpret_cast<int*>(ws + L.ctrl);
+    const bool use_graph = options && options->cuda_graph != 0;
+    CgGraph graph;
     float* minv = precond == LSM_PRECOND_ILLUMINATION ? reinterpret_cast<float*>(ws + L.minv) : nullptr;
     double* sz = minv ? reinterpret_cast<double*>(ws + L.sz) : nullptr;
     const float2* dall = reinterpret_cast<const float2*>(d);
@@ -732,13 +827,36 @@ int rls_window_solve_ex(const lsm_grid* grid, const float* slowness, const lsm_f
         int gi = 0;
         LSM_CHECK(cg_update_p(p, s, n, ss, 1, state, 1, gi, pp, st, minv, sz));
         CgState hs;
+        double rel = 0.0, rel0 = 0.0;
+        int nfwd = 1, nadj = 2, it = 0;
+        bool broke = false;
+        if (use_graph) {
+            // the iterations run on the device; the host waits once for the window
+            if (!graph.exec) {
+                SweepArgs ag = a;
+                ag.shot0_dev = shot0_dev;
+                const CgVectors v{m_inout, p, s, r, q, qq, pp, ss, sz, minv, state, nd, n, lambda};
+                rc = build_cg_graph(graph, ag, K, nsm, transform, v);
+                if (rc != LSM_OK) return rc;
+            }
+            LSM_CHECK(cg_loop_setup(state, shot0_dev, start, max_iter, cg_tol, st));
+            LSM_CHECK(cudaGraphLaunch(graph.exec, st));
+            LSM_CHECK(cudaMemcpyAsync(&hs, state, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+            LSM_CHECK(cudaStreamSynchronize(st));
+            it = hs.iter;
+            rel0 = hs.rel0;
+            rel = hs.rel;
+            broke = hs.breakdown != 0;
+            nfwd += it;
+            nadj += it;
+            count_launch(1 + graph.body_launches * it);
+        } else {
         LSM_CHECK(cudaMemcpyAsync(&hs, state, sizeof(CgState), cudaMemcpyDeviceToHost, st));
         LSM_CHECK(cudaStreamSynchronize(st));
         const double bnorm = std::sqrt(hs.bb);
-        double rel = bnorm > 0.0 ? std::sqrt(hs.ss[gi]) / bnorm : 0.0;
-        const double rel0 = rel;
-        int nfwd = 1, nadj = 2, it = 0;
-        bool broke = hs.breakdown != 0;
+        rel = bnorm > 0.0 ? std::sqrt(hs.ss[gi]) / bnorm : 0.0;
+        rel0 = rel;
+        broke = hs.breakdown != 0;
         while (!broke && it < max_iter && !(rel <= cg_tol)) {
             // q = A_k p ; alpha ; m += alpha p ; r -= alpha q
             LSM_CHECK(run_forward(a, start, K, p, q, nsm, st, transform));
@@ -756,6 +874,7 @@ int rls_window_solve_ex(const lsm_grid* grid, const float* slowness, const lsm_f
             LSM_CHECK(cudaStreamSynchronize(st));
             broke = hs.breakdown != 0;
             rel = bnorm > 0.0 ? std::sqrt(hs.ss[gi]) / bnorm : 0.0;
+        }
         }
         const auto t1 = std::chrono::steady_clock::now();
         const int idx = k - first_window;

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kRedThreads) update_mr_kernel(float* __restric
     const double qq = sum_partials(qq_part, nred, sh);
     const double pp = sum_partials(pp_part, nred, sh);
     const double delta = qq + lam * pp;
-    const double gamma = st->gamma[gi];
+    const double gamma = st->gamma[gi < 0 ? st->gi : gi];
     const bool bad = !(delta > 0.0) || !isfinite(delta) || !isfinite(gamma);
     const double alpha = bad ? 0.0 : gamma / delta;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -160,6 +160,10 @@ __global__ void __launch_bounds__(kRedThreads) update_p_kernel(float* __restrict
                                                            double* __restrict__ pp_part, const float* __restrict__ minv,
                                                            const double* __restrict__ sz_part) {
     __shared__ double sh[40];
+    if (gi_old < 0) {  // device-driven loop: slots from the state (cg_loop_test flips them afterwards)
+        gi_old = st->gi;
+        gi_new = gi_old ^ 1;
+    }
     const double ssum = sum_partials(ss_part, nred, sh);
     const double gnew = minv ? sum_partials(sz_part, nred, sh) : ssum;
     const double gold = first ? 1.0 : st->gamma[gi_old];
@@ -257,7 +261,36 @@ __global__ void zero_state_kernel(CgState* st) {
         st->alpha = st->beta = st->delta = st->bb = 0.0;
         st->ss[0] = st->ss[1] = 0.0;
         st->breakdown = 0;
+        st->gi = 0;
+        st->iter = st->max_iter = 0;
+        st->tol = st->rel0 = st->rel = 0.0;
     }
+}
+
+__global__ void loop_setup_kernel(CgState* st, int* shot0_dev, int shot0, int max_iter, double tol) {
+    if (threadIdx.x == 0) {
+        st->gi = 0;
+        st->iter = 0;
+        st->max_iter = max_iter;
+        st->tol = tol;
+        *shot0_dev = shot0;
+    }
+}
+
+// The stopping test of the window loop (same order and arithmetic as the host-driven loop):
+// after an iteration the new gamma slot becomes current; rel = sqrt(ss[gi]) / sqrt(bb).
+__global__ void loop_test_kernel(CgState* st, cudaGraphConditionalHandle handle, int advance) {
+    if (threadIdx.x != 0) return;
+    if (advance) {
+        st->gi ^= 1;
+        st->iter += 1;
+    }
+    const double bnorm = sqrt(st->bb);
+    const double rel = bnorm > 0.0 ? sqrt(st->ss[st->gi]) / bnorm : 0.0;
+    st->rel = rel;
+    if (!advance) st->rel0 = rel;
+    const bool cont = st->breakdown == 0 && st->iter < st->max_iter && !(rel <= st->tol);
+    cudaGraphSetConditional(handle, cont ? 1u : 0u);
 }
 
 // ------------------------------------------------------------------ launchers
@@ -317,6 +350,30 @@ cudaError_t cg_zero_state(CgState* state, cudaStream_t st) {
     zero_state_kernel<<<1, 32, 0, st>>>(state);
     count_launch();
     return cudaGetLastError();
+}
+
+cudaError_t cg_loop_setup(CgState* state, int* shot0_dev, int shot0, int max_iter, double tol, cudaStream_t st) {
+    ProfScope prof_(KC_VECTOR, st);
+    loop_setup_kernel<<<1, 32, 0, st>>>(state, shot0_dev, shot0, max_iter, tol);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t cg_loop_test(CgState* state, cudaGraphConditionalHandle handle, int advance, cudaStream_t st) {
+    ProfScope prof_(KC_VECTOR, st);
+    loop_test_kernel<<<1, 32, 0, st>>>(state, handle, advance);
+    count_launch();
+    return cudaGetLastError();
+}
+
+void cg_loop_test_node_params(cudaKernelNodeParams* kp, void** args) {
+    *kp = cudaKernelNodeParams{};
+    kp->func = reinterpret_cast<void*>(loop_test_kernel);
+    kp->gridDim = dim3(1);
+    kp->blockDim = dim3(32);
+    kp->sharedMemBytes = 0;
+    kp->kernelParams = args;
+    kp->extra = nullptr;
 }
 
 cudaError_t cg_illumination(const float2* S, int rows, int n, float* illum, float* block_max, cudaStream_t st) {

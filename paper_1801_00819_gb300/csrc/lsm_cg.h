@@ -16,7 +16,12 @@ struct CgState {
     double bb;        // ||A_k^T d_k||^2
     double ss[2];     // ||s||^2 matching gamma's slots (the stopping rule's numerator)
     int breakdown;
-    int pad;
+    // device-driven iteration loop (CUDA-graph CG): slot of the current gamma, iterations done,
+    // iteration limit, tolerance, and the stopping-rule ratios before the first / after the last
+    // iteration
+    int gi;
+    int iter, max_iter;
+    double tol, rel0, rel;
 };
 
 cudaError_t cg_reduce_image(const float* part, int nparts, int n, const float* m, float lam, int acc, float* out,
@@ -36,6 +41,17 @@ cudaError_t cg_illumination(const float2* S, int rows, int n, float* illum, floa
 cudaError_t cg_precond_finalize(const float* illum, int n, const float* block_max, double eps, float* minv,
                                 cudaStream_t st);
 cudaError_t cg_store_sum(const double* part, CgState* state, cudaStream_t st);
+
+// Device-driven CG loop.  gi = -1 in cg_update_mr / cg_update_p means "the slot in state->gi"
+// (cg_update_p then writes slot state->gi ^ 1); cg_loop_setup resets the loop counters and stores
+// the window's first shot for the sweeps' shot0_dev; cg_loop_test (one thread) advances the loop
+// when `advance` is set (flips state->gi, counts the iteration), evaluates the stopping rule
+// ||s|| / ||A_k^T d_k|| <= tol, the iteration limit and the breakdown flag, and sets the conditional
+// handle of the enclosing WHILE node to 1 to continue or 0 to stop.
+cudaError_t cg_loop_setup(CgState* state, int* shot0_dev, int shot0, int max_iter, double tol, cudaStream_t st);
+cudaError_t cg_loop_test(CgState* state, cudaGraphConditionalHandle handle, int advance, cudaStream_t st);
+// kernel-node parameters of cg_loop_test for explicit graph construction (args must outlive the call)
+void cg_loop_test_node_params(cudaKernelNodeParams* kp, void** args);
 cudaError_t cg_zero_state(CgState* state, cudaStream_t st);
 
 }  // namespace lsm

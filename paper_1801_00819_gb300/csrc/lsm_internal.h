@@ -30,6 +30,8 @@ struct SweepArgs {
     float2* dout;                  // forward output [nshots][nw][nrec]
     const float* m;                // forward model [nz][nx]
     float* part;                   // adjoint per-block partial images [grid][nz][nx]
+    const int* shot0_dev;          // if set, shot0 is read from this device int (graph-replayed
+                                   // CG iterations, whose window start changes between launches)
 };
 
 // Arguments of the gradient kernel (lsm_grad.cuh) over the items of shots [shot0, shot0+nshots).

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(sweep_max_threads<V>()) sweep_kernel(const Swe
     const int nslots = w_last - w_first + 1;  // <= a.wslots
     const int iw = ok ? item / a.nshots : w_first;
     const int ishot = ok ? item - iw * a.nshots : 0;
-    const int shot = a.shot0 + ishot;
+    const int shot = (a.shot0_dev ? __ldg(a.shot0_dev) : a.shot0) + ishot;
     const int slot = shot % a.ring;
     const int wslot = iw - w_first;
     const int nz = a.nz;

@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(224, 2) tc_sweep_kernel(const SweepArgs a) {
     const bool ok = item < nitems;
     const int iw = ok ? item / a.nshots : 0;
     const int ishot = ok ? item - iw * a.nshots : 0;
-    const int shot = a.shot0 + ishot;
+    const int shot = (a.shot0_dev ? __ldg(a.shot0_dev) : a.shot0) + ishot;
     const int slot = shot % a.ring;
     const int nz = a.nz;
 

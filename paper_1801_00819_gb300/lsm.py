@@ -66,10 +66,11 @@ class lsm_freqs(ctypes.Structure):
 
 
 class lsm_solve_options(ctypes.Structure):
-    _fields_ = [("preconditioner", ctypes.c_int), ("precond_eps", ctypes.c_double), ("transform", ctypes.c_int)]
+    _fields_ = [("preconditioner", ctypes.c_int), ("precond_eps", ctypes.c_double), ("transform", ctypes.c_int),
+                ("cuda_graph", ctypes.c_int)]
 
 
-def _options(preconditioner=None, precond_eps=1e-2, transform="fft"):
+def _options(preconditioner=None, precond_eps=1e-2, transform="fft", cuda_graph=False):
     if transform not in TRANSFORMS:
         raise ValueError(f"unknown transform {transform!r}")
     if preconditioner is None:
@@ -78,7 +79,7 @@ def _options(preconditioner=None, precond_eps=1e-2, transform="fft"):
         pc = LSM_PRECOND_ILLUMINATION
     else:
         raise ValueError(f"unknown preconditioner {preconditioner!r}")
-    return lsm_solve_options(pc, float(precond_eps), TRANSFORMS[transform])
+    return lsm_solve_options(pc, float(precond_eps), TRANSFORMS[transform], 1 if cuda_graph else 0)
 
 
 class lsm_line(ctypes.Structure):
@@ -313,11 +314,13 @@ def lsm_born_gradient(grid, slowness, sref, freqs, geom, m, g, d_out, grad_m, gr
 
 def rls_window_solve(grid, slowness, freqs, geom, d, lam, K, slide, cg_tol, max_iter, m_inout, workspace,
                      first_window=0, n_windows=0, stream=None, raise_on_breakdown=True, preconditioner=None,
-                     precond_eps=1e-2, transform="fft"):
+                     precond_eps=1e-2, transform="fft", cuda_graph=False):
     """Sliding-window CG solve; returns (status, [stats dicts]).  m_inout is updated in place.
 
-    preconditioner=None calls rls_window_solve; "illumination" calls rls_window_solve_ex with the
-    diagonal source-illumination preconditioner (stabiliser precond_eps times its maximum).
+    With the defaults this calls rls_window_solve; otherwise rls_window_solve_ex with the options:
+    preconditioner="illumination" (diagonal source-illumination preconditioner, stabiliser
+    precond_eps times its maximum), a tensor-core `transform`, or cuda_graph=True (each window's CG
+    iterations replayed as one CUDA graph with a device-side stopping test).
     """
     lib = load_library()
     nwin = lib.lsm_num_windows(int(geom.c.ns), int(K), int(slide))
@@ -326,10 +329,10 @@ def rls_window_solve(grid, slowness, freqs, geom, d, lam, K, slide, cg_tol, max_
     args = (ctypes.byref(grid.c), _ptr(slowness), ctypes.byref(freqs.c), ctypes.byref(geom.c), _ptr(d), float(lam),
             int(K), int(slide), float(cg_tol), int(max_iter), int(first_window), int(n_windows), _ptr(m_inout), stats,
             cap, _ptr(workspace), _nbytes(workspace), _stream(stream))
-    if preconditioner is None and transform == "fft":
+    if preconditioner is None and transform == "fft" and not cuda_graph:
         st = lib.rls_window_solve(*args)
     else:
-        opts = _options(preconditioner, precond_eps, transform)
+        opts = _options(preconditioner, precond_eps, transform, cuda_graph)
         st = lib.rls_window_solve_ex(*args, ctypes.byref(opts))
     last = nwin if n_windows <= 0 else min(nwin, first_window + n_windows)
     out = [stats[i].as_dict() for i in range(max(0, last - first_window))]
@@ -347,7 +350,8 @@ class LineProblem:
         self.cg_tol, self.max_iter, self.m_inout, self.workspace, self.stream = cg_tol, max_iter, m_inout, workspace, stream
 
 
-def rls_multi_line_solve(problems, preconditioner=None, precond_eps=1e-2, raise_on_error=True, transform="fft"):
+def rls_multi_line_solve(problems, preconditioner=None, precond_eps=1e-2, raise_on_error=True, transform="fft",
+                         cuda_graph=False):
     """Solve several LineProblems concurrently; returns ([status], [[stats dicts]])."""
     lib = load_library()
     n = len(problems)
@@ -361,7 +365,7 @@ def rls_multi_line_solve(problems, preconditioner=None, precond_eps=1e-2, raise_
                           int(pr.slide), float(pr.cg_tol), int(pr.max_iter), _ptr(pr.m_inout),
                           ctypes.cast(stats, ctypes.POINTER(lsm_window_stats)), nwin, _ptr(pr.workspace),
                           _nbytes(pr.workspace), _stream(pr.stream), 0)
-    opts = ctypes.byref(_options(preconditioner, precond_eps, transform))
+    opts = ctypes.byref(_options(preconditioner, precond_eps, transform, cuda_graph))
     st = lib.rls_multi_line_solve(arr, n, opts)
     statuses = [int(arr[i].status) for i in range(n)]
     out = [[keep[i][0][k].as_dict() for k in range(keep[i][1])] for i in range(n)]
