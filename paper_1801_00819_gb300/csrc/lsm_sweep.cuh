@@ -87,16 +87,29 @@ __device__ __forceinline__ void step_down_adjoint(float2 (&v)[V], const Twiddles
 template <int V>
 constexpr int sweep_max_threads() { return V >= 24 ? 256 : 512; }
 
+// Image rows of the adjoint: each warp writes SPW rows per depth (its items' imaging terms; with
+// more than two items per warp they are first summed pairwise by shuffles), at a row stride of
+// SLAB floats that puts a warp's two rows on different banks.
+template <int N, int V>
+struct ImageRows {
+    static constexpr int T = Plan<N, V>::T;
+    static constexpr int IPW = 32 / T;
+    static constexpr int SPW = IPW >= 2 ? 2 : 1;
+    static constexpr int SLAB = N + (SPW > 1 ? (T >= 4 ? T : 4) : 0);
+    static_assert(SLAB % 4 == 0, "image rows are summed as float4");
+};
+
 // Bytes of dynamic shared memory for a block of `warps` warps whose items span at most `wslots`
 // frequencies (mirrored on the host by sweep_shape): per-item exchange buffers, the block's
 // double-buffered staging of [wslots][Phi row, D row] plus one model row, and the adjoint's
-// double-buffered per-warp image rows.
+// double-buffered image rows.
 template <int N, int V>
 constexpr size_t sweep_smem_bytes(int warps, int wslots, bool adjoint) {
+    using IR = ImageRows<N, V>;
     return (size_t)Plan<N, V>::TAB * sizeof(float2) +
            (size_t)warps * (32 / Plan<N, V>::T) * Plan<N, V>::BUF * sizeof(float2) +
            2 * ((size_t)wslots * 2 * N * sizeof(float2) + (size_t)N * sizeof(float)) +
-           (adjoint ? (size_t)2 * warps * N * sizeof(float) : 0);
+           (adjoint ? (size_t)2 * warps * IR::SPW * IR::SLAB * sizeof(float) : 0);
 }
 
 template <int N, int V, int MODE>
@@ -133,7 +146,7 @@ __global__ void __launch_bounds__(sweep_max_threads<V>()) sweep_kernel(const Swe
     float2* stage = smem + ipb * P::BUF;
     const int stage_buf = a.wslots * 2 * N;  // float2 per staging buffer (coefficients)
     float* mstage = reinterpret_cast<float*>(stage + 2 * stage_buf);  // [2][N]
-    float* img = mstage + 2 * N;                                        // [2][nwarps][N]
+    float* img = mstage + 2 * N;                                        // [2][nwarps * SPW][SLAB]
 
     Twiddles<N, V> tw;
     init_twiddles<N, V>(tw, t, tab);
@@ -208,23 +221,24 @@ __global__ void __launch_bounds__(sweep_max_threads<V>()) sweep_kernel(const Swe
             for (int r = 0; r < V; ++r) v[r] = buf[P::phys(P::xpos(t, r))];
         }
         float* part = a.part + (size_t)blockIdx.x * nz * N;
-        // s holds S_j; the row of depth j+1 is requested right after imaging depth j so that
-        // its HBM latency hides behind the propagation step
+        // s holds S_j; the row of depth j+1 is requested after the image rows of depth j are
+        // summed, right before the propagation step that hides its HBM latency
         float2 s[V];
         load_row<N, V>(s, Sitem, t, ok);
         for (int j = 0; j < nz; ++j) {
             float c[V];
 #pragma unroll
             for (int r = 0; r < V; ++r) c[r] = fmaf(s[r].x, v[r].x, s[r].y * v[r].y);
-            if (j + 1 < nz) load_row<N, V>(s, Sitem + (size_t)(j + 1) * N, t, ok);
-            // sum the items of this warp (lanes with equal t hold equal x)
+            using IR = ImageRows<N, V>;
+            // with more than two items per warp, sum the items of equal parity (lanes with equal
+            // t hold equal x); the two remaining groups write one image row each
 #pragma unroll
-            for (int off = T; off < 32; off <<= 1) {
+            for (int off = 2 * T; off < 32; off <<= 1) {
 #pragma unroll
                 for (int r = 0; r < V; ++r) c[r] += __shfl_xor_sync(0xffffffffu, c[r], off);
             }
-            float* slab = img + ((size_t)(j & 1) * nwarps + warp) * N;
-            if (sub == 0) {
+            if (sub < IR::SPW) {
+                float* slab = img + ((size_t)(j & 1) * nwarps * IR::SPW + warp * IR::SPW + sub) * IR::SLAB;
 #pragma unroll
                 for (int r = 0; r < V; ++r) slab[P::xpos(t, r)] = c[r];
             }
@@ -232,14 +246,27 @@ __global__ void __launch_bounds__(sweep_max_threads<V>()) sweep_kernel(const Swe
             __syncthreads();  // image rows of depth j and staged rows of depth j are visible
             if (j + 2 < nz) stage_rows(j + 1, (j + 1) & 1, false);
             {
-                const float* rows = img + (size_t)(j & 1) * nwarps * N;
-                for (int x = threadIdx.x; x < N; x += blockDim.x) {
-                    float acc = 0.f;
-                    for (int w = 0; w < nwarps; ++w) acc += rows[w * N + x];
-                    part[(size_t)j * N + x] = acc;
+                // the block's partial row: the image rows summed in a fixed order, four columns a thread
+                const int nslab = nwarps * IR::SPW;
+                const float4* rows4 = reinterpret_cast<const float4*>(img + (size_t)(j & 1) * nslab * IR::SLAB);
+                float4* prow = reinterpret_cast<float4*>(part + (size_t)j * N);
+                for (int x4 = threadIdx.x; x4 < N / 4; x4 += blockDim.x) {
+                    float4 acc = rows4[x4];
+                    for (int w = 1; w < nslab; ++w) {
+                        const float4 u4 = rows4[w * (IR::SLAB / 4) + x4];
+                        acc.x += u4.x;
+                        acc.y += u4.y;
+                        acc.z += u4.z;
+                        acc.w += u4.w;
+                    }
+                    prow[x4] = acc;
                 }
             }
-            if (j + 1 < nz) step_down_adjoint<N, V>(v, tw, buf, t, phi_of(j & 1), dss_of(j & 1));
+            if (j + 1 < nz) {
+                // S_{j+1} is requested here so that its HBM latency hides behind the propagation step
+                load_row<N, V>(s, Sitem + (size_t)(j + 1) * N, t, ok);
+                step_down_adjoint<N, V>(v, tw, buf, t, phi_of(j & 1), dss_of(j & 1));
+            }
         }
     } else {  // MODE_FORWARD
 #pragma unroll
