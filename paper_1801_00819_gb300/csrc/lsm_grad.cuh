@@ -227,16 +227,20 @@ __global__ void __launch_bounds__(256) gradient_kernel(const GradArgs a) {
             }
             __syncthreads();
             {
-                const float* rows_m = img + (size_t)(b * 2 + 0) * nwarps * N;
-                const float* rows_s = img + (size_t)(b * 2 + 1) * nwarps * N;
-                for (int x = threadIdx.x; x < N; x += blockDim.x) {
-                    float am = 0.f, as = 0.f;
-                    for (int w2 = 0; w2 < nwarps; ++w2) {
-                        am += rows_m[w2 * N + x];
-                        as += rows_s[w2 * N + x];
+                // the block's partial rows: the warps' rows summed in warp order, four columns a thread
+                const float4* rows_m = reinterpret_cast<const float4*>(img + (size_t)(b * 2 + 0) * nwarps * N);
+                const float4* rows_s = reinterpret_cast<const float4*>(img + (size_t)(b * 2 + 1) * nwarps * N);
+                float4* pm = reinterpret_cast<float4*>(a.part_m + ((size_t)blockIdx.x * nz + j) * N);
+                float4* ps = reinterpret_cast<float4*>(a.part_s + ((size_t)blockIdx.x * nz + j) * N);
+                for (int x4 = threadIdx.x; x4 < N / 4; x4 += blockDim.x) {
+                    float4 am = rows_m[x4], as = rows_s[x4];
+                    for (int w2 = 1; w2 < nwarps; ++w2) {
+                        const float4 um = rows_m[w2 * (N / 4) + x4], us = rows_s[w2 * (N / 4) + x4];
+                        am.x += um.x; am.y += um.y; am.z += um.z; am.w += um.w;
+                        as.x += us.x; as.y += us.y; as.z += us.z; as.w += us.w;
                     }
-                    a.part_m[((size_t)blockIdx.x * nz + j) * N + x] = am;
-                    a.part_s[((size_t)blockIdx.x * nz + j) * N + x] = as;
+                    pm[x4] = am;
+                    ps[x4] = as;
                 }
             }
         }

@@ -99,16 +99,23 @@ struct ImageRows {
     static_assert(SLAB % 4 == 0, "image rows are summed as float4");
 };
 
+// Depth rows per staging buffer: the source sweep stages the coefficient rows of two depth steps at
+// a time, so its blocks meet at a barrier every other step (0.91 -> 0.86 ms on a 512 x 256 window
+// of 16 shots x 128 frequencies); the forward sweep measured no gain from it, and the adjoint sums
+// its image rows across the block at every depth.
+constexpr int stage_depths(int mode) { return mode == MODE_SOURCE ? 2 : 1; }
+
 // Bytes of dynamic shared memory for a block of `warps` warps whose items span at most `wslots`
 // frequencies (mirrored on the host by sweep_shape): per-item exchange buffers, the block's
-// double-buffered staging of [wslots][Phi row, D row] plus one model row, and the adjoint's
-// double-buffered image rows.
+// double-buffered staging of [depth steps][wslots][Phi row, D row] plus one model row per step,
+// and the adjoint's double-buffered image rows.
 template <int N, int V>
-constexpr size_t sweep_smem_bytes(int warps, int wslots, bool adjoint) {
+constexpr size_t sweep_smem_bytes(int warps, int wslots, int mode) {
+    const bool adjoint = mode == MODE_ADJOINT;
     using IR = ImageRows<N, V>;
     return (size_t)Plan<N, V>::TAB * sizeof(float2) +
            (size_t)warps * (32 / Plan<N, V>::T) * Plan<N, V>::BUF * sizeof(float2) +
-           2 * ((size_t)wslots * 2 * N * sizeof(float2) + (size_t)N * sizeof(float)) +
+           2 * (size_t)stage_depths(mode) * ((size_t)wslots * 2 * N * sizeof(float2) + (size_t)N * sizeof(float)) +
            (adjoint ? (size_t)2 * warps * IR::SPW * IR::SLAB * sizeof(float) : 0);
 }
 
@@ -141,12 +148,14 @@ __global__ void __launch_bounds__(sweep_max_threads<V>()) sweep_kernel(const Swe
     const int wslot = iw - w_first;
     const int nz = a.nz;
 
-    // shared memory: exchange buffers | staging [2][wslots][2][N] float2 + [2][N] float | images
+    // shared memory: exchange buffers | staging [2][DEP][wslots][2][N] float2 + [2][DEP][N] float |
+    // images.  Depth step k (0 .. nz-2) reads staging buffer (k / DEP) % 2, slot k % DEP.
+    constexpr int DEP = stage_depths(MODE);
     float2* buf = smem + (warp * IPW + sub) * P::BUF;
     float2* stage = smem + ipb * P::BUF;
-    const int stage_buf = a.wslots * 2 * N;  // float2 per staging buffer (coefficients)
-    float* mstage = reinterpret_cast<float*>(stage + 2 * stage_buf);  // [2][N]
-    float* img = mstage + 2 * N;                                        // [2][nwarps * SPW][SLAB]
+    const int stage_buf = a.wslots * 2 * N;  // float2 per staging slot (coefficients)
+    float* mstage = reinterpret_cast<float*>(stage + 2 * DEP * stage_buf);  // [2][DEP][N]
+    float* img = mstage + 2 * DEP * N;                                        // [2][nwarps * SPW][SLAB]
 
     Twiddles<N, V> tw;
     init_twiddles<N, V>(tw, t, tab);
@@ -156,7 +165,7 @@ __global__ void __launch_bounds__(sweep_max_threads<V>()) sweep_kernel(const Swe
     float2 v[V];
 
     // the whole block stages the Phi and D rows of depth `row` for its frequencies into
-    // buffer b (and the model row when asked), as one cp.async group per thread
+    // staging slot b (and the model row when asked), as one cp.async group per thread
     auto stage_rows = [&](int row, int b, bool with_model) {
         constexpr int CH = N / 2;  // 16-byte chunks per complex row
         float2* dst = stage + b * stage_buf;
@@ -177,13 +186,15 @@ __global__ void __launch_bounds__(sweep_max_threads<V>()) sweep_kernel(const Swe
     };
     auto phi_of = [&](int b) -> const float2* { return stage + b * stage_buf + (wslot * 2) * N; };
     auto dss_of = [&](int b) -> const float2* { return stage + b * stage_buf + (wslot * 2 + 1) * N; };
+    auto slot_of = [&](int k) { return ((k / DEP) & 1) * DEP + k % DEP; };  // staging slot of step k
 
     if constexpr (MODE == MODE_SOURCE) {
         const int xs = ok ? __ldg(a.src_ix + shot) : -1;
         const float2 w = ok ? __ldg(a.wavelet + iw) : make_float2(0.f, 0.f);
 #pragma unroll
         for (int r = 0; r < V; ++r) v[r] = (P::xpos(t, r) == xs) ? w : make_float2(0.f, 0.f);
-        if (nz > 1) stage_rows(0, 0, false);
+        // step k propagates with row k; steps are staged DEP at a time, one group ahead
+        for (int k = 0; k < DEP && k + 1 < nz; ++k) stage_rows(k, slot_of(k), false);
         for (int j = 0; j < nz; ++j) {
             if (ok) {
                 float2* row = Sitem + (size_t)j * N;
@@ -191,10 +202,12 @@ __global__ void __launch_bounds__(sweep_max_threads<V>()) sweep_kernel(const Swe
                 for (int r = 0; r < V; ++r) __stcs(row + P::xpos(t, r), v[r]);
             }
             if (j + 1 < nz) {
-                cp_async_wait_all();
-                __syncthreads();
-                if (j + 2 < nz) stage_rows(j + 1, (j + 1) & 1, false);
-                step_down<N, V>(v, tw, buf, t, phi_of(j & 1), dss_of(j & 1));
+                if (j % DEP == 0) {
+                    cp_async_wait_all();
+                    __syncthreads();
+                    for (int k = j + DEP; k < j + 2 * DEP && k + 1 < nz; ++k) stage_rows(k, slot_of(k), false);
+                }
+                step_down<N, V>(v, tw, buf, t, phi_of(slot_of(j)), dss_of(slot_of(j)));
             }
         }
     } else if constexpr (MODE == MODE_ADJOINT) {
@@ -272,25 +285,31 @@ __global__ void __launch_bounds__(sweep_max_threads<V>()) sweep_kernel(const Swe
 #pragma unroll
         for (int r = 0; r < V; ++r) v[r] = make_float2(0.f, 0.f);
         // step k (k = 0 .. nz-2) propagates with row j = nz-2-k and then adds model row j, both
-        // from buffer k & 1; the deepest model row is staged on its own into buffer 1 first
+        // from staging slot slot_of(k); the deepest model row is staged on its own into the
+        // first slot of buffer 1, which the steps of that buffer only overwrite after a barrier
         for (int c = threadIdx.x; c < N / 4; c += blockDim.x)
-            cp_async16(mstage + N + 4 * c, a.m + (size_t)(nz - 1) * N + 4 * c);
+            cp_async16(mstage + DEP * N + 4 * c, a.m + (size_t)(nz - 1) * N + 4 * c);
         cp_async_commit();
-        if (nz > 1) stage_rows(nz - 2, 0, true);
+        for (int k = 0; k < DEP && k + 1 < nz; ++k) stage_rows(nz - 2 - k, slot_of(k), true);
         for (int j = nz - 1; j >= 0; --j) {
             // request S_j before propagating U_{j+1} so the load overlaps the step
             float2 s[V];
             load_row<N, V>(s, Sitem + (size_t)j * N, t, ok);
-            cp_async_wait_all();
-            __syncthreads();
+            const int k = nz - 2 - j;  // -1 for the deepest row, which is not propagated
+            if (k < 0 || k % DEP == 0) {
+                cp_async_wait_all();
+                __syncthreads();
+            }
             const float* mrow;
-            if (j + 1 < nz) {
-                const int k = nz - 2 - j;
-                if (j >= 1) stage_rows(j - 1, (k + 1) & 1, true);
-                step_down<N, V>(v, tw, buf, t, phi_of(k & 1), dss_of(k & 1));
-                mrow = mstage + (k & 1) * N;
+            if (k >= 0) {
+                if (k % DEP == 0) {
+                    for (int k2 = k + DEP; k2 < k + 2 * DEP && k2 + 1 < nz; ++k2)
+                        stage_rows(nz - 2 - k2, slot_of(k2), true);
+                }
+                step_down<N, V>(v, tw, buf, t, phi_of(slot_of(k)), dss_of(slot_of(k)));
+                mrow = mstage + slot_of(k) * N;
             } else {
-                mrow = mstage + N;
+                mrow = mstage + DEP * N;
             }
 #pragma unroll
             for (int r = 0; r < V; ++r) {
@@ -387,7 +406,7 @@ struct Dispatch {
                                         227 * 1024);
         });
         if (e != cudaSuccess) return e;
-        if (sh.smem != sweep_smem_bytes<N, V>(sh.warps, a.wslots, MODE == MODE_ADJOINT)) return cudaErrorInvalidValue;
+        if (sh.smem != sweep_smem_bytes<N, V>(sh.warps, a.wslots, MODE)) return cudaErrorInvalidValue;
         ProfScope prof_(MODE == MODE_SOURCE ? KC_SOURCE : MODE == MODE_ADJOINT ? KC_ADJOINT : KC_FORWARD, st);
         sweep_kernel<N, V, MODE><<<sh.blocks, sh.warps * 32, sh.smem, st>>>(a);
         count_launch();
@@ -536,7 +555,7 @@ struct Dispatch {
     }                                                                                             \
     static int max_warps_##NN(int mode) { return Dispatch<NN>::max_warps(mode); }                 \
     static size_t smem_##NN(int mode, int warps, int wslots) {                                    \
-        return sweep_smem_bytes<NN, Dispatch<NN>::V>(warps, wslots, mode == MODE_ADJOINT);        \
+        return sweep_smem_bytes<NN, Dispatch<NN>::V>(warps, wslots, mode);        \
     }                                                                                             \
     static cudaError_t tables_grad_##NN(const TableArgs& a, cudaStream_t st) {                    \
         return Dispatch<NN>::tables_grad(a, st);                                                  \

@@ -465,11 +465,16 @@ __global__ void __launch_bounds__(224, 2) tc_sweep_kernel(const SweepArgs a) {
                     slab[tc_xpos<N>(lane, j, e)] = fmaf(s.x[j][e].x, u.x[j][e].x, s.x[j][e].y * u.x[j][e].y);
             __syncthreads();
             {
-                const float* rows = img + (size_t)(jz & 1) * nwarps * N;
-                for (int x = threadIdx.x; x < N; x += blockDim.x) {
-                    float acc = 0.f;
-                    for (int w2 = 0; w2 < nwarps; ++w2) acc += rows[w2 * N + x];
-                    part[(size_t)jz * N + x] = acc;
+                // the block's partial row: the warps' rows summed in warp order, four columns a thread
+                const float4* rows = reinterpret_cast<const float4*>(img + (size_t)(jz & 1) * nwarps * N);
+                float4* prow = reinterpret_cast<float4*>(part + (size_t)jz * N);
+                for (int x4 = threadIdx.x; x4 < N / 4; x4 += blockDim.x) {
+                    float4 acc = rows[x4];
+                    for (int w2 = 1; w2 < nwarps; ++w2) {
+                        const float4 u4 = rows[w2 * (N / 4) + x4];
+                        acc.x += u4.x; acc.y += u4.y; acc.z += u4.z; acc.w += u4.w;
+                    }
+                    prow[x4] = acc;
                 }
             }
             if (jz + 1 < nz) {

@@ -1,12 +1,14 @@
 """Run one window of A and A^T on a synthetic survey, for timing and profiling the sweep kernels.
 
-    python -m paper_1801_00819_gb300.sweep_case [--workload realistic|tiny] [--reps N]
+    python -m paper_1801_00819_gb300.sweep_case [--workload realistic|tiny] [--reps N] [--gradient]
 
 Prepares the workload's grid, velocity, geometry and frequencies on the device, random data for
 one window of K shots, then calls lsm_forward and lsm_adjoint through the C ABI `reps` times each
 (each call builds the coefficient tables, computes the window's source wavefields and runs one
 sweep).  Prints per-class kernel times from the library's event timing.  The inputs are random,
-so no modelling pass precedes the timed calls.
+so no modelling pass precedes the timed calls.  With --gradient it also calls lsm_born_gradient
+(d = A(s) m and the gradients for a random data-space gradient g) on the same window, with the
+reference slowness held at the row means of the model.
 """
 
 from __future__ import annotations
@@ -29,6 +31,7 @@ def main():
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--shots", type=int, default=0, help="shots per call (default: the window length)")
     ap.add_argument("--transform", default="fft", help="fft, dft_bf16x3, dft_fp16x3 or dft_bf16x1")
+    ap.add_argument("--gradient", action="store_true", help="also time lsm_born_gradient on the window")
     args = ap.parse_args()
 
     import torch
@@ -47,10 +50,18 @@ def main():
     img = torch.empty_like(m)
     out = torch.empty_like(d)
     ws = workspace(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, K, L.LSM_OP_ADJOINT))
+    if args.gradient:
+        ws_g = workspace(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, K, L.LSM_OP_GRADIENT))
+        sref = torch.as_tensor(np.asarray(sv.slowness, dtype=np.float64).mean(axis=1), device="cuda")
+        grad_m = torch.empty_like(m)
+        grad_s = torch.empty_like(m)
     L.lsm_profile_start()
     for _ in range(args.reps):
         L.lsm_forward(ds.grid, ds.slowness, ds.freqs, ds.geom, m, out, 0, K, ws, transform=args.transform)
         L.lsm_adjoint(ds.grid, ds.slowness, ds.freqs, ds.geom, d, img, 0, K, ws, transform=args.transform)
+        if args.gradient:
+            L.lsm_born_gradient(ds.grid, ds.slowness, sref, ds.freqs, ds.geom, m, d, out, grad_m, grad_s, 0, K,
+                                ws_g)
     torch.cuda.synchronize()
     prof = L.lsm_profile_stop()
     print(json.dumps({"workload": sv.name, "transform": args.transform, "K": K, "nw": sv.nw, "nz": sv.nz, "nx": sv.nx,
