@@ -529,11 +529,11 @@ def batching_arm(args):
             out.append(st)
         return out
 
-    def concurrent():
+    def concurrent(graph=False):
         for pr in lines:
             pr.m_inout.zero_()
         torch.cuda.synchronize()
-        _, st = lsm.rls_multi_line_solve(lines)
+        _, st = lsm.rls_multi_line_solve(lines, cuda_graph=graph)
         return st
 
     for _ in range(max(args.warmup, 1)):
@@ -543,6 +543,13 @@ def batching_arm(args):
     st_conc = [concurrent() for _ in range(args.steps)][-1]
     torch.cuda.synchronize()
     t_conc = (time.perf_counter() - t0) / args.steps
+    # the same concurrent solve with each window's CG iterations replayed as a CUDA graph
+    concurrent(graph=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st_graph = [concurrent(graph=True) for _ in range(args.steps)][-1]
+    torch.cuda.synchronize()
+    t_graph = (time.perf_counter() - t0) / args.steps
     t0 = time.perf_counter()
     st_seq = sequential()
     torch.cuda.synchronize()
@@ -560,7 +567,12 @@ def batching_arm(args):
            "timing": "host wall clock around each whole solve, GPU synchronised on both sides",
            "sequential_ms": round(1e3 * t_seq, 1), "concurrent_ms": round(1e3 * t_conc, 1),
            "speedup_concurrent_vs_sequential": round(t_seq / t_conc, 3),
-           "sequential_units_per_s": round(units_of(st_seq) / t_seq, 1)}
+           "sequential_units_per_s": round(units_of(st_seq) / t_seq, 1),
+           "concurrent_cuda_graph_ms": round(1e3 * t_graph, 1),
+           "concurrent_cuda_graph_units_per_s": round(units_of(st_graph) / t_graph, 1),
+           "speedup_concurrent_cuda_graph_vs_sequential": round(t_seq / t_graph, 3),
+           "cuda_graph_same_iterations": [[w["iters"] for w in st] for st in st_graph] ==
+                                         [[w["iters"] for w in st] for st in st_conc]}
     print(json.dumps(out), flush=True)
 
 
