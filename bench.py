@@ -173,11 +173,12 @@ def bytes_per_unit(nx, nrec, nz, K):
 
 def kernel_source_hash():
     """Hash of the sources the sweep kernels are compiled from (lsm_fft.cuh, lsm_sweep.cuh,
-    lsm_internal.h and the per-nx instantiation files)."""
+    lsm_async.cuh, lsm_internal.h and the per-nx instantiation files)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1801_00819_gb300", "csrc")
     names = sorted(n for n in os.listdir(csrc)
-                   if n in ("lsm_fft.cuh", "lsm_sweep.cuh", "lsm_internal.h") or n.startswith("sweep_n"))
+                   if n in ("lsm_fft.cuh", "lsm_sweep.cuh", "lsm_async.cuh", "lsm_internal.h")
+                   or n.startswith("sweep_n"))
     for name in names:
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(name.encode())

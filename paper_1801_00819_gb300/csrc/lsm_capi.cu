@@ -128,9 +128,8 @@ SweepShape gradient_shape(int nx, int nshots, int nw, int num_sms) {
     const int ipw = 32 / T;
     const int nitems = nshots * nw;
     const int warps_total = (nitems + ipw - 1) / ipw;
-    auto smem_of = [&](int w) {
-        return (size_t)w * ipw * (size_t)(nx + nx / 16) * sizeof(float2) + (size_t)4 * w * nx * sizeof(float);
-    };
+    auto wslots_of = [&](int w) { return std::min(nw, (w * ipw + nshots - 1) / nshots + 1); };
+    auto smem_of = [&](int w) { return ops->gradient_smem(w, wslots_of(w)); };
     int maxw = std::min(8, ops->gradient_max_warps());
     while (maxw > 1 && smem_of(maxw) > 227 * 1024) --maxw;
     int warps = (warps_total + num_sms - 1) / num_sms;
@@ -138,7 +137,7 @@ SweepShape gradient_shape(int nx, int nshots, int nw, int num_sms) {
     SweepShape s;
     s.warps = warps;
     s.blocks = (warps_total + warps - 1) / warps;
-    s.wslots = 0;
+    s.wslots = wslots_of(warps);
     s.smem = smem_of(warps);
     return s;
 }
@@ -644,6 +643,7 @@ int lsm_born_gradient(const lsm_grid* grid, const float* slowness, const double*
     ga.part_s = reinterpret_cast<float*>(ws + L.part_s);
     ga.dout = reinterpret_cast<float2*>(d_out);
     const SweepShape sh = gradient_shape(grid->nx, nshots, freqs->nw, nsm);
+    ga.wslots = sh.wslots;
     LSM_CHECK(launch_gradient(ga, sh, st));
     const int n = grid->nx * grid->nz;
     double* ssp = reinterpret_cast<double*>(ws + L.ss);

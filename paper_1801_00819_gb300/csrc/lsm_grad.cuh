@@ -10,30 +10,33 @@
 // down once and keeps only every `c`-th depth (checkpoints); phase 2 walks the depth segments from
 // the bottom, recomputes each segment's S and R rows from their checkpoints into a small per-item
 // buffer, and runs the U and mu recursions in registers.  Per-depth gradient rows are summed over
-// the block's items and written as block partials (reduced later in a fixed order).
+// the block's items and written as block partials (reduced later in a fixed order).  The Phi and D
+// rows of each depth are staged once per block (for the few frequencies its items span) into
+// double-buffered shared memory with cp.async, and both wavefields of a loop step read them there.
 #pragma once
 
+#include "lsm_async.cuh"
 #include "lsm_fft.cuh"
 #include "lsm_internal.h"
 
 namespace lsm {
 
-// generic one-step propagation in registers with coefficients read from the global tables
+// one propagation step in registers; phi and dss point at the staged rows in shared memory
 template <int N, int V, bool ADJ>
 __device__ __forceinline__ void grad_step(float2 (&v)[V], const Twiddles<N, V>& tw, float2* buf, int t,
                                           const float2* __restrict__ phi, const float2* __restrict__ dss) {
     constexpr int T = Plan<N, V>::T;
     if (ADJ) {
 #pragma unroll
-        for (int r = 0; r < V; ++r) v[r] = cmulc(v[r], __ldg(dss + Plan<N, V>::xpos(t, r)));
+        for (int r = 0; r < V; ++r) v[r] = cmulc(v[r], dss[Plan<N, V>::xpos(t, r)]);
     }
     fft_forward<N, V>(v, tw, buf, t);
 #pragma unroll
-    for (int r = 0; r < V; ++r) v[r] = ADJ ? cmulc(v[r], __ldg(phi + t + T * r)) : cmul(v[r], __ldg(phi + t + T * r));
+    for (int r = 0; r < V; ++r) v[r] = ADJ ? cmulc(v[r], phi[t + T * r]) : cmul(v[r], phi[t + T * r]);
     fft_inverse<N, V>(v, tw, buf, t);
     if (!ADJ) {
 #pragma unroll
-        for (int r = 0; r < V; ++r) v[r] = cmul(v[r], __ldg(dss + Plan<N, V>::xpos(t, r)));
+        for (int r = 0; r < V; ++r) v[r] = cmul(v[r], dss[Plan<N, V>::xpos(t, r)]);
     }
 }
 
@@ -53,11 +56,12 @@ __device__ __forceinline__ void grad_load(float2 (&v)[V], const float2* __restri
     for (int r = 0; r < V; ++r) v[r] = ok ? row[t + T * r] : make_float2(0.f, 0.f);
 }
 
-// dynamic shared memory: exchange buffers + [2 buffers][2 images][warps][N] floats
+// dynamic shared memory: exchange buffers + [2 buffers][2 images][warps][N] floats + staged
+// coefficient rows [2 buffers][wslots][Phi, D][N] float2 (mirrored on the host by gradient_shape)
 template <int N, int V>
-constexpr size_t gradient_smem_bytes(int warps) {
+constexpr size_t gradient_smem_bytes(int warps, int wslots) {
     return (size_t)warps * (32 / Plan<N, V>::T) * Plan<N, V>::BUF * sizeof(float2) +
-           (size_t)2 * 2 * warps * N * sizeof(float);
+           (size_t)2 * 2 * warps * N * sizeof(float) + (size_t)2 * wslots * 2 * N * sizeof(float2);
 }
 
 template <int N, int V>
@@ -78,7 +82,11 @@ __global__ void __launch_bounds__(256) gradient_kernel(const GradArgs a) {
     const int nitems = a.nshots * a.nw;
     const int item = blockIdx.x * ipb + warp * IPW + sub;
     const bool ok = item < nitems;
-    const int iw = ok ? item / a.nshots : 0;
+    // items are frequency-major: the block's items span frequencies w_first .. w_last
+    const int w_first = min(blockIdx.x * ipb, nitems - 1) / a.nshots;
+    const int w_last = (min((blockIdx.x + 1) * ipb, nitems) - 1) / a.nshots;
+    const int nslots = w_last - w_first + 1;  // <= a.wslots
+    const int iw = ok ? item / a.nshots : w_first;
     const int ishot = ok ? item - iw * a.nshots : 0;
     const int shot = a.shot0 + ishot;
     const int nz = a.nz;
@@ -86,12 +94,30 @@ __global__ void __launch_bounds__(256) gradient_kernel(const GradArgs a) {
     const int ncp = (nz + c - 1) / c;
     float2* buf = smem + (warp * IPW + sub) * P::BUF;
     float* img = reinterpret_cast<float*>(smem + ipb * P::BUF);  // [2][2][nwarps][N]
+    float2* stage = reinterpret_cast<float2*>(img + 4 * nwarps * N);  // [2][wslots][2][N]
+    const int stage_buf = a.wslots * 2 * N;
+    const int wslot = iw - w_first;
 
     Twiddles<N, V> tw;
     init_twiddles<N, V>(tw, t);
 
-    const float2* phi_w = a.phi + (size_t)iw * nz * N;
-    const float2* dss_w = a.dss + (size_t)iw * nz * N;
+    // the whole block stages the Phi and D rows of depth `row` for its frequencies into buffer b,
+    // one cp.async group per thread
+    auto stage_row = [&](int row, int b) {
+        constexpr int CH = N / 2;  // 16-byte chunks per complex row
+        float2* dst = stage + b * stage_buf;
+        for (int q = threadIdx.x; q < nslots * 2 * CH; q += blockDim.x) {
+            const int sl = q / (2 * CH);
+            const int rem = q - sl * 2 * CH;
+            const int which = rem / CH;
+            const int ch = rem - which * CH;
+            const float2* src = (which ? a.dss : a.phi) + ((size_t)(w_first + sl) * nz + row) * N + 2 * ch;
+            cp_async16(dst + (sl * 2 + which) * N + 2 * ch, src);
+        }
+        cp_async_commit();
+    };
+    auto phi_s = [&](int b) -> const float2* { return stage + b * stage_buf + (wslot * 2) * N; };
+    auto dss_s = [&](int b) -> const float2* { return stage + b * stage_buf + (wslot * 2 + 1) * N; };
     const size_t slot = ok ? (size_t)item : 0;
     float2* Sck = a.ckpt + slot * 2 * ncp * N;
     float2* Rck = Sck + (size_t)ncp * N;
@@ -126,14 +152,19 @@ __global__ void __launch_bounds__(256) gradient_kernel(const GradArgs a) {
 #pragma unroll
             for (int r = 0; r < V; ++r) R[r] = buf[P::phys(t + T * r)];
         }
+        // step j reads buffer j % 2; the rows of step j + 1 are staged while step j runs
+        if (nz > 1) stage_row(0, 0);
         for (int j = 0; j < nz; ++j) {
             if (j % c == 0) {
                 grad_store<N, V>(Sck + (size_t)(j / c) * N, S, t, ok);
                 grad_store<N, V>(Rck + (size_t)(j / c) * N, R, t, ok);
             }
             if (j + 1 < nz) {
-                grad_step<N, V, false>(S, tw, buf, t, phi_w + (size_t)j * N, dss_w + (size_t)j * N);
-                grad_step<N, V, true>(R, tw, buf, t, phi_w + (size_t)j * N, dss_w + (size_t)j * N);
+                cp_async_wait_all();
+                __syncthreads();  // rows of step j visible; every warp is done with step j - 1
+                if (j + 2 < nz) stage_row(j + 1, (j + 1) & 1);
+                grad_step<N, V, false>(S, tw, buf, t, phi_s(j & 1), dss_s(j & 1));
+                grad_step<N, V, true>(R, tw, buf, t, phi_s(j & 1), dss_s(j & 1));
             }
         }
     }
@@ -147,27 +178,53 @@ __global__ void __launch_bounds__(256) gradient_kernel(const GradArgs a) {
         const int j0 = seg * c;
         const int j1 = min(j0 + c, nz);
         {
-            // S rows j0 .. jmax (jmax = j1 when a deeper row exists, for S_{j+1} at j = j1 - 1)
+            // S rows j0 .. jmax (jmax = j1 when a deeper row exists, for S_{j+1} at j = j1 - 1);
+            // step j reads buffer (j - j0) % 2
             const int jmax = j1 < nz ? j1 : nz - 1;
             float2 S[V];
             grad_load<N, V>(S, Sck + (size_t)seg * N, t, ok);
+            __syncthreads();  // every warp is done with the staging buffers of the previous loop
+            if (j0 < jmax) stage_row(j0, 0);
             for (int j = j0; j <= jmax; ++j) {
                 grad_store<N, V>(Sseg + (size_t)(j - j0) * N, S, t, ok);
-                if (j < jmax) grad_step<N, V, false>(S, tw, buf, t, phi_w + (size_t)j * N, dss_w + (size_t)j * N);
+                if (j < jmax) {
+                    const int b = (j - j0) & 1;
+                    cp_async_wait_all();
+                    __syncthreads();
+                    if (j + 1 < jmax) stage_row(j + 1, b ^ 1);
+                    grad_step<N, V, false>(S, tw, buf, t, phi_s(b), dss_s(b));
+                }
             }
         }
         {
+            // R rows j0 .. j1 - 1
             float2 R[V];
             grad_load<N, V>(R, Rck + (size_t)seg * N, t, ok);
+            __syncthreads();
+            if (j0 + 1 < j1) stage_row(j0, 0);
             for (int j = j0; j < j1; ++j) {
                 grad_store<N, V>(Rseg + (size_t)(j - j0) * N, R, t, ok);
-                if (j + 1 < j1) grad_step<N, V, true>(R, tw, buf, t, phi_w + (size_t)j * N, dss_w + (size_t)j * N);
+                if (j + 1 < j1) {
+                    const int b = (j - j0) & 1;
+                    cp_async_wait_all();
+                    __syncthreads();
+                    if (j + 2 < j1) stage_row(j + 1, b ^ 1);
+                    grad_step<N, V, true>(R, tw, buf, t, phi_s(b), dss_s(b));
+                }
             }
         }
+        // phase 2 of the segment: row j of step j is in buffer (j1 - 1 - j) % 2; rows j1 - 1 and
+        // j1 - 2 are staged up front, and row j - 2 replaces row j once every warp is past step j
+        __syncthreads();
+        stage_row(j1 - 1, 0);
+        if (j1 - 2 >= j0) stage_row(j1 - 2, 1);
+        cp_async_wait_all();
+        __syncthreads();
         for (int j = j1 - 1; j >= j0; --j, ++depth_count) {
             const float* mrow = a.m + (size_t)j * N;
             // P_j U_{j+1} (zero at the deepest row)
-            if (j + 1 < nz) grad_step<N, V, false>(U, tw, buf, t, phi_w + (size_t)j * N, dss_w + (size_t)j * N);
+            const int bj = (j1 - 1 - j) & 1;
+            if (j + 1 < nz) grad_step<N, V, false>(U, tw, buf, t, phi_s(bj), dss_s(bj));
             float2 Rj[V];
             grad_load<N, V>(Rj, Rseg + (size_t)(j - j0) * N, t, ok);
             float gs[V], gm[V];
@@ -195,7 +252,7 @@ __global__ void __launch_bounds__(256) gradient_kernel(const GradArgs a) {
             for (int r = 0; r < V; ++r) gs[r] = -wdz * gs[r];
             // mu_j = m_j R_j + P_j^H mu_{j+1}
             if (j + 1 < nz) {
-                grad_step<N, V, true>(mu, tw, buf, t, phi_w + (size_t)j * N, dss_w + (size_t)j * N);
+                grad_step<N, V, true>(mu, tw, buf, t, phi_s(bj), dss_s(bj));
             } else {
 #pragma unroll
                 for (int r = 0; r < V; ++r) mu[r] = make_float2(0.f, 0.f);
@@ -225,7 +282,9 @@ __global__ void __launch_bounds__(256) gradient_kernel(const GradArgs a) {
                     slab_s[t + T * r] = ok ? gs[r] : 0.f;
                 }
             }
-            __syncthreads();
+            cp_async_wait_all();
+            __syncthreads();  // image rows visible; row j - 1 staged and visible; every warp is past step j
+            if (j - 2 >= j0) stage_row(j - 2, bj);
             {
                 // the block's partial rows: the warps' rows summed in warp order, four columns a thread
                 const float4* rows_m = reinterpret_cast<const float4*>(img + (size_t)(b * 2 + 0) * nwarps * N);

@@ -40,6 +40,7 @@ struct GradArgs {
     int shot0, nshots;
     int rec_identity;
     int ckpt_every;                // depth checkpoint stride of S and R
+    int wslots;                    // staging slots: most frequencies any block's items span
     float dz;
     const int* src_ix;
     const int* rec_ix;
@@ -97,6 +98,7 @@ struct NxOps {
     cudaError_t (*tables_natural)(const TableArgs& a, cudaStream_t st);
     cudaError_t (*tc_sweep)(int mode, int prec, const SweepArgs& a, const SweepShape& shape, cudaStream_t st);
     size_t (*tc_smem)(int mode, int warps);
+    size_t (*gradient_smem)(int warps, int wslots);
 };
 // The operations for nx, or nullptr when nx is not supported.
 const NxOps* nx_ops(int nx);

@@ -21,21 +21,13 @@
 //   MODE_FORWARD: U <- P_j U_{j+1} + S_j m_j from j = nz-1 up to 0; record U_0.
 #pragma once
 
+#include "lsm_async.cuh"
 #include "lsm_fft.cuh"
 #include "lsm_grad.cuh"
 #include "lsm_internal.h"
 #include "lsm_tc.cuh"
 
 namespace lsm {
-
-// ------------------------------------------------------------------ cp.async helpers
-
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // ------------------------------------------------------------------ one depth step
 
@@ -520,7 +512,7 @@ struct Dispatch {
                                             227 * 1024);
             });
             if (e != cudaSuccess) return e;
-            if (sh.smem != gradient_smem_bytes<N, VG>(sh.warps)) return cudaErrorInvalidValue;
+            if (sh.smem != gradient_smem_bytes<N, VG>(sh.warps, a.wslots)) return cudaErrorInvalidValue;
             ProfScope prof_(KC_GRADIENT, st);
             gradient_kernel<N, VG><<<sh.blocks, sh.warps * 32, sh.smem, st>>>(a);
             count_launch();
@@ -528,6 +520,11 @@ struct Dispatch {
         } else {
             return cudaErrorNotSupported;
         }
+    }
+
+    static size_t gradient_smem(int warps, int wslots) {
+        if constexpr (kGrad) return gradient_smem_bytes<N, VG>(warps, wslots);
+        else return 0;
     }
 
     static int gradient_max_warps() {
@@ -572,8 +569,11 @@ struct Dispatch {
         return Dispatch<NN>::tc_sweep(mode, prec, a, sh, st);                                     \
     }                                                                                             \
     static size_t tc_smem_##NN(int mode, int warps) { return Dispatch<NN>::tc_smem(mode, warps); } \
+    static size_t gradient_smem_##NN(int warps, int wslots) {                                     \
+        return Dispatch<NN>::gradient_smem(warps, wslots);                                        \
+    }                                                                                             \
     extern const NxOps kNxOps_##NN = {NN, Dispatch<NN>::V, Dispatch<NN>::kGrad, tables_##NN, sweep_##NN,        \
                                       max_warps_##NN, smem_##NN, tables_grad_##NN, gradient_##NN,  \
                                       gradient_max_warps_##NN, Dispatch<NN>::kTc, tables_natural_##NN, \
-                                      tc_sweep_##NN, tc_smem_##NN};                               \
+                                      tc_sweep_##NN, tc_smem_##NN, gradient_smem_##NN};           \
     }
