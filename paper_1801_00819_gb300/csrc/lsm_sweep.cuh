@@ -94,8 +94,9 @@ struct ImageRows {
 // Depth rows per staging buffer: the source sweep stages the coefficient rows of two depth steps at
 // a time, so its blocks meet at a barrier every other step (0.91 -> 0.86 ms on a 512 x 256 window
 // of 16 shots x 128 frequencies); the forward sweep measured no gain from it, and the adjoint sums
-// its image rows across the block at every depth.
-constexpr int stage_depths(int mode) { return mode == MODE_SOURCE ? 2 : 1; }
+// its image rows across the block at every depth.  Above 512 columns the doubled staging would
+// leave room for only half the warps per block, so the source sweep stages one step at a time.
+constexpr int stage_depths(int mode, int n) { return mode == MODE_SOURCE && n <= 512 ? 2 : 1; }
 
 // Bytes of dynamic shared memory for a block of `warps` warps whose items span at most `wslots`
 // frequencies (mirrored on the host by sweep_shape): per-item exchange buffers, the block's
@@ -107,7 +108,7 @@ constexpr size_t sweep_smem_bytes(int warps, int wslots, int mode) {
     using IR = ImageRows<N, V>;
     return (size_t)Plan<N, V>::TAB * sizeof(float2) +
            (size_t)warps * (32 / Plan<N, V>::T) * Plan<N, V>::BUF * sizeof(float2) +
-           2 * (size_t)stage_depths(mode) * ((size_t)wslots * 2 * N * sizeof(float2) + (size_t)N * sizeof(float)) +
+           2 * (size_t)stage_depths(mode, N) * ((size_t)wslots * 2 * N * sizeof(float2) + (size_t)N * sizeof(float)) +
            (adjoint ? (size_t)2 * warps * IR::SPW * IR::SLAB * sizeof(float) : 0);
 }
 
@@ -142,7 +143,7 @@ __global__ void __launch_bounds__(sweep_max_threads<V>()) sweep_kernel(const Swe
 
     // shared memory: exchange buffers | staging [2][DEP][wslots][2][N] float2 + [2][DEP][N] float |
     // images.  Depth step k (0 .. nz-2) reads staging buffer (k / DEP) % 2, slot k % DEP.
-    constexpr int DEP = stage_depths(MODE);
+    constexpr int DEP = stage_depths(MODE, N);
     float2* buf = smem + (warp * IPW + sub) * P::BUF;
     float2* stage = smem + ipb * P::BUF;
     const int stage_buf = a.wslots * 2 * N;  // float2 per staging slot (coefficients)
