@@ -53,11 +53,32 @@ __global__ void __launch_bounds__(kRedThreads) reduce_image_kernel(const float* 
     float4* o4 = reinterpret_cast<float4*>(out);
     double ss = 0.0, sz = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += gridDim.x * blockDim.x) {
-        float4 s = acc ? o4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int c = 0; c < nparts; ++c) {
-            const float4 q = __ldcs(p4 + (size_t)c * n4 + i);
-            s.x += q.x; s.y += q.y; s.z += q.z; s.w += q.w;
+        // eight partial sums (partials 8k + u go to sum u, the tail to sum 0) keep eight loads in
+        // flight per thread; they are combined in a fixed tree, so the result is deterministic
+        float4 a[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        int c = 0;
+        for (; c + 8 <= nparts; c += 8) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float4 q = __ldcs(p4 + (size_t)(c + u) * n4 + i);
+                a[u].x += q.x; a[u].y += q.y; a[u].z += q.z; a[u].w += q.w;
+            }
         }
+        for (; c < nparts; ++c) {
+            const float4 q = __ldcs(p4 + (size_t)c * n4 + i);
+            a[0].x += q.x; a[0].y += q.y; a[0].z += q.z; a[0].w += q.w;
+        }
+#pragma unroll
+        for (int h = 4; h > 0; h >>= 1) {
+#pragma unroll
+            for (int u = 0; u < h; ++u) {
+                a[u].x += a[u + h].x; a[u].y += a[u + h].y; a[u].z += a[u + h].z; a[u].w += a[u + h].w;
+            }
+        }
+        float4 s = acc ? o4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        s.x += a[0].x; s.y += a[0].y; s.z += a[0].z; s.w += a[0].w;
         if (m) {
             const float4 mm = m4[i];
             s.x = fmaf(-lam, mm.x, s.x); s.y = fmaf(-lam, mm.y, s.y);
@@ -85,6 +106,7 @@ __global__ void __launch_bounds__(kRedThreads) norm2_c64_kernel(const float2* __
     const float4* q4 = reinterpret_cast<const float4*>(q);
     const size_t n4 = n2 / 2;
     double acc = 0.0;
+#pragma unroll 4
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
         const float4 v = q4[i];
         acc += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
@@ -138,6 +160,7 @@ __global__ void __launch_bounds__(kRedThreads) update_mr_kernel(float* __restric
     float4* r4 = reinterpret_cast<float4*>(r);
     const float4* q4 = reinterpret_cast<const float4*>(q);
     const size_t h4 = n2 / 2;
+#pragma unroll 4
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < h4; i += (size_t)gridDim.x * blockDim.x) {
         float4 x = r4[i];
         const float4 y = q4[i];
