@@ -34,7 +34,7 @@ struct TcShape {
     static constexpr int R2 = N / 16;
     static constexpr int NT = R2 / 8;             // n-tiles (8 columns each)
     static constexpr int KS = (R2 + 15) / 16;     // k-steps (16) of the right product
-    static constexpr int LD = R2 + 4;             // padded row stride of the per-warp buffer
+    static constexpr int LD = R2 == 8 ? 12 : R2;  // row stride of the per-warp buffer (see tc_phys)
     static constexpr int BUF = 16 * LD;           // float2 per warp
     // constant fragments: left A (F16) [6 variants][32 lanes][4 x b32]; right B (F_R2) [KS][NT][6][32][2]
     static constexpr int A_WORDS = 6 * 32 * 4;
@@ -204,7 +204,18 @@ struct TcItem {
     float2 x[TcShape<N>::NT][4];  // the item, accumulator layout
 };
 
-// left product: out = F16 . M (CONJ: conj(F16)), M read from the per-warp buffer laid out [16][LD]
+// Position of matrix element (row, col) in the per-warp buffer: row stride LD and the column XORed
+// with a function of the row's low bits, chosen (by exhaustive search over linear XOR maps) so that
+// both the accumulator-layout writes (rows g, columns 2 c) and the operand-layout reads (rows 2 c,
+// columns g) of a half-warp touch 16 different 8-byte bank pairs.  The XOR stays inside the row.
+template <int N>
+__device__ __forceinline__ int tc_phys(int row, int col) {
+    using S = TcShape<N>;
+    const int sw = S::R2 == 8 ? ((row & 1) | (row & 4)) : ((row & 1) | ((row & 2) << 2) | (row & 4));
+    return row * S::LD + (col ^ sw);
+}
+
+// left product: out = F16 . M (CONJ: conj(F16)), M read from the per-warp buffer (tc_phys layout)
 template <int N, int PREC, bool CONJ>
 __device__ __forceinline__ void tc_left(TcItem<N>& out, const float2* buf, const uint32_t* Afr, int lane) {
     using S = TcShape<N>;
@@ -225,8 +236,8 @@ __device__ __forceinline__ void tc_left(TcItem<N>& out, const float2* buf, const
         uint32_t Br[2][2], Bi[2][2];
 #pragma unroll
         for (int w = 0; w < 2; ++w) {
-            const float2 v0 = buf[(2 * tig + 8 * w) * S::LD + 8 * j + g];
-            const float2 v1 = buf[(2 * tig + 8 * w + 1) * S::LD + 8 * j + g];
+            const float2 v0 = buf[tc_phys<N>(2 * tig + 8 * w, 8 * j + g)];
+            const float2 v1 = buf[tc_phys<N>(2 * tig + 8 * w + 1, 8 * j + g)];
             split_pack<PREC>(v0.x, v1.x, Br[0][w], Br[1][w]);
             split_pack<PREC>(v0.y, v1.y, Bi[0][w], Bi[1][w]);
         }
@@ -279,7 +290,7 @@ __device__ __forceinline__ void tc_right(TcItem<N>& out, const TcItem<N>& in, co
     }
 }
 
-// write the item (accumulator layout, matrix rows x columns) to the per-warp buffer [16][LD]
+// write the item (accumulator layout, matrix rows x columns) to the per-warp buffer (tc_phys layout)
 template <int N>
 __device__ __forceinline__ void tc_store(const TcItem<N>& it, float2* buf, int lane) {
     using S = TcShape<N>;
@@ -287,7 +298,7 @@ __device__ __forceinline__ void tc_store(const TcItem<N>& it, float2* buf, int l
 #pragma unroll
     for (int j = 0; j < S::NT; ++j)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) buf[(g + 8 * (e >> 1)) * S::LD + 8 * j + 2 * tig + (e & 1)] = it.x[j][e];
+        for (int e = 0; e < 4; ++e) buf[tc_phys<N>(g + 8 * (e >> 1), 8 * j + 2 * tig + (e & 1))] = it.x[j][e];
 }
 
 // column index (natural position for the matrix rows n1, columns n2) of element (j, e)
