@@ -34,7 +34,7 @@ struct TcShape {
     static constexpr int R2 = N / 16;
     static constexpr int NT = R2 / 8;             // n-tiles (8 columns each)
     static constexpr int KS = (R2 + 15) / 16;     // k-steps (16) of the right product
-    static constexpr int LD = R2 == 8 ? 12 : R2;  // row stride of the per-warp buffer (see tc_phys)
+    static constexpr int LD = R2 + 4;             // row stride of the per-warp buffer (see tc_phys)
     static constexpr int BUF = 16 * LD;           // float2 per warp
     // constant fragments: left A (F16) [6 variants][32 lanes][4 x b32]; right B (F_R2) [KS][NT][6][32][2]
     static constexpr int A_WORDS = 6 * 32 * 4;
@@ -204,15 +204,15 @@ struct TcItem {
     float2 x[TcShape<N>::NT][4];  // the item, accumulator layout
 };
 
-// Position of matrix element (row, col) in the per-warp buffer: row stride LD and the column XORed
-// with a function of the row's low bits, chosen (by exhaustive search over linear XOR maps) so that
-// both the accumulator-layout writes (rows g, columns 2 c) and the operand-layout reads (rows 2 c,
-// columns g) of a half-warp touch 16 different 8-byte bank pairs.  The XOR stays inside the row.
+// Position of matrix element (row, col) in the per-warp buffer: row stride LD = R2 + 4 and the
+// column's low three bits XORed with s(row) = (row & 1) | (row & 4), found by exhaustive search over
+// linear XOR maps so that both the accumulator-layout writes (rows g, columns 2 c) and the
+// operand-layout reads (rows 2 c, columns g) of a half-warp touch 16 different 8-byte bank pairs.
+// The XOR stays inside each group of 8 columns, so every element a lane touches is one of two
+// per-lane bases plus a compile-time offset.
 template <int N>
 __device__ __forceinline__ int tc_phys(int row, int col) {
-    using S = TcShape<N>;
-    const int sw = S::R2 == 8 ? ((row & 1) | (row & 4)) : ((row & 1) | ((row & 2) << 2) | (row & 4));
-    return row * S::LD + (col ^ sw);
+    return row * TcShape<N>::LD + (col ^ ((row & 1) | (row & 4)));
 }
 
 // left product: out = F16 . M (CONJ: conj(F16)), M read from the per-warp buffer (tc_phys layout)
@@ -220,6 +220,8 @@ template <int N, int PREC, bool CONJ>
 __device__ __forceinline__ void tc_left(TcItem<N>& out, const float2* buf, const uint32_t* Afr, int lane) {
     using S = TcShape<N>;
     const int g = lane >> 2, tig = lane & 3;
+    // operand element (row 2 tig + 8 w + q, column 8 j + g) = buf[lb_q + 8 w LD + 8 j]
+    const int lb0 = tc_phys<N>(2 * tig, g), lb1 = tc_phys<N>(2 * tig + 1, g);
     uint32_t Ar[2][4], Ai[2][4], An[2][4];
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
@@ -236,8 +238,8 @@ __device__ __forceinline__ void tc_left(TcItem<N>& out, const float2* buf, const
         uint32_t Br[2][2], Bi[2][2];
 #pragma unroll
         for (int w = 0; w < 2; ++w) {
-            const float2 v0 = buf[tc_phys<N>(2 * tig + 8 * w, 8 * j + g)];
-            const float2 v1 = buf[tc_phys<N>(2 * tig + 8 * w + 1, 8 * j + g)];
+            const float2 v0 = buf[lb0 + 8 * w * S::LD + 8 * j];
+            const float2 v1 = buf[lb1 + 8 * w * S::LD + 8 * j];
             split_pack<PREC>(v0.x, v1.x, Br[0][w], Br[1][w]);
             split_pack<PREC>(v0.y, v1.y, Bi[0][w], Bi[1][w]);
         }
@@ -295,10 +297,12 @@ template <int N>
 __device__ __forceinline__ void tc_store(const TcItem<N>& it, float2* buf, int lane) {
     using S = TcShape<N>;
     const int g = lane >> 2, tig = lane & 3;
+    // accumulator element (row g + 8 h, column 8 j + 2 tig + e0) = buf[sb_e0 + 8 h LD + 8 j]
+    const int sb0 = tc_phys<N>(g, 2 * tig), sb1 = tc_phys<N>(g, 2 * tig + 1);
 #pragma unroll
     for (int j = 0; j < S::NT; ++j)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) buf[tc_phys<N>(g + 8 * (e >> 1), 8 * j + 2 * tig + (e & 1))] = it.x[j][e];
+        for (int e = 0; e < 4; ++e) buf[((e & 1) ? sb1 : sb0) + 8 * (e >> 1) * S::LD + 8 * j] = it.x[j][e];
 }
 
 // column index (natural position for the matrix rows n1, columns n2) of element (j, e)
