@@ -256,7 +256,7 @@ Layout make_layout(const lsm_grid* g, const lsm_geom* geo, const lsm_freqs* f, i
         L.part_s = take((size_t)L.nparts * plane * sizeof(float));
         L.ckpt = take(items * 2 * ncp * nx * sizeof(float2));
         L.seg = take(items * (2 * c + 1) * nx * sizeof(float2));
-        L.ss = take(kRedBlocks * sizeof(double));
+        L.ss = take(kImgRedBlocks * sizeof(double));
     }
     if (op == LSM_OP_SOLVE) {
         const size_t nd = (size_t)nshots * nw * geo->nrec;
@@ -266,15 +266,15 @@ Layout make_layout(const lsm_grid* g, const lsm_geom* geo, const lsm_freqs* f, i
         L.q = take(nd * sizeof(float2));
         L.qq = take(kRedBlocks * sizeof(double));
         L.pp = take(kRedBlocks * sizeof(double));
-        L.ss = take(kRedBlocks * sizeof(double));
+        L.ss = take(kImgRedBlocks * sizeof(double));
         L.state = take(sizeof(CgState));
         L.ctrl = take(sizeof(int));
         L.illum = take(plane * sizeof(float));
         L.minv = take(plane * sizeof(float));
         L.bmax = take(kIllumBlocks * sizeof(float));
-        L.sz = take(kRedBlocks * sizeof(double));
+        L.sz = take(kImgRedBlocks * sizeof(double));
     } else if (op == LSM_OP_ADJOINT) {
-        L.ss = take(kRedBlocks * sizeof(double));
+        L.ss = take(kImgRedBlocks * sizeof(double));
     }
     L.total = off;
     return L;

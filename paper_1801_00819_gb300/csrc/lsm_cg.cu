@@ -40,56 +40,76 @@ __device__ __forceinline__ double sum_partials(const double* __restrict__ part, 
 }
 
 // out[i] = (acc ? out[i] : 0) + sum_c part[c][i] - lam * m[i];  partial sums of out[i]^2 and,
-// when minv is given, of out[i]^2 minv[i] (s.z for preconditioned CG)
+// when minv is given, of out[i]^2 minv[i] (s.z for preconditioned CG).  A block takes 64 float4
+// columns at a time and gives each column four threads: thread group q sums partials q, q + 4, ...
+// with four accumulators (sixteen loads in flight per column), and the four group sums are added in
+// a fixed order, so the result is deterministic.
+constexpr int kImgCols = 64;                       // float4 columns per block and pass
+constexpr int kImgGroups = kRedThreads / kImgCols;  // threads per column
 __global__ void __launch_bounds__(kRedThreads) reduce_image_kernel(const float* __restrict__ part, int nparts, int n4,
                                                                const float* __restrict__ m, float lam, int acc,
                                                                float* __restrict__ out, double* __restrict__ ss_part,
                                                                const float* __restrict__ minv,
                                                                double* __restrict__ sz_part) {
     __shared__ double sh[40];
+    __shared__ float4 grp_sum[kImgGroups - 1][kImgCols];
     const float4* p4 = reinterpret_cast<const float4*>(part);
     const float4* m4 = reinterpret_cast<const float4*>(m);
     const float4* w4 = reinterpret_cast<const float4*>(minv);
     float4* o4 = reinterpret_cast<float4*>(out);
+    const int col = threadIdx.x % kImgCols, grp = threadIdx.x / kImgCols;
     double ss = 0.0, sz = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += gridDim.x * blockDim.x) {
-        // eight partial sums (partials 8k + u go to sum u, the tail to sum 0) keep eight loads in
-        // flight per thread; they are combined in a fixed tree, so the result is deterministic
-        float4 a[8];
+    for (int base = blockIdx.x * kImgCols; base < n4; base += gridDim.x * kImgCols) {  // uniform per block
+        const int i = base + col;
+        constexpr int U = 4;  // accumulators (loads in flight) per thread; 8 measured no faster
+        float4 a[U];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) a[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-        int c = 0;
-        for (; c + 8 <= nparts; c += 8) {
+        for (int u = 0; u < U; ++u) a[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < n4) {
+            int c = grp;
+            for (; c + (U - 1) * kImgGroups < nparts; c += U * kImgGroups) {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const float4 q = __ldcs(p4 + (size_t)(c + u) * n4 + i);
-                a[u].x += q.x; a[u].y += q.y; a[u].z += q.z; a[u].w += q.w;
+                for (int u = 0; u < U; ++u) {
+                    const float4 q = __ldcs(p4 + (size_t)(c + u * kImgGroups) * n4 + i);
+                    a[u].x += q.x; a[u].y += q.y; a[u].z += q.z; a[u].w += q.w;
+                }
+            }
+            for (; c < nparts; c += kImgGroups) {
+                const float4 q = __ldcs(p4 + (size_t)c * n4 + i);
+                a[0].x += q.x; a[0].y += q.y; a[0].z += q.z; a[0].w += q.w;
             }
         }
-        for (; c < nparts; ++c) {
-            const float4 q = __ldcs(p4 + (size_t)c * n4 + i);
-            a[0].x += q.x; a[0].y += q.y; a[0].z += q.z; a[0].w += q.w;
-        }
 #pragma unroll
-        for (int h = 4; h > 0; h >>= 1) {
+        for (int h = U / 2; h > 0; h >>= 1) {
 #pragma unroll
             for (int u = 0; u < h; ++u) {
                 a[u].x += a[u + h].x; a[u].y += a[u + h].y; a[u].z += a[u + h].z; a[u].w += a[u + h].w;
             }
         }
-        float4 s = acc ? o4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        s.x += a[0].x; s.y += a[0].y; s.z += a[0].z; s.w += a[0].w;
-        if (m) {
-            const float4 mm = m4[i];
-            s.x = fmaf(-lam, mm.x, s.x); s.y = fmaf(-lam, mm.y, s.y);
-            s.z = fmaf(-lam, mm.z, s.z); s.w = fmaf(-lam, mm.w, s.w);
+        if (grp > 0) grp_sum[grp - 1][col] = a[0];
+        __syncthreads();
+        if (grp == 0 && i < n4) {
+            float4 s = acc ? o4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            s.x += a[0].x; s.y += a[0].y; s.z += a[0].z; s.w += a[0].w;
+#pragma unroll
+            for (int q = 0; q < kImgGroups - 1; ++q) {
+                const float4 b = grp_sum[q][col];
+                s.x += b.x; s.y += b.y; s.z += b.z; s.w += b.w;
+            }
+            if (m) {
+                const float4 mm = m4[i];
+                s.x = fmaf(-lam, mm.x, s.x); s.y = fmaf(-lam, mm.y, s.y);
+                s.z = fmaf(-lam, mm.z, s.z); s.w = fmaf(-lam, mm.w, s.w);
+            }
+            o4[i] = s;
+            ss += (double)s.x * s.x + (double)s.y * s.y + (double)s.z * s.z + (double)s.w * s.w;
+            if (minv) {
+                const float4 w = w4[i];
+                sz += (double)s.x * s.x * w.x + (double)s.y * s.y * w.y + (double)s.z * s.z * w.z +
+                      (double)s.w * s.w * w.w;
+            }
         }
-        o4[i] = s;
-        ss += (double)s.x * s.x + (double)s.y * s.y + (double)s.z * s.z + (double)s.w * s.w;
-        if (minv) {
-            const float4 w = w4[i];
-            sz += (double)s.x * s.x * w.x + (double)s.y * s.y * w.y + (double)s.z * s.z * w.z + (double)s.w * s.w * w.w;
-        }
+        __syncthreads();  // grp_sum is rewritten by the next pass
     }
     const double tot = block_sum(ss, sh);
     if (threadIdx.x == 0 && ss_part) ss_part[blockIdx.x] = tot;
@@ -321,7 +341,7 @@ __global__ void loop_test_kernel(CgState* st, cudaGraphConditionalHandle handle,
 cudaError_t cg_reduce_image(const float* part, int nparts, int n, const float* m, float lam, int acc, float* out,
                             double* ss_part, cudaStream_t st, const float* minv, double* sz_part) {
     ProfScope prof_(KC_VECTOR, st);
-    reduce_image_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(part, nparts, n / 4, m, lam, acc, out, ss_part, minv,
+    reduce_image_kernel<<<kImgRedBlocks, kRedThreads, 0, st>>>(part, nparts, n / 4, m, lam, acc, out, ss_part, minv,
                                                             sz_part);
     count_launch();
     return cudaGetLastError();
@@ -355,7 +375,7 @@ cudaError_t cg_update_p(float* p, const float* s, int n, const double* ss_part, 
                         int gi_old, int gi_new, double* pp_part, cudaStream_t st, const float* minv,
                         const double* sz_part) {
     ProfScope prof_(KC_VECTOR, st);
-    update_p_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(p, s, n / 4, ss_part, kRedBlocks, first, state, gi_old,
+    update_p_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(p, s, n / 4, ss_part, kImgRedBlocks, first, state, gi_old,
                                                          gi_new, pp_part, minv, sz_part);
     count_launch();
     return cudaGetLastError();
@@ -363,7 +383,7 @@ cudaError_t cg_update_p(float* p, const float* s, int n, const double* ss_part, 
 
 cudaError_t cg_store_sum(const double* part, CgState* state, cudaStream_t st) {
     ProfScope prof_(KC_VECTOR, st);
-    store_sum_kernel<<<1, kRedThreads, 0, st>>>(part, kRedBlocks, state);
+    store_sum_kernel<<<1, kRedThreads, 0, st>>>(part, kImgRedBlocks, state);
     count_launch();
     return cudaGetLastError();
 }

@@ -9,6 +9,9 @@ namespace lsm {
 
 // Fixed reduction grid: partial-sum arrays have exactly this many entries.
 constexpr int kRedBlocks = 296;
+// cg_reduce_image runs on a grid of its own size; its partial sums (ss_part, sz_part, and the ones
+// cg_store_sum and cg_update_p read back) have exactly kImgRedBlocks entries.
+constexpr int kImgRedBlocks = 512;
 
 struct CgState {
     double gamma[2];  // s.z of the current and the next iterate (slots alternate); z = s unpreconditioned
