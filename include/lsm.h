@@ -218,7 +218,10 @@ int lsm_adjoint_static(const lsm_grid* grid, const float* slowness, const lsm_fr
  * this library launches is bracketed by CUDA events recorded on the stream it is launched on;
  * lsm_profile_stop() waits for those events and reports, per kernel class, the number of launches
  * and the summed event time in milliseconds.  Timing adds two event records per launch.  Not
- * thread safe: profile one caller at a time.
+ * thread safe: profile one caller at a time.  lsm_profile_start_classes(mask) times only the
+ * kernel classes whose bit (1 << LSM_KCLASS_...) is set in mask, so that a benchmark can time the
+ * kernels it reports without adding event records around the others; lsm_profile_start() times
+ * every class.
  */
 #define LSM_KCLASS_TABLES 0   /* reference slowness and coefficient tables */
 #define LSM_KCLASS_SOURCE 1   /* source-wavefield depth sweep */
@@ -234,6 +237,7 @@ typedef struct {
 } lsm_profile;
 
 void lsm_profile_start(void);
+void lsm_profile_start_classes(unsigned class_mask);
 int lsm_profile_stop(lsm_profile* out);
 
 /*

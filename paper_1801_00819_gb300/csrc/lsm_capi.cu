@@ -42,6 +42,7 @@ struct ProfRecord {
     cudaEvent_t begin, end;
 };
 static std::atomic<bool> g_prof_on{false};
+static std::atomic<unsigned> g_prof_mask{~0u};  // kernel classes timed while profiling is on
 static std::mutex g_prof_mu;  // guards g_prof and g_event_pool
 static std::vector<ProfRecord> g_prof;
 static std::vector<cudaEvent_t> g_event_pool;
@@ -63,7 +64,7 @@ static cudaEvent_t pooled_event() {
 }
 
 void profile_mark(int cls, cudaStream_t st, bool begin) {
-    if (!g_prof_on || g_capturing) return;
+    if (!g_prof_on || g_capturing || !((g_prof_mask.load(std::memory_order_relaxed) >> cls) & 1u)) return;
     if (begin) {
         g_pending_begin = pooled_event();
         if (g_pending_begin) cudaEventRecord(g_pending_begin, st);
@@ -945,8 +946,11 @@ const char* lsm_status_string(int status) {
 
 unsigned long long lsm_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
-void lsm_profile_start(void) {
+void lsm_profile_start(void) { lsm_profile_start_classes(~0u); }
+
+void lsm_profile_start_classes(unsigned class_mask) {
     std::lock_guard<std::mutex> lock(g_prof_mu);
+    g_prof_mask = class_mask;
     for (auto& r : g_prof) {
         g_event_pool.push_back(r.begin);
         g_event_pool.push_back(r.end);

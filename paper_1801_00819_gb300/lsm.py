@@ -33,7 +33,7 @@ LSM_CHECKPOINT_EVERY = 16
 EXPORTED = ("lsm_workspace_bytes", "lsm_forward", "lsm_adjoint", "lsm_num_windows", "rls_window_solve",
             "lsm_status_string", "lsm_kernel_launches", "lsm_profile_start", "lsm_profile_stop",
             "lsm_adjoint_static", "lsm_born_gradient", "rls_window_solve_ex", "rls_multi_line_solve",
-            "lsm_forward_ex", "lsm_adjoint_ex")
+            "lsm_forward_ex", "lsm_adjoint_ex", "lsm_profile_start_classes")
 
 TRANSFORMS = {"fft": 0, "dft_bf16x3": 1, "dft_fp16x3": 2, "dft_bf16x1": 3}
 
@@ -161,6 +161,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lsm_kernel_launches.argtypes = []
     lib.lsm_profile_start.restype = None
     lib.lsm_profile_start.argtypes = []
+    lib.lsm_profile_start_classes.restype = None
+    lib.lsm_profile_start_classes.argtypes = [ctypes.c_uint]
     lib.lsm_profile_stop.restype = ctypes.c_int
     lib.lsm_profile_stop.argtypes = [ctypes.POINTER(lsm_profile)]
     _lib_handle = lib
@@ -243,9 +245,16 @@ def lsm_kernel_launches() -> int:
     return int(load_library().lsm_kernel_launches())
 
 
-def lsm_profile_start() -> None:
-    """Start per-launch CUDA-event timing of every kernel the library launches."""
-    load_library().lsm_profile_start()
+def lsm_profile_start(classes=None) -> None:
+    """Start per-launch CUDA-event timing of the kernels the library launches: every class, or
+    only the named ones (names from KERNEL_CLASSES), leaving the others without event records."""
+    if classes is None:
+        load_library().lsm_profile_start()
+    else:
+        mask = 0
+        for name in classes:
+            mask |= 1 << KERNEL_CLASSES.index(name)
+        load_library().lsm_profile_start_classes(ctypes.c_uint(mask))
 
 
 def lsm_profile_stop() -> dict:

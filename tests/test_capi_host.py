@@ -35,7 +35,7 @@ def test_header_declares_expected_entry_points():
                                             "rls_window_solve", "lsm_status_string", "lsm_kernel_launches",
                                             "lsm_profile_start", "lsm_profile_stop", "lsm_adjoint_static",
                                             "lsm_born_gradient", "rls_window_solve_ex", "rls_multi_line_solve",
-                                            "lsm_forward_ex", "lsm_adjoint_ex"])
+                                            "lsm_forward_ex", "lsm_adjoint_ex", "lsm_profile_start_classes"])
 
 
 def test_library_exports_every_declared_symbol(lib):
