@@ -331,6 +331,37 @@ typedef struct {
 
 int rls_multi_line_solve(lsm_line* lines, int nlines, const lsm_solve_options* options);
 
+/*
+ * Launch-shape autotuning (an implementation choice, not a step of the paper's method).  The depth
+ * sweeps run a fixed number of (shot, frequency) items per warp, and the number of warps per block
+ * sets how many items share a block's staged coefficient rows and how the launch fills the SMs;
+ * the default spreads a launch evenly over the SMs.  lsm_autotune times every admissible number of
+ * warps per block for the source, A^T and A sweeps of launches over `nshots` shots of this grid and
+ * frequency set (for a solve: nshots = K), with the FP32 FFTs or, when options->transform selects
+ * one, the tensor-core DFT products, and records the fastest.  From then on every launch on the
+ * current device with the same (nx, mode, transform, nshots, nw) uses the recorded shape
+ * (process-wide, thread safe); results stay within the same tolerances, but A^T's sum over block
+ * partial images, and so its last bits, follow the shape.  The A^T candidates never use more
+ * blocks than the default, so lsm_workspace_bytes is unchanged.  Needs a workspace of
+ * lsm_workspace_bytes(grid, geom, freqs, nshots, LSM_OP_SOLVE); runs shots [0, nshots) on
+ * zero-valued inputs, overwrites the workspace, and returns after synchronising the stream.
+ * `report` (may be NULL) receives, per sweep, the chosen and the default warps per block with their
+ * mean launch times in ms and the number of shapes timed.  lsm_autotune_reset forgets every
+ * recorded shape.
+ */
+typedef struct {
+    int warps, heuristic_warps, candidates;
+    double ms, heuristic_ms;
+} lsm_tune_entry;
+typedef struct {
+    lsm_tune_entry source, adjoint, forward;
+} lsm_tune_report;
+
+int lsm_autotune(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs,
+                 const lsm_geom* geom, int nshots, const lsm_solve_options* options,
+                 void* workspace, size_t workspace_bytes, void* stream, lsm_tune_report* report);
+void lsm_autotune_reset(void);
+
 /* Human-readable name of a status code (static string). */
 const char* lsm_status_string(int status);
 

@@ -12,6 +12,8 @@ from .lsm import (  # noqa: F401
     LineProblem,
     LsmError,
     lsm_adjoint,
+    lsm_autotune,
+    lsm_autotune_reset,
     lsm_born_gradient,
     lsm_forward,
     lsm_kernel_launches,

@@ -13,8 +13,10 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "../../include/lsm.h"
@@ -96,25 +98,68 @@ const NxOps* nx_ops(int nx) {
 
 bool nx_supported(int nx) { return nx_ops(nx) != nullptr; }
 
-SweepShape sweep_shape(int nx, int mode, int nshots, int nw, int num_sms) {
+// ------------------------------------------------------------------ launch shapes and their tuning
+// A launch shape is the number of warps per block (items per block = warps x items per warp); the
+// heuristic spreads a launch's warps evenly over the SMs.  lsm_autotune measures the alternatives
+// and records the fastest per (device, nx, sweep mode, transform, shots, frequencies); launches use
+// a recorded shape, the workspace layout always the heuristic one (the tuner never picks an adjoint
+// shape with more blocks, i.e. more partial images, than the heuristic's).
+struct TuneKey {
+    int dev, nx, mode, transform, nshots, nw;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(dev, nx, mode, transform, nshots, nw) < std::tie(o.dev, o.nx, o.mode, o.transform, o.nshots, o.nw);
+    }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, int> g_tune;
+
+static TuneKey tune_key(int nx, int mode, int transform, int nshots, int nw) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) cudaGetLastError();
+    return TuneKey{dev, nx, mode, transform, nshots, nw};
+}
+static int tuned_warps(int nx, int mode, int transform, int nshots, int nw) {
+    const TuneKey k = tune_key(nx, mode, transform, nshots, nw);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(k);
+    return it == g_tune.end() ? 0 : it->second;
+}
+
+// most warps per block a sweep of this mode can take (registers, shared memory)
+static int sweep_max_warps(int nx, int mode, int nshots, int nw) {
     const NxOps* ops = nx_ops(nx);
     const int V = ops->points_per_thread;
-    const int T = nx / V;
-    const int ipw = 32 / T;
-    const int nitems = nshots * nw;
-    const int warps_total = (nitems + ipw - 1) / ipw;
+    const int ipw = 32 / (nx / V);
     auto wslots_of = [&](int w) { return std::min(nw, (w * ipw + nshots - 1) / nshots + 1); };
-    auto smem_of = [&](int w) { return ops->smem(mode, w, wslots_of(w)); };
     int maxw = std::min(V >= 24 ? 8 : 16, ops->max_warps(mode));
-    while (maxw > 1 && smem_of(maxw) > 227 * 1024) --maxw;
-    int warps = (warps_total + num_sms - 1) / num_sms;
-    warps = std::max(1, std::min(warps, maxw));
+    while (maxw > 1 && ops->smem(mode, maxw, wslots_of(maxw)) > 227 * 1024) --maxw;
+    return maxw;
+}
+
+static SweepShape sweep_shape_for(int nx, int mode, int nshots, int nw, int warps) {
+    const NxOps* ops = nx_ops(nx);
+    const int ipw = 32 / (nx / ops->points_per_thread);
+    const int warps_total = (nshots * nw + ipw - 1) / ipw;
     SweepShape s;
     s.warps = warps;
     s.blocks = (warps_total + warps - 1) / warps;
-    s.wslots = wslots_of(warps);
-    s.smem = smem_of(warps);
+    s.wslots = std::min(nw, (warps * ipw + nshots - 1) / nshots + 1);
+    s.smem = ops->smem(mode, warps, s.wslots);
     return s;
+}
+
+SweepShape sweep_shape_heuristic(int nx, int mode, int nshots, int nw, int num_sms) {
+    const int ipw = 32 / (nx / nx_ops(nx)->points_per_thread);
+    const int warps_total = (nshots * nw + ipw - 1) / ipw;
+    int warps = (warps_total + num_sms - 1) / num_sms;
+    warps = std::max(1, std::min(warps, sweep_max_warps(nx, mode, nshots, nw)));
+    return sweep_shape_for(nx, mode, nshots, nw, warps);
+}
+
+SweepShape sweep_shape(int nx, int mode, int nshots, int nw, int num_sms) {
+    const int w = tuned_warps(nx, mode, 0, nshots, nw);
+    if (w > 0) return sweep_shape_for(nx, mode, nshots, nw, w);
+    return sweep_shape_heuristic(nx, mode, nshots, nw, num_sms);
 }
 
 bool gradient_nx_supported(int nx) {
@@ -143,19 +188,27 @@ SweepShape gradient_shape(int nx, int nshots, int nw, int num_sms) {
     return s;
 }
 
-// tensor-core variants: one item per warp, up to 8 warps per block
-SweepShape tc_shape(int nx, int mode, int nshots, int nw, int num_sms) {
-    const NxOps* ops = nx_ops(nx);
+// tensor-core variants: one item per warp, up to 7 warps per block (two blocks per SM)
+static SweepShape tc_shape_for(int nx, int mode, int nshots, int nw, int warps) {
     const int nitems = nshots * nw;
-    // one item per warp, up to 7 warps per block, two blocks per SM
-    int warps = (nitems + 2 * num_sms - 1) / (2 * num_sms);
-    warps = std::max(1, std::min(warps, 7));
     SweepShape s;
     s.warps = warps;
     s.blocks = (nitems + warps - 1) / warps;
     s.wslots = 0;
-    s.smem = ops->tc_smem(mode, warps);
+    s.smem = nx_ops(nx)->tc_smem(mode, warps);
     return s;
+}
+
+SweepShape tc_shape_heuristic(int nx, int mode, int nshots, int nw, int num_sms) {
+    int warps = (nshots * nw + 2 * num_sms - 1) / (2 * num_sms);
+    warps = std::max(1, std::min(warps, 7));
+    return tc_shape_for(nx, mode, nshots, nw, warps);
+}
+
+SweepShape tc_shape(int nx, int mode, int nshots, int nw, int num_sms, int transform) {
+    const int w = tuned_warps(nx, mode, transform, nshots, nw);
+    if (w > 0) return tc_shape_for(nx, mode, nshots, nw, w);
+    return tc_shape_heuristic(nx, mode, nshots, nw, num_sms);
 }
 
 cudaError_t launch_tables_grad(const TableArgs& a, cudaStream_t st) { return nx_ops(a.nx)->tables_grad(a, st); }
@@ -242,10 +295,10 @@ Layout make_layout(const lsm_grid* g, const lsm_geom* geo, const lsm_freqs* f, i
     L.S = take((size_t)nshots * nw * plane * sizeof(float2));
     L.nparts = 0;
     if (op == LSM_OP_ADJOINT || op == LSM_OP_SOLVE) {
-        const SweepShape sh = sweep_shape(g->nx, MODE_ADJOINT, nshots, (int)nw, num_sms);
+        const SweepShape sh = sweep_shape_heuristic(g->nx, MODE_ADJOINT, nshots, (int)nw, num_sms);
         L.nparts = sh.blocks;
         if (nx_ops(g->nx)->has_tc)
-            L.nparts = std::max(L.nparts, tc_shape(g->nx, MODE_ADJOINT, nshots, (int)nw, num_sms).blocks);
+            L.nparts = std::max(L.nparts, tc_shape_heuristic(g->nx, MODE_ADJOINT, nshots, (int)nw, num_sms).blocks);
     } else if (op == LSM_OP_GRADIENT) {
         L.nparts = gradient_shape(g->nx, nshots, (int)nw, num_sms).blocks;
     }
@@ -386,7 +439,7 @@ cudaError_t launch_any(int mode, int transform, SweepArgs& a, int n, int num_sms
         if (blocks) *blocks = sh.blocks;
         return launch_sweep(mode, a, sh, st);
     }
-    const SweepShape sh = tc_shape(a.nx, mode, n, a.nw, num_sms);
+    const SweepShape sh = tc_shape(a.nx, mode, n, a.nw, num_sms, transform);
     if (blocks) *blocks = sh.blocks;
     return nx_ops(a.nx)->tc_sweep(mode, transform, a, sh, st);
 }
@@ -651,6 +704,121 @@ int lsm_born_gradient(const lsm_grid* grid, const float* slowness, const double*
     if (grad_m) LSM_CHECK(cg_reduce_image(ga.part_m, sh.blocks, n, nullptr, 0.f, 0, grad_m, ssp, st));
     if (grad_s) LSM_CHECK(cg_reduce_image(ga.part_s, sh.blocks, n, nullptr, 0.f, 0, grad_s, ssp, st));
     return LSM_OK;
+}
+
+// ------------------------------------------------------------------ lsm_autotune
+
+// Mean time of `reps` launches of one sweep shape (after one untimed launch), in ms.
+static cudaError_t time_shape(int mode, int transform, SweepArgs a, const SweepShape& sh, cudaStream_t st,
+                              cudaEvent_t e0, cudaEvent_t e1, int reps, double* ms) {
+    auto launch = [&]() -> cudaError_t {
+        if (transform == 0) {
+            a.wslots = sh.wslots;
+            return launch_sweep(mode, a, sh, st);
+        }
+        return nx_ops(a.nx)->tc_sweep(mode, transform, a, sh, st);
+    };
+    cudaError_t e = launch();
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventRecord(e0, st)) != cudaSuccess) return e;
+    for (int i = 0; i < reps; ++i)
+        if ((e = launch()) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(e1, st)) != cudaSuccess) return e;
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return e;
+    float t = 0.f;
+    if ((e = cudaEventElapsedTime(&t, e0, e1)) != cudaSuccess) return e;
+    *ms = (double)t / reps;
+    return cudaSuccess;
+}
+
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~EventPair() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
+int lsm_autotune(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs, const lsm_geom* geom,
+                 int nshots, const lsm_solve_options* options, void* workspace, size_t workspace_bytes, void* stream,
+                 lsm_tune_report* report) {
+    int rc = validate_common(grid, freqs, geom);
+    if (rc != LSM_OK) return rc;
+    if (!aligned16(slowness) || !aligned16(workspace)) return LSM_ERR_ARG;
+    if (nshots < 1 || nshots > geom->ns) return LSM_ERR_ARG;
+    int transform = 0;
+    rc = transform_of(options, grid, geom, &transform);
+    if (rc != LSM_OK) return rc;
+    const int nsm = num_sms_current();
+    const Layout L = make_layout(grid, geom, freqs, nshots, LSM_OP_SOLVE, nsm);
+    if (workspace_bytes < L.total) return LSM_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(workspace);
+    const int nx = grid->nx, nw = freqs->nw;
+    // forget earlier choices for this problem, so that the set-up below runs the heuristic shapes
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        for (int mode = 0; mode < 3; ++mode) g_tune.erase(tune_key(nx, mode, transform, nshots, nw));
+    }
+    rc = prepare(grid, slowness, freqs, geom, L, ws, st, nullptr, transform ? TABLES_NATURAL : TABLES_SWEEP);
+    if (rc != LSM_OK) return rc;
+    SweepArgs a = base_args(grid, freqs, geom, L, ws);
+    a.shot0 = 0;
+    a.nshots = nshots;
+    a.m = reinterpret_cast<const float*>(ws + L.p);
+    a.dout = reinterpret_cast<float2*>(ws + L.q);
+    a.din = reinterpret_cast<const float2*>(ws + L.r);
+    const size_t nd = (size_t)nshots * nw * geom->nrec;
+    LSM_CHECK(cudaMemsetAsync(ws + L.p, 0, (size_t)nx * grid->nz * sizeof(float), st));
+    LSM_CHECK(cudaMemsetAsync(ws + L.r, 0, nd * sizeof(float2), st));
+    LSM_CHECK(run_source(a, 0, nshots, nsm, st, transform));  // the ring the A and A^T sweeps read
+    EventPair ev;
+    LSM_CHECK(cudaEventCreate(&ev.a));
+    LSM_CHECK(cudaEventCreate(&ev.b));
+    const int modes[3] = {MODE_SOURCE, MODE_ADJOINT, MODE_FORWARD};
+    lsm_tune_entry* out[3] = {report ? &report->source : nullptr, report ? &report->adjoint : nullptr,
+                              report ? &report->forward : nullptr};
+    for (int mi = 0; mi < 3; ++mi) {
+        const int mode = modes[mi];
+        const SweepShape h = transform ? tc_shape_heuristic(nx, mode, nshots, nw, nsm)
+                                       : sweep_shape_heuristic(nx, mode, nshots, nw, nsm);
+        const int maxw = transform ? 7 : sweep_max_warps(nx, mode, nshots, nw);
+        // the adjoint keeps at most the heuristic's number of blocks (partial images in the layout)
+        const int minw = mode == MODE_ADJOINT ? h.warps : 1;
+        int best_w = h.warps, ncand = 0;
+        double best_ms = 0.0, h_ms = 0.0;
+        for (int w = minw; w <= maxw; ++w) {
+            const SweepShape sh = transform ? tc_shape_for(nx, mode, nshots, nw, w)
+                                            : sweep_shape_for(nx, mode, nshots, nw, w);
+            if (sh.smem > 227 * 1024) continue;
+            double ms = 0.0;
+            LSM_CHECK(time_shape(mode, transform, a, sh, st, ev.a, ev.b, 3, &ms));
+            ++ncand;
+            if (w == h.warps) h_ms = ms;
+            if (ncand == 1 || ms < best_ms) {
+                best_ms = ms;
+                best_w = w;
+            }
+        }
+        {
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            g_tune[tune_key(nx, mode, transform, nshots, nw)] = best_w;
+        }
+        if (out[mi]) {
+            out[mi]->warps = best_w;
+            out[mi]->heuristic_warps = h.warps;
+            out[mi]->ms = best_ms;
+            out[mi]->heuristic_ms = h_ms;
+            out[mi]->candidates = ncand;
+        }
+    }
+    LSM_CHECK(cudaStreamSynchronize(st));
+    return LSM_OK;
+}
+
+void lsm_autotune_reset(void) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune.clear();
 }
 
 int lsm_num_windows(int ns, int K, int slide) {

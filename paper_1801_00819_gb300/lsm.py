@@ -33,7 +33,8 @@ LSM_CHECKPOINT_EVERY = 16
 EXPORTED = ("lsm_workspace_bytes", "lsm_forward", "lsm_adjoint", "lsm_num_windows", "rls_window_solve",
             "lsm_status_string", "lsm_kernel_launches", "lsm_profile_start", "lsm_profile_stop",
             "lsm_adjoint_static", "lsm_born_gradient", "rls_window_solve_ex", "rls_multi_line_solve",
-            "lsm_forward_ex", "lsm_adjoint_ex", "lsm_profile_start_classes")
+            "lsm_forward_ex", "lsm_adjoint_ex", "lsm_profile_start_classes", "lsm_autotune",
+            "lsm_autotune_reset")
 
 TRANSFORMS = {"fft": 0, "dft_bf16x3": 1, "dft_fp16x3": 2, "dft_bf16x1": 3}
 
@@ -107,6 +108,19 @@ class lsm_profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_ulonglong * 6), ("ms", ctypes.c_double * 6)]
 
 
+class lsm_tune_entry(ctypes.Structure):
+    _fields_ = [("warps", ctypes.c_int), ("heuristic_warps", ctypes.c_int), ("candidates", ctypes.c_int),
+                ("ms", ctypes.c_double), ("heuristic_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"warps": int(self.warps), "heuristic_warps": int(self.heuristic_warps),
+                "candidates": int(self.candidates), "ms": float(self.ms), "heuristic_ms": float(self.heuristic_ms)}
+
+
+class lsm_tune_report(ctypes.Structure):
+    _fields_ = [("source", lsm_tune_entry), ("adjoint", lsm_tune_entry), ("forward", lsm_tune_entry)]
+
+
 _lib_handle = None
 
 
@@ -155,6 +169,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rls_window_solve_ex.argtypes = list(lib.rls_window_solve.argtypes) + [ctypes.POINTER(lsm_solve_options)]
     lib.rls_multi_line_solve.restype = ctypes.c_int
     lib.rls_multi_line_solve.argtypes = [ctypes.POINTER(lsm_line), ctypes.c_int, ctypes.POINTER(lsm_solve_options)]
+    lib.lsm_autotune.restype = ctypes.c_int
+    lib.lsm_autotune.argtypes = [ctypes.POINTER(lsm_grid), ctypes.c_void_p, ctypes.POINTER(lsm_freqs),
+                                 ctypes.POINTER(lsm_geom), ctypes.c_int, ctypes.POINTER(lsm_solve_options),
+                                 ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.POINTER(lsm_tune_report)]
+    lib.lsm_autotune_reset.restype = None
+    lib.lsm_autotune_reset.argtypes = []
     lib.lsm_status_string.restype = ctypes.c_char_p
     lib.lsm_status_string.argtypes = [ctypes.c_int]
     lib.lsm_kernel_launches.restype = ctypes.c_ulonglong
@@ -381,3 +401,21 @@ def rls_multi_line_solve(problems, preconditioner=None, precond_eps=1e-2, raise_
     if st != LSM_OK and raise_on_error:
         raise LsmError(st, "rls_multi_line_solve")
     return statuses, out
+
+
+def lsm_autotune(grid, slowness, freqs, geom, nshots, workspace, stream=None, transform="fft") -> dict:
+    """Time every admissible launch shape of the source, A^T and A sweeps for launches over `nshots`
+    shots and record the fastest for later launches (see include/lsm.h).  `workspace` must hold
+    lsm_workspace_bytes(..., nshots, LSM_OP_SOLVE).  Returns {sweep: {warps, heuristic_warps,
+    candidates, ms, heuristic_ms}}."""
+    rep = lsm_tune_report()
+    st = load_library().lsm_autotune(ctypes.byref(grid.c), _ptr(slowness), ctypes.byref(freqs.c),
+                                      ctypes.byref(geom.c), int(nshots), ctypes.byref(_options(transform=transform)),
+                                      _ptr(workspace), _nbytes(workspace), _stream(stream), ctypes.byref(rep))
+    _check(st, "lsm_autotune")
+    return {"source": rep.source.as_dict(), "adjoint": rep.adjoint.as_dict(), "forward": rep.forward.as_dict()}
+
+
+def lsm_autotune_reset() -> None:
+    """Forget every launch shape recorded by lsm_autotune."""
+    load_library().lsm_autotune_reset()

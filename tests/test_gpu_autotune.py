@@ -1,0 +1,113 @@
+"""Launch-shape autotuning (lsm_autotune): the recorded shapes are admissible, launches that use
+them still match the FP64 oracle, and A^T stays deterministic under a recorded shape."""
+
+import numpy as np
+import pytest
+
+from oracle import lsm_oracle as O
+from synth import random_case, config_precision_subsample
+from tests._helpers import oracle_operator, rel_l2, device_survey
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture()
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1801_00819_gb300 as L
+    L.lsm_autotune_reset()
+    yield torch
+    L.lsm_autotune_reset()  # later tests run the default shapes
+
+
+def _tune(torch, ds, K, transform="fft"):
+    import paper_1801_00819_gb300 as L
+    ws = torch.empty(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, K, L.LSM_OP_SOLVE), dtype=torch.uint8,
+                     device="cuda")
+    rep = L.lsm_autotune(ds.grid, ds.slowness, ds.freqs, ds.geom, K, ws, transform=transform)
+    for sweep, e in rep.items():
+        assert e["candidates"] >= 1 and 1 <= e["warps"] and e["ms"] > 0.0, (sweep, e)
+        assert e["ms"] <= e["heuristic_ms"] * 1.0000001 or e["heuristic_ms"] == 0.0, (sweep, e)
+    assert rep["adjoint"]["warps"] >= rep["adjoint"]["heuristic_warps"]  # no more partial images
+    return rep
+
+
+def test_tuned_shapes_keep_operator_and_solve_parity(torch_cuda):
+    import paper_1801_00819_gb300 as L
+    torch = torch_cuda
+    sv = random_case(128, 24, 6, 10, seed=7)
+    op = oracle_operator(sv)
+    ds = device_survey(sv)
+    K = 3
+    rep = _tune(torch, ds, K)
+    print(rep)
+    ws = torch.empty(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, K, L.LSM_OP_ADJOINT), dtype=torch.uint8,
+                     device="cuda")
+    m = np.asarray(sv.reflectivity, dtype=np.float32)
+    rng = np.random.default_rng(3)
+    d = (rng.normal(size=(K, sv.nw, sv.nx)) + 1j * rng.normal(size=(K, sv.nw, sv.nx))).astype(np.complex64)
+    for shot0 in (0, 2):
+        out = torch.empty((K, sv.nw, sv.nx), dtype=torch.complex64, device="cuda")
+        L.lsm_forward(ds.grid, ds.slowness, ds.freqs, ds.geom, torch.as_tensor(m, device="cuda"), out, shot0, K, ws)
+        imgs = []
+        for _ in range(2):
+            img = torch.empty((sv.nz, sv.nx), dtype=torch.float32, device="cuda")
+            L.lsm_adjoint(ds.grid, ds.slowness, ds.freqs, ds.geom, torch.as_tensor(d, device="cuda"), img, shot0, K,
+                          ws)
+            imgs.append(img.cpu().numpy())
+        torch.cuda.synchronize()
+        shots = np.arange(shot0, shot0 + K)
+        assert rel_l2(out.cpu().numpy(), op.forward(m.astype(np.float64), shots=shots)) <= 1e-4
+        assert rel_l2(imgs[0], op.adjoint(d.astype(np.complex128), shots=shots)) <= 1e-4
+        np.testing.assert_array_equal(imgs[0], imgs[1])
+
+
+def test_tuned_shapes_keep_sliding_solve_parity(torch_cuda):
+    """The tiny workload's sliding solve (window 4, slide 2, 10 iterations), whose A and A^T sweeps run
+    over K = 4 shots, once on the default and once on the tuned shapes: both match the oracle."""
+    import paper_1801_00819_gb300 as L
+    from synth import config_tiny
+    torch = torch_cuda
+    sv = config_tiny()
+    op = oracle_operator(sv)
+    ds = device_survey(sv)
+    m = np.asarray(sv.reflectivity, dtype=np.float32).astype(np.float64)
+    clean = op.forward(m)
+    dd = (clean + sv.noise_pct * np.sqrt(np.mean(np.abs(clean) ** 2)) * sv.noise()).astype(np.complex64)
+    lam = float(np.float32(O.regularisation_from_adjoint(op, dd.astype(np.complex128))))
+    m_ref, _ = O.rls_solve(op, dd.astype(np.complex128), lam, sv.window, sv.slide, sv.cg_iters)
+    wss = torch.empty(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, sv.window, L.LSM_OP_SOLVE),
+                      dtype=torch.uint8, device="cuda")
+
+    def solve():
+        mm = torch.zeros((sv.nz, sv.nx), dtype=torch.float32, device="cuda")
+        L.rls_window_solve(ds.grid, ds.slowness, ds.freqs, ds.geom, torch.as_tensor(dd, device="cuda"), lam,
+                           sv.window, sv.slide, 0.0, sv.cg_iters, mm, wss)
+        torch.cuda.synchronize()
+        return mm.cpu().numpy().astype(np.float64)
+
+    m_default = solve()
+    _tune(torch, ds, sv.window)
+    m_tuned = solve()
+    assert rel_l2(m_default, m_ref) <= 1e-4
+    assert rel_l2(m_tuned, m_ref) <= 1e-4
+
+
+def test_tuned_tensor_core_shapes_keep_parity(torch_cuda):
+    import paper_1801_00819_gb300 as L
+    torch = torch_cuda
+    sv = config_precision_subsample(128)
+    op = oracle_operator(sv)
+    ds = device_survey(sv)
+    K = 3
+    _tune(torch, ds, K, transform="dft_fp16x3")
+    ws = torch.empty(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, K, L.LSM_OP_ADJOINT), dtype=torch.uint8,
+                     device="cuda")
+    m = np.asarray(sv.reflectivity, dtype=np.float32)
+    out = torch.empty((K, sv.nw, sv.nx), dtype=torch.complex64, device="cuda")
+    L.lsm_forward(ds.grid, ds.slowness, ds.freqs, ds.geom, torch.as_tensor(m, device="cuda"), out, 0, K, ws,
+                  transform="dft_fp16x3")
+    torch.cuda.synchronize()
+    assert rel_l2(out.cpu().numpy(), op.forward(m.astype(np.float64), shots=np.arange(K))) <= 1e-4
