@@ -532,6 +532,17 @@ def batching_arm(args):
         lines.append(lsm.LineProblem(ds.grid, ds.slowness, ds.freqs, ds.geom, d, lam, K, sv.slide, sv.cg_tol,
                                      sv.cg_iters, m, ws, torch.cuda.Stream()))
     torch.cuda.synchronize()
+    tuned = []
+    if not args.no_autotune:  # launch shapes per line, before any timed solve
+        for pr in lines:
+            rep = lsm.lsm_autotune(pr.grid, pr.slowness, pr.freqs, pr.geom, pr.K, pr.workspace)
+            entry = {"nx": pr.grid.c.nx, "K": pr.K, "warps": {k: v["warps"] for k, v in rep.items()},
+                     "heuristic_warps": {k: v["heuristic_warps"] for k, v in rep.items()}}
+            if pr.slide != pr.K:
+                entry["refill_source_warps"] = lsm.lsm_autotune(pr.grid, pr.slowness, pr.freqs, pr.geom, pr.slide,
+                                                                pr.workspace)["source"]["warps"]
+            tuned.append(entry)
+        torch.cuda.synchronize()
 
     def units_of(stats_per_line):
         total = 0
@@ -592,7 +603,8 @@ def batching_arm(args):
            "concurrent_cuda_graph_units_per_s": round(units_of(st_graph) / t_graph, 1),
            "speedup_concurrent_cuda_graph_vs_sequential": round(t_seq / t_graph, 3),
            "cuda_graph_same_iterations": [[w["iters"] for w in st] for st in st_graph] ==
-                                         [[w["iters"] for w in st] for st in st_conc]}
+                                         [[w["iters"] for w in st] for st in st_conc],
+           "autotune": tuned or None}
     print(json.dumps(out), flush=True)
 
 
