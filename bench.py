@@ -75,6 +75,20 @@ def dist_info():
     return rank, world, local
 
 
+def reduce_over_ranks(units, t_ms, world, device):
+    """Whole-job totals of one timed region: the units every rank processed (each rank solves its
+    own survey line, whose CG iteration counts may differ) and the slowest rank's time."""
+    if world <= 1:
+        return float(units), float(t_ms)
+    import torch
+    import torch.distributed as dist
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(t.item())
+
+
 def workload(name, rank=0):
     from synth import config_realistic, config_tiny
 
@@ -291,16 +305,10 @@ def gpu_arm(args):
     barrier()
     clk = clocks.stop()
     t_ms = ev0.elapsed_time(ev1)
-    t_max = t_ms
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-
     units_per_pass = K * nw * nz
     units = sum((w["n_forward"] + w["n_adjoint"]) / 2 * units_per_pass for st in stats for w in st)
-    value = units * world / (t_max / 1e3)
+    units_all, t_max = reduce_over_ranks(units, t_ms, world, "cuda")
+    value = units_all / (t_max / 1e3)
     iters = [w["iters"] for w in stats[-1]]
     final_res = [w["rel_res"] for w in stats[-1]]
 
@@ -374,13 +382,9 @@ def gpu_arm(args):
         e1.record(stream)
         torch.cuda.synchronize()
         te = e0.elapsed_time(e1)
-        if world > 1:
-            import torch.distributed as dist
-            tt = torch.tensor([te], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
         units_e = sum((w["n_forward"] + w["n_adjoint"]) / 2 * units_per_pass for st in stats_e for w in st)
-        out["e2e"] = {"value": round(units_e * world / (te / 1e3), 1), "unit": "units/s",
+        units_e_all, te = reduce_over_ranks(units_e, te, world, "cuda")
+        out["e2e"] = {"value": round(units_e_all / (te / 1e3), 1), "unit": "units/s",
                       "h2d_bytes_per_step": int(d_host.numel() * 8 + s_host.numel() * 4),
                       "d2h_bytes_per_step": int(img_host.numel() * 4), "ms_per_step": round(te / args.steps, 3)}
 
