@@ -357,9 +357,11 @@ def gpu_arm(args):
            "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items() if k not in ("vector", "gradient")},
            "kernel_launches": {k: v["launches"] for k, v in prof.items() if k not in ("vector", "gradient")},
            "cg": {"windows": len(stats[-1]), "iters_per_window": iters, "total_iters": int(sum(iters)),
-                  "max_final_rel_res": max(final_res), "time_to_tol_ms": round(t_max / args.steps, 3)}}
+                  "max_final_rel_res": max(final_res), "time_to_tol_ms": round(t_max / args.steps, 3),
+                  "loop": "host-driven (the A / A^T sweeps are event-timed for the roofline)"}}
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers; nothing is event-timed here, so the solve
+    # runs the library's default loop, each window's CG iterations as one CUDA graph
     if not args.no_e2e:
         d_host = d.cpu().pin_memory()
         s_host = torch.as_tensor(s32).pin_memory()
@@ -386,7 +388,8 @@ def gpu_arm(args):
         units_e_all, te = reduce_over_ranks(units_e, te, world, "cuda")
         out["e2e"] = {"value": round(units_e_all / (te / 1e3), 1), "unit": "units/s",
                       "h2d_bytes_per_step": int(d_host.numel() * 8 + s_host.numel() * 4),
-                      "d2h_bytes_per_step": int(img_host.numel() * 4), "ms_per_step": round(te / args.steps, 3)}
+                      "d2h_bytes_per_step": int(img_host.numel() * 4), "ms_per_step": round(te / args.steps, 3),
+                      "cg_loop": "CUDA graph (library default)"}
 
     # the paper's preconditioned variant (illumination preconditioner), one untimed-by-contract solve
     if not args.no_variants:
@@ -501,7 +504,8 @@ def reference_arm(args):
 def batching_arm(args):
     """Eight independent survey lines (nx 256..1024 incl. 384, 640, 768, 896; K 4..32), every window
     to 1e-3: one step solves all lines concurrently (rls_multi_line_solve, a stream per line); the
-    comparison loops the plain per-line solve over the same lines."""
+    comparison loops the plain per-line solve over the same lines.  Both run the host-driven CG loop;
+    a third arm runs the concurrent solve with graph-replayed CG iterations."""
     import numpy as np
     import torch
 
@@ -560,7 +564,7 @@ def batching_arm(args):
         for pr in lines:
             pr.m_inout.zero_()
             _, st = L.rls_window_solve(pr.grid, pr.slowness, pr.freqs, pr.geom, pr.d, pr.lam, pr.K, pr.slide,
-                                       pr.cg_tol, pr.max_iter, pr.m_inout, pr.workspace)
+                                       pr.cg_tol, pr.max_iter, pr.m_inout, pr.workspace, cuda_graph=False)
             out.append(st)
         return out
 

@@ -267,12 +267,15 @@ int lsm_profile_stop(lsm_profile* out);
 #define LSM_TRANSFORM_DFT_FP16X3 2
 #define LSM_TRANSFORM_DFT_BF16X1 3
 /*
- *   cuda_graph: nonzero runs each window's CG iterations as one CUDA graph -- a conditional WHILE
+ *   cuda_graph: > 0 runs each window's CG iterations as one CUDA graph -- a conditional WHILE
  *     node whose body is one iteration (A, the vector updates, A^T, the stopping test evaluated on
  *     the device) -- so the host waits once per window instead of once per iteration.  The kernels
  *     and their order are those of the host-driven loop, so results and iteration counts are
  *     identical.  The graph is built once per call on a private stream; kernels inside it are not
- *     seen by lsm_profile_start / lsm_profile_stop.
+ *     seen by lsm_profile_start / lsm_profile_stop.  < 0 runs the host-driven loop (the host reads
+ *     the stopping test back after every iteration).  0, the default (also for rls_window_solve and
+ *     NULL options), runs the graph unless lsm_profile_start / lsm_profile_start_classes is timing
+ *     the A or A^T sweeps, which needs the host-driven loop.
  */
 typedef struct {
     int preconditioner;

@@ -65,6 +65,12 @@ static cudaEvent_t pooled_event() {
     return e;
 }
 
+// whether lsm_profile_start(_classes) is timing the A or A^T sweeps (they cannot be timed inside a
+// graph's conditional body)
+static bool profiling_sweeps() {
+    return g_prof_on && (g_prof_mask.load(std::memory_order_relaxed) & ((1u << KC_ADJOINT) | (1u << KC_FORWARD)));
+}
+
 void profile_mark(int cls, cudaStream_t st, bool begin) {
     if (!g_prof_on || g_capturing || !((g_prof_mask.load(std::memory_order_relaxed) >> cls) & 1u)) return;
     if (begin) {
@@ -957,7 +963,9 @@ int rls_window_solve_ex(const lsm_grid* grid, const float* slowness, const lsm_f
     double* ss = reinterpret_cast<double*>(ws + L.ss);
     CgState* state = reinterpret_cast<CgState*>(ws + L.state);
     int* shot0_dev = reinterpret_cast<int*>(ws + L.ctrl);
-    const bool use_graph = options && options->cuda_graph != 0;
+    // cuda_graph > 0: graph; < 0: host-driven loop; 0: graph unless the sweeps are being event-timed
+    const int graph_opt = options ? options->cuda_graph : 0;
+    const bool use_graph = graph_opt > 0 || (graph_opt == 0 && !profiling_sweeps());
     CgGraph graph;
     float* minv = precond == LSM_PRECOND_ILLUMINATION ? reinterpret_cast<float*>(ws + L.minv) : nullptr;
     double* sz = minv ? reinterpret_cast<double*>(ws + L.sz) : nullptr;

@@ -71,7 +71,7 @@ class lsm_solve_options(ctypes.Structure):
                 ("cuda_graph", ctypes.c_int)]
 
 
-def _options(preconditioner=None, precond_eps=1e-2, transform="fft", cuda_graph=False):
+def _options(preconditioner=None, precond_eps=1e-2, transform="fft", cuda_graph=None):
     if transform not in TRANSFORMS:
         raise ValueError(f"unknown transform {transform!r}")
     if preconditioner is None:
@@ -80,7 +80,8 @@ def _options(preconditioner=None, precond_eps=1e-2, transform="fft", cuda_graph=
         pc = LSM_PRECOND_ILLUMINATION
     else:
         raise ValueError(f"unknown preconditioner {preconditioner!r}")
-    return lsm_solve_options(pc, float(precond_eps), TRANSFORMS[transform], 1 if cuda_graph else 0)
+    graph = 0 if cuda_graph is None else (1 if cuda_graph else -1)  # None: the library's default
+    return lsm_solve_options(pc, float(precond_eps), TRANSFORMS[transform], graph)
 
 
 class lsm_line(ctypes.Structure):
@@ -343,13 +344,14 @@ def lsm_born_gradient(grid, slowness, sref, freqs, geom, m, g, d_out, grad_m, gr
 
 def rls_window_solve(grid, slowness, freqs, geom, d, lam, K, slide, cg_tol, max_iter, m_inout, workspace,
                      first_window=0, n_windows=0, stream=None, raise_on_breakdown=True, preconditioner=None,
-                     precond_eps=1e-2, transform="fft", cuda_graph=False):
+                     precond_eps=1e-2, transform="fft", cuda_graph=None):
     """Sliding-window CG solve; returns (status, [stats dicts]).  m_inout is updated in place.
 
     With the defaults this calls rls_window_solve; otherwise rls_window_solve_ex with the options:
     preconditioner="illumination" (diagonal source-illumination preconditioner, stabiliser
-    precond_eps times its maximum), a tensor-core `transform`, or cuda_graph=True (each window's CG
-    iterations replayed as one CUDA graph with a device-side stopping test).
+    precond_eps times its maximum), a tensor-core `transform`, or cuda_graph=True / False (each
+    window's CG iterations replayed as one CUDA graph with a device-side stopping test, or the
+    host-driven loop; None: the graph unless the A / A^T sweeps are being event-timed).
     """
     lib = load_library()
     nwin = lib.lsm_num_windows(int(geom.c.ns), int(K), int(slide))
@@ -358,7 +360,7 @@ def rls_window_solve(grid, slowness, freqs, geom, d, lam, K, slide, cg_tol, max_
     args = (ctypes.byref(grid.c), _ptr(slowness), ctypes.byref(freqs.c), ctypes.byref(geom.c), _ptr(d), float(lam),
             int(K), int(slide), float(cg_tol), int(max_iter), int(first_window), int(n_windows), _ptr(m_inout), stats,
             cap, _ptr(workspace), _nbytes(workspace), _stream(stream))
-    if preconditioner is None and transform == "fft" and not cuda_graph:
+    if preconditioner is None and transform == "fft" and cuda_graph is None:
         st = lib.rls_window_solve(*args)
     else:
         opts = _options(preconditioner, precond_eps, transform, cuda_graph)
@@ -380,7 +382,7 @@ class LineProblem:
 
 
 def rls_multi_line_solve(problems, preconditioner=None, precond_eps=1e-2, raise_on_error=True, transform="fft",
-                         cuda_graph=False):
+                         cuda_graph=None):
     """Solve several LineProblems concurrently; returns ([status], [[stats dicts]])."""
     lib = load_library()
     n = len(problems)

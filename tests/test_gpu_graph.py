@@ -1,5 +1,6 @@
 """CUDA-graph CG (lsm_solve_options.cuda_graph): each window's iterations replayed by a conditional
-WHILE node with the stopping test on the device.  The graph runs the host-driven loop's kernels in
+WHILE node with the stopping test on the device (the default), against the host-driven loop
+(cuda_graph=False).  The graph runs the host-driven loop's kernels in
 the same order, so images must be bitwise identical and iteration counts equal, and both must match
 the FP64 oracle's solve."""
 
@@ -53,7 +54,7 @@ def test_graph_fixed_iterations_bitwise_equal_and_oracle(torch_cuda):
     op = oracle_operator(sv)
     d, lam = _data(sv, op)
     ds = device_survey(sv)
-    _, m_e, st_e = _solve(torch_cuda, ds, d, lam, sv.window, sv.slide, 0.0, sv.cg_iters)
+    _, m_e, st_e = _solve(torch_cuda, ds, d, lam, sv.window, sv.slide, 0.0, sv.cg_iters, cuda_graph=False)
     _, m_g, st_g = _solve(torch_cuda, ds, d, lam, sv.window, sv.slide, 0.0, sv.cg_iters, cuda_graph=True)
     np.testing.assert_array_equal(m_g, m_e)
     _same_stats(st_g, st_e)
@@ -66,7 +67,7 @@ def test_graph_tolerance_stopping_matches_host_loop_and_oracle(torch_cuda):
     op = oracle_operator(sv)
     d, lam = _data(sv, op)
     ds = device_survey(sv)
-    _, m_e, st_e = _solve(torch_cuda, ds, d, lam, 3, 2, 1e-2, 50)
+    _, m_e, st_e = _solve(torch_cuda, ds, d, lam, 3, 2, 1e-2, 50, cuda_graph=False)
     _, m_g, st_g = _solve(torch_cuda, ds, d, lam, 3, 2, 1e-2, 50, cuda_graph=True)
     np.testing.assert_array_equal(m_g, m_e)
     _same_stats(st_g, st_e)
@@ -91,7 +92,7 @@ def test_graph_preconditioned_and_tensor_core_variants(torch_cuda):
     d, lam = _data(sv, op)
     ds = device_survey(sv)
     kw = dict(preconditioner="illumination", precond_eps=1e-2)
-    _, m_e, st_e = _solve(torch_cuda, ds, d, lam, sv.window, sv.slide, 1e-3, 30, **kw)
+    _, m_e, st_e = _solve(torch_cuda, ds, d, lam, sv.window, sv.slide, 1e-3, 30, cuda_graph=False, **kw)
     _, m_g, st_g = _solve(torch_cuda, ds, d, lam, sv.window, sv.slide, 1e-3, 30, cuda_graph=True, **kw)
     np.testing.assert_array_equal(m_g, m_e)
     _same_stats(st_g, st_e)
@@ -100,7 +101,7 @@ def test_graph_preconditioned_and_tensor_core_variants(torch_cuda):
     op2 = oracle_operator(sv2)
     d2, lam2 = _data(sv2, op2)
     ds2 = device_survey(sv2)
-    _, m_e2, st_e2 = _solve(torch_cuda, ds2, d2, lam2, 3, 2, 0.0, 4, transform="dft_fp16x3")
+    _, m_e2, st_e2 = _solve(torch_cuda, ds2, d2, lam2, 3, 2, 0.0, 4, transform="dft_fp16x3", cuda_graph=False)
     _, m_g2, st_g2 = _solve(torch_cuda, ds2, d2, lam2, 3, 2, 0.0, 4, transform="dft_fp16x3", cuda_graph=True)
     np.testing.assert_array_equal(m_g2, m_e2)
     _same_stats(st_g2, st_e2)
@@ -127,7 +128,7 @@ def test_graph_multi_line_equals_solo_host_loop(torch_cuda):
         ds = to_device(sv.nx, sv.nz, sv.dx, sv.dz, np.asarray(sv.slowness, np.float32), sv.src_ix, sv.rec_ix,
                        sv.freqs, sv.wavelet)
         K, slide = 2 + i, 1
-        _, m_solo, st_solo = _solve(torch_cuda, ds, d, lam, K, slide, 1e-2, 20)
+        _, m_solo, st_solo = _solve(torch_cuda, ds, d, lam, K, slide, 1e-2, 20, cuda_graph=False)
         solo.append((m_solo, st_solo))
         ws = workspace(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, K, L.LSM_OP_SOLVE))
         m = torch_cuda.zeros((sv.nz, sv.nx), dtype=torch_cuda.float32, device="cuda")
@@ -139,3 +140,22 @@ def test_graph_multi_line_equals_solo_host_loop(torch_cuda):
     for pr, st, (m_solo, st_solo) in zip(probs, stats, solo):
         np.testing.assert_array_equal(pr.m_inout.cpu().numpy(), m_solo)
         _same_stats(st, st_solo)
+
+
+def test_default_is_graph_unless_sweeps_are_timed(torch_cuda):
+    """The default loop is the graph (its kernels are not event-timed), except while the A / A^T
+    sweeps are being timed; both give the same image."""
+    import paper_1801_00819_gb300 as L
+    sv = config_tiny()
+    op = oracle_operator(sv)
+    d, lam = _data(sv, op)
+    ds = device_survey(sv)
+    L.lsm_profile_start(classes=("vector",))
+    _, m_a, _ = _solve(torch_cuda, ds, d, lam, sv.window, sv.slide, 0.0, sv.cg_iters)
+    prof = L.lsm_profile_stop()
+    assert prof["vector"]["launches"] < 3 * 2 * sv.cg_iters  # only the set-up kernels outside the graph
+    L.lsm_profile_start(classes=("adjoint", "forward"))
+    _, m_b, _ = _solve(torch_cuda, ds, d, lam, sv.window, sv.slide, 0.0, sv.cg_iters)
+    prof = L.lsm_profile_stop()
+    assert prof["adjoint"]["launches"] == 3 * (2 + sv.cg_iters)  # the host-driven loop, every sweep timed
+    np.testing.assert_array_equal(m_a, m_b)
