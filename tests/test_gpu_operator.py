@@ -25,6 +25,9 @@ CASES = [
     (512, 10, 2, 3),
     (1024, 6, 1, 3),
     (64, 1, 3, 3),
+    # degenerate: one frequency; one shot and one frequency with two depths
+    (128, 12, 3, 1),
+    (256, 2, 1, 1),
     # mixed-radix widths nx = q 2^a, q = 3, 5, 7
     (48, 10, 2, 3),
     (96, 8, 3, 4),

@@ -165,3 +165,28 @@ def test_preconditioned_tolerance_stopping_matches_oracle(torch_cuda):
     assert [s["iters"] for s in st_gpu] == [s.iters for s in st_ref]
     assert all(s["rel_res"] <= 1e-2 for s in st_gpu)
     assert rel_l2(m_gpu, m_ref) <= TOL
+
+
+@pytest.mark.parametrize("n_shots", [1, 2])
+def test_single_frequency_window_of_one_shot_solve(torch_cuda, n_shots):
+    """Degenerate surveys: one frequency and a window of K = 1 shot sliding by 1 (one window per
+    shot).  The normal matrix of one shot at one frequency has rank at most 2 nx, so with the
+    data-scaled lambda (about 5e-5 of the top eigenvalue of A^T A here) four CG iterates move by
+    about 30 % under 1e-7 relative perturbations of each operator application, in FP64 as in FP32.
+    lambda is therefore set to the top eigenvalue (power iteration on the oracle), which leaves the
+    problem well conditioned (iterates move by about 1e-7 under the same perturbations)."""
+    sv = random_case(64, 6, n_shots, 1, seed=17)
+    op = oracle_operator(sv)
+    d, _ = _oracle_data(sv, op)
+    x = np.random.default_rng(0).normal(size=(sv.nz, sv.nx))
+    for _ in range(30):
+        y = op.adjoint(op.forward(x))
+        top = np.linalg.norm(y) / np.linalg.norm(x)
+        x = y / np.linalg.norm(y)
+    lam = float(np.float32(top))
+    ds = device_survey(sv)
+    m_gpu, st = _gpu_solve(torch_cuda, ds, d, lam, 1, 1, 0.0, 4)
+    assert [w["start"] for w in st] == list(range(n_shots)) and all(w["iters"] == 4 for w in st)
+    m_ref, st_ref = O.rls_solve(op, d.astype(np.complex128), lam, 1, 1, 4)
+    assert [w["start"] for w in st] == [w.start for w in st_ref]
+    assert rel_l2(m_gpu, m_ref) <= 1e-4
