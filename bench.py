@@ -189,11 +189,11 @@ def bytes_per_unit(nx, nrec, nz, K):
 
 def kernel_source_hash():
     """Hash of the sources the sweep kernels are compiled from (lsm_fft.cuh, lsm_sweep.cuh,
-    lsm_async.cuh, lsm_internal.h and the per-nx instantiation files)."""
+    lsm_async.cuh, lsm_internal.h, lsm_cg.h and the per-nx instantiation files)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1801_00819_gb300", "csrc")
     names = sorted(n for n in os.listdir(csrc)
-                   if n in ("lsm_fft.cuh", "lsm_sweep.cuh", "lsm_async.cuh", "lsm_internal.h")
+                   if n in ("lsm_fft.cuh", "lsm_sweep.cuh", "lsm_async.cuh", "lsm_internal.h", "lsm_cg.h")
                    or n.startswith("sweep_n"))
     for name in names:
         with open(os.path.join(csrc, name), "rb") as fh:
@@ -292,7 +292,7 @@ def gpu_arm(args):
     clocks.start()
     launches0 = L.lsm_kernel_launches()
     # event timing of the sweep and table kernels only: the roofline needs the sweeps' times, and
-    # event records around the four short CG vector launches per iteration would slow the solve
+    # event records around the two short CG vector launches per iteration would slow the solve
     L.lsm_profile_start(classes=("tables", "source", "adjoint", "forward"))
     ev0.record(stream)
     stats = []

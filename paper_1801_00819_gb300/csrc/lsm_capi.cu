@@ -324,7 +324,8 @@ Layout make_layout(const lsm_grid* g, const lsm_geom* geo, const lsm_freqs* f, i
         L.s = take(plane * sizeof(float));
         L.r = take(nd * sizeof(float2));
         L.q = take(nd * sizeof(float2));
-        L.qq = take(kRedBlocks * sizeof(double));
+        // |q|^2 partials: one per block of the CG iteration's forward sweep (at most one per item)
+        L.qq = take(std::max((size_t)kRedBlocks, (size_t)nshots * nw) * sizeof(double));
         L.pp = take(kRedBlocks * sizeof(double));
         L.ss = take(kImgRedBlocks * sizeof(double));
         L.state = take(sizeof(CgState));
@@ -458,12 +459,12 @@ cudaError_t run_source(SweepArgs a, int shot0, int n, int num_sms, cudaStream_t 
 }
 
 cudaError_t run_forward(SweepArgs a, int shot0, int n, const float* m, float2* dout, int num_sms, cudaStream_t st,
-                        int transform = 0) {
+                        int transform = 0, int* blocks = nullptr) {
     a.shot0 = shot0;
     a.nshots = n;
     a.m = m;
     a.dout = dout;
-    return launch_any(MODE_FORWARD, transform, a, n, num_sms, st, nullptr);
+    return launch_any(MODE_FORWARD, transform, a, n, num_sms, st, blocks);
 }
 
 // Adjoint sweep into the block partial images; returns the number of partials in *nparts.
@@ -875,6 +876,49 @@ struct CgVectors {
     double lambda;
 };
 
+// One CG iteration after a window's set-up (Eq. 11): q = A p; alpha = gamma / (||q||^2 + lambda
+// ||p||^2); m += alpha p; r -= alpha q; s = A^T r - lambda m; beta; p = s (or M^-1 s) + beta p.
+// gi is the current gamma slot (-1: the state's, for the device-driven loop; cg_update_p then
+// writes slot state->gi ^ 1).  With the register-FFT sweeps the vector work rides in the sweeps
+// and the image reduction: the forward sweep emits the |q|^2 partials, the adjoint sweep forms alpha
+// and applies r -= alpha q as it loads r, and the reduction applies m += alpha p, so an iteration
+// is four launches.  The tensor-core transforms run the separate vector kernels (six launches).
+static cudaError_t cg_iteration(SweepArgs a, int start, int K, int nsm, int transform, const CgVectors& v, int gi,
+                                cudaStream_t st) {
+    int nparts = 0;
+    cudaError_t e;
+    if (transform == 0) {
+        int nqq = 0;
+        SweepArgs af = a;
+        af.qq_part = v.qq;
+        e = run_forward(af, start, K, v.p, v.q, nsm, st, 0, &nqq);
+        SweepArgs aa = a;
+        aa.r_io = v.r;
+        aa.dq = v.q;
+        aa.qq_in = v.qq;
+        aa.nqq = nqq;
+        aa.pp_in = v.pp;
+        aa.npp = kRedBlocks;
+        aa.cg_gi = gi;
+        aa.lam = v.lambda;
+        aa.cg = v.state;
+        if (e == cudaSuccess) e = run_adjoint(aa, start, K, nullptr, nsm, st, &nparts, 0);
+        if (e == cudaSuccess)
+            e = cg_reduce_image(a.part, nparts, v.n, v.m, (float)v.lambda, 0, v.s, v.ss, st, v.minv, v.sz, v.p,
+                                v.state);
+    } else {
+        e = run_forward(a, start, K, v.p, v.q, nsm, st, transform);
+        if (e == cudaSuccess) e = cg_norm2_c64(v.q, v.nd, v.qq, st);
+        if (e == cudaSuccess) e = cg_update_mr(v.m, v.p, v.n, v.r, v.q, v.nd, v.qq, v.pp, v.lambda, v.state, gi, st);
+        if (e == cudaSuccess) e = run_adjoint(a, start, K, v.r, nsm, st, &nparts, transform);
+        if (e == cudaSuccess)
+            e = cg_reduce_image(a.part, nparts, v.n, v.m, (float)v.lambda, 0, v.s, v.ss, st, v.minv, v.sz);
+    }
+    if (e == cudaSuccess)
+        e = cg_update_p(v.p, v.s, v.n, v.ss, 0, v.state, gi, gi < 0 ? -1 : gi ^ 1, v.pp, st, v.minv, v.sz);
+    return e;
+}
+
 static int build_cg_graph(CgGraph& G, SweepArgs a, int K, int nsm, int transform, const CgVectors& v) {
     LSM_CHECK(cudaStreamCreateWithFlags(&G.cs, cudaStreamNonBlocking));
     LSM_CHECK(cudaGraphCreate(&G.graph, 0));
@@ -899,14 +943,7 @@ static int build_cg_graph(CgGraph& G, SweepArgs a, int K, int nsm, int transform
     G.capturing = true;
     g_capturing = true;
     g_captured_launches = 0;
-    int nparts = 0;
-    cudaError_t e = run_forward(a, 0, K, v.p, v.q, nsm, G.cs, transform);
-    if (e == cudaSuccess) e = cg_norm2_c64(v.q, v.nd, v.qq, G.cs);
-    if (e == cudaSuccess) e = cg_update_mr(v.m, v.p, v.n, v.r, v.q, v.nd, v.qq, v.pp, v.lambda, v.state, -1, G.cs);
-    if (e == cudaSuccess) e = run_adjoint(a, 0, K, v.r, nsm, G.cs, &nparts, transform);
-    if (e == cudaSuccess)
-        e = cg_reduce_image(a.part, nparts, v.n, v.m, (float)v.lambda, 0, v.s, v.ss, G.cs, v.minv, v.sz);
-    if (e == cudaSuccess) e = cg_update_p(v.p, v.s, v.n, v.ss, 0, v.state, -1, -1, v.pp, G.cs, v.minv, v.sz);
+    cudaError_t e = cg_iteration(a, 0, K, nsm, transform, v, -1, G.cs);
     if (e == cudaSuccess) e = cg_loop_test(v.state, handle, 1, G.cs);
     g_capturing = false;
     G.body_launches = g_captured_launches;
@@ -1034,15 +1071,9 @@ int rls_window_solve_ex(const lsm_grid* grid, const float* slowness, const lsm_f
         rel = bnorm > 0.0 ? std::sqrt(hs.ss[gi]) / bnorm : 0.0;
         rel0 = rel;
         broke = hs.breakdown != 0;
+        const CgVectors v{m_inout, p, s, r, q, qq, pp, ss, sz, minv, state, nd, n, lambda};
         while (!broke && it < max_iter && !(rel <= cg_tol)) {
-            // q = A_k p ; alpha ; m += alpha p ; r -= alpha q
-            LSM_CHECK(run_forward(a, start, K, p, q, nsm, st, transform));
-            LSM_CHECK(cg_norm2_c64(q, nd, qq, st));
-            LSM_CHECK(cg_update_mr(m_inout, p, n, r, q, nd, qq, pp, lambda, state, gi, st));
-            // s = A_k^T r - lambda m ; beta ; p = s + beta p
-            LSM_CHECK(run_adjoint(a, start, K, r, nsm, st, &nparts, transform));
-            LSM_CHECK(cg_reduce_image(a.part, nparts, n, m_inout, lamf, 0, s, ss, st, minv, sz));
-            LSM_CHECK(cg_update_p(p, s, n, ss, 0, state, gi, gi ^ 1, pp, st, minv, sz));
+            LSM_CHECK(cg_iteration(a, start, K, nsm, transform, v, gi, st));
             gi ^= 1;
             ++nfwd;
             ++nadj;

@@ -40,21 +40,28 @@ __device__ __forceinline__ double sum_partials(const double* __restrict__ part, 
 }
 
 // out[i] = (acc ? out[i] : 0) + sum_c part[c][i] - lam * m[i];  partial sums of out[i]^2 and,
-// when minv is given, of out[i]^2 minv[i] (s.z for preconditioned CG).  A block takes 64 float4
+// when minv is given, of out[i]^2 minv[i] (s.z for preconditioned CG).  With pdir given, the CG
+// iteration's model update m += alpha pdir (alpha from the state, skipped after a breakdown) is
+// applied first and m is written back.  A block takes 64 float4
 // columns at a time and gives each column four threads: thread group q sums partials q, q + 4, ...
 // with four accumulators (sixteen loads in flight per column), and the four group sums are added in
 // a fixed order, so the result is deterministic.
 constexpr int kImgCols = 64;                       // float4 columns per block and pass
 constexpr int kImgGroups = kRedThreads / kImgCols;  // threads per column
 __global__ void __launch_bounds__(kRedThreads) reduce_image_kernel(const float* __restrict__ part, int nparts, int n4,
-                                                               const float* __restrict__ m, float lam, int acc,
+                                                               float* __restrict__ m, float lam, int acc,
                                                                float* __restrict__ out, double* __restrict__ ss_part,
                                                                const float* __restrict__ minv,
-                                                               double* __restrict__ sz_part) {
+                                                               double* __restrict__ sz_part,
+                                                              const float* __restrict__ pdir,
+                                                              const CgState* __restrict__ st) {
     __shared__ double sh[40];
     __shared__ float4 grp_sum[kImgGroups - 1][kImgCols];
     const float4* p4 = reinterpret_cast<const float4*>(part);
-    const float4* m4 = reinterpret_cast<const float4*>(m);
+    float4* m4 = reinterpret_cast<float4*>(m);
+    const float4* d4 = reinterpret_cast<const float4*>(pdir);
+    const bool mupd = pdir && st->breakdown == 0;
+    const float alpha = mupd ? (float)st->alpha : 0.f;
     const float4* w4 = reinterpret_cast<const float4*>(minv);
     float4* o4 = reinterpret_cast<float4*>(out);
     const int col = threadIdx.x % kImgCols, grp = threadIdx.x / kImgCols;
@@ -97,7 +104,13 @@ __global__ void __launch_bounds__(kRedThreads) reduce_image_kernel(const float* 
                 s.x += b.x; s.y += b.y; s.z += b.z; s.w += b.w;
             }
             if (m) {
-                const float4 mm = m4[i];
+                float4 mm = m4[i];
+                if (mupd) {
+                    const float4 y = d4[i];
+                    mm.x = fmaf(alpha, y.x, mm.x); mm.y = fmaf(alpha, y.y, mm.y);
+                    mm.z = fmaf(alpha, y.z, mm.z); mm.w = fmaf(alpha, y.w, mm.w);
+                    m4[i] = mm;
+                }
                 s.x = fmaf(-lam, mm.x, s.x); s.y = fmaf(-lam, mm.y, s.y);
                 s.z = fmaf(-lam, mm.z, s.z); s.w = fmaf(-lam, mm.w, s.w);
             }
@@ -338,11 +351,12 @@ __global__ void loop_test_kernel(CgState* st, cudaGraphConditionalHandle handle,
 
 // ------------------------------------------------------------------ launchers
 
-cudaError_t cg_reduce_image(const float* part, int nparts, int n, const float* m, float lam, int acc, float* out,
-                            double* ss_part, cudaStream_t st, const float* minv, double* sz_part) {
+cudaError_t cg_reduce_image(const float* part, int nparts, int n, float* m, float lam, int acc, float* out,
+                            double* ss_part, cudaStream_t st, const float* minv, double* sz_part, const float* p,
+                            const CgState* state) {
     ProfScope prof_(KC_VECTOR, st);
     reduce_image_kernel<<<kImgRedBlocks, kRedThreads, 0, st>>>(part, nparts, n / 4, m, lam, acc, out, ss_part, minv,
-                                                            sz_part);
+                                                            sz_part, p, state);
     count_launch();
     return cudaGetLastError();
 }

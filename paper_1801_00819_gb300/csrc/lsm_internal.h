@@ -10,6 +10,8 @@
 
 namespace lsm {
 
+struct CgState;  // lsm_cg.h
+
 enum SweepMode { MODE_SOURCE = 0, MODE_ADJOINT = 1, MODE_FORWARD = 2 };
 
 // Arguments of one depth sweep over the (shot, frequency) items of shots [shot0, shot0+nshots).
@@ -32,6 +34,17 @@ struct SweepArgs {
     float* part;                   // adjoint per-block partial images [grid][nz][nx]
     const int* shot0_dev;          // if set, shot0 is read from this device int (graph-replayed
                                    // CG iterations, whose window start changes between launches)
+    // CG vector work folded into the sweeps of one CG iteration (all null / 0 outside it):
+    double* qq_part;               // forward: one partial sum of |q|^2 over the recorded data per block
+    float2* r_io;                  // adjoint: the residual r, updated in place to r - alpha q while it
+                                   // is injected (replaces din)
+    const float2* dq;              // adjoint: q = A p of this iteration, [nshots][nw][nrec]
+    const double* qq_in;           // adjoint: the forward sweep's |q|^2 partials (nqq entries)
+    const double* pp_in;           // adjoint: ||p||^2 partials (npp entries)
+    int nqq, npp;
+    int cg_gi;                     // slot of the current gamma in cg; -1: cg->gi (device-driven loop)
+    double lam;                    // Tikhonov weight lambda
+    CgState* cg;                   // gamma (read); delta, alpha and the breakdown flag (block 0 writes)
 };
 
 // Arguments of the gradient kernel (lsm_grad.cuh) over the items of shots [shot0, shot0+nshots).

@@ -22,6 +22,7 @@
 #pragma once
 
 #include "lsm_async.cuh"
+#include "lsm_cg.h"
 #include "lsm_fft.cuh"
 #include "lsm_grad.cuh"
 #include "lsm_internal.h"
@@ -37,6 +38,33 @@ __device__ __forceinline__ void load_row(float2 (&v)[V], const float2* __restric
     using P = Plan<N, V>;
 #pragma unroll
     for (int r = 0; r < V; ++r) v[r] = ok ? __ldcs(row + P::xpos(t, r)) : make_float2(0.f, 0.f);
+}
+
+// w[0] = sum of w[0 .. H) as a fixed tree: halves of ceil(H/2) are added elementwise until one remains
+template <int H, int V>
+__device__ __forceinline__ void tree_sum(float (&w)[V]) {
+    if constexpr (H > 1) {
+        constexpr int HALF = (H + 1) / 2;
+#pragma unroll
+        for (int r = 0; r < H - HALF; ++r) w[r] += w[r + HALF];
+        tree_sum<HALF, V>(w);
+    }
+}
+
+// sum of part[0 .. n) in a fixed order (thread i takes entries i, i + blockDim, ...; then a fixed
+// shuffle tree and the warps in order), returned to every thread of the block; sh: blockDim / 32
+// doubles of shared scratch, free on entry
+__device__ __forceinline__ double sweep_sum_partials(const double* __restrict__ part, int n, double* sh) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v += part[i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    __syncthreads();  // the scratch's previous readers are done
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh[w];
+    return tot;
 }
 
 // phi, dss: this depth's rows staged in shared memory
@@ -204,11 +232,67 @@ __global__ void __launch_bounds__(sweep_max_threads<V>()) sweep_kernel(const Swe
             }
         }
     } else if constexpr (MODE == MODE_ADJOINT) {
+        // Inside a CG iteration the residual update r <- r - alpha q (alpha = gamma / (||q||^2 +
+        // lambda ||p||^2), Eq. 11) is applied here, as each item loads its data: every block forms
+        // alpha from the same partial sums in the same order; a non-positive or non-finite
+        // denominator sets the breakdown flag and leaves r as it is.
+        const size_t drow_off = ((size_t)ishot * a.nw + iw) * a.nrec;
+        float alpha = 0.f;
+        bool upd = false;
+        float2 qv[V];
+        if (a.r_io && a.rec_identity) {
+            // r and q are requested before alpha is formed, so their latency hides behind it (and
+            // no store to r sits between two loads)
+#pragma unroll
+            for (int r = 0; r < V; ++r) {
+                v[r] = ok ? __ldcs(a.r_io + drow_off + P::xpos(t, r)) : make_float2(0.f, 0.f);
+                qv[r] = ok ? __ldcs(a.dq + drow_off + P::xpos(t, r)) : make_float2(0.f, 0.f);
+            }
+        }
+        if (a.r_io) {
+            double* sh = reinterpret_cast<double*>(stage);  // scratch until staging starts below
+            const double qq = sweep_sum_partials(a.qq_in, a.nqq, sh);
+            const double pp = sweep_sum_partials(a.pp_in, a.npp, sh);
+            const int gi = a.cg_gi < 0 ? a.cg->gi : a.cg_gi;
+            const double gamma = a.cg->gamma[gi];
+            const double delta = qq + a.lam * pp;
+            const bool bad = !(delta > 0.0) || !isfinite(delta) || !isfinite(gamma);
+            const double al = bad ? 0.0 : gamma / delta;
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                a.cg->delta = delta;
+                a.cg->alpha = al;
+                if (bad) a.cg->breakdown = 1;
+            }
+            alpha = (float)al;
+            upd = !bad;
+            __syncthreads();  // every thread has read the scratch
+        }
         if (nz > 1) stage_rows(0, 0, false);
         // R_0: data injected at the receivers
-        const float2* drow = a.din + ((size_t)ishot * a.nw + iw) * a.nrec;
+        const float2* drow = a.r_io ? nullptr : a.din + drow_off;
+        auto r_updated = [&](int rr) -> float2 {  // r[rr] - alpha q[rr], stored back
+            float2 x = a.r_io[drow_off + rr];
+            if (upd) {
+                const float2 y = a.dq[drow_off + rr];
+                x.x = fmaf(-alpha, y.x, x.x);
+                x.y = fmaf(-alpha, y.y, x.y);
+                a.r_io[drow_off + rr] = x;
+            }
+            return x;
+        };
         if (a.rec_identity) {
-            load_row<N, V>(v, drow, t, ok);
+            if (a.r_io) {
+                if (upd && ok) {
+#pragma unroll
+                    for (int r = 0; r < V; ++r) {
+                        v[r].x = fmaf(-alpha, qv[r].x, v[r].x);
+                        v[r].y = fmaf(-alpha, qv[r].y, v[r].y);
+                        __stcs(a.r_io + drow_off + P::xpos(t, r), v[r]);
+                    }
+                }
+            } else {
+                load_row<N, V>(v, drow, t, ok);
+            }
         } else {
             __syncwarp();
             for (int x = t; x < P::BUF; x += T) buf[x] = make_float2(0.f, 0.f);
@@ -216,7 +300,7 @@ __global__ void __launch_bounds__(sweep_max_threads<V>()) sweep_kernel(const Swe
             if (ok) {
                 const int* rix = a.rec_ix + (size_t)shot * a.nrec;
                 for (int rr = t; rr < a.nrec; rr += T) {
-                    const float2 dv = __ldg(drow + rr);
+                    const float2 dv = a.r_io ? r_updated(rr) : __ldg(drow + rr);
                     const int x = P::phys(__ldg(rix + rr));
                     atomicAdd(&buf[x].x, dv.x);
                     atomicAdd(&buf[x].y, dv.y);
@@ -325,6 +409,41 @@ __global__ void __launch_bounds__(sweep_max_threads<V>()) sweep_kernel(const Swe
             if (ok) {
                 const int* rix = a.rec_ix + (size_t)shot * a.nrec;
                 for (int rr = t; rr < a.nrec; rr += T) orow[rr] = buf[P::phys(__ldg(rix + rr))];
+            }
+        }
+        if (a.qq_part) {
+            // the block's partial sum of |q|^2 over the data it recorded (the CG step length's
+            // denominator), in a fixed order: each thread's elements, a shuffle tree, warps in order
+            // (a thread's own |q|^2 terms are added as a float32 tree -- relative error at most
+            // ceil(log2 V) 2^-24, V <= 56 -- because float64 arithmetic is slow on this part; the sums
+            // across threads and warps are float64)
+            double e = 0.0;
+            if (ok) {
+                if (a.rec_identity) {
+                    float w[V];
+#pragma unroll
+                    for (int r = 0; r < V; ++r) w[r] = fmaf(v[r].x, v[r].x, v[r].y * v[r].y);
+                    tree_sum<V, V>(w);
+                    e = (double)w[0];
+                } else {
+                    const int* rix = a.rec_ix + (size_t)shot * a.nrec;
+                    for (int rr = t; rr < a.nrec; rr += T) {
+                        const float2 u = buf[P::phys(__ldg(rix + rr))];
+                        e += (double)u.x * u.x + (double)u.y * u.y;
+                    }
+                }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+            double* sh = reinterpret_cast<double*>(stage);
+            cp_async_wait_all();
+            __syncthreads();  // every warp is past its last staged row
+            if (lane == 0) sh[warp] = e;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double tot = 0.0;
+                for (int w = 0; w < nwarps; ++w) tot += sh[w];
+                a.qq_part[blockIdx.x] = tot;
             }
         }
     }
