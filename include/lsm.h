@@ -69,7 +69,8 @@ extern "C" {
 #define LSM_OP_SOLVE 2
 #define LSM_OP_GRADIENT 3
 
-/* depth stride of the source / adjoint wavefield checkpoints kept by lsm_born_gradient */
+/* default depth stride of the source / adjoint wavefield checkpoints kept by lsm_born_gradient
+ * (lsm_autotune_gradient may record another one of 8, 16, 32) */
 #define LSM_CHECKPOINT_EVERY 16
 
 typedef struct {
@@ -145,8 +146,9 @@ int lsm_adjoint(const lsm_grid* grid, const float* slowness, const lsm_freqs* fr
  *   mu_nz = 0, mu_j = m_j R_j + P_j^H mu_{j+1};
  *   grad_m_j = Re sum conj(S_j) R_j   (= A^T g, Eq. 2),
  *   grad_s_j = Re sum i w dz [conj(R_j) P_j U_{j+1} + conj(mu_{j+1}) S_{j+1}],
- * summed over the shots and frequencies.  S and R are swept down once keeping only every
- * LSM_CHECKPOINT_EVERY-th depth, and recomputed segment by segment while U and mu run up.
+ * summed over the shots and frequencies.  S and R are swept down once keeping only every c-th
+ * depth, and recomputed segment by segment while U and mu run up; c is LSM_CHECKPOINT_EVERY unless
+ * lsm_autotune_gradient recorded a stride for this problem (the results do not depend on c).
  *   m: device float32 [nz][nx];
  *   g: device complex64 [nshots][nw][nrec], dL/dRe(d) + i dL/dIm(d) (the convention of PyTorch
  *      complex gradients), or NULL to only model d;
@@ -363,6 +365,30 @@ typedef struct {
 int lsm_autotune(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs,
                  const lsm_geom* geom, int nshots, const lsm_solve_options* options,
                  void* workspace, size_t workspace_bytes, void* stream, lsm_tune_report* report);
+
+/*
+ * Checkpoint stride of lsm_born_gradient.  The gradient sweep keeps S and R at every c-th depth and
+ * recomputes them segment by segment, so its arithmetic and its results are the same for every c;
+ * c sets how many checkpoint and segment rows each (shot, frequency) item keeps and how much of
+ * that traffic stays in L2.  lsm_autotune_gradient times the gradient kernel of a launch over
+ * `nshots` shots of this grid and frequency set at c = LSM_CHECKPOINT_EVERY, 8, 16 and 32 (strides
+ * above nz act as nz) and records the fastest; from then on lsm_born_gradient calls on the current
+ * device with the same (nx, nz, nshots, nw) use it.  lsm_workspace_bytes(..., LSM_OP_GRADIENT)
+ * already reserves room for every candidate.  Needs a workspace of
+ * lsm_workspace_bytes(grid, geom, freqs, nshots, LSM_OP_GRADIENT); runs shots [0, nshots) on
+ * zero-valued model and data-space gradient, overwrites the workspace, and returns after
+ * synchronising the stream.  Gradients need nx <= 512 (LSM_ERR_UNSUPPORTED_NX otherwise).
+ * `report` (may be NULL) receives the chosen and the default stride, their mean launch times in
+ * ms and the number of strides timed.  lsm_autotune_reset also forgets recorded strides.
+ */
+typedef struct {
+    int stride, default_stride, candidates;
+    double ms, default_ms;
+} lsm_ckpt_tune_report;
+
+int lsm_autotune_gradient(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs,
+                          const lsm_geom* geom, int nshots, void* workspace, size_t workspace_bytes,
+                          void* stream, lsm_ckpt_tune_report* report);
 void lsm_autotune_reset(void);
 
 /* Human-readable name of a status code (static string). */

@@ -14,6 +14,7 @@ from .lsm import (  # noqa: F401
     lsm_adjoint,
     lsm_autotune,
     lsm_autotune_reset,
+    lsm_autotune_gradient,
     lsm_born_gradient,
     lsm_forward,
     lsm_kernel_launches,

@@ -131,6 +131,37 @@ static int tuned_warps(int nx, int mode, int transform, int nshots, int nw) {
     return it == g_tune.end() ? 0 : it->second;
 }
 
+// Checkpoint stride of the gradient sweep (lsm_born_gradient): S and R are kept every c-th depth
+// and recomputed segment by segment, so the arithmetic is the same for every c; c sets how many
+// checkpoint and segment rows each item keeps, and with them the memory traffic.
+// lsm_autotune_gradient times the candidates and records the fastest per (device, nx, nz, shots,
+// frequencies); the layout reserves room for the largest candidate's rows.
+static const int kCkptStrides[] = {8, 16, 32};
+struct CkptKey {
+    int dev, nx, nz, nshots, nw;
+    bool operator<(const CkptKey& o) const {
+        return std::tie(dev, nx, nz, nshots, nw) < std::tie(o.dev, o.nx, o.nz, o.nshots, o.nw);
+    }
+};
+static std::map<CkptKey, int> g_ckpt_tune;  // guarded by g_tune_mu
+static CkptKey ckpt_key(int nx, int nz, int nshots, int nw) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) cudaGetLastError();
+    return CkptKey{dev, nx, nz, nshots, nw};
+}
+static int ckpt_stride(int nx, int nz, int nshots, int nw) {
+    const CkptKey k = ckpt_key(nx, nz, nshots, nw);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_ckpt_tune.find(k);
+    return std::min(it == g_ckpt_tune.end() ? LSM_CHECKPOINT_EVERY : it->second, nz);
+}
+// rows of nx complex values one item keeps at stride c: S and R checkpoints, then the segment's
+// S rows (c + 1) and R rows (c)
+static size_t ckpt_rows(int c, int nz) {
+    c = std::min(c, nz);
+    return 2 * (size_t)((nz + c - 1) / c) + 2 * (size_t)c + 1;
+}
+
 // most warps per block a sweep of this mode can take (registers, shared memory)
 static int sweep_max_warps(int nx, int mode, int nshots, int nw) {
     const NxOps* ops = nx_ops(nx);
@@ -271,7 +302,7 @@ struct Layout {
     // offsets in bytes from the workspace base
     size_t src, rec, freq, wav, sref, phi, dss, S, part;
     size_t p, s, r, q, qq, pp, ss, state;
-    size_t ckpt, seg, part_s;  // gradient op
+    size_t ckpt, part_s, tune_m, tune_g;  // gradient op
     size_t illum, minv, bmax, sz;  // preconditioned solve
     size_t ctrl;                   // solve: window start read by graph-replayed sweeps
     size_t total;
@@ -311,12 +342,13 @@ Layout make_layout(const lsm_grid* g, const lsm_geom* geo, const lsm_freqs* f, i
     L.part = take((size_t)L.nparts * plane * sizeof(float));
     if (op == LSM_OP_GRADIENT) {
         const size_t items = (size_t)nshots * nw;
-        const size_t c = LSM_CHECKPOINT_EVERY;
-        const size_t ncp = (nz + c - 1) / c;
+        size_t rows = ckpt_rows(LSM_CHECKPOINT_EVERY, (int)nz);
+        for (int c : kCkptStrides) rows = std::max(rows, ckpt_rows(c, (int)nz));
         L.part_s = take((size_t)L.nparts * plane * sizeof(float));
-        L.ckpt = take(items * 2 * ncp * nx * sizeof(float2));
-        L.seg = take(items * (2 * c + 1) * nx * sizeof(float2));
+        L.ckpt = take(items * rows * nx * sizeof(float2));  // checkpoints, then segments (per stride)
         L.ss = take(kImgRedBlocks * sizeof(double));
+        L.tune_m = take(plane * sizeof(float));  // lsm_autotune_gradient's zero inputs
+        L.tune_g = take(items * geo->nrec * sizeof(float2));
     }
     if (op == LSM_OP_SOLVE) {
         const size_t nd = (size_t)nshots * nw * geo->nrec;
@@ -650,6 +682,35 @@ int lsm_adjoint_static(const lsm_grid* grid, const float* slowness, const lsm_fr
     return LSM_OK;
 }
 
+// Arguments of the gradient kernel over shots [shot0, shot0 + nshots) at checkpoint stride c: the
+// checkpoint rows of every item, then its segment rows, in the layout's gradient region.
+static GradArgs grad_args(const lsm_grid* grid, const lsm_freqs* freqs, const lsm_geom* geom, const Layout& L,
+                          char* ws, int shot0, int nshots, int c) {
+    GradArgs ga{};
+    ga.nx = grid->nx;
+    ga.nz = grid->nz;
+    ga.nw = freqs->nw;
+    ga.nrec = geom->nrec;
+    ga.shot0 = shot0;
+    ga.nshots = nshots;
+    ga.rec_identity = geom->rec_ix == nullptr ? 1 : 0;
+    ga.ckpt_every = c;
+    ga.dz = grid->dz;
+    ga.src_ix = reinterpret_cast<const int*>(ws + L.src);
+    ga.rec_ix = geom->rec_ix ? reinterpret_cast<const int*>(ws + L.rec) : nullptr;
+    ga.wavelet = reinterpret_cast<const float2*>(ws + L.wav);
+    ga.freq_hz = reinterpret_cast<const float*>(ws + L.freq);
+    ga.phi = reinterpret_cast<const float2*>(ws + L.phi);
+    ga.dss = reinterpret_cast<const float2*>(ws + L.dss);
+    const size_t items = (size_t)nshots * freqs->nw;
+    const size_t ncp = (size_t)((grid->nz + c - 1) / c);
+    ga.ckpt = reinterpret_cast<float2*>(ws + L.ckpt);
+    ga.seg = ga.ckpt + items * 2 * ncp * grid->nx;
+    ga.part_m = reinterpret_cast<float*>(ws + L.part);
+    ga.part_s = reinterpret_cast<float*>(ws + L.part_s);
+    return ga;
+}
+
 int lsm_born_gradient(const lsm_grid* grid, const float* slowness, const double* sref, const lsm_freqs* freqs,
                       const lsm_geom* geom, const float* m, const float* g, float* d_out, float* grad_m, float* grad_s,
                       int shot0, int nshots, void* workspace, size_t workspace_bytes, void* stream) {
@@ -680,28 +741,10 @@ int lsm_born_gradient(const lsm_grid* grid, const float* slowness, const double*
     }
     rc = prepare(grid, slowness, freqs, geom, L, ws, st, sref, TABLES_GRADIENT);
     if (rc != LSM_OK) return rc;
-    GradArgs ga{};
-    ga.nx = grid->nx;
-    ga.nz = grid->nz;
-    ga.nw = freqs->nw;
-    ga.nrec = geom->nrec;
-    ga.shot0 = shot0;
-    ga.nshots = nshots;
-    ga.rec_identity = geom->rec_ix == nullptr ? 1 : 0;
-    ga.ckpt_every = LSM_CHECKPOINT_EVERY;
-    ga.dz = grid->dz;
-    ga.src_ix = reinterpret_cast<const int*>(ws + L.src);
-    ga.rec_ix = geom->rec_ix ? reinterpret_cast<const int*>(ws + L.rec) : nullptr;
-    ga.wavelet = reinterpret_cast<const float2*>(ws + L.wav);
-    ga.freq_hz = reinterpret_cast<const float*>(ws + L.freq);
-    ga.phi = reinterpret_cast<const float2*>(ws + L.phi);
-    ga.dss = reinterpret_cast<const float2*>(ws + L.dss);
+    GradArgs ga = grad_args(grid, freqs, geom, L, ws, shot0, nshots,
+                            ckpt_stride(grid->nx, grid->nz, nshots, freqs->nw));
     ga.m = m;
     ga.g = reinterpret_cast<const float2*>(g);
-    ga.ckpt = reinterpret_cast<float2*>(ws + L.ckpt);
-    ga.seg = reinterpret_cast<float2*>(ws + L.seg);
-    ga.part_m = reinterpret_cast<float*>(ws + L.part);
-    ga.part_s = reinterpret_cast<float*>(ws + L.part_s);
     ga.dout = reinterpret_cast<float2*>(d_out);
     const SweepShape sh = gradient_shape(grid->nx, nshots, freqs->nw, nsm);
     ga.wslots = sh.wslots;
@@ -826,6 +869,78 @@ int lsm_autotune(const lsm_grid* grid, const float* slowness, const lsm_freqs* f
 void lsm_autotune_reset(void) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune.clear();
+    g_ckpt_tune.clear();
+}
+
+int lsm_autotune_gradient(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs, const lsm_geom* geom,
+                          int nshots, void* workspace, size_t workspace_bytes, void* stream,
+                          lsm_ckpt_tune_report* report) {
+    int rc = validate_common(grid, freqs, geom);
+    if (rc != LSM_OK) return rc;
+    if (!aligned16(slowness) || !aligned16(workspace)) return LSM_ERR_ARG;
+    if (nshots < 1 || nshots > geom->ns) return LSM_ERR_ARG;
+    if (!gradient_nx_supported(grid->nx)) return LSM_ERR_UNSUPPORTED_NX;
+    const int nsm = num_sms_current();
+    const Layout L = make_layout(grid, geom, freqs, nshots, LSM_OP_GRADIENT, nsm);
+    if (workspace_bytes < L.total) return LSM_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(workspace);
+    const int nx = grid->nx, nz = grid->nz, nw = freqs->nw;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_ckpt_tune.erase(ckpt_key(nx, nz, nshots, nw));
+    }
+    rc = prepare(grid, slowness, freqs, geom, L, ws, st, nullptr, TABLES_GRADIENT);
+    if (rc != LSM_OK) return rc;
+    LSM_CHECK(cudaMemsetAsync(ws + L.tune_m, 0, (size_t)nx * nz * sizeof(float), st));
+    LSM_CHECK(cudaMemsetAsync(ws + L.tune_g, 0, (size_t)nshots * nw * geom->nrec * sizeof(float2), st));
+    const SweepShape sh = gradient_shape(nx, nshots, nw, nsm);
+    EventPair ev;
+    LSM_CHECK(cudaEventCreate(&ev.a));
+    LSM_CHECK(cudaEventCreate(&ev.b));
+    const int def = std::min(LSM_CHECKPOINT_EVERY, nz);
+    int best = def, ncand = 0;
+    double best_ms = 0.0, def_ms = 0.0;
+    int tried[sizeof(kCkptStrides) / sizeof(int) + 1];
+    for (int i = 0; i <= (int)(sizeof(kCkptStrides) / sizeof(int)); ++i) {
+        // the default first, then the candidates (strides above nz act as nz and are timed once)
+        const int c = std::min(i == 0 ? LSM_CHECKPOINT_EVERY : kCkptStrides[i - 1], nz);
+        bool seen = false;
+        for (int k = 0; k < ncand; ++k) seen = seen || tried[k] == c;
+        if (seen) continue;
+        tried[ncand++] = c;
+        GradArgs ga = grad_args(grid, freqs, geom, L, ws, 0, nshots, c);
+        ga.m = reinterpret_cast<const float*>(ws + L.tune_m);
+        ga.g = reinterpret_cast<const float2*>(ws + L.tune_g);
+        ga.wslots = sh.wslots;
+        LSM_CHECK(launch_gradient(ga, sh, st));  // untimed first launch
+        LSM_CHECK(cudaEventRecord(ev.a, st));
+        constexpr int reps = 3;
+        for (int r = 0; r < reps; ++r) LSM_CHECK(launch_gradient(ga, sh, st));
+        LSM_CHECK(cudaEventRecord(ev.b, st));
+        LSM_CHECK(cudaEventSynchronize(ev.b));
+        float t = 0.f;
+        LSM_CHECK(cudaEventElapsedTime(&t, ev.a, ev.b));
+        const double ms = (double)t / reps;
+        if (c == def) def_ms = ms;
+        if (ncand == 1 || ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_ckpt_tune[ckpt_key(nx, nz, nshots, nw)] = best;
+    }
+    if (report) {
+        report->stride = best;
+        report->default_stride = def;
+        report->candidates = ncand;
+        report->ms = best_ms;
+        report->default_ms = def_ms;
+    }
+    LSM_CHECK(cudaStreamSynchronize(st));
+    return LSM_OK;
 }
 
 int lsm_num_windows(int ns, int K, int slide) {

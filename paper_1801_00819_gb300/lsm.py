@@ -34,7 +34,7 @@ EXPORTED = ("lsm_workspace_bytes", "lsm_forward", "lsm_adjoint", "lsm_num_window
             "lsm_status_string", "lsm_kernel_launches", "lsm_profile_start", "lsm_profile_stop",
             "lsm_adjoint_static", "lsm_born_gradient", "rls_window_solve_ex", "rls_multi_line_solve",
             "lsm_forward_ex", "lsm_adjoint_ex", "lsm_profile_start_classes", "lsm_autotune",
-            "lsm_autotune_reset")
+            "lsm_autotune_reset", "lsm_autotune_gradient")
 
 TRANSFORMS = {"fft": 0, "dft_bf16x3": 1, "dft_fp16x3": 2, "dft_bf16x1": 3}
 
@@ -122,6 +122,11 @@ class lsm_tune_report(ctypes.Structure):
     _fields_ = [("source", lsm_tune_entry), ("adjoint", lsm_tune_entry), ("forward", lsm_tune_entry)]
 
 
+class lsm_ckpt_tune_report(ctypes.Structure):
+    _fields_ = [("stride", ctypes.c_int), ("default_stride", ctypes.c_int), ("candidates", ctypes.c_int),
+                ("ms", ctypes.c_double), ("default_ms", ctypes.c_double)]
+
+
 _lib_handle = None
 
 
@@ -174,6 +179,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lsm_autotune.argtypes = [ctypes.POINTER(lsm_grid), ctypes.c_void_p, ctypes.POINTER(lsm_freqs),
                                  ctypes.POINTER(lsm_geom), ctypes.c_int, ctypes.POINTER(lsm_solve_options),
                                  ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.POINTER(lsm_tune_report)]
+    lib.lsm_autotune_gradient.restype = ctypes.c_int
+    lib.lsm_autotune_gradient.argtypes = [ctypes.POINTER(lsm_grid), ctypes.c_void_p, ctypes.POINTER(lsm_freqs),
+                                          ctypes.POINTER(lsm_geom), ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
+                                          ctypes.c_void_p, ctypes.POINTER(lsm_ckpt_tune_report)]
     lib.lsm_autotune_reset.restype = None
     lib.lsm_autotune_reset.argtypes = []
     lib.lsm_status_string.restype = ctypes.c_char_p
@@ -418,6 +427,21 @@ def lsm_autotune(grid, slowness, freqs, geom, nshots, workspace, stream=None, tr
     return {"source": rep.source.as_dict(), "adjoint": rep.adjoint.as_dict(), "forward": rep.forward.as_dict()}
 
 
+def lsm_autotune_gradient(grid, slowness, freqs, geom, nshots, workspace, stream=None) -> dict:
+    """Time lsm_born_gradient's kernel at each candidate checkpoint stride for launches over `nshots`
+    shots and record the fastest for later calls (see include/lsm.h).  `workspace` must hold
+    lsm_workspace_bytes(..., nshots, LSM_OP_GRADIENT).  Returns {stride, default_stride, candidates,
+    ms, default_ms}."""
+    rep = lsm_ckpt_tune_report()
+    st = load_library().lsm_autotune_gradient(ctypes.byref(grid.c), _ptr(slowness), ctypes.byref(freqs.c),
+                                               ctypes.byref(geom.c), int(nshots), _ptr(workspace),
+                                               _nbytes(workspace), _stream(stream), ctypes.byref(rep))
+    _check(st, "lsm_autotune_gradient")
+    return {"stride": int(rep.stride), "default_stride": int(rep.default_stride),
+            "candidates": int(rep.candidates), "ms": float(rep.ms), "default_ms": float(rep.default_ms)}
+
+
 def lsm_autotune_reset() -> None:
-    """Forget every launch shape recorded by lsm_autotune."""
+    """Forget every launch shape recorded by lsm_autotune and every stride recorded by
+    lsm_autotune_gradient."""
     load_library().lsm_autotune_reset()

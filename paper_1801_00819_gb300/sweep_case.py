@@ -1,6 +1,6 @@
 """Run one window of A and A^T on a synthetic survey, for timing and profiling the sweep kernels.
 
-    python -m paper_1801_00819_gb300.sweep_case [--workload realistic|tiny] [--reps N] [--gradient]
+    python -m paper_1801_00819_gb300.sweep_case [--workload realistic|tiny] [--reps N] [--gradient [--tune-gradient]]
 
 Prepares the workload's grid, velocity, geometry and frequencies on the device, random data for
 one window of K shots, then calls lsm_forward and lsm_adjoint through the C ABI `reps` times each
@@ -32,6 +32,8 @@ def main():
     ap.add_argument("--shots", type=int, default=0, help="shots per call (default: the window length)")
     ap.add_argument("--transform", default="fft", help="fft, dft_bf16x3, dft_fp16x3 or dft_bf16x1")
     ap.add_argument("--gradient", action="store_true", help="also time lsm_born_gradient on the window")
+    ap.add_argument("--tune-gradient", action="store_true",
+                    help="with --gradient: record the fastest checkpoint stride (lsm_autotune_gradient) first")
     args = ap.parse_args()
 
     import torch
@@ -55,6 +57,9 @@ def main():
         sref = torch.as_tensor(np.asarray(sv.slowness, dtype=np.float64).mean(axis=1), device="cuda")
         grad_m = torch.empty_like(m)
         grad_s = torch.empty_like(m)
+    tune = None
+    if args.gradient and args.tune_gradient:
+        tune = L.lsm_autotune_gradient(ds.grid, ds.slowness, ds.freqs, ds.geom, K, ws_g)
     L.lsm_profile_start()
     for _ in range(args.reps):
         L.lsm_forward(ds.grid, ds.slowness, ds.freqs, ds.geom, m, out, 0, K, ws, transform=args.transform)
@@ -66,7 +71,8 @@ def main():
     prof = L.lsm_profile_stop()
     print(json.dumps({"workload": sv.name, "transform": args.transform, "K": K, "nw": sv.nw, "nz": sv.nz, "nx": sv.nx,
                       "per_launch_ms": {k: (v["ms"] / v["launches"] if v["launches"] else 0.0)
-                                        for k, v in prof.items()}}))
+                                        for k, v in prof.items()},
+                      "gradient_stride_tune": tune}))
 
 
 if __name__ == "__main__":

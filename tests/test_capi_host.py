@@ -36,7 +36,7 @@ def test_header_declares_expected_entry_points():
                                             "lsm_profile_start", "lsm_profile_stop", "lsm_adjoint_static",
                                             "lsm_born_gradient", "rls_window_solve_ex", "rls_multi_line_solve",
                                             "lsm_forward_ex", "lsm_adjoint_ex", "lsm_profile_start_classes",
-                                            "lsm_autotune", "lsm_autotune_reset"])
+                                            "lsm_autotune", "lsm_autotune_reset", "lsm_autotune_gradient"])
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -195,5 +195,37 @@ def test_autotune_validation_before_any_launch(lib):
     with pytest.raises(lib.LsmError) as ei:  # nx 64 has no tensor-core variant
         lib.lsm_autotune(g, fake, f, geo, 2, FakeWs(sol), stream=0, transform="dft_bf16x3")
     assert ei.value.status == lib.LSM_ERR_UNSUPPORTED_NX
+    lib.lsm_autotune_reset()
+    assert lib.lsm_kernel_launches() == before
+
+
+def test_gradient_stride_tuning_validation_before_any_launch(lib):
+    """lsm_autotune_gradient checks its shot count and workspace size on the host first, and the
+    gradient workspace reserves room for every candidate stride."""
+    before = lib.lsm_kernel_launches()
+    g, geo, f = _holders(lib)
+    grad = lib.lsm_workspace_bytes(g, geo, f, 2, lib.LSM_OP_GRADIENT)
+    assert grad > 0
+
+    class FakeWs:
+        def __init__(self, n):
+            self.n = n
+
+        def numel(self):
+            return self.n
+
+        def element_size(self):
+            return 1
+
+        def data_ptr(self):
+            return 1 << 20
+    fake = 1 << 20
+    for nshots in (0, 4):  # the survey has 3 shots
+        with pytest.raises(lib.LsmError) as ei:
+            lib.lsm_autotune_gradient(g, fake, f, geo, nshots, FakeWs(1 << 30), stream=0)
+        assert ei.value.status == lib.LSM_ERR_ARG
+    with pytest.raises(lib.LsmError) as ei:
+        lib.lsm_autotune_gradient(g, fake, f, geo, 2, FakeWs(grad - 1), stream=0)
+    assert ei.value.status == lib.LSM_ERR_WORKSPACE
     lib.lsm_autotune_reset()
     assert lib.lsm_kernel_launches() == before

@@ -111,3 +111,47 @@ def test_tuned_tensor_core_shapes_keep_parity(torch_cuda):
                   transform="dft_fp16x3")
     torch.cuda.synchronize()
     assert rel_l2(out.cpu().numpy(), op.forward(m.astype(np.float64), shots=np.arange(K))) <= 1e-4
+
+
+@pytest.mark.parametrize("shape", [(64, 40, 3, 5), (128, 20, 2, 4)], ids=lambda s: "x".join(map(str, s)))
+def test_gradient_stride_tuning_keeps_gradients_bitwise(torch_cuda, shape):
+    """lsm_autotune_gradient records one of the candidate checkpoint strides; the gradients and the
+    modelled data computed afterwards are bitwise the default stride's (the segments replay the same
+    steps from their checkpoints) and match the FP64 oracle."""
+    import paper_1801_00819_gb300 as L
+    torch = torch_cuda
+    nx, nz, ns, nw = shape
+    sv = random_case(nx, nz, ns, nw, seed=nx + 3)
+    ds = device_survey(sv)
+    op = oracle_operator(sv)
+    m = np.asarray(sv.reflectivity, dtype=np.float32)
+    rng = np.random.default_rng(nx)
+    dobs = (rng.normal(size=(ns, nw, op.nrec)) + 1j * rng.normal(size=(ns, nw, op.nrec))) * 0.05
+    g = (op.forward(m.astype(np.float64)) - dobs) * 2.0
+    sref = torch.as_tensor(op.sref, device="cuda")
+    ws = torch.empty(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, ns, L.LSM_OP_GRADIENT), dtype=torch.uint8,
+                     device="cuda")
+    mt = torch.as_tensor(m, device="cuda")
+    gt = torch.as_tensor(g.astype(np.complex64), device="cuda")
+
+    def run():
+        gm, gs = torch.empty_like(mt), torch.empty_like(mt)
+        d = torch.empty((ns, nw, op.nrec), dtype=torch.complex64, device="cuda")
+        L.lsm_born_gradient(ds.grid, ds.slowness, sref, ds.freqs, ds.geom, mt, gt, d, gm, gs, 0, ns, ws)
+        torch.cuda.synchronize()
+        return gm.cpu().numpy(), gs.cpu().numpy(), d.cpu().numpy()
+
+    gm0, gs0, d0 = run()
+    rep = L.lsm_autotune_gradient(ds.grid, ds.slowness, ds.freqs, ds.geom, ns, ws)
+    print(rep)
+    assert rep["default_stride"] == min(L.lsm.LSM_CHECKPOINT_EVERY, nz)
+    assert rep["stride"] in {min(c, nz) for c in (8, 16, 32)}
+    assert rep["candidates"] == len({min(c, nz) for c in (8, 16, 32, L.lsm.LSM_CHECKPOINT_EVERY)})
+    assert 0.0 < rep["ms"] <= rep["default_ms"]
+    gm1, gs1, d1 = run()
+    np.testing.assert_array_equal(gm1, gm0)
+    np.testing.assert_array_equal(gs1, gs0)
+    np.testing.assert_array_equal(d1, d0)
+    gm_ref, gs_ref = O.born_gradients(op, m.astype(np.float64), g)
+    assert rel_l2(gm1, gm_ref) <= 1e-4
+    assert rel_l2(gs1, gs_ref) <= 1e-4
