@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from oracle import lsm_oracle as O
-from synth import config_tiny, random_case
+from synth import config_tiny, config_realistic, random_case
 from tests._helpers import oracle_operator, rel_l2, device_survey
 
 pytestmark = pytest.mark.gpu
@@ -220,3 +220,61 @@ def test_receiver_subset_sliding_solve(torch_cuda):
         assert abs(g["rel_res0"] - r.rel_res0) <= 1e-3 * r.rel_res0
         assert abs(g["rel_res"] - r.rel_res) <= 1e-2 * r.rel_res
     assert rel_l2(m_gpu, m_ref) <= 1e-4
+
+
+def test_realistic_window_cg_matches_host_cg_over_library_operator(torch_cuda):
+    """Full size, in the launch configuration bench.py times (512 x 256, 128 frequencies, the first
+    window of 16 shots): three device CG iterations from m = 0 equal host float64 CG (Eq. 11) run
+    over the library's own A and A^T, which tests/test_gpu_operator.py checks against the oracle at
+    this size.  This is a property check of the fused vector steps (|q|^2 partials in the forward
+    sweep, alpha and r -= alpha q in the adjoint sweep, m += alpha p in the image reduction); the
+    oracle's own solve is out of reach at this size."""
+    import paper_1801_00819_gb300 as L
+    torch = torch_cuda
+    sv = config_realistic()
+    ds = device_survey(sv)
+    K, nw, nz, nx, nrec = sv.window, sv.nw, sv.nz, sv.nx, ds.nrec
+    ws_op = torch.empty(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, K, L.LSM_OP_ADJOINT), dtype=torch.uint8,
+                        device="cuda")
+
+    def A(m):
+        out = torch.empty((K, nw, nrec), dtype=torch.complex64, device="cuda")
+        L.lsm_forward(ds.grid, ds.slowness, ds.freqs, ds.geom, torch.as_tensor(m.astype(np.float32), device="cuda"),
+                      out, 0, K, ws_op)
+        return out.cpu().numpy().astype(np.complex128)
+
+    def AT(d):
+        img = torch.empty((nz, nx), dtype=torch.float32, device="cuda")
+        L.lsm_adjoint(ds.grid, ds.slowness, ds.freqs, ds.geom, torch.as_tensor(d.astype(np.complex64), device="cuda"),
+                      img, 0, K, ws_op)
+        return img.cpu().numpy().astype(np.float64)
+
+    clean = A(np.asarray(sv.reflectivity, dtype=np.float64))
+    rng = np.random.default_rng(4)
+    noise = rng.normal(size=clean.shape) + 1j * rng.normal(size=clean.shape)
+    d = (clean + 0.02 * np.sqrt(np.mean(np.abs(clean) ** 2)) * noise / np.sqrt(2)).astype(np.complex64)
+    d = d.astype(np.complex128)
+    b = AT(d)
+    lam = float(np.float32(1e-3 * np.abs(b).max()))
+
+    m = np.zeros((nz, nx))
+    r = d.copy()
+    s = b.copy()
+    p = s.copy()
+    gamma = float(np.sum(s * s))
+    for _ in range(3):
+        q = A(p)
+        alpha = gamma / (float(np.sum(np.abs(q) ** 2)) + lam * float(np.sum(p * p)))
+        m = m + alpha * p
+        r = r - alpha * q
+        s = AT(r) - lam * m
+        g_new = float(np.sum(s * s))
+        p = s + (g_new / gamma) * p
+        gamma = g_new
+
+    d_all = np.zeros((sv.ns, nw, nrec), dtype=np.complex64)
+    d_all[:K] = d
+    m_gpu, st = _gpu_solve(torch, ds, d_all, lam, K, sv.slide, 0.0, 3, n_windows=1)
+    assert len(st) == 1 and st[0]["start"] == 0 and st[0]["iters"] == 3
+    assert rel_l2(m_gpu, m) <= 1e-4
+    assert abs(st[0]["rel_res"] - np.sqrt(gamma / np.sum(b * b))) <= 1e-3 * st[0]["rel_res"]
