@@ -278,3 +278,23 @@ def test_realistic_window_cg_matches_host_cg_over_library_operator(torch_cuda):
     assert len(st) == 1 and st[0]["start"] == 0 and st[0]["iters"] == 3
     assert rel_l2(m_gpu, m) <= 1e-4
     assert abs(st[0]["rel_res"] - np.sqrt(gamma / np.sum(b * b))) <= 1e-3 * st[0]["rel_res"]
+
+
+@pytest.mark.parametrize("shape", [(16, 12, 5, 40, 21), (1024, 8, 3, 3, 22)], ids=["nx16", "nx1024"])
+def test_extreme_width_sliding_solve(torch_cuda, shape):
+    """The narrowest and widest supported widths through the sliding solve (K = 2, slide 1, two CG
+    iterations per window): at nx = 16 one thread holds a whole item (32 items per warp), at
+    nx = 1024 a warp holds one item, which changes how the sweeps' fused |q|^2 partials and
+    residual update are laid out over lanes.  Two iterations keep the iterates insensitive to
+    rounding (1e-7 relative perturbations of the oracle's operator move them by about 1e-6)."""
+    nx, nz, ns, nw, seed = shape
+    sv = random_case(nx, nz, ns, nw, seed=seed)
+    op = oracle_operator(sv)
+    d, lam = _oracle_data(sv, op)
+    ds = device_survey(sv)
+    m_gpu, st = _gpu_solve(torch_cuda, ds, d, lam, 2, 1, 0.0, 2)
+    m_ref, st_ref = O.rls_solve(op, d.astype(np.complex128), lam, 2, 1, 2)
+    assert [w["start"] for w in st] == [w.start for w in st_ref] == list(range(ns - 1))
+    for g, r in zip(st, st_ref):
+        assert abs(g["rel_res0"] - r.rel_res0) <= 1e-3 * r.rel_res0
+    assert rel_l2(m_gpu, m_ref) <= 1e-4
