@@ -237,7 +237,7 @@ static SweepShape tc_shape_for(int nx, int mode, int nshots, int nw, int warps) 
 }
 
 SweepShape tc_shape_heuristic(int nx, int mode, int nshots, int nw, int num_sms) {
-    const int per_sm = nx >= 1024 ? 1 : 2;  // blocks an SM holds (shared memory, registers)
+    const int per_sm = nx > 512 ? 1 : 2;  // blocks an SM holds (shared memory, registers)
     int warps = (nshots * nw + per_sm * num_sms - 1) / (per_sm * num_sms);
     warps = std::max(1, std::min(warps, 7));
     return tc_shape_for(nx, mode, nshots, nw, warps);

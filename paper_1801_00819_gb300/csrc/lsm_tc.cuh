@@ -1,5 +1,5 @@
 // Lateral transforms as DFT-matrix products on the tensor cores (precision variants of the split-step
-// depth step, Examples section).  For N = 16 R2 (R2 = 8, 16, 32, 64), one item's N points are the
+// depth step, Examples section).  For N = 16 R2 (R2 = 8, 16, ..., 64), one item's N points are the
 // 16 x R2 matrix X[n1][n2] = u[R2 n1 + n2] and the forward DFT is the four-step product
 //   Z = (F16 X . W) F_R2,  Z[k1][k2] = U[k1 + 16 k2],  W[k1][n2] = exp(-2 pi i k1 n2 / N),
 // F_R the R-point DFT matrix; the inverse is X = conj(F16) ((Z conj(F_R2)) . conj(W)) (the 1/N
@@ -30,8 +30,8 @@ enum TcPrecision { PREC_FP32 = 0, PREC_BF16X3 = 1, PREC_FP16X3 = 2, PREC_BF16X1 
 
 template <int N>
 struct TcShape {
-    static_assert(N == 128 || N == 256 || N == 512 || N == 1024,
-                  "tensor-core transforms for nx = 128, 256, 512, 1024");
+    static_assert(N % 128 == 0 && N >= 128 && N <= 1024,
+                  "tensor-core transforms for nx = 128 k, k = 1 .. 8 (R2 a multiple of 8)");
     static constexpr int R2 = N / 16;
     static constexpr int NT = R2 / 8;             // n-tiles (8 columns each)
     static constexpr int KS = (R2 + 15) / 16;     // k-steps (16) of the right product
@@ -392,9 +392,9 @@ constexpr size_t tc_smem_bytes(int warps, bool adjoint) {
 // one item per warp, coefficients read straight from the tables (Phi in natural frequency order).
 template <int N, int PREC, int MODE>
 // Up to 7 warps per block and two blocks per SM (at most 146 registers a thread): the 2,048 items of a
-// 512-wide window of 16 shots x 128 frequencies then run in a single wave on 152 SMs.  At N = 1024 an
-// item is twice as large and one block per SM leaves a thread up to 255 registers.
-__global__ void __launch_bounds__(224, N >= 1024 ? 1 : 2) tc_sweep_kernel(const SweepArgs a) {
+// 512-wide window of 16 shots x 128 frequencies then run in a single wave on 152 SMs.  Above N = 512
+// an item takes more registers and one block per SM leaves a thread up to 255.
+__global__ void __launch_bounds__(224, N > 512 ? 1 : 2) tc_sweep_kernel(const SweepArgs a) {
     using S = TcShape<N>;
     constexpr int NT = S::NT;
     extern __shared__ float4 smem_f4[];
