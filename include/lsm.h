@@ -261,8 +261,8 @@ int lsm_profile_stop(lsm_profile* out);
  *     tensor cores (four-step 16 x nx/16 factorisation, mma.sync with FP32 accumulation), with every
  *     FP32 operand split as hi + lo in bf16 (three products), in fp16 with the lo part scaled by
  *     2^11 (three products), or bf16 hi only (one product).  These are precision variants for
- *     nx = 128, 256, 384, 512, 640, 768, 896, 1024 with receivers at every column (rec_ix NULL);
- *     LSM_ERR_UNSUPPORTED_NX or LSM_ERR_ARG otherwise.
+ *     every supported nx (for nx/16 not a multiple of 8 the 16 x nx/16 matrix is zero-padded to
+ *     whole 8-column tiles) with receivers at every column (rec_ix NULL); LSM_ERR_ARG otherwise.
  */
 #define LSM_TRANSFORM_FFT 0
 #define LSM_TRANSFORM_DFT_BF16X3 1

@@ -551,8 +551,8 @@ struct Dispatch {
         }
     }
 
-    // tensor-core transform variants (nx = 128, 256, 384, ..., 1024: multiples of 128)
-    static constexpr bool kTc = N % 128 == 0 && N <= 1024;
+    // tensor-core transform variants (every supported nx: N = 16 R2, columns padded to a multiple of 8)
+    static constexpr bool kTc = N % 16 == 0 && N <= 1024;
 
     static cudaError_t tables_natural(const TableArgs& a, cudaStream_t st) {
         const size_t total = (size_t)a.nw * a.nz * N;

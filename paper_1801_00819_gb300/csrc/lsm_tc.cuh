@@ -30,12 +30,12 @@ enum TcPrecision { PREC_FP32 = 0, PREC_BF16X3 = 1, PREC_FP16X3 = 2, PREC_BF16X1 
 
 template <int N>
 struct TcShape {
-    static_assert(N % 128 == 0 && N >= 128 && N <= 1024,
-                  "tensor-core transforms for nx = 128 k, k = 1 .. 8 (R2 a multiple of 8)");
+    static_assert(N % 16 == 0 && N >= 16 && N <= 1024, "tensor-core transforms for nx = 16 R2 <= 1024");
     static constexpr int R2 = N / 16;
-    static constexpr int NT = R2 / 8;             // n-tiles (8 columns each)
+    static constexpr int NT = (R2 + 7) / 8;       // n-tiles (8 columns each)
+    static constexpr bool PAD = R2 % 8 != 0;      // columns R2 .. 8 NT - 1 are zero padding
     static constexpr int KS = (R2 + 15) / 16;     // k-steps (16) of the right product
-    static constexpr int LD = R2 + 4;             // row stride of the per-warp buffer (see tc_phys)
+    static constexpr int LD = 8 * NT + 4;         // row stride of the per-warp buffer (see tc_phys)
     static constexpr int BUF = 16 * LD;           // float2 per warp
     // constant fragments: left A (F16) [6 variants][32 lanes][4 x b32]; right B (F_R2) [KS][NT][6][32][2]
     static constexpr int A_WORDS = 6 * 32 * 4;
@@ -177,7 +177,7 @@ __device__ void tc_build_constants(uint32_t* Afr, uint32_t* Bfr) {
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             const int k = 16 * kk + 2 * tig + 8 * w + q;
-            if (k < S::R2) {
+            if (k < S::R2 && n < S::R2) {  // zero rows and columns beyond R2 keep the padding zero
                 float sn, cs;
                 sincospif(-2.0f * (float)((k * n) % S::R2) / (float)S::R2, &sn, &cs);
                 re[q] = cs;
@@ -306,7 +306,13 @@ __device__ __forceinline__ void tc_store(const TcItem<N>& it, float2* buf, int l
         for (int e = 0; e < 4; ++e) buf[((e & 1) ? sb1 : sb0) + 8 * (e >> 1) * S::LD + 8 * j] = it.x[j][e];
 }
 
-// column index (natural position for the matrix rows n1, columns n2) of element (j, e)
+// whether element (j, e) of a lane is a real column of the 16 x R2 matrix (not zero padding)
+template <int N>
+__device__ __forceinline__ bool tc_valid(int lane, int j, int e) {
+    return !TcShape<N>::PAD || 8 * j + 2 * (lane & 3) + (e & 1) < TcShape<N>::R2;
+}
+// column index (natural position for the matrix rows n1, columns n2) of element (j, e); real
+// columns only
 template <int N>
 __device__ __forceinline__ int tc_xpos(int lane, int j, int e) {
     const int g = lane >> 2, tig = lane & 3;
@@ -360,7 +366,7 @@ __device__ __forceinline__ void tc_phase_step(TcItem<N>& u, float2* buf, const u
     for (int j = 0; j < S::NT; ++j)
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const float2 p = __ldg(phi + tc_kpos<N>(lane, j, e));
+            const float2 p = tc_valid<N>(lane, j, e) ? __ldg(phi + tc_kpos<N>(lane, j, e)) : make_float2(0.f, 0.f);
             z.x[j][e] = CONJ_PHI ? cmulc(z.x[j][e], p) : cmul(z.x[j][e], p);
         }
     tc_right<N, PREC, true>(y, z, Bfr, lane);
@@ -435,15 +441,18 @@ __global__ void __launch_bounds__(224, N > 512 ? 1 : 2) tc_sweep_kernel(const Sw
         for (int j = 0; j < NT; ++j)
 #pragma unroll
             for (int e = 0; e < 4; ++e)
-                v.x[j][e] = ok ? __ldcs(row + tc_xpos<N>(lane, j, e)) : make_float2(0.f, 0.f);
+                v.x[j][e] = ok && tc_valid<N>(lane, j, e) ? __ldcs(row + tc_xpos<N>(lane, j, e))
+                                                          : make_float2(0.f, 0.f);
     };
     auto mul_d = [&](TcItem<N>& v, const float2* drow, bool conj) {
 #pragma unroll
         for (int j = 0; j < NT; ++j)
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const float2 dd = __ldg(drow + tc_xpos<N>(lane, j, e));
-                v.x[j][e] = conj ? cmulc(v.x[j][e], dd) : cmul(v.x[j][e], dd);
+                if (tc_valid<N>(lane, j, e)) {
+                    const float2 dd = __ldg(drow + tc_xpos<N>(lane, j, e));
+                    v.x[j][e] = conj ? cmulc(v.x[j][e], dd) : cmul(v.x[j][e], dd);
+                }
             }
     };
 
@@ -453,14 +462,16 @@ __global__ void __launch_bounds__(224, N > 512 ? 1 : 2) tc_sweep_kernel(const Sw
 #pragma unroll
         for (int j = 0; j < NT; ++j)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) u.x[j][e] = tc_xpos<N>(lane, j, e) == xs ? w : make_float2(0.f, 0.f);
+            for (int e = 0; e < 4; ++e)
+                u.x[j][e] = tc_valid<N>(lane, j, e) && tc_xpos<N>(lane, j, e) == xs ? w : make_float2(0.f, 0.f);
         for (int jz = 0; jz < nz; ++jz) {
             if (ok) {
                 float2* row = Sitem + (size_t)jz * N;
 #pragma unroll
                 for (int j = 0; j < NT; ++j)
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) __stcs(row + tc_xpos<N>(lane, j, e), u.x[j][e]);
+                    for (int e = 0; e < 4; ++e)
+                        if (tc_valid<N>(lane, j, e)) __stcs(row + tc_xpos<N>(lane, j, e), u.x[j][e]);
             }
             if (jz + 1 < nz) {
                 tc_phase_step<N, PREC, false>(u, buf, Afr, Bfr, tws, phi_w + (size_t)jz * N, lane);
@@ -479,7 +490,8 @@ __global__ void __launch_bounds__(224, N > 512 ? 1 : 2) tc_sweep_kernel(const Sw
             for (int j = 0; j < NT; ++j)
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
-                    slab[tc_xpos<N>(lane, j, e)] = fmaf(s.x[j][e].x, u.x[j][e].x, s.x[j][e].y * u.x[j][e].y);
+                    if (tc_valid<N>(lane, j, e))
+                        slab[tc_xpos<N>(lane, j, e)] = fmaf(s.x[j][e].x, u.x[j][e].x, s.x[j][e].y * u.x[j][e].y);
             __syncthreads();
             {
                 // the block's partial row: the warps' rows summed in warp order, four columns a thread
@@ -516,7 +528,7 @@ __global__ void __launch_bounds__(224, N > 512 ? 1 : 2) tc_sweep_kernel(const Sw
             for (int j = 0; j < NT; ++j)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const float mm = __ldg(mrow + tc_xpos<N>(lane, j, e));
+                    const float mm = tc_valid<N>(lane, j, e) ? __ldg(mrow + tc_xpos<N>(lane, j, e)) : 0.f;
                     u.x[j][e].x = fmaf(s.x[j][e].x, mm, u.x[j][e].x);
                     u.x[j][e].y = fmaf(s.x[j][e].y, mm, u.x[j][e].y);
                 }
@@ -526,7 +538,8 @@ __global__ void __launch_bounds__(224, N > 512 ? 1 : 2) tc_sweep_kernel(const Sw
 #pragma unroll
             for (int j = 0; j < NT; ++j)
 #pragma unroll
-                for (int e = 0; e < 4; ++e) orow[tc_xpos<N>(lane, j, e)] = u.x[j][e];
+                for (int e = 0; e < 4; ++e)
+                    if (tc_valid<N>(lane, j, e)) orow[tc_xpos<N>(lane, j, e)] = u.x[j][e];
         }
     }
 }

@@ -308,7 +308,7 @@ def lsm_forward(grid, slowness, freqs, geom, m, d_out, shot0, nshots, workspace,
     """d_out[nshots][nw][nrec] (complex64) = A m for shots shot0 .. shot0+nshots-1.
 
     transform: "fft" (FP32 register FFTs) or a tensor-core precision variant ("dft_bf16x3",
-    "dft_fp16x3", "dft_bf16x1"; nx a multiple of 128 up to 1024, receivers at every column)."""
+    "dft_fp16x3", "dft_bf16x1"; every supported nx, receivers at every column)."""
     lib = load_library()
     args = (ctypes.byref(grid.c), _ptr(slowness), ctypes.byref(freqs.c), ctypes.byref(geom.c), _ptr(m), _ptr(d_out),
             int(shot0), int(nshots), _ptr(workspace), _nbytes(workspace), _stream(stream))

@@ -123,10 +123,6 @@ def test_static_scratch_variant_rejects_oversize_problems_before_launch(lib):
 def test_tensor_core_transform_validation(lib):
     before = lib.lsm_kernel_launches()
     fake = 1 << 20
-    g, geo, f = _holders(lib, nx=64)
-    with pytest.raises(lib.LsmError) as ei:  # nx 64 has no tensor-core variant
-        lib.lsm_forward(g, fake, f, geo, fake, fake, 0, 1, None, stream=0, transform="dft_bf16x3")
-    assert ei.value.status == lib.LSM_ERR_UNSUPPORTED_NX
     g, geo, f = _holders(lib, nx=128, rec=np.tile(np.arange(64), (3, 1)))
     with pytest.raises(lib.LsmError) as ei:  # receiver lists are not taken by the variants
         lib.lsm_adjoint(g, fake, f, geo, fake, fake, 0, 1, None, stream=0, transform="dft_fp16x3")
@@ -192,9 +188,11 @@ def test_autotune_validation_before_any_launch(lib):
     with pytest.raises(lib.LsmError) as ei:
         lib.lsm_autotune(g, fake, f, geo, 2, FakeWs(sol - 1), stream=0)
     assert ei.value.status == lib.LSM_ERR_WORKSPACE
-    with pytest.raises(lib.LsmError) as ei:  # nx 64 has no tensor-core variant
-        lib.lsm_autotune(g, fake, f, geo, 2, FakeWs(sol), stream=0, transform="dft_bf16x3")
-    assert ei.value.status == lib.LSM_ERR_UNSUPPORTED_NX
+    g2, geo2, f2 = _holders(lib, nx=64, rec=np.tile(np.arange(32), (3, 1)))
+    sol2 = lib.lsm_workspace_bytes(g2, geo2, f2, 2, lib.LSM_OP_SOLVE)
+    with pytest.raises(lib.LsmError) as ei:  # the tensor-core variants take no receiver list
+        lib.lsm_autotune(g2, fake, f2, geo2, 2, FakeWs(sol2), stream=0, transform="dft_bf16x3")
+    assert ei.value.status == lib.LSM_ERR_ARG
     lib.lsm_autotune_reset()
     assert lib.lsm_kernel_launches() == before
 

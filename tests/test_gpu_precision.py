@@ -27,7 +27,7 @@ def _subsampled_problem(nx=128):
     return config_precision_subsample(nx)
 
 
-@pytest.mark.parametrize("nx", [128, 256, 384, 512, 640, 768, 896, 1024])
+@pytest.mark.parametrize("nx", [16, 32, 48, 64, 80, 96, 112, 128, 160, 192, 224, 256, 320, 384, 448, 512, 640, 768, 896, 1024])
 def test_transform_precisions_against_oracle(nx):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
