@@ -351,7 +351,9 @@ def gpu_arm(args):
     hbm = {"bound": "hbm", "achieved": round(hbm_ach, 1), "peak": hbm_peak, "unit": "GB/s",
            "frac": round(hbm_ach / hbm_peak, 4), "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"
            if peak_src == "measured" else "fallback 6.8 TB/s (MEASURED_PEAKS.json absent)"}
-    primary, secondary = (alu, hbm) if alu["frac"] >= hbm["frac"] else (hbm, alu)
+    # the sweeps are bound by the FP32 pipe and its dependency latency (ncu: FMA pipe 54-57 % busy,
+    # DRAM 35-40 %), so the FP32 roofline is the primary one and HBM the secondary
+    primary, secondary = alu, hbm
     roofline = dict(primary)
     roofline["traffic"] = traffic
     roofline["kernel"] = f"{dom} sweep (sweep_kernel MODE_{dom.upper()}, nx={nx})"
