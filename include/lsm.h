@@ -367,22 +367,27 @@ int lsm_autotune(const lsm_grid* grid, const float* slowness, const lsm_freqs* f
                  void* workspace, size_t workspace_bytes, void* stream, lsm_tune_report* report);
 
 /*
- * Checkpoint stride of lsm_born_gradient.  The gradient sweep keeps S and R at every c-th depth and
- * recomputes them segment by segment, so its arithmetic and its results are the same for every c;
- * c sets how many checkpoint and segment rows each (shot, frequency) item keeps and how much of
- * that traffic stays in L2.  lsm_autotune_gradient times the gradient kernel of a launch over
- * `nshots` shots of this grid and frequency set at c = LSM_CHECKPOINT_EVERY, 8, 16 and 32 (strides
- * above nz act as nz) and records the fastest; from then on lsm_born_gradient calls on the current
- * device with the same (nx, nz, nshots, nw) use it.  lsm_workspace_bytes(..., LSM_OP_GRADIENT)
- * already reserves room for every candidate.  Needs a workspace of
- * lsm_workspace_bytes(grid, geom, freqs, nshots, LSM_OP_GRADIENT); runs shots [0, nshots) on
- * zero-valued model and data-space gradient, overwrites the workspace, and returns after
- * synchronising the stream.  Gradients need nx <= 512 (LSM_ERR_UNSUPPORTED_NX otherwise).
- * `report` (may be NULL) receives the chosen and the default stride, their mean launch times in
- * ms and the number of strides timed.  lsm_autotune_reset also forgets recorded strides.
+ * Checkpoint stride and launch shape of lsm_born_gradient.  The gradient sweep keeps S and R at
+ * every c-th depth and recomputes them segment by segment, so its arithmetic and its results are the
+ * same for every c; c sets how many checkpoint and segment rows each (shot, frequency) item keeps
+ * and how much of that traffic stays in L2.  The number of warps per block sets how evenly the
+ * launch's blocks fill the SMs' last round.  lsm_autotune_gradient times the gradient kernel of a
+ * launch over `nshots` shots of this grid and frequency set at c = LSM_CHECKPOINT_EVERY, 8, 16 and
+ * 32 (strides above nz act as nz) and at the default number of warps per block and up to two fewer,
+ * and records the fastest pair; from then on lsm_born_gradient calls on the current device with the
+ * same (nx, nz, nshots, nw) use it.  lsm_workspace_bytes(..., LSM_OP_GRADIENT) already reserves
+ * room for every candidate.  Needs a workspace of lsm_workspace_bytes(grid, geom, freqs, nshots,
+ * LSM_OP_GRADIENT); runs shots [0, nshots) on zero-valued model and data-space gradient, overwrites
+ * the workspace, and returns after synchronising the stream.  Gradients need nx <= 512
+ * (LSM_ERR_UNSUPPORTED_NX otherwise).  `report` (may be NULL) receives the chosen and the default
+ * stride and warps per block, their mean launch times in ms and the number of pairs timed.  The
+ * gradients do not depend on the stride; the warps per block change the block partition of the
+ * image sums and so their last bits.  lsm_autotune_reset also forgets these choices.
  */
 typedef struct {
-    int stride, default_stride, candidates;
+    int stride, default_stride;
+    int warps, default_warps;
+    int candidates;
     double ms, default_ms;
 } lsm_ckpt_tune_report;
 

@@ -143,7 +143,10 @@ struct CkptKey {
         return std::tie(dev, nx, nz, nshots, nw) < std::tie(o.dev, o.nx, o.nz, o.nshots, o.nw);
     }
 };
-static std::map<CkptKey, int> g_ckpt_tune;  // guarded by g_tune_mu
+struct GradTune {
+    int stride, warps;  // checkpoint stride; warps per block (0: the heuristic's)
+};
+static std::map<CkptKey, GradTune> g_ckpt_tune;  // guarded by g_tune_mu
 static CkptKey ckpt_key(int nx, int nz, int nshots, int nw) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) cudaGetLastError();
@@ -153,7 +156,13 @@ static int ckpt_stride(int nx, int nz, int nshots, int nw) {
     const CkptKey k = ckpt_key(nx, nz, nshots, nw);
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_ckpt_tune.find(k);
-    return std::min(it == g_ckpt_tune.end() ? LSM_CHECKPOINT_EVERY : it->second, nz);
+    return std::min(it == g_ckpt_tune.end() ? LSM_CHECKPOINT_EVERY : it->second.stride, nz);
+}
+static int tuned_gradient_warps(int nx, int nz, int nshots, int nw) {
+    const CkptKey k = ckpt_key(nx, nz, nshots, nw);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_ckpt_tune.find(k);
+    return it == g_ckpt_tune.end() ? 0 : it->second.warps;
 }
 // rows of nx complex values one item keeps at stride c: S and R checkpoints, then the segment's
 // S rows (c + 1) and R rows (c)
@@ -204,25 +213,45 @@ bool gradient_nx_supported(int nx) {
     return ops && ops->has_gradient;
 }
 
-SweepShape gradient_shape(int nx, int nshots, int nw, int num_sms) {
+// gradient launch with `warps` warps per block (at most the heuristic's, so shared memory fits)
+static SweepShape gradient_shape_for(int nx, int nshots, int nw, int warps) {
     const NxOps* ops = nx_ops(nx);
     const int V = gradient_points_per_thread();
-    const int T = nx / V;
-    const int ipw = 32 / T;
-    const int nitems = nshots * nw;
-    const int warps_total = (nitems + ipw - 1) / ipw;
-    auto wslots_of = [&](int w) { return std::min(nw, (w * ipw + nshots - 1) / nshots + 1); };
-    auto smem_of = [&](int w) { return ops->gradient_smem(w, wslots_of(w)); };
-    int maxw = std::min(8, ops->gradient_max_warps());
-    while (maxw > 1 && smem_of(maxw) > 227 * 1024) --maxw;
-    int warps = (warps_total + num_sms - 1) / num_sms;
-    warps = std::max(1, std::min(warps, maxw));
+    const int ipw = 32 / (nx / V);
+    const int warps_total = (nshots * nw + ipw - 1) / ipw;
     SweepShape s;
     s.warps = warps;
     s.blocks = (warps_total + warps - 1) / warps;
-    s.wslots = wslots_of(warps);
-    s.smem = smem_of(warps);
+    s.wslots = std::min(nw, (warps * ipw + nshots - 1) / nshots + 1);
+    s.smem = ops->gradient_smem(warps, s.wslots);
     return s;
+}
+
+// the heuristic: a launch's warps spread evenly over the SMs, within the register and shared-memory
+// limits of one block
+SweepShape gradient_shape(int nx, int nshots, int nw, int num_sms) {
+    const NxOps* ops = nx_ops(nx);
+    const int V = gradient_points_per_thread();
+    const int ipw = 32 / (nx / V);
+    const int warps_total = (nshots * nw + ipw - 1) / ipw;
+    int maxw = std::min(8, ops->gradient_max_warps());
+    while (maxw > 1 && gradient_shape_for(nx, nshots, nw, maxw).smem > 227 * 1024) --maxw;
+    int warps = (warps_total + num_sms - 1) / num_sms;
+    warps = std::max(1, std::min(warps, maxw));
+    return gradient_shape_for(nx, nshots, nw, warps);
+}
+
+// lsm_autotune_gradient's warps-per-block candidates: the heuristic's and up to two fewer (more,
+// smaller blocks even out the last round of blocks); the layout keeps partial images for the
+// smallest
+static int gradient_min_warps(int nx, int nshots, int nw, int num_sms) {
+    return std::max(1, gradient_shape(nx, nshots, nw, num_sms).warps - 2);
+}
+
+// the shape lsm_born_gradient launches: a recorded one, else the heuristic
+static SweepShape gradient_launch_shape(int nx, int nz, int nshots, int nw, int num_sms) {
+    const int w = tuned_gradient_warps(nx, nz, nshots, nw);
+    return w > 0 ? gradient_shape_for(nx, nshots, nw, w) : gradient_shape(nx, nshots, nw, num_sms);
 }
 
 // tensor-core variants: one item per warp, up to 7 warps per block (two blocks per SM)
@@ -338,7 +367,7 @@ Layout make_layout(const lsm_grid* g, const lsm_geom* geo, const lsm_freqs* f, i
         if (nx_ops(g->nx)->has_tc)
             L.nparts = std::max(L.nparts, tc_shape_heuristic(g->nx, MODE_ADJOINT, nshots, (int)nw, num_sms).blocks);
     } else if (op == LSM_OP_GRADIENT) {
-        L.nparts = gradient_shape(g->nx, nshots, (int)nw, num_sms).blocks;
+        L.nparts = gradient_shape_for(g->nx, nshots, (int)nw, gradient_min_warps(g->nx, nshots, (int)nw, num_sms)).blocks;
     }
     L.part = take((size_t)L.nparts * plane * sizeof(float));
     if (op == LSM_OP_GRADIENT) {
@@ -747,7 +776,7 @@ int lsm_born_gradient(const lsm_grid* grid, const float* slowness, const double*
     ga.m = m;
     ga.g = reinterpret_cast<const float2*>(g);
     ga.dout = reinterpret_cast<float2*>(d_out);
-    const SweepShape sh = gradient_shape(grid->nx, nshots, freqs->nw, nsm);
+    const SweepShape sh = gradient_launch_shape(grid->nx, grid->nz, nshots, freqs->nw, nsm);
     ga.wslots = sh.wslots;
     LSM_CHECK(launch_gradient(ga, sh, st));
     const int n = grid->nx * grid->nz;
@@ -895,38 +924,47 @@ int lsm_autotune_gradient(const lsm_grid* grid, const float* slowness, const lsm
     if (rc != LSM_OK) return rc;
     LSM_CHECK(cudaMemsetAsync(ws + L.tune_m, 0, (size_t)nx * nz * sizeof(float), st));
     LSM_CHECK(cudaMemsetAsync(ws + L.tune_g, 0, (size_t)nshots * nw * geom->nrec * sizeof(float2), st));
-    const SweepShape sh = gradient_shape(nx, nshots, nw, nsm);
+    const SweepShape h = gradient_shape(nx, nshots, nw, nsm);
+    const int wmin = gradient_min_warps(nx, nshots, nw, nsm);
     EventPair ev;
     LSM_CHECK(cudaEventCreate(&ev.a));
     LSM_CHECK(cudaEventCreate(&ev.b));
     const int def = std::min(LSM_CHECKPOINT_EVERY, nz);
-    int best = def, ncand = 0;
-    double best_ms = 0.0, def_ms = 0.0;
-    int tried[sizeof(kCkptStrides) / sizeof(int) + 1];
+    int strides[sizeof(kCkptStrides) / sizeof(int) + 1];
+    int nstrides = 0;
     for (int i = 0; i <= (int)(sizeof(kCkptStrides) / sizeof(int)); ++i) {
         // the default first, then the candidates (strides above nz act as nz and are timed once)
         const int c = std::min(i == 0 ? LSM_CHECKPOINT_EVERY : kCkptStrides[i - 1], nz);
         bool seen = false;
-        for (int k = 0; k < ncand; ++k) seen = seen || tried[k] == c;
-        if (seen) continue;
-        tried[ncand++] = c;
-        GradArgs ga = grad_args(grid, freqs, geom, L, ws, 0, nshots, c);
-        ga.m = reinterpret_cast<const float*>(ws + L.tune_m);
-        ga.g = reinterpret_cast<const float2*>(ws + L.tune_g);
-        ga.wslots = sh.wslots;
-        LSM_CHECK(launch_gradient(ga, sh, st));  // untimed first launch
-        LSM_CHECK(cudaEventRecord(ev.a, st));
-        constexpr int reps = 3;
-        for (int r = 0; r < reps; ++r) LSM_CHECK(launch_gradient(ga, sh, st));
-        LSM_CHECK(cudaEventRecord(ev.b, st));
-        LSM_CHECK(cudaEventSynchronize(ev.b));
-        float t = 0.f;
-        LSM_CHECK(cudaEventElapsedTime(&t, ev.a, ev.b));
-        const double ms = (double)t / reps;
-        if (c == def) def_ms = ms;
-        if (ncand == 1 || ms < best_ms) {
-            best_ms = ms;
-            best = c;
+        for (int k = 0; k < nstrides; ++k) seen = seen || strides[k] == c;
+        if (!seen) strides[nstrides++] = c;
+    }
+    GradTune best{def, h.warps};
+    int ncand = 0;
+    double best_ms = 0.0, def_ms = 0.0;
+    for (int w = h.warps; w >= wmin; --w) {
+        const SweepShape sh = gradient_shape_for(nx, nshots, nw, w);
+        for (int k = 0; k < nstrides; ++k) {
+            const int c = strides[k];
+            GradArgs ga = grad_args(grid, freqs, geom, L, ws, 0, nshots, c);
+            ga.m = reinterpret_cast<const float*>(ws + L.tune_m);
+            ga.g = reinterpret_cast<const float2*>(ws + L.tune_g);
+            ga.wslots = sh.wslots;
+            LSM_CHECK(launch_gradient(ga, sh, st));  // untimed first launch
+            LSM_CHECK(cudaEventRecord(ev.a, st));
+            constexpr int reps = 3;
+            for (int r = 0; r < reps; ++r) LSM_CHECK(launch_gradient(ga, sh, st));
+            LSM_CHECK(cudaEventRecord(ev.b, st));
+            LSM_CHECK(cudaEventSynchronize(ev.b));
+            float t = 0.f;
+            LSM_CHECK(cudaEventElapsedTime(&t, ev.a, ev.b));
+            const double ms = (double)t / reps;
+            ++ncand;
+            if (c == def && w == h.warps) def_ms = ms;
+            if (ncand == 1 || ms < best_ms) {
+                best_ms = ms;
+                best = GradTune{c, w};
+            }
         }
     }
     {
@@ -934,8 +972,10 @@ int lsm_autotune_gradient(const lsm_grid* grid, const float* slowness, const lsm
         g_ckpt_tune[ckpt_key(nx, nz, nshots, nw)] = best;
     }
     if (report) {
-        report->stride = best;
+        report->stride = best.stride;
         report->default_stride = def;
+        report->warps = best.warps;
+        report->default_warps = h.warps;
         report->candidates = ncand;
         report->ms = best_ms;
         report->default_ms = def_ms;

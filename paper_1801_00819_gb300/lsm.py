@@ -123,8 +123,9 @@ class lsm_tune_report(ctypes.Structure):
 
 
 class lsm_ckpt_tune_report(ctypes.Structure):
-    _fields_ = [("stride", ctypes.c_int), ("default_stride", ctypes.c_int), ("candidates", ctypes.c_int),
-                ("ms", ctypes.c_double), ("default_ms", ctypes.c_double)]
+    _fields_ = [("stride", ctypes.c_int), ("default_stride", ctypes.c_int), ("warps", ctypes.c_int),
+                ("default_warps", ctypes.c_int), ("candidates", ctypes.c_int), ("ms", ctypes.c_double),
+                ("default_ms", ctypes.c_double)]
 
 
 _lib_handle = None
@@ -428,17 +429,18 @@ def lsm_autotune(grid, slowness, freqs, geom, nshots, workspace, stream=None, tr
 
 
 def lsm_autotune_gradient(grid, slowness, freqs, geom, nshots, workspace, stream=None) -> dict:
-    """Time lsm_born_gradient's kernel at each candidate checkpoint stride for launches over `nshots`
-    shots and record the fastest for later calls (see include/lsm.h).  `workspace` must hold
-    lsm_workspace_bytes(..., nshots, LSM_OP_GRADIENT).  Returns {stride, default_stride, candidates,
-    ms, default_ms}."""
+    """Time lsm_born_gradient's kernel at each candidate checkpoint stride and warps per block for
+    launches over `nshots` shots and record the fastest pair for later calls (see include/lsm.h).
+    `workspace` must hold lsm_workspace_bytes(..., nshots, LSM_OP_GRADIENT).  Returns {stride,
+    default_stride, warps, default_warps, candidates, ms, default_ms}."""
     rep = lsm_ckpt_tune_report()
     st = load_library().lsm_autotune_gradient(ctypes.byref(grid.c), _ptr(slowness), ctypes.byref(freqs.c),
                                                ctypes.byref(geom.c), int(nshots), _ptr(workspace),
                                                _nbytes(workspace), _stream(stream), ctypes.byref(rep))
     _check(st, "lsm_autotune_gradient")
-    return {"stride": int(rep.stride), "default_stride": int(rep.default_stride),
-            "candidates": int(rep.candidates), "ms": float(rep.ms), "default_ms": float(rep.default_ms)}
+    return {"stride": int(rep.stride), "default_stride": int(rep.default_stride), "warps": int(rep.warps),
+            "default_warps": int(rep.default_warps), "candidates": int(rep.candidates), "ms": float(rep.ms),
+            "default_ms": float(rep.default_ms)}
 
 
 def lsm_autotune_reset() -> None:
