@@ -39,7 +39,8 @@
  *    least lsm_workspace_bytes(...) bytes.  Host arrays are read during the call only.
  *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *    lsm_forward and lsm_adjoint are asynchronous on that stream.  rls_window_solve
- *    synchronises the stream once per CG iteration (to test convergence) and before returning.
+ *    synchronises the stream once per window with the default graph-replayed CG loop (once per CG
+ *    iteration with the host-driven loop, to test convergence) and before returning.
  *  - Errors: every entry point returns an LSM_* status; arguments are validated on the host
  *    before anything is launched.  A call that fails validation launches nothing and leaves
  *    outputs untouched.  No kernel in this library waits on another block or device, so none

@@ -4,7 +4,8 @@
 // frequency arrays, launch geometry, and the sliding-window CG driver (block-row section,
 // Eq. 10 and Eq. 11).  Every arithmetic step of the operator and of CG runs in the kernels of
 // lsm_sweep.cuh and lsm_cg.cu; the host only sequences them and reads one small state struct
-// per CG iteration to test the stopping rule.
+// per CG iteration (host-driven loop) or per window (graph-replayed loop, where the stopping rule
+// is tested on the device).
 #include <cuda_runtime.h>
 
 #include <algorithm>
