@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 from oracle import lsm_oracle as O
-from synth import random_case, config_tiny, config_realistic
+from synth import random_case, config_tiny, config_realistic, config_precision
 from tests._helpers import oracle_operator, rel_l2, device_survey
 
 pytestmark = pytest.mark.gpu
@@ -191,6 +191,36 @@ def test_realistic_full_size_sampled_items(torch_cuda):
     img = _gpu_adjoint(torch_cuda, ds, d, shot0, K)
     assert rel_l2(img, ref) <= TOL
     # full-size dot-product property on the whole window
+    dd = (rng.normal(size=(K, sv.nw, sv.nx)) + 1j * rng.normal(size=(K, sv.nw, sv.nx))).astype(np.complex64)
+    lhs = O.real_dot(got, dd.astype(np.complex128))
+    rhs = O.real_dot(m, _gpu_adjoint(torch_cuda, ds, dd, shot0, K))
+    assert abs(lhs - rhs) <= 1e-4 * abs(lhs)
+
+
+def test_largest_workload_full_size_sampled_items(torch_cuda):
+    """The largest workload, 1024 x 512 with 256 frequencies, one 16-shot window from shot 96
+    (about 21 GB of workspace): A compared on sampled (shot, frequency) rows, A^T on data that is
+    zero except at sampled items, which the oracle migrates one by one, and the dot-product
+    property on the whole window."""
+    sv = config_precision()
+    ds = device_survey(sv)
+    K, shot0 = sv.window, 96
+    m = np.asarray(sv.reflectivity, dtype=np.float32).astype(np.float64)
+    got = _gpu_forward(torch_cuda, ds, m, shot0, K)
+    samples = [(0, 0), (7, 128), (15, 255)]
+    op = oracle_operator(sv)
+    for ishot, iw in samples:
+        ref = op.with_freqs([iw]).forward(m, shots=[shot0 + ishot])[0, 0]
+        assert rel_l2(got[ishot, iw], ref) <= TOL, (ishot, iw)
+    rng = np.random.default_rng(5)
+    d = np.zeros((K, sv.nw, sv.nx), dtype=np.complex64)
+    ref = np.zeros((sv.nz, sv.nx))
+    for ishot, iw in samples[1:]:
+        row = (rng.normal(size=sv.nx) + 1j * rng.normal(size=sv.nx)).astype(np.complex64)
+        d[ishot, iw] = row
+        ref += op.with_freqs([iw]).adjoint(row[None, None, :].astype(np.complex128), shots=[shot0 + ishot])
+    img = _gpu_adjoint(torch_cuda, ds, d, shot0, K)
+    assert rel_l2(img, ref) <= TOL
     dd = (rng.normal(size=(K, sv.nw, sv.nx)) + 1j * rng.normal(size=(K, sv.nw, sv.nx))).astype(np.complex64)
     lhs = O.real_dot(got, dd.astype(np.complex128))
     rhs = O.real_dot(m, _gpu_adjoint(torch_cuda, ds, dd, shot0, K))
