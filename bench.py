@@ -43,6 +43,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+METRIC = "shot*omega*depth steps/s for A+A^T (window-RLS solve to 1e-3 residual)"
 FP32_LANES_PER_SM = 128     # FP32 FMA lanes per Blackwell SM
 FALLBACK_HBM_GBS = 6800.0   # profiling recipe's fallback copy bandwidth
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sweep_kernels_realistic_512x256.md")
@@ -61,10 +62,9 @@ def parse_args():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="run the default launch shapes instead of tuning them before the untimed warm-up")
-    ap.add_argument("--cpu-sample-freqs", type=int, default=128,
-                    help="frequencies in the GPU arm's cpu_baseline sample (about 10-30 s of oracle work)")
     ap.add_argument("--ref-sample-freqs", type=int, default=16,
-                    help="frequencies per step of the reference arm's sample")
+                    help="frequencies of the oracle sample timed by the reference arm (each step) and by the GPU "
+                         "arm's cpu_baseline (repeated for at least 10 s)")
     return ap.parse_args()
 
 
@@ -270,6 +270,13 @@ def gpu_arm(args):
                                                              ws)["source"]}
         torch.cuda.synchronize()
 
+    # the FP32 roofline's denominator, measured on this GPU before the warm-up (FMA-chain kernels)
+    try:
+        fp32_peak = L.lsm_measure_fp32_peak()
+    except Exception as exc:  # reported, and the derived figure used instead
+        fp32_peak = {"error": str(exc)}
+    torch.cuda.synchronize()
+
     nwin = L.lsm_num_windows(ns, K, sv.slide)
     prof = {}
 
@@ -323,6 +330,7 @@ def gpu_arm(args):
     launches = L.lsm_kernel_launches() - launches0
     barrier()
     clk = clocks.stop()
+    m_fp32 = m.clone()  # the plain FP32 solve's image, for the variants' comparisons
     t_ms = ev0.elapsed_time(ev1)
     units_per_pass = K * nw * nz
     units = sum((w["n_forward"] + w["n_adjoint"]) / 2 * units_per_pass for st in stats for w in st)
@@ -338,7 +346,9 @@ def gpu_arm(args):
     by = bytes_per_unit(nx, ds.nrec, nz, K, cg_adjoint=dom == "adjoint") * units_per_pass
     sm_max = clk.get("sm_max_mhz") or 2070.0
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
-    alu_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    alu_derived = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    measured_fp32 = [v for k, v in fp32_peak.items() if k in ("ffma", "ffma2")]
+    alu_peak = max(measured_fp32) if measured_fp32 else alu_derived
     peaks, peak_src = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
     alu_ach = fl / (avg_ms / 1e3) / 1e12
@@ -346,8 +356,14 @@ def gpu_arm(args):
     traffic = profiled_traffic(dom)
     alu = {"bound": "alu", "achieved": round(alu_ach, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
            "frac": round(alu_ach / alu_peak, 4),
-           "peak_source": f"derived: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
-                          f"{sm_max:g} MHz"}
+           "peak_source": ("measured in this run (of measured): lsm_measure_fp32_peak, FMA-chain kernels on 8 "
+                           "blocks of 256 threads per SM, best of 5 CUDA-event-timed launches, the faster of scalar "
+                           f"FFMA {fp32_peak['ffma']:.2f} and paired FFMA2 {fp32_peak['ffma2']:.2f} TFLOP/s")
+           if measured_fp32 else f"derived (measurement failed: {fp32_peak.get('error')}): "
+                                 f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:g} MHz",
+           "peak_derived": round(alu_derived, 2),
+           "peak_derived_source": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                                  f"{sm_max:g} MHz"}
     hbm = {"bound": "hbm", "achieved": round(hbm_ach, 1), "peak": hbm_peak, "unit": "GB/s",
            "frac": round(hbm_ach / hbm_peak, 4), "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"
            if peak_src == "measured" else "fallback 6.8 TB/s (MEASURED_PEAKS.json absent)"}
@@ -370,7 +386,7 @@ def gpu_arm(args):
                               "timed region",
                 "value": round(units_per_pass / ((fwd_ms + adj_ms) / 1e3), 1), "unit": "units/s",
                 "t_A_ms": round(fwd_ms, 4), "t_AT_ms": round(adj_ms, 4)}
-    out = {"metric": "shot*omega*depth steps/s for A+A^T (window-RLS solve to 1e-3 residual)",
+    out = {"metric": METRIC,
            "value": round(value, 1), "unit": "units/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
@@ -452,9 +468,44 @@ def gpu_arm(args):
             "total_iters": int(sum(w["iters"] for w in stg)),
             "same_iterations_as_plain": [w["iters"] for w in stg] == iters,
             "time_to_tol_vs_plain": round((t_max / args.steps) / tg[-1], 3)}
+        # the lateral transforms on the tensor cores (split FP16 / BF16 three-term DFT products),
+        # every window to the same 1e-3 stopping threshold as the plain FP32 solve
+        ref_norm = float(torch.linalg.vector_norm(m_fp32))
+        out["variants"]["tensor_core_transforms"] = {}
+        kernels = {"dft_fp16x3": "mma.sync four-step DFT products (lsm_tc.cuh)",
+                   "dft_bf16x3": "mma.sync four-step DFT products (lsm_tc.cuh)",
+                   "dft_fp16x3_tcgen05": "tcgen05.mma four-step DFT products, TMEM accumulators (lsm_tc5.cuh)",
+                   "dft_bf16x3_tcgen05": "tcgen05.mma four-step DFT products, TMEM accumulators (lsm_tc5.cuh)"}
+        # per-launch times of the window's sweeps with every transform (3 event-timed launches each,
+        # after one untimed; the plain FFT sweeps for comparison)
+        sweep_ms = {"fft": {k: round(v["ms"], 4) for k, v in
+                            L.lsm_autotune(ds.grid, ds.slowness, ds.freqs, ds.geom, K, ws).items()}}
+        for transform in kernels:
+            rep = L.lsm_autotune(ds.grid, ds.slowness, ds.freqs, ds.geom, K, ws, transform=transform)
+            sweep_ms[transform] = {k: round(v["ms"], 4) for k, v in rep.items()}
+        torch.cuda.synchronize()
+        out["variants"]["sweep_launch_ms_by_transform"] = sweep_ms
+        for transform in kernels:
+            m.zero_()
+            torch.cuda.synchronize()
+            v0.record(stream)
+            _, stt = L.rls_window_solve(ds.grid, ds.slowness, ds.freqs, ds.geom, d, lam, K, sv.slide, sv.cg_tol,
+                                        sv.cg_iters, m, ws, transform=transform)
+            v1.record(stream)
+            torch.cuda.synchronize()
+            tt = v0.elapsed_time(v1)
+            out["variants"]["tensor_core_transforms"][transform] = {
+                "time_to_tol_ms": round(tt, 3), "total_iters": int(sum(w["iters"] for w in stt)),
+                "iters_per_window": [w["iters"] for w in stt],
+                "max_final_rel_res": max(w["rel_res"] for w in stt),
+                "image_rel_l2_vs_fp32_solve": float(torch.linalg.vector_norm(m - m_fp32)) / ref_norm,
+                "time_to_tol_vs_plain": round((t_max / args.steps) / tt, 3),
+                "kernel": kernels[transform]}
+        if world == 1:
+            out["variants"]["batching_reduced"] = batching_reduced_variant(L, torch, args)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(sv, args.cpu_sample_freqs)
+        out["cpu_baseline"] = cpu_baseline(sv, args.ref_sample_freqs)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -491,12 +542,23 @@ def host_cores():
         return os.cpu_count()
 
 
-def cpu_baseline(sv, n_freqs, n_shots=5):
-    units, dt = oracle_sample(sv, n_freqs, n_shots)
-    return {"value": round(units / dt, 2), "unit": "units/s", "cores": host_cores(), "kind": "oracle",
-            "sample": f"FP64 oracle (numpy, naive DFT matrices), one A + A^T on {n_shots} shots x "
-                      f"{min(n_freqs, sv.nw)} frequencies x {sv.nz} depths at {sv.nx} columns = {units} units "
-                      f"in {dt:.2f} s"}
+def sample_text(sv, n_freqs):
+    return (f"one A + A^T of the FP64 oracle (numpy, naive DFT matrices) on 1 shot x {min(n_freqs, sv.nw)} "
+            f"frequencies x {sv.nz} depths at {sv.nx} columns of the workload = {min(n_freqs, sv.nw) * sv.nz} units")
+
+
+def cpu_baseline(sv, n_freqs, min_seconds=10.0):
+    """The oracle on the same bounded sample as the reference arm's steps, repeated until at least
+    min_seconds of host time (after one untimed repetition)."""
+    oracle_sample(sv, n_freqs)
+    units, secs, reps = 0, 0.0, 0
+    while secs < min_seconds or reps < 3:
+        u, dt = oracle_sample(sv, n_freqs)
+        units += u
+        secs += dt
+        reps += 1
+    return {"value": round(units / secs, 2), "unit": "units/s", "cores": host_cores(), "kind": "oracle",
+            "sample": f"{sample_text(sv, n_freqs)}, repeated {reps} times ({secs:.1f} s)"}
 
 
 def reference_arm(args):
@@ -505,24 +567,137 @@ def reference_arm(args):
         return
     sv = workload(args.workload, 0)
     for _ in range(args.warmup):
-        oracle_sample(sv, min(4, args.ref_sample_freqs))
-    units_total, t_total, per = 0, 0.0, []
+        oracle_sample(sv, args.ref_sample_freqs)
+    units_total, t_total = 0, 0.0
     for _ in range(args.steps):
         u, dt = oracle_sample(sv, args.ref_sample_freqs)
         units_total += u
         t_total += dt
-        per.append(dt)
     value = units_total / t_total
     base = {"value": round(value, 2), "unit": "units/s", "cores": host_cores(), "kind": "oracle",
-            "sample": f"each step: one A + A^T on 1 shot x {min(args.ref_sample_freqs, sv.nw)} frequencies of the "
-                      f"workload (FP64 numpy oracle)"}
-    out = {"impl": "reference", "metric": "shot*omega*depth steps/s for A+A^T (window-RLS solve to 1e-3 residual)",
+            "sample": f"each step: {sample_text(sv, args.ref_sample_freqs)}"}
+    out = {"impl": "reference", "metric": METRIC,
            "value": round(value, 2), "unit": "units/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(1e3 * t_total / args.steps, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
-           "config": workload_config(sv, l2_note=False), "cpu_baseline": base,
+           "config": workload_config(sv), "cpu_baseline": base,
            "e2e": {"value": round(value, 2), "unit": "units/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def build_line(L, lsm, torch, sv):
+    """One survey line on the device: data d = A m + noise modelled with the library, lambda =
+    1e-3 max|A^T d|, a solve workspace, a zero image and a stream of its own."""
+    import numpy as np
+
+    from paper_1801_00819_gb300.device import to_device, workspace
+
+    ds = to_device(sv.nx, sv.nz, sv.dx, sv.dz, sv.slowness, sv.src_ix, sv.rec_ix, sv.freqs, sv.wavelet)
+    K = sv.window
+    m_true = torch.as_tensor(np.asarray(sv.reflectivity, dtype=np.float32), device="cuda")
+    d = torch.empty((sv.ns, sv.nw, ds.nrec), dtype=torch.complex64, device="cuda")
+    ws_f = workspace(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, K, L.LSM_OP_ADJOINT))
+    for s0 in range(0, sv.ns, K):
+        n = min(K, sv.ns - s0)
+        L.lsm_forward(ds.grid, ds.slowness, ds.freqs, ds.geom, m_true, d[s0:s0 + n], s0, n, ws_f)
+    rms = float(torch.sqrt(torch.mean(torch.abs(d) ** 2)))
+    d += sv.noise_pct * rms * torch.as_tensor(sv.noise().astype(np.complex64), device="cuda")
+    adj = torch.zeros((sv.nz, sv.nx), dtype=torch.float32, device="cuda")
+    for s0 in range(0, sv.ns, K):
+        n = min(K, sv.ns - s0)
+        L.lsm_adjoint(ds.grid, ds.slowness, ds.freqs, ds.geom, d[s0:s0 + n], adj, s0, n, ws_f, accumulate=True)
+    lam = 1e-3 * float(adj.abs().max())
+    del ws_f
+    ws = workspace(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, K, L.LSM_OP_SOLVE))
+    m = torch.zeros((sv.nz, sv.nx), dtype=torch.float32, device="cuda")
+    return lsm.LineProblem(ds.grid, ds.slowness, ds.freqs, ds.geom, d, lam, K, sv.slide, sv.cg_tol, sv.cg_iters, m,
+                           ws, torch.cuda.Stream())
+
+
+def tune_lines(lsm, lines):
+    """Launch shapes of every line's window (K shots) and refill (slide shots) sweeps."""
+    tuned = []
+    for pr in lines:
+        rep = lsm.lsm_autotune(pr.grid, pr.slowness, pr.freqs, pr.geom, pr.K, pr.workspace)
+        entry = {"nx": pr.grid.c.nx, "K": pr.K, "warps": {k: v["warps"] for k, v in rep.items()},
+                 "heuristic_warps": {k: v["heuristic_warps"] for k, v in rep.items()}}
+        if pr.slide != pr.K:
+            entry["refill_source_warps"] = lsm.lsm_autotune(pr.grid, pr.slowness, pr.freqs, pr.geom, pr.slide,
+                                                            pr.workspace)["source"]["warps"]
+        tuned.append(entry)
+    return tuned
+
+
+def line_units(lines, stats_per_line):
+    total = 0
+    for pr, st in zip(lines, stats_per_line):
+        per_pass = pr.K * pr.freqs.c.nw * pr.grid.c.nz
+        total += sum((w["n_forward"] + w["n_adjoint"]) / 2 * per_pass for w in st)
+    return total
+
+
+def batching_reduced_variant(L, torch, args):
+    """The eight-line batching workload cut to each line's first three windows and every other
+    frequency: every window of every line to 1e-3, solved line after line with the plain FP32 solve
+    (the library's default loop) and all lines together (rls_multi_line_solve: one host worker and
+    stream per line).  Host wall clock around each whole solve, the GPU synchronised on both sides;
+    best of two runs each."""
+    from paper_1801_00819_gb300 import lsm
+    from synth import config_batching_lines_reduced
+
+    lines = [build_line(L, lsm, torch, sv) for sv in config_batching_lines_reduced()]
+    torch.cuda.synchronize()
+    tuned = tune_lines(lsm, lines) if not args.no_autotune else None
+    torch.cuda.synchronize()
+
+    def looped():
+        out = []
+        for pr in lines:
+            pr.m_inout.zero_()
+            _, st = L.rls_window_solve(pr.grid, pr.slowness, pr.freqs, pr.geom, pr.d, pr.lam, pr.K, pr.slide,
+                                       pr.cg_tol, pr.max_iter, pr.m_inout, pr.workspace)
+            out.append(st)
+        return out
+
+    def together():
+        for pr in lines:
+            pr.m_inout.zero_()
+        torch.cuda.synchronize()
+        return lsm.rls_multi_line_solve(lines)[1]
+
+    def timed(fn):
+        best, stats = None, None
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = fn()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            if best is None or dt < best:
+                best, stats = dt, st
+        return best, stats
+
+    together()  # first launches and graph instantiations outside the timing
+    t_loop, st_loop = timed(looped)
+    imgs_loop = [pr.m_inout.clone() for pr in lines]
+    t_tog, st_tog = timed(together)
+    same = all(torch.equal(a, pr.m_inout) for a, pr in zip(imgs_loop, lines))
+    out = {"workload": "batching (reduced): the 8 lines nx 256-1024 (incl. 384, 640, 768, 896), nz = nx/2, "
+                       "each line's first 3 windows of K 4-32 shots, every other frequency (52-91), CG to 1e-3",
+           "lines": [{"nx": pr.grid.c.nx, "shots": pr.geom.c.ns, "freqs": pr.freqs.c.nw, "K": pr.K,
+                      "slide": pr.slide, "iters": int(sum(w["iters"] for w in st))}
+                     for pr, st in zip(lines, st_tog)],
+           "looped_ms": round(1e3 * t_loop, 1), "together_ms": round(1e3 * t_tog, 1),
+           "speedup_together_vs_looped": round(t_loop / t_tog, 3),
+           "units_per_s_together": round(line_units(lines, st_tog) / t_tog, 1),
+           "units_per_s_looped": round(line_units(lines, st_loop) / t_loop, 1),
+           "max_final_rel_res": max(w["rel_res"] for st in st_tog for w in st),
+           "images_bitwise_equal": bool(same),
+           "timing": "host wall clock around each whole solve, GPU synchronised on both sides, best of 2",
+           "autotune": tuned}
+    del lines
+    torch.cuda.empty_cache()
+    return out
 
 
 def batching_arm(args):
@@ -530,58 +705,24 @@ def batching_arm(args):
     to 1e-3: one step solves all lines concurrently (rls_multi_line_solve, a stream per line); the
     comparison loops the plain per-line solve over the same lines.  Both run the host-driven CG loop;
     a third arm runs the concurrent solve with graph-replayed CG iterations."""
-    import numpy as np
     import torch
 
     import paper_1801_00819_gb300 as L
     from paper_1801_00819_gb300 import build as B
     from paper_1801_00819_gb300 import lsm
-    from paper_1801_00819_gb300.device import to_device, workspace
     from synth import config_batching_lines
 
     torch.cuda.set_device(0)
     B.build()
-    lines = []
-    for sv in config_batching_lines():
-        ds = to_device(sv.nx, sv.nz, sv.dx, sv.dz, sv.slowness, sv.src_ix, sv.rec_ix, sv.freqs, sv.wavelet)
-        K = sv.window
-        m_true = torch.as_tensor(np.asarray(sv.reflectivity, dtype=np.float32), device="cuda")
-        d = torch.empty((sv.ns, sv.nw, ds.nrec), dtype=torch.complex64, device="cuda")
-        ws_f = workspace(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, K, L.LSM_OP_ADJOINT))
-        for s0 in range(0, sv.ns, K):
-            n = min(K, sv.ns - s0)
-            L.lsm_forward(ds.grid, ds.slowness, ds.freqs, ds.geom, m_true, d[s0:s0 + n], s0, n, ws_f)
-        rms = float(torch.sqrt(torch.mean(torch.abs(d) ** 2)))
-        d += sv.noise_pct * rms * torch.as_tensor(sv.noise().astype(np.complex64), device="cuda")
-        adj = torch.zeros((sv.nz, sv.nx), dtype=torch.float32, device="cuda")
-        for s0 in range(0, sv.ns, K):
-            n = min(K, sv.ns - s0)
-            L.lsm_adjoint(ds.grid, ds.slowness, ds.freqs, ds.geom, d[s0:s0 + n], adj, s0, n, ws_f, accumulate=True)
-        lam = 1e-3 * float(adj.abs().max())
-        del ws_f
-        ws = workspace(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, K, L.LSM_OP_SOLVE))
-        m = torch.zeros((sv.nz, sv.nx), dtype=torch.float32, device="cuda")
-        lines.append(lsm.LineProblem(ds.grid, ds.slowness, ds.freqs, ds.geom, d, lam, K, sv.slide, sv.cg_tol,
-                                     sv.cg_iters, m, ws, torch.cuda.Stream()))
+    lines = [build_line(L, lsm, torch, sv) for sv in config_batching_lines()]
     torch.cuda.synchronize()
     tuned = []
     if not args.no_autotune:  # launch shapes per line, before any timed solve
-        for pr in lines:
-            rep = lsm.lsm_autotune(pr.grid, pr.slowness, pr.freqs, pr.geom, pr.K, pr.workspace)
-            entry = {"nx": pr.grid.c.nx, "K": pr.K, "warps": {k: v["warps"] for k, v in rep.items()},
-                     "heuristic_warps": {k: v["heuristic_warps"] for k, v in rep.items()}}
-            if pr.slide != pr.K:
-                entry["refill_source_warps"] = lsm.lsm_autotune(pr.grid, pr.slowness, pr.freqs, pr.geom, pr.slide,
-                                                                pr.workspace)["source"]["warps"]
-            tuned.append(entry)
+        tuned = tune_lines(lsm, lines)
         torch.cuda.synchronize()
 
     def units_of(stats_per_line):
-        total = 0
-        for pr, st in zip(lines, stats_per_line):
-            per_pass = pr.K * pr.freqs.c.nw * pr.grid.c.nz
-            total += sum((w["n_forward"] + w["n_adjoint"]) / 2 * per_pass for w in st)
-        return total
+        return line_units(lines, stats_per_line)
 
     def sequential():
         out = []

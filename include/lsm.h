@@ -43,8 +43,9 @@
  *    iteration with the host-driven loop, to test convergence) and before returning.
  *  - Errors: every entry point returns an LSM_* status; arguments are validated on the host
  *    before anything is launched.  A call that fails validation launches nothing and leaves
- *    outputs untouched.  No kernel in this library waits on another block or device, so none
- *    can hang; LSM_ERR_TIMEOUT is reserved.
+ *    outputs untouched.  No kernel in this library waits on another block or device; the only
+ *    waits are the tcgen05 transforms' waits on their own tensor-core work, each bounded (about a
+ *    second, LSM_ERR_TIMEOUT).
  *  - Thread safety: calls sharing a workspace must be serialised by the caller.
  */
 #ifndef LSM_GB300_H
@@ -62,7 +63,7 @@ extern "C" {
 #define LSM_ERR_WORKSPACE (-3)      /* workspace smaller than lsm_workspace_bytes() */
 #define LSM_ERR_BREAKDOWN (-4)      /* CG step length undefined: q^T q + lambda p^T p <= 0 or
                                        not finite (e.g. non-finite input data) */
-#define LSM_ERR_TIMEOUT (-5)        /* reserved: a bounded device wait expired */
+#define LSM_ERR_TIMEOUT (-5)        /* a bounded device wait expired (tcgen05 transforms) */
 #define LSM_ERR_UNSUPPORTED_NX (-6) /* nx is not one of the supported widths (see Grid) */
 
 #define LSM_OP_FORWARD 0
@@ -205,8 +206,13 @@ int rls_window_solve(const lsm_grid* grid, const float* slowness, const lsm_freq
  *  - The caller still owns and passes d and m_out; nothing is allocated, freed or resized.
  *  - Problems whose scratch (lsm_workspace_bytes(..., LSM_OP_ADJOINT)) exceeds
  *    LSM_STATIC_SCRATCH_BYTES are rejected with LSM_ERR_WORKSPACE before anything is launched.
- *  - The first call on each device looks up the array's device address (cudaGetSymbolAddress) and
- *    caches it; make that first call before any stream capture on that device.
+ *  - Each call made outside a stream capture looks up the array's device address on the current
+ *    device (cudaGetSymbolAddress) and remembers it; a call made while `stream` is being captured
+ *    uses the remembered address, so make the first call on each device before any stream capture
+ *    (and again after a device reset, which reloads the library's device code).
+ *  - The host arrays (src_ix, rec_ix, freq_hz, wavelet) are copied into a host buffer owned by the
+ *    call before it returns, like every other entry point does: the caller may change or free
+ *    them, pinned or not, as soon as the call returns.
  *  - All calls share the one array and it keeps the last call's contents; every region is fully
  *    rewritten before it is read, so results do not depend on earlier calls.  Calls that overlap
  *    on the GPU (other streams, other host threads) race on the array: serialise them.
@@ -265,10 +271,22 @@ int lsm_profile_stop(lsm_profile* out);
  *     every supported nx (for nx/16 not a multiple of 8 the 16 x nx/16 matrix is zero-padded to
  *     whole 8-column tiles) with receivers at every column (rec_ix NULL); LSM_ERR_ARG otherwise.
  */
+/*
+ *     LSM_TRANSFORM_DFT_FP16X3_TCGEN05, _BF16X3_TCGEN05: the same four-step DFT products, split FP16
+ *     (lo scaled by 2^11, two accumulators) or split BF16 three-term, on the fifth-generation tensor
+ *     cores: tcgen05.mma issued by one thread per 128-thread CTA with 128-byte-swizzled operands in
+ *     shared memory and FP32 accumulators in tensor memory, eight (shot, frequency) items per CTA
+ *     stacked as the MMA's 128 rows.  nx = 512 only (LSM_ERR_UNSUPPORTED_NX otherwise), receivers at
+ *     every column.  Every wait of these kernels on the tensor core is bounded (about a second);
+ *     one that runs out leaves NaN in the call's outputs, and rls_window_solve_ex then returns
+ *     LSM_ERR_TIMEOUT.
+ */
 #define LSM_TRANSFORM_FFT 0
 #define LSM_TRANSFORM_DFT_BF16X3 1
 #define LSM_TRANSFORM_DFT_FP16X3 2
 #define LSM_TRANSFORM_DFT_BF16X1 3
+#define LSM_TRANSFORM_DFT_FP16X3_TCGEN05 4
+#define LSM_TRANSFORM_DFT_BF16X3_TCGEN05 5
 /*
  *   cuda_graph: > 0 runs each window's CG iterations as one CUDA graph -- a conditional WHILE
  *     node whose body is one iteration (A, the vector updates, A^T, the stopping test evaluated on
@@ -304,6 +322,32 @@ int rls_window_solve_ex(const lsm_grid* grid, const float* slowness, const lsm_f
                         float* m_inout, lsm_window_stats* stats, int stats_cap,
                         void* workspace, size_t workspace_bytes, void* stream,
                         const lsm_solve_options* options);
+
+/*
+ * One sliding-window solve sharded over several ranks (processes, typically one per GPU) by
+ * frequency.  Inside a window the (shot, frequency) items of A and A^T are independent (Eq. 1,
+ * Eq. 2), so each rank runs the operator on its own subset of the frequencies -- `freqs` and `d`
+ * ([ns][nw_rank][nrec]) hold this rank's frequencies only -- while the model-space vectors (image,
+ * CG directions) are kept whole on every rank.  Two sums over the ranks make the ranks' CG identical
+ * (Eq. 10, Eq. 11): the image of every A^T (nz nx float32 values, once per CG iteration and twice
+ * per window set-up) and ||q||^2 of every A (one float64 value per CG iteration), each through the
+ * caller's callback
+ *   allreduce(ctx, buf, count, is_double, stream): replace `count` float32 (is_double == 0) or
+ *   float64 values at device address `buf` by their sum over the ranks, ordered on `stream`;
+ *   return 0 on success (anything else ends the solve with LSM_ERR_CUDA).
+ * Every rank must call with the same grid, slowness, geometry, lambda, K, slide, tolerance, limits
+ * and image; the ranks then take the same iterations and return the same image (up to the order in
+ * which the callback adds the ranks' values).  Plain CG with the FP32 FFT transforms and the
+ * host-driven loop; the workspace is lsm_workspace_bytes(grid, geom, freqs, K, LSM_OP_SOLVE) for this
+ * rank's frequencies.  Other arguments and results as for rls_window_solve.
+ */
+typedef int (*lsm_allreduce_fn)(void* ctx, void* buf, size_t count, int is_double, void* stream);
+int rls_window_solve_sharded(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs,
+                             const lsm_geom* geom, const float* d, double lambda, int K, int slide,
+                             double cg_tol, int max_iter, int first_window, int n_windows,
+                             float* m_inout, lsm_window_stats* stats, int stats_cap,
+                             void* workspace, size_t workspace_bytes, void* stream,
+                             lsm_allreduce_fn allreduce, void* allreduce_ctx);
 
 /*
  * Several independent survey lines solved together (batching): each line is a complete
@@ -396,6 +440,26 @@ int lsm_autotune_gradient(const lsm_grid* grid, const float* slowness, const lsm
                           const lsm_geom* geom, int nshots, void* workspace, size_t workspace_bytes,
                           void* stream, lsm_ckpt_tune_report* report);
 void lsm_autotune_reset(void);
+
+/*
+ * Measured FP32 arithmetic peak of the current device, in TFLOP/s (a measurement utility with no
+ * counterpart in the paper: the depth sweeps are bound by the FP32 pipe, and their roofline is
+ * reported against this).  Times, with CUDA events on `stream`, launches of a kernel whose threads
+ * run independent chains of fused multiply-adds (eight 256-thread blocks per SM), once with scalar
+ * FMA instructions and once with the paired FP32 FMA instructions of sm_100-class GPUs; each result
+ * is the flop count (2 per FMA) over the fastest of five timed launches.  Synchronises the stream;
+ * takes about 20 ms.  Returns LSM_ERR_ARG for NULL outputs, LSM_ERR_CUDA on a CUDA failure.
+ */
+int lsm_measure_fp32_peak(double* tflops_ffma, double* tflops_ffma2, void* stream);
+
+/*
+ * Self-check of the bounded device waits (a failure-handling check with no counterpart in the
+ * paper).  Launches one block that waits on an mbarrier nothing arrives at, with the same bounded
+ * wait the tcgen05 transforms use; the wait must give up after about a second and the kernel return
+ * normally.  Returns LSM_ERR_TIMEOUT when it did (the expected outcome: the context stays usable),
+ * LSM_OK if the wait completed, LSM_ERR_CUDA on a CUDA failure.  Synchronises the stream.
+ */
+int lsm_check_bounded_wait(void* stream);
 
 /* Human-readable name of a status code (static string). */
 const char* lsm_status_string(int status);

@@ -18,6 +18,7 @@ from .lsm import (  # noqa: F401
     lsm_born_gradient,
     lsm_forward,
     lsm_kernel_launches,
+    lsm_measure_fp32_peak,
     lsm_num_windows,
     lsm_profile_start,
     lsm_profile_stop,

@@ -273,7 +273,21 @@ SweepShape tc_shape_heuristic(int nx, int mode, int nshots, int nw, int num_sms)
     return tc_shape_for(nx, mode, nshots, nw, warps);
 }
 
+// tcgen05 variants: a fixed shape of 8 items per 128-thread CTA
+static bool is_tc5(int transform) {
+    return transform == LSM_TRANSFORM_DFT_FP16X3_TCGEN05 || transform == LSM_TRANSFORM_DFT_BF16X3_TCGEN05;
+}
+static SweepShape tc5_shape(int nx, int nshots, int nw) {
+    SweepShape s;
+    s.warps = 4;
+    s.blocks = (nshots * nw + 7) / 8;
+    s.wslots = 0;
+    s.smem = nx_ops(nx)->tc5_smem;
+    return s;
+}
+
 SweepShape tc_shape(int nx, int mode, int nshots, int nw, int num_sms, int transform) {
+    if (is_tc5(transform)) return tc5_shape(nx, nshots, nw);
     const int w = tuned_warps(nx, mode, transform, nshots, nw);
     if (w > 0) return tc_shape_for(nx, mode, nshots, nw, w);
     return tc_shape_heuristic(nx, mode, nshots, nw, num_sms);
@@ -336,6 +350,8 @@ struct Layout {
     size_t ckpt, part_s, tune_m, tune_g;  // gradient op
     size_t illum, minv, bmax, sz;  // preconditioned solve
     size_t ctrl;                   // solve: window start read by graph-replayed sweeps
+    size_t err;                    // int: set by a tcgen05 sweep whose bounded wait ran out
+    size_t img, qqt;               // sharded solve: local image, all-reduced ||q||^2
     size_t total;
     int ring, nparts;
 };
@@ -367,6 +383,7 @@ Layout make_layout(const lsm_grid* g, const lsm_geom* geo, const lsm_freqs* f, i
         L.nparts = sh.blocks;
         if (nx_ops(g->nx)->has_tc)
             L.nparts = std::max(L.nparts, tc_shape_heuristic(g->nx, MODE_ADJOINT, nshots, (int)nw, num_sms).blocks);
+        if (nx_ops(g->nx)->has_tc5) L.nparts = std::max(L.nparts, tc5_shape(g->nx, nshots, (int)nw).blocks);
     } else if (op == LSM_OP_GRADIENT) {
         L.nparts = gradient_shape_for(g->nx, nshots, (int)nw, gradient_min_warps(g->nx, nshots, (int)nw, num_sms)).blocks;
     }
@@ -397,9 +414,12 @@ Layout make_layout(const lsm_grid* g, const lsm_geom* geo, const lsm_freqs* f, i
         L.minv = take(plane * sizeof(float));
         L.bmax = take(kIllumBlocks * sizeof(float));
         L.sz = take(kImgRedBlocks * sizeof(double));
+        L.img = take(plane * sizeof(float));  // sharded solve: this rank's image before the all-reduce
+        L.qqt = take(sizeof(double));         // sharded solve: ||q||^2 summed over the ranks
     } else if (op == LSM_OP_ADJOINT) {
         L.ss = take(kImgRedBlocks * sizeof(double));
     }
+    L.err = take(sizeof(int));
     L.total = off;
     return L;
 }
@@ -451,6 +471,7 @@ int prepare(const lsm_grid* g, const float* slowness, const lsm_freqs* f, const 
     std::memcpy(host.data() + L.freq, f->freq_hz, nw * sizeof(float));
     std::memcpy(host.data() + L.wav, f->wavelet, nw * sizeof(float2));
     LSM_CHECK(cudaMemcpyAsync(ws, host.data(), head, cudaMemcpyHostToDevice, st));
+    LSM_CHECK(cudaMemsetAsync(ws + L.err, 0, sizeof(int), st));
     if (sref_override) {
         LSM_CHECK(cudaMemcpyAsync(ws + L.sref, sref_override, (size_t)g->nz * sizeof(double), cudaMemcpyDeviceToDevice,
                                   st));
@@ -498,6 +519,7 @@ SweepArgs base_args(const lsm_grid* g, const lsm_freqs* f, const lsm_geom* geo, 
     a.dss = reinterpret_cast<const float2*>(ws + L.dss);
     a.S = reinterpret_cast<float2*>(ws + L.S);
     a.part = reinterpret_cast<float*>(ws + L.part);
+    a.dev_err = reinterpret_cast<int*>(ws + L.err);
     return a;
 }
 
@@ -543,6 +565,11 @@ cudaError_t run_adjoint(SweepArgs a, int shot0, int n, const float2* din, int nu
 int transform_of(const lsm_solve_options* o, const lsm_grid* g, const lsm_geom* geo, int* transform) {
     *transform = o ? o->transform : LSM_TRANSFORM_FFT;
     if (*transform == LSM_TRANSFORM_FFT) return LSM_OK;
+    if (is_tc5(*transform)) {
+        if (!nx_ops(g->nx)->has_tc5) return LSM_ERR_UNSUPPORTED_NX;
+        if (geo->rec_ix) return LSM_ERR_ARG;  // receivers at every column
+        return LSM_OK;
+    }
     if (*transform != LSM_TRANSFORM_DFT_BF16X3 && *transform != LSM_TRANSFORM_DFT_FP16X3 &&
         *transform != LSM_TRANSFORM_DFT_BF16X1)
         return LSM_ERR_ARG;
@@ -630,8 +657,7 @@ int lsm_adjoint_ex(const lsm_grid* grid, const float* slowness, const lsm_freqs*
 // Scratch for lsm_adjoint_static: a fixed file-scope device array instead of a caller-provided
 // workspace.  Every GPU that loads this library holds these LSM_STATIC_SCRATCH_BYTES until the
 // process exits.  Host code must not hand `g_static_scratch` itself to a kernel (on the host it
-// names a stand-in, not device memory): each device's address is looked up once with
-// cudaGetSymbolAddress and cached.
+// names a stand-in, not device memory): the device address comes from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_static_scratch[LSM_STATIC_SCRATCH_BYTES];
 
 namespace {
@@ -640,21 +666,32 @@ constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
 void* g_static_ptr[kMaxDevices] = {};
 
-// Device address of the static scratch on the current device (looked up on first use).
-int static_scratch_address(void** out) {
+// Device address of the static scratch on the current device for work issued to `st`.  The address
+// is looked up again on every call made outside a stream capture (so a device reset, after which the
+// module and its array are loaded anew, is picked up) and cached per device; a call made while `st`
+// is being captured uses the cached address, so the first call on a device must come before any
+// capture.
+int static_scratch_address(cudaStream_t st, void** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
         return LSM_ERR_CUDA;
     }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return LSM_ERR_CUDA;
+    }
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || p == nullptr) {
             cudaGetLastError();
             return LSM_ERR_CUDA;
         }
         g_static_ptr[dev] = p;
+    } else if (!g_static_ptr[dev]) {
+        return LSM_ERR_CUDA;  // no address looked up outside a capture yet
     }
     *out = g_static_ptr[dev];
     return LSM_OK;
@@ -671,38 +708,16 @@ int lsm_adjoint_static(const lsm_grid* grid, const float* slowness, const lsm_fr
     const int nsm = num_sms_current();
     const Layout L = make_layout(grid, geom, freqs, nshots, LSM_OP_ADJOINT, nsm);
     if (L.total > (size_t)LSM_STATIC_SCRATCH_BYTES) return LSM_ERR_WORKSPACE;
-    void* base = nullptr;
-    rc = static_scratch_address(&base);
-    if (rc != LSM_OK) return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    void* base = nullptr;
+    rc = static_scratch_address(st, &base);
+    if (rc != LSM_OK) return rc;
     char* ws = static_cast<char*>(base);
-    // host arrays go straight from the caller's memory to the scratch (no staging buffer)
-    const size_t nw = (size_t)freqs->nw;
-    LSM_CHECK(cudaMemcpyAsync(ws + L.src, geom->src_ix, (size_t)geom->ns * sizeof(int), cudaMemcpyHostToDevice, st));
-    if (geom->rec_ix)
-        LSM_CHECK(cudaMemcpyAsync(ws + L.rec, geom->rec_ix, (size_t)geom->ns * geom->nrec * sizeof(int),
-                                  cudaMemcpyHostToDevice, st));
-    LSM_CHECK(cudaMemcpyAsync(ws + L.freq, freqs->freq_hz, nw * sizeof(float), cudaMemcpyHostToDevice, st));
-    LSM_CHECK(cudaMemcpyAsync(ws + L.wav, freqs->wavelet, nw * sizeof(float2), cudaMemcpyHostToDevice, st));
-    {
-        ProfScope prof_(KC_TABLES, st);
-        reference_slowness_kernel<<<grid->nz, 256, 0, st>>>(slowness, grid->nx, grid->nz,
-                                                            reinterpret_cast<double*>(ws + L.sref));
-    }
-    count_launch();
-    LSM_CHECK(cudaGetLastError());
-    TableArgs ta;
-    ta.nx = grid->nx;
-    ta.nz = grid->nz;
-    ta.nw = freqs->nw;
-    ta.dx = grid->dx;
-    ta.dz = grid->dz;
-    ta.slowness = slowness;
-    ta.sref = reinterpret_cast<const double*>(ws + L.sref);
-    ta.freq_hz = reinterpret_cast<const float*>(ws + L.freq);
-    ta.phi = reinterpret_cast<float2*>(ws + L.phi);
-    ta.dss = reinterpret_cast<float2*>(ws + L.dss);
-    LSM_CHECK(launch_tables(ta, st));
+    // the same set-up as lsm_adjoint: the host arrays are first copied into a host buffer owned by
+    // this call (so the caller may change or free them as soon as the call returns), then the
+    // reference slowness and the coefficient tables are built in the scratch
+    rc = prepare(grid, slowness, freqs, geom, L, ws, st, nullptr, TABLES_SWEEP);
+    if (rc != LSM_OK) return rc;
     // every scratch region below is fully written before it is read: nothing needs clearing
     SweepArgs a = base_args(grid, freqs, geom, L, ws);
     LSM_CHECK(run_source(a, shot0, nshots, nsm, st));
@@ -861,6 +876,14 @@ int lsm_autotune(const lsm_grid* grid, const float* slowness, const lsm_freqs* f
                               report ? &report->forward : nullptr};
     for (int mi = 0; mi < 3; ++mi) {
         const int mode = modes[mi];
+        if (is_tc5(transform)) {
+            // one fixed launch shape: timed for the report, nothing recorded
+            const SweepShape sh = tc5_shape(nx, nshots, nw);
+            double ms = 0.0;
+            LSM_CHECK(time_shape(mode, transform, a, sh, st, ev.a, ev.b, 3, &ms));
+            if (out[mi]) *out[mi] = lsm_tune_entry{sh.warps, sh.warps, 1, ms, ms};
+            continue;
+        }
         const SweepShape h = transform ? tc_shape_heuristic(nx, mode, nshots, nw, nsm)
                                        : sweep_shape_heuristic(nx, mode, nshots, nw, nsm);
         const int maxw = transform ? 7 : sweep_max_warps(nx, mode, nshots, nw);
@@ -1022,6 +1045,33 @@ struct CgGraph {
     }
 };
 
+// A window solve sharded over ranks by frequency: every rank runs the operator on its own
+// frequencies and the hooks sum, over the ranks, the images of A^T and ||q||^2 (the only places where
+// a sum over (shot, frequency) items meets the model-space vectors, which every rank keeps whole).
+struct ShardHooks {
+    lsm_allreduce_fn fn;
+    void* ctx;
+    float* img;        // [nz][nx] this rank's image before the sum
+    double* qq_total;  // ||q||^2 of this rank's items, then of all ranks' items
+};
+
+static cudaError_t shard_sum(const ShardHooks* h, void* buf, size_t count, int is_double, cudaStream_t st) {
+    return h->fn(h->ctx, buf, count, is_double, st) == 0 ? cudaSuccess : cudaErrorUnknown;
+}
+
+// s = A^T(...) - lambda m over all ranks from this rank's block partial images: the partials are
+// summed into the rank's image, the images are summed over the ranks, and the rest of the reduction
+// (m += alpha p when p and state are given, s = image - lambda m, the ||s||^2 partials) runs on the
+// sum as a single partial.
+static cudaError_t shard_reduce_image(const ShardHooks* h, const float* part, int nparts, int n, float* m, float lam,
+                                      float* s, double* ss, cudaStream_t st, const float* minv, double* sz,
+                                      const float* p = nullptr, const CgState* state = nullptr) {
+    cudaError_t e = cg_reduce_image(part, nparts, n, nullptr, 0.f, 0, h->img, nullptr, st);
+    if (e == cudaSuccess) e = shard_sum(h, h->img, (size_t)n, 0, st);
+    if (e == cudaSuccess) e = cg_reduce_image(h->img, 1, n, m, lam, 0, s, ss, st, minv, sz, p, state);
+    return e;
+}
+
 struct CgVectors {
     float *m, *p, *s;
     float2 *r, *q;
@@ -1031,6 +1081,7 @@ struct CgVectors {
     size_t nd;
     int n;
     double lambda;
+    const ShardHooks* shard;  // null: one rank
 };
 
 // One CG iteration after a window's set-up (Eq. 11): q = A p; alpha = gamma / (||q||^2 + lambda
@@ -1054,13 +1105,22 @@ static cudaError_t cg_iteration(SweepArgs a, int start, int K, int nsm, int tran
         aa.dq = v.q;
         aa.qq_in = v.qq;
         aa.nqq = nqq;
+        if (v.shard) {  // alpha needs ||q||^2 over every rank's items
+            if (e == cudaSuccess) e = cg_sum_partials(v.qq, nqq, v.shard->qq_total, st);
+            if (e == cudaSuccess) e = shard_sum(v.shard, v.shard->qq_total, 1, 1, st);
+            aa.qq_in = v.shard->qq_total;
+            aa.nqq = 1;
+        }
         aa.pp_in = v.pp;
         aa.npp = kRedBlocks;
         aa.cg_gi = gi;
         aa.lam = v.lambda;
         aa.cg = v.state;
         if (e == cudaSuccess) e = run_adjoint(aa, start, K, nullptr, nsm, st, &nparts, 0);
-        if (e == cudaSuccess)
+        if (e == cudaSuccess && v.shard)
+            e = shard_reduce_image(v.shard, a.part, nparts, v.n, v.m, (float)v.lambda, v.s, v.ss, st, v.minv, v.sz, v.p,
+                                   v.state);
+        else if (e == cudaSuccess)
             e = cg_reduce_image(a.part, nparts, v.n, v.m, (float)v.lambda, 0, v.s, v.ss, st, v.minv, v.sz, v.p,
                                 v.state);
     } else {
@@ -1112,10 +1172,13 @@ static int build_cg_graph(CgGraph& G, SweepArgs a, int K, int nsm, int transform
     return LSM_OK;
 }
 
-int rls_window_solve_ex(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs, const lsm_geom* geom,
+// The sliding-window solve; `shard_fn` (with `shard_ctx`) set: this rank's share of a solve sharded
+// by frequency (plain CG, FP32 FFT transforms, host-driven loop).
+static int window_solve(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs, const lsm_geom* geom,
                         const float* d, double lambda, int K, int slide, double cg_tol, int max_iter,
                         int first_window, int n_windows, float* m_inout, lsm_window_stats* stats, int stats_cap,
-                        void* workspace, size_t workspace_bytes, void* stream, const lsm_solve_options* options) {
+                        void* workspace, size_t workspace_bytes, void* stream, const lsm_solve_options* options,
+                        lsm_allreduce_fn shard_fn, void* shard_ctx) {
     int rc = validate_common(grid, freqs, geom);
     if (rc != LSM_OK) return rc;
     if (!aligned16(slowness) || !aligned16(d) || !aligned16(m_inout) || !aligned16(workspace)) return LSM_ERR_ARG;
@@ -1128,6 +1191,7 @@ int rls_window_solve_ex(const lsm_grid* grid, const float* slowness, const lsm_f
     int transform = 0;
     rc = transform_of(options, grid, geom, &transform);
     if (rc != LSM_OK) return rc;
+    if (shard_fn && (transform != 0 || precond != LSM_PRECOND_NONE)) return LSM_ERR_ARG;
     const int ns = geom->ns;
     const int nwin = lsm_num_windows(ns, K, slide);
     if (nwin == 0) return LSM_ERR_ARG;
@@ -1159,7 +1223,9 @@ int rls_window_solve_ex(const lsm_grid* grid, const float* slowness, const lsm_f
     int* shot0_dev = reinterpret_cast<int*>(ws + L.ctrl);
     // cuda_graph > 0: graph; < 0: host-driven loop; 0: graph unless the sweeps are being event-timed
     const int graph_opt = options ? options->cuda_graph : 0;
-    const bool use_graph = graph_opt > 0 || (graph_opt == 0 && !profiling_sweeps());
+    const bool use_graph = !shard_fn && (graph_opt > 0 || (graph_opt == 0 && !profiling_sweeps()));
+    ShardHooks hooks{shard_fn, shard_ctx, reinterpret_cast<float*>(ws + L.img), reinterpret_cast<double*>(ws + L.qqt)};
+    const ShardHooks* shard = shard_fn ? &hooks : nullptr;
     CgGraph graph;
     float* minv = precond == LSM_PRECOND_ILLUMINATION ? reinterpret_cast<float*>(ws + L.minv) : nullptr;
     double* sz = minv ? reinterpret_cast<double*>(ws + L.sz) : nullptr;
@@ -1187,14 +1253,20 @@ int rls_window_solve_ex(const lsm_grid* grid, const float* slowness, const lsm_f
         LSM_CHECK(cg_zero_state(state, st));
         // b = A_k^T d_k  ->  ||b||^2
         LSM_CHECK(run_adjoint(a, start, K, dk, nsm, st, &nparts, transform));
-        LSM_CHECK(cg_reduce_image(a.part, nparts, n, nullptr, 0.f, 0, s, ss, st));
+        if (shard)
+            LSM_CHECK(shard_reduce_image(shard, a.part, nparts, n, nullptr, 0.f, s, ss, st, nullptr, nullptr));
+        else
+            LSM_CHECK(cg_reduce_image(a.part, nparts, n, nullptr, 0.f, 0, s, ss, st));
         LSM_CHECK(cg_store_sum(ss, state, st));
         // r = d_k - A_k m
         LSM_CHECK(run_forward(a, start, K, m_inout, q, nsm, st, transform));
         LSM_CHECK(cg_residual(dk, q, r, nd, st));
         // s = A_k^T r - lambda m ; p = s ; gamma = ||s||^2
         LSM_CHECK(run_adjoint(a, start, K, r, nsm, st, &nparts, transform));
-        LSM_CHECK(cg_reduce_image(a.part, nparts, n, m_inout, lamf, 0, s, ss, st, minv, sz));
+        if (shard)
+            LSM_CHECK(shard_reduce_image(shard, a.part, nparts, n, m_inout, lamf, s, ss, st, minv, sz));
+        else
+            LSM_CHECK(cg_reduce_image(a.part, nparts, n, m_inout, lamf, 0, s, ss, st, minv, sz));
         int gi = 0;
         LSM_CHECK(cg_update_p(p, s, n, ss, 1, state, 1, gi, pp, st, minv, sz));
         CgState hs;
@@ -1206,7 +1278,7 @@ int rls_window_solve_ex(const lsm_grid* grid, const float* slowness, const lsm_f
             if (!graph.exec) {
                 SweepArgs ag = a;
                 ag.shot0_dev = shot0_dev;
-                const CgVectors v{m_inout, p, s, r, q, qq, pp, ss, sz, minv, state, nd, n, lambda};
+                const CgVectors v{m_inout, p, s, r, q, qq, pp, ss, sz, minv, state, nd, n, lambda, nullptr};
                 rc = build_cg_graph(graph, ag, K, nsm, transform, v);
                 if (rc != LSM_OK) return rc;
             }
@@ -1228,7 +1300,7 @@ int rls_window_solve_ex(const lsm_grid* grid, const float* slowness, const lsm_f
         rel = bnorm > 0.0 ? std::sqrt(hs.ss[gi]) / bnorm : 0.0;
         rel0 = rel;
         broke = hs.breakdown != 0;
-        const CgVectors v{m_inout, p, s, r, q, qq, pp, ss, sz, minv, state, nd, n, lambda};
+        const CgVectors v{m_inout, p, s, r, q, qq, pp, ss, sz, minv, state, nd, n, lambda, shard};
         while (!broke && it < max_iter && !(rel <= cg_tol)) {
             LSM_CHECK(cg_iteration(a, start, K, nsm, transform, v, gi, st));
             gi ^= 1;
@@ -1242,6 +1314,13 @@ int rls_window_solve_ex(const lsm_grid* grid, const float* slowness, const lsm_f
         }
         }
         const auto t1 = std::chrono::steady_clock::now();
+        if (transform != 0) {
+            // a tcgen05 sweep whose bounded wait on the tensor core ran out leaves NaN and this flag
+            int err = 0;
+            LSM_CHECK(cudaMemcpyAsync(&err, ws + L.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+            LSM_CHECK(cudaStreamSynchronize(st));
+            if (err) return LSM_ERR_TIMEOUT;
+        }
         const int idx = k - first_window;
         if (idx < stats_cap) {
             stats[idx].start = start;
@@ -1255,6 +1334,25 @@ int rls_window_solve_ex(const lsm_grid* grid, const float* slowness, const lsm_f
         if (broke) return LSM_ERR_BREAKDOWN;
     }
     return LSM_OK;
+}
+
+int rls_window_solve_ex(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs, const lsm_geom* geom,
+                        const float* d, double lambda, int K, int slide, double cg_tol, int max_iter,
+                        int first_window, int n_windows, float* m_inout, lsm_window_stats* stats, int stats_cap,
+                        void* workspace, size_t workspace_bytes, void* stream, const lsm_solve_options* options) {
+    return window_solve(grid, slowness, freqs, geom, d, lambda, K, slide, cg_tol, max_iter, first_window, n_windows,
+                        m_inout, stats, stats_cap, workspace, workspace_bytes, stream, options, nullptr, nullptr);
+}
+
+int rls_window_solve_sharded(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs,
+                             const lsm_geom* geom, const float* d, double lambda, int K, int slide, double cg_tol,
+                             int max_iter, int first_window, int n_windows, float* m_inout, lsm_window_stats* stats,
+                             int stats_cap, void* workspace, size_t workspace_bytes, void* stream,
+                             lsm_allreduce_fn allreduce, void* allreduce_ctx) {
+    if (!allreduce) return LSM_ERR_ARG;
+    return window_solve(grid, slowness, freqs, geom, d, lambda, K, slide, cg_tol, max_iter, first_window, n_windows,
+                        m_inout, stats, stats_cap, workspace, workspace_bytes, stream, nullptr, allreduce,
+                        allreduce_ctx);
 }
 
 int rls_window_solve(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs, const lsm_geom* geom,

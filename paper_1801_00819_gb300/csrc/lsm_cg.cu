@@ -311,6 +311,13 @@ __global__ void __launch_bounds__(kRedThreads) store_sum_kernel(const double* __
     if (threadIdx.x == 0) st->bb = tot;
 }
 
+// *out = sum of part[0 .. n) in the fixed order of sum_partials
+__global__ void __launch_bounds__(kRedThreads) sum_to_kernel(const double* __restrict__ part, int n, double* out) {
+    __shared__ double sh[40];
+    const double tot = sum_partials(part, n, sh);
+    if (threadIdx.x == 0) *out = tot;
+}
+
 __global__ void zero_state_kernel(CgState* st) {
     if (threadIdx.x == 0) {
         st->gamma[0] = st->gamma[1] = 0.0;
@@ -398,6 +405,13 @@ cudaError_t cg_update_p(float* p, const float* s, int n, const double* ss_part, 
 cudaError_t cg_store_sum(const double* part, CgState* state, cudaStream_t st) {
     ProfScope prof_(KC_VECTOR, st);
     store_sum_kernel<<<1, kRedThreads, 0, st>>>(part, kImgRedBlocks, state);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t cg_sum_partials(const double* part, int n, double* out, cudaStream_t st) {
+    ProfScope prof_(KC_VECTOR, st);
+    sum_to_kernel<<<1, kRedThreads, 0, st>>>(part, n, out);
     count_launch();
     return cudaGetLastError();
 }

@@ -47,6 +47,8 @@ cudaError_t cg_illumination(const float2* S, int rows, int n, float* illum, floa
 cudaError_t cg_precond_finalize(const float* illum, int n, const float* block_max, double eps, float* minv,
                                 cudaStream_t st);
 cudaError_t cg_store_sum(const double* part, CgState* state, cudaStream_t st);
+// *out = the sum of n partials in a fixed order (one block)
+cudaError_t cg_sum_partials(const double* part, int n, double* out, cudaStream_t st);
 
 // Device-driven CG loop.  gi = -1 in cg_update_mr / cg_update_p means "the slot in state->gi"
 // (cg_update_p then writes slot state->gi ^ 1); cg_loop_setup resets the loop counters and stores

@@ -45,6 +45,7 @@ struct SweepArgs {
     int cg_gi;                     // slot of the current gamma in cg; -1: cg->gi (device-driven loop)
     double lam;                    // Tikhonov weight lambda
     CgState* cg;                   // gamma (read); delta, alpha and the breakdown flag (block 0 writes)
+    int* dev_err;                  // set to 1 by a kernel whose bounded wait on the tensor core ran out
 };
 
 // Arguments of the gradient kernel (lsm_grad.cuh) over the items of shots [shot0, shot0+nshots).
@@ -112,6 +113,8 @@ struct NxOps {
     cudaError_t (*tc_sweep)(int mode, int prec, const SweepArgs& a, const SweepShape& shape, cudaStream_t st);
     size_t (*tc_smem)(int mode, int warps);
     size_t (*gradient_smem)(int warps, int wslots);
+    bool has_tc5;                 // tcgen05 transform variants exist for this nx
+    size_t tc5_smem;              // their dynamic shared memory per CTA
 };
 // The operations for nx, or nullptr when nx is not supported.
 const NxOps* nx_ops(int nx);

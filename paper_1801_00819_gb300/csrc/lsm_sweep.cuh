@@ -27,6 +27,7 @@
 #include "lsm_grad.cuh"
 #include "lsm_internal.h"
 #include "lsm_tc.cuh"
+#include "lsm_tc5.cuh"
 
 namespace lsm {
 
@@ -592,11 +593,44 @@ struct Dispatch {
         }
     }
 
+    // tcgen05 transform variants (nx = 512): 8 items per 128-thread CTA
+    static constexpr bool kTc5 = N == 512;
+
+    template <int PREC, int MODE>
+    static cudaError_t tc5_launch(const SweepArgs& a, const SweepShape& sh, cudaStream_t st) {
+        if constexpr (kTc5) {
+            static DeviceOnce configured;
+            cudaError_t e = configured.run([] {
+                return cudaFuncSetAttribute(tc5_sweep_kernel<N, PREC, MODE>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc5_smem_bytes<N>());
+            });
+            if (e != cudaSuccess) return e;
+            if (sh.smem != tc5_smem_bytes<N>() || sh.warps != 4) return cudaErrorInvalidValue;
+            ProfScope prof_(MODE == MODE_SOURCE ? KC_SOURCE : MODE == MODE_ADJOINT ? KC_ADJOINT : KC_FORWARD, st);
+            tc5_sweep_kernel<N, PREC, MODE><<<sh.blocks, 128, sh.smem, st>>>(a);
+            count_launch();
+            return cudaGetLastError();
+        } else {
+            return cudaErrorNotSupported;
+        }
+    }
+
+    template <int PREC>
+    static cudaError_t tc5_mode(int mode, const SweepArgs& a, const SweepShape& sh, cudaStream_t st) {
+        switch (mode) {
+            case MODE_SOURCE: return tc5_launch<PREC, MODE_SOURCE>(a, sh, st);
+            case MODE_ADJOINT: return tc5_launch<PREC, MODE_ADJOINT>(a, sh, st);
+            default: return tc5_launch<PREC, MODE_FORWARD>(a, sh, st);
+        }
+    }
+
     static cudaError_t tc_sweep(int mode, int prec, const SweepArgs& a, const SweepShape& sh, cudaStream_t st) {
         switch (prec) {
             case PREC_BF16X3: return tc_mode<PREC_BF16X3>(mode, a, sh, st);
             case PREC_FP16X3: return tc_mode<PREC_FP16X3>(mode, a, sh, st);
             case PREC_BF16X1: return tc_mode<PREC_BF16X1>(mode, a, sh, st);
+            case PREC_FP16X3_TC5: return tc5_mode<PREC_FP16X3_TC5>(mode, a, sh, st);
+            case PREC_BF16X3_TC5: return tc5_mode<PREC_BF16X3_TC5>(mode, a, sh, st);
             default: return cudaErrorInvalidValue;
         }
     }
@@ -695,5 +729,6 @@ struct Dispatch {
     extern const NxOps kNxOps_##NN = {NN, Dispatch<NN>::V, Dispatch<NN>::kGrad, tables_##NN, sweep_##NN,        \
                                       max_warps_##NN, smem_##NN, tables_grad_##NN, gradient_##NN,  \
                                       gradient_max_warps_##NN, Dispatch<NN>::kTc, tables_natural_##NN, \
-                                      tc_sweep_##NN, tc_smem_##NN, gradient_smem_##NN};           \
+                                      tc_sweep_##NN, tc_smem_##NN, gradient_smem_##NN,            \
+                                      Dispatch<NN>::kTc5, Dispatch<NN>::kTc5 ? tc5_smem_bytes<512>() : 0}; \
     }

@@ -1,0 +1,539 @@
+// Depth sweeps with the lateral transforms as DFT-matrix products on the fifth-generation tensor
+// cores (tcgen05: single-thread MMAs with shared-memory operands and TMEM accumulators), a precision
+// variant of the split-step depth step (Examples section).
+//
+// Four-step factorisation, N = 16 R: an item's points x[R n1 + n2] form X[n1][n2] (16 x R) and
+//   forward  Y = F16 X,  Y'[k1][n2] = Y[k1][n2] w^(k1 n2),  Z = Y' F_R,  Z[k1][k2] = x^[k1 + 16 k2],
+//   inverse  Y'' = Z conj(F_R),  Y'''[k1][n2] = Y''[k1][n2] w^-(k1 n2),  X' = conj(F16) Y''',
+// w = exp(-2 pi i / N); the 1/N sits in the phase-shift table (natural frequency order).  Every
+// product is one real GEMM with the data as the M = 128-row operand and the real form of the DFT
+// matrix as the N operand: a complex row vector enters as its interleaved (re, im) values and the
+// constant matrix [[Fr, -Fi], [Fi, Fr]] (interleaved the same way) gives the interleaved (re, im)
+// outputs.  Operands are split as x = hi + lo in 16 bits and every product takes the three terms
+// hi hi + hi lo + lo hi:
+//   BF16: hi = bf16(x), lo = bf16(x - hi), all three terms in one FP32 accumulator;
+//   FP16: hi = fp16(x), lo = fp16((x - hi) 2^11), hi hi in one accumulator and the two scaled cross
+//         terms in a second one, added as acc0 + 2^-11 acc1; each item is brought to a largest
+//         component in [1/2, 1) by an exact power-of-two scale before each depth step (FP16's exponent
+//         range) and scaled back after it.
+// A row of an operand holds [hi | lo] along K, so the three terms are three K ranges of the same
+// two tiles (A hi x B hi, A hi x B lo, A lo x B hi).  The inverse products use the forward matrices
+// through conj(M conj(F)) = conj(conj(M) F): the operand is written conjugated and the accumulator
+// read back conjugated, so only F16 and F_R are kept in shared memory.
+//
+// One CTA of 128 threads runs 8 (shot, frequency) items through the whole depth loop.  The left
+// products (16-point, contraction over n1) take rows (item, n2): two tiles of 128 rows, four items
+// each, and thread t owns row t of both tiles, i.e. column n2 = t % 32 of items t / 32 and
+// 4 + t / 32; the wavefield lives in those registers between depth steps.  The right products
+// (R-point, contraction over n2) take rows (item, k1): one tile of 8 x 16 rows, thread t owns row t.
+// The passage between the two row layouts goes through the shared-memory operand tile.  One thread
+// issues the MMAs of a stage and commits them to an mbarrier that every thread waits on (bounded:
+// a wait that runs out sets the error flag, the CTA stops and writes NaN to its outputs).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "lsm_fft.cuh"
+#include "lsm_internal.h"
+#include "lsm_tc.cuh"
+#include "lsm_umma.cuh"
+
+namespace lsm {
+
+// tcgen05 transform precisions (numbering continues TcPrecision)
+enum Tc5Precision { PREC_FP16X3_TC5 = 4, PREC_BF16X3_TC5 = 5 };
+
+template <int N>
+struct Tc5Shape {
+    static_assert(N == 512, "tcgen05 transforms: nx = 512");
+    static constexpr int R = N / 16;          // 32
+    static constexpr int ITEMS = 8;           // items per CTA
+    static constexpr int THREADS = 128;
+    // shared memory (bytes from the 1024-aligned base): the constant B operands of the left product
+    // (32 rows x 64 K = 4 KB) and of the right product (64 rows x 128 K = 16 KB), the A operand (two 128-row K blocks: the two left tiles, or the hi and lo halves of the
+    // right tile), the twiddles in both index orders and the adjoint's per-warp image rows
+    static constexpr int A_BYTES = 2 * 128 * 128;
+    static constexpr int OFF_BLF = 0;
+    static constexpr int OFF_BRF = OFF_BLF + 32 * 128;
+    static constexpr int OFF_A = OFF_BRF + 2 * 64 * 128;
+    static constexpr int OFF_TW = OFF_A + A_BYTES;             // w^(k1 n2) as [k1][n2] float2
+    static constexpr int OFF_TWT = OFF_TW + 16 * R * 8;        // the same as [n2][k1]
+    static constexpr int OFF_IMG = OFF_TWT + 16 * R * 8;       // adjoint: [4 warps][N] float
+    static constexpr int BYTES = OFF_IMG + 4 * N * 4;
+    static constexpr size_t SMEM = (size_t)BYTES + 1024;       // + alignment slack
+    // TMEM columns: left accumulators [tile][acc][32], right accumulators [acc][64]
+    static constexpr uint32_t TM_L = 0;
+    static constexpr uint32_t TM_R = 128;
+    static constexpr uint32_t TM_COLS = 256;
+};
+
+template <int PREC>
+struct Tc5Split {
+    static constexpr bool FP16 = PREC == PREC_FP16X3_TC5;
+    // packed 16-bit pair (lo half = first value) of hi parts and of lo parts of (x0, x1)
+    static __device__ __forceinline__ void split(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+        if constexpr (FP16) {
+            const __half2 h = __floats2half2_rn(x0, x1);
+            const float2 hf = __half22float2(h);
+            const __half2 l = __floats2half2_rn((x0 - hf.x) * 2048.f, (x1 - hf.y) * 2048.f);
+            hi = *reinterpret_cast<const uint32_t*>(&h);
+            lo = *reinterpret_cast<const uint32_t*>(&l);
+        } else {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+            const float2 hf = __bfloat1622float2(h);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+            hi = *reinterpret_cast<const uint32_t*>(&h);
+            lo = *reinterpret_cast<const uint32_t*>(&l);
+        }
+    }
+    static __device__ __forceinline__ uint16_t hi16(float x) {
+        if constexpr (FP16) {
+            const __half h = __float2half_rn(x);
+            return *reinterpret_cast<const uint16_t*>(&h);
+        } else {
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            return *reinterpret_cast<const uint16_t*>(&h);
+        }
+    }
+    static __device__ __forceinline__ float hi_value(float x) {
+        if constexpr (FP16) return __half2float(__float2half_rn(x));
+        else return __bfloat162float(__float2bfloat16_rn(x));
+    }
+    static __device__ __forceinline__ uint16_t lo16(float x) {
+        const float r = x - hi_value(x);
+        if constexpr (FP16) {
+            const __half h = __float2half_rn(r * 2048.f);
+            return *reinterpret_cast<const uint16_t*>(&h);
+        } else {
+            const __nv_bfloat16 h = __float2bfloat16_rn(r);
+            return *reinterpret_cast<const uint16_t*>(&h);
+        }
+    }
+};
+
+// Constant B operand of one complex product with a DFT matrix G[n][k] = exp(sgn 2 pi i n k / L)
+// (contraction over n, output k), in the real interleaved form: row c = 2 k + o (o = 0 re, 1 im) of
+// nrows = 2 L rows; K element 2 n + q (q = 0 re, 1 im) of the hi part, and kper + 2 n + q of the lo
+// part.  K runs in blocks of 64 elements, block b at base + b * nrows * 128.
+template <int PREC>
+__device__ void tc5_build_dft(unsigned char* base, int L, int sgn, int kper) {
+    using SP = Tc5Split<PREC>;
+    const int nrows = 2 * L;
+    const int kk = 2 * L;  // K elements of each part (hi, lo)
+    for (int idx = threadIdx.x; idx < nrows * kk; idx += blockDim.x) {
+        const int c = idx / kk, k = idx % kk;
+        const int kf = c >> 1, o = c & 1, n = k >> 1, q = k & 1;
+        float sn, cs;
+        sincospif((float)sgn * 2.0f * (float)((n * kf) % L) / (float)L, &sn, &cs);
+        // (Gr + i Gi)(xr + i xi): re = Gr xr - Gi xi, im = Gi xr + Gr xi
+        const float b = o == 0 ? (q == 0 ? cs : -sn) : (q == 0 ? sn : cs);
+        const int khi = k, klo = kper + k;
+        *reinterpret_cast<uint16_t*>(base + (khi / 64) * nrows * 128 + umma::sw128_offset(c, khi % 64)) = SP::hi16(b);
+        *reinterpret_cast<uint16_t*>(base + (klo / 64) * nrows * 128 + umma::sw128_offset(c, klo % 64)) = SP::lo16(b);
+    }
+}
+
+// Issue the three split products of one stage: D (+)= A[k ranges] B[k ranges]; A and B are K-major
+// 128B-swizzled operands whose K axis is [hi (kper) | lo (kper)] in blocks of 64; kper = 32 or 64.
+template <int PREC>
+__device__ __forceinline__ void tc5_issue(uint32_t d0, uint32_t d1, uint32_t a_base, int a_rows, uint32_t b_base,
+                                          int b_rows, int kper, uint32_t idesc) {
+    constexpr bool FP16 = PREC == PREC_FP16X3_TC5;
+    auto kaddr = [](uint32_t base, int rows, int k) { return base + (uint32_t)((k / 64) * rows * 128 + (k % 64) * 2); };
+    const int steps = kper / 16;
+    // hi x hi
+    for (int s = 0; s < steps; ++s)
+        umma::mma_f16(d0, umma::desc_sw128(kaddr(a_base, a_rows, 16 * s)), umma::desc_sw128(kaddr(b_base, b_rows, 16 * s)),
+                      idesc, s > 0);
+    // hi x lo, lo x hi (FP16: second accumulator, scaled by 2^11)
+    const uint32_t dx = FP16 ? d1 : d0;
+    for (int s = 0; s < steps; ++s)
+        umma::mma_f16(dx, umma::desc_sw128(kaddr(a_base, a_rows, 16 * s)),
+                      umma::desc_sw128(kaddr(b_base, b_rows, kper + 16 * s)), idesc, FP16 ? s > 0 : true);
+    for (int s = 0; s < steps; ++s)
+        umma::mma_f16(dx, umma::desc_sw128(kaddr(a_base, a_rows, kper + 16 * s)),
+                      umma::desc_sw128(kaddr(b_base, b_rows, 16 * s)), idesc, true);
+}
+
+template <int N>
+constexpr size_t tc5_smem_bytes() { return Tc5Shape<N>::SMEM; }
+
+template <int N, int PREC, int MODE>
+__global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
+    using S = Tc5Shape<N>;
+    using SP = Tc5Split<PREC>;
+    constexpr bool FP16 = SP::FP16;
+    constexpr int R = S::R;
+    extern __shared__ unsigned char tc5_smem_raw[];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tslot;
+    unsigned char* base = tc5_smem_raw + ((1024u - (umma::smem_u32(tc5_smem_raw) & 1023u)) & 1023u);
+    const uint32_t sbase = umma::smem_u32(base);
+    float2* TW = reinterpret_cast<float2*>(base + S::OFF_TW);    // [k1][n2]
+    float2* TWT = reinterpret_cast<float2*>(base + S::OFF_TWT);  // [n2][k1]
+    float* img = reinterpret_cast<float*>(base + S::OFF_IMG);    // [4][N]
+    unsigned char* Abuf = base + S::OFF_A;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nitems = a.nshots * a.nw;
+    const int shot0 = a.shot0_dev ? __ldg(a.shot0_dev) : a.shot0;
+    const int nz = a.nz;
+
+    // ---- set-up: constants, barrier, TMEM
+    tc5_build_dft<PREC>(base + S::OFF_BLF, 16, -1, 32);
+    tc5_build_dft<PREC>(base + S::OFF_BRF, R, -1, 64);
+    for (int idx = tid; idx < 16 * R; idx += blockDim.x) {
+        const int k1 = idx / R, n2 = idx % R;
+        float sn, cs;
+        sincospif(-2.0f * (float)((k1 * n2) % N) / (float)N, &sn, &cs);
+        TW[idx] = make_float2(cs, sn);
+        TWT[n2 * 16 + k1] = make_float2(cs, sn);
+    }
+    umma::fence_smem_to_async();
+    if (tid == 0) umma::mbar_init(&bar, 1);
+    if (warp == 0) umma::tmem_alloc(&tslot, S::TM_COLS);
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = tslot;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    uint32_t phase = 0;
+    bool alive = true;
+
+    // items of this thread in the left-product layout: tile tau holds items 4 tau + warp, column n2
+    int itemL[2], iwL[2], shotL[2];
+    bool okL[2];
+#pragma unroll
+    for (int tau = 0; tau < 2; ++tau) {
+        itemL[tau] = blockIdx.x * S::ITEMS + 4 * tau + warp;
+        okL[tau] = itemL[tau] < nitems;
+        iwL[tau] = okL[tau] ? itemL[tau] / a.nshots : 0;
+        shotL[tau] = okL[tau] ? shot0 + (itemL[tau] - iwL[tau] * a.nshots) : shot0;
+    }
+    // item of this thread in the right-product layout: row t = 16 item + k1
+    const int itemR = blockIdx.x * S::ITEMS + tid / 16;
+    const int k1R = tid % 16;
+    const int iwR = itemR < nitems ? itemR / a.nshots : 0;
+    const int n2 = lane;
+
+    // the wavefield: u[tau][n1] = x[R n1 + n2] of item 4 tau + warp
+    float2 u[2][16];
+
+    // wait for the MMAs of a stage; every thread agrees on the outcome
+    // (the phase advances only when every thread saw it complete, so that after a failure every
+    // thread still names the pending phase)
+    auto stage_wait = [&]() -> bool {
+        const bool ok = umma::mbar_wait(&bar, phase);
+        umma::fence_after_sync();
+        const bool all = __syncthreads_and(ok) != 0;
+        if (all) phase ^= 1u;
+        return all;
+    };
+    constexpr uint32_t IDESC_L = umma::idesc_f16(!FP16, 128, 32);
+    constexpr uint32_t IDESC_R = umma::idesc_f16(!FP16, 128, 64);
+
+    // one depth step on u: F^-1 (phi . F u) (conj(phi) when CONJ); phi rows of depth jz
+    auto transform_step = [&](int jz, bool conj_phi) -> bool {
+        // FP16: per-item power-of-two scale (the item is this warp's 32 lanes in each tile)
+        int ex[2] = {0, 0};
+        if constexpr (FP16) {
+#pragma unroll
+            for (int tau = 0; tau < 2; ++tau) {
+                float mx = 0.f;
+#pragma unroll
+                for (int n1 = 0; n1 < 16; ++n1) mx = fmaxf(mx, fmaxf(fabsf(u[tau][n1].x), fabsf(u[tau][n1].y)));
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                if (mx > 0.f && mx <= 3.0e38f) frexpf(mx, &ex[tau]);
+                ex[tau] = max(-100, min(ex[tau], 100));
+                const float down = ldexpf(1.f, -ex[tau]);
+#pragma unroll
+                for (int n1 = 0; n1 < 16; ++n1) u[tau][n1] = make_float2(u[tau][n1].x * down, u[tau][n1].y * down);
+            }
+        }
+        // (1) left operand tiles: row t, K = [hi: (re, im) of n1 = 0..15 | lo: same]
+#pragma unroll
+        for (int tau = 0; tau < 2; ++tau) {
+            unsigned char* tile = Abuf + tau * 16384;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {  // chunk c: n1 = 4c .. 4c+3
+                uint32_t h[4], l[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) SP::split(u[tau][4 * c + q].x, u[tau][4 * c + q].y, h[q], l[q]);
+                *reinterpret_cast<uint4*>(tile + umma::sw128_offset(tid, 8 * c)) = make_uint4(h[0], h[1], h[2], h[3]);
+                *reinterpret_cast<uint4*>(tile + umma::sw128_offset(tid, 32 + 8 * c)) = make_uint4(l[0], l[1], l[2], l[3]);
+            }
+        }
+        umma::fence_smem_to_async();
+        umma::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            umma::fence_after_sync();
+#pragma unroll
+            for (int tau = 0; tau < 2; ++tau)
+                tc5_issue<PREC>(tmem + S::TM_L + tau * 64, tmem + S::TM_L + tau * 64 + 32,
+                                sbase + S::OFF_A + tau * 16384, 128, sbase + S::OFF_BLF, 32, 32, IDESC_L);
+            umma::mma_commit(&bar);
+        }
+        if (!stage_wait()) return false;
+        // (2) Y[k1][n2] of both tiles -> twiddle -> right operand rows (item, k1), K = 2 n2 + q
+#pragma unroll
+        for (int tau = 0; tau < 2; ++tau) {
+            float y[32];
+            umma::tmem_ld32(tmem + lane_base + S::TM_L + tau * 64, y);
+            if constexpr (FP16) {
+                float y2[32];
+                umma::tmem_ld32(tmem + lane_base + S::TM_L + tau * 64 + 32, y2);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) y[i] = fmaf(y2[i], 1.f / 2048.f, y[i]);
+            }
+            const int row0 = (4 * tau + warp) * 16;
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) {
+                const float2 v = cmul(make_float2(y[2 * k1], y[2 * k1 + 1]), TW[k1 * R + n2]);
+                uint32_t h, l;
+                SP::split(v.x, v.y, h, l);
+                *reinterpret_cast<uint32_t*>(Abuf + umma::sw128_offset(row0 + k1, 2 * n2)) = h;
+                *reinterpret_cast<uint32_t*>(Abuf + 16384 + umma::sw128_offset(row0 + k1, 2 * n2)) = l;
+            }
+        }
+        umma::fence_smem_to_async();
+        umma::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            umma::fence_after_sync();
+            tc5_issue<PREC>(tmem + S::TM_R, tmem + S::TM_R + 64, sbase + S::OFF_A, 128, sbase + S::OFF_BRF, 64, 64,
+                            IDESC_R);
+            umma::mma_commit(&bar);
+        }
+        if (!stage_wait()) return false;
+        // (3) Z[k1][k2] (row t) -> phase shift -> right operand of the inverse, same rows
+        {
+            const float2* prow = a.phi + ((size_t)iwR * nz + jz) * N;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {  // k2 = 16 half .. 16 half + 15
+                float z[32];
+                umma::tmem_ld32(tmem + lane_base + S::TM_R + 32 * half, z);
+                if constexpr (FP16) {
+                    float z2[32];
+                    umma::tmem_ld32(tmem + lane_base + S::TM_R + 64 + 32 * half, z2);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) z[i] = fmaf(z2[i], 1.f / 2048.f, z[i]);
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {  // chunk: k2 = 16 half + 4 c .. + 3
+                    uint32_t h[4], l[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int k2l = 4 * c + q;
+                        const float2 p = __ldg(prow + k1R + 16 * (16 * half + k2l));
+                        const float2 zz = make_float2(z[2 * k2l], z[2 * k2l + 1]);
+                        const float2 v = conj_phi ? cmulc(zz, p) : cmul(zz, p);
+                        SP::split(v.x, -v.y, h[q], l[q]);  // conjugated: the inverse runs on F_R
+                    }
+                    const int kel = 32 * half + 8 * c;  // K element of the chunk within the hi block
+                    *reinterpret_cast<uint4*>(Abuf + umma::sw128_offset(tid, kel)) = make_uint4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<uint4*>(Abuf + 16384 + umma::sw128_offset(tid, kel)) =
+                        make_uint4(l[0], l[1], l[2], l[3]);
+                }
+            }
+        }
+        umma::fence_smem_to_async();
+        umma::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            umma::fence_after_sync();
+            tc5_issue<PREC>(tmem + S::TM_R, tmem + S::TM_R + 64, sbase + S::OFF_A, 128, sbase + S::OFF_BRF, 64, 64,
+                            IDESC_R);
+            umma::mma_commit(&bar);
+        }
+        if (!stage_wait()) return false;
+        // (4) the accumulator holds conj(Y'') (row t = (item, k1), columns n2); conj(Y''') = conj(Y'') w^(k1 n2)
+        // is the left operand of the inverse, rows (item, n2), K = 2 k1 + q
+        {
+            const int item_local = tid / 16;
+            unsigned char* tile = Abuf + (item_local / 4) * 16384;
+            const int rowb = (item_local % 4) * 32;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {  // n2 = 16 half .. 16 half + 15
+                float y[32];
+                umma::tmem_ld32(tmem + lane_base + S::TM_R + 32 * half, y);
+                if constexpr (FP16) {
+                    float y2[32];
+                    umma::tmem_ld32(tmem + lane_base + S::TM_R + 64 + 32 * half, y2);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) y[i] = fmaf(y2[i], 1.f / 2048.f, y[i]);
+                }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int nn = 16 * half + i;
+                    const float2 v = cmul(make_float2(y[2 * i], y[2 * i + 1]), TWT[nn * 16 + k1R]);
+                    uint32_t h, l;
+                    SP::split(v.x, v.y, h, l);
+                    *reinterpret_cast<uint32_t*>(tile + umma::sw128_offset(rowb + nn, 2 * k1R)) = h;
+                    *reinterpret_cast<uint32_t*>(tile + umma::sw128_offset(rowb + nn, 32 + 2 * k1R)) = l;
+                }
+            }
+        }
+        umma::fence_smem_to_async();
+        umma::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            umma::fence_after_sync();
+#pragma unroll
+            for (int tau = 0; tau < 2; ++tau)
+                tc5_issue<PREC>(tmem + S::TM_L + tau * 64, tmem + S::TM_L + tau * 64 + 32,
+                                sbase + S::OFF_A + tau * 16384, 128, sbase + S::OFF_BLF, 32, 32, IDESC_L);
+            umma::mma_commit(&bar);
+        }
+        if (!stage_wait()) return false;
+        // (5) x'[R n1 + n2] = conj(accumulator) of both tiles back into the registers
+#pragma unroll
+        for (int tau = 0; tau < 2; ++tau) {
+            float x[32];
+            umma::tmem_ld32(tmem + lane_base + S::TM_L + tau * 64, x);
+            if constexpr (FP16) {
+                float x2[32];
+                umma::tmem_ld32(tmem + lane_base + S::TM_L + tau * 64 + 32, x2);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) x[i] = fmaf(x2[i], 1.f / 2048.f, x[i]);
+            }
+            const float up = FP16 ? ldexpf(1.f, ex[tau]) : 1.f;
+#pragma unroll
+            for (int n1 = 0; n1 < 16; ++n1) u[tau][n1] = make_float2(x[2 * n1] * up, -x[2 * n1 + 1] * up);
+        }
+        umma::fence_before_sync();
+        __syncthreads();  // every TMEM read is done before the next stage's MMAs overwrite it
+        return true;
+    };
+
+    auto mul_d = [&](int jz, bool conj) {
+#pragma unroll
+        for (int tau = 0; tau < 2; ++tau) {
+            const float2* drow = a.dss + ((size_t)iwL[tau] * nz + jz) * N;
+#pragma unroll
+            for (int n1 = 0; n1 < 16; ++n1) {
+                const float2 dd = __ldg(drow + R * n1 + n2);
+                u[tau][n1] = conj ? cmulc(u[tau][n1], dd) : cmul(u[tau][n1], dd);
+            }
+        }
+    };
+    auto srow = [&](int tau, int jz) -> float2* {
+        const int slot = shotL[tau] % a.ring;
+        return a.S + (((size_t)slot * a.nw + iwL[tau]) * nz + jz) * (size_t)N;
+    };
+
+    if constexpr (MODE == MODE_SOURCE) {
+#pragma unroll
+        for (int tau = 0; tau < 2; ++tau) {
+            const int xs = okL[tau] ? __ldg(a.src_ix + shotL[tau]) : -1;
+            const float2 w = okL[tau] ? __ldg(a.wavelet + iwL[tau]) : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int n1 = 0; n1 < 16; ++n1) u[tau][n1] = (R * n1 + n2 == xs) ? w : make_float2(0.f, 0.f);
+        }
+        for (int jz = 0; jz < nz; ++jz) {
+#pragma unroll
+            for (int tau = 0; tau < 2; ++tau)
+                if (okL[tau]) {
+                    float2* row = srow(tau, jz);
+#pragma unroll
+                    for (int n1 = 0; n1 < 16; ++n1) __stcs(row + R * n1 + n2, alive ? u[tau][n1] : make_float2(NAN, NAN));
+                }
+            if (jz + 1 < nz && alive) {
+                alive = transform_step(jz, false);
+                mul_d(jz, false);
+            }
+        }
+    } else if constexpr (MODE == MODE_ADJOINT) {
+        // receivers at every column (the tensor-core variants take no receiver list)
+#pragma unroll
+        for (int tau = 0; tau < 2; ++tau) {
+            const float2* drow = a.din + ((size_t)(shotL[tau] - shot0) * a.nw + iwL[tau]) * a.nrec;
+#pragma unroll
+            for (int n1 = 0; n1 < 16; ++n1)
+                u[tau][n1] = okL[tau] ? __ldcs(drow + R * n1 + n2) : make_float2(0.f, 0.f);
+        }
+        float* part = a.part + (size_t)blockIdx.x * nz * N;
+        for (int jz = 0; jz < nz; ++jz) {
+            float c[16];
+#pragma unroll
+            for (int n1 = 0; n1 < 16; ++n1) c[n1] = 0.f;
+#pragma unroll
+            for (int tau = 0; tau < 2; ++tau)
+                if (okL[tau]) {
+                    const float2* row = srow(tau, jz);
+#pragma unroll
+                    for (int n1 = 0; n1 < 16; ++n1) {
+                        const float2 s = __ldcs(row + R * n1 + n2);
+                        c[n1] += fmaf(s.x, u[tau][n1].x, s.y * u[tau][n1].y);
+                    }
+                }
+#pragma unroll
+            for (int n1 = 0; n1 < 16; ++n1) img[warp * N + R * n1 + n2] = alive ? c[n1] : NAN;
+            __syncthreads();
+            {
+                const float4* rows4 = reinterpret_cast<const float4*>(img);
+                float4* prow = reinterpret_cast<float4*>(part + (size_t)jz * N);
+                for (int x4 = tid; x4 < N / 4; x4 += blockDim.x) {
+                    float4 acc = rows4[x4];
+#pragma unroll
+                    for (int w2 = 1; w2 < 4; ++w2) {
+                        const float4 v4 = rows4[w2 * (N / 4) + x4];
+                        acc.x += v4.x; acc.y += v4.y; acc.z += v4.z; acc.w += v4.w;
+                    }
+                    prow[x4] = acc;
+                }
+            }
+            __syncthreads();  // the image rows are read before the next depth overwrites them
+            if (jz + 1 < nz && alive) {
+                mul_d(jz, true);
+                alive = transform_step(jz, true);
+            }
+        }
+    } else {  // MODE_FORWARD
+#pragma unroll
+        for (int tau = 0; tau < 2; ++tau)
+#pragma unroll
+            for (int n1 = 0; n1 < 16; ++n1) u[tau][n1] = make_float2(0.f, 0.f);
+        for (int jz = nz - 1; jz >= 0; --jz) {
+            if (jz + 1 < nz && alive) {
+                alive = transform_step(jz, false);
+                mul_d(jz, false);
+            }
+            const float* mrow = a.m + (size_t)jz * N;
+#pragma unroll
+            for (int tau = 0; tau < 2; ++tau)
+                if (okL[tau]) {
+                    const float2* row = srow(tau, jz);
+#pragma unroll
+                    for (int n1 = 0; n1 < 16; ++n1) {
+                        const float2 s = __ldcs(row + R * n1 + n2);
+                        const float mm = __ldg(mrow + R * n1 + n2);
+                        u[tau][n1].x = fmaf(s.x, mm, u[tau][n1].x);
+                        u[tau][n1].y = fmaf(s.y, mm, u[tau][n1].y);
+                    }
+                }
+        }
+#pragma unroll
+        for (int tau = 0; tau < 2; ++tau)
+            if (okL[tau]) {
+                float2* orow = a.dout + ((size_t)(shotL[tau] - shot0) * a.nw + iwL[tau]) * a.nrec;
+#pragma unroll
+                for (int n1 = 0; n1 < 16; ++n1) orow[R * n1 + n2] = alive ? u[tau][n1] : make_float2(NAN, NAN);
+            }
+    }
+
+    // ---- tear-down: a stage that ran out of time may still have MMAs in flight; wait for them
+    // (bounded) before the columns are freed, and record the failure
+    if (!alive) {
+        if (tid == 0 && a.dev_err) atomicExch(a.dev_err, 1);
+        umma::mbar_wait(&bar, phase);
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) umma::tmem_free(tmem, S::TM_COLS);
+}
+
+}  // namespace lsm

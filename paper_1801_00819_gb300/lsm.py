@@ -34,9 +34,11 @@ EXPORTED = ("lsm_workspace_bytes", "lsm_forward", "lsm_adjoint", "lsm_num_window
             "lsm_status_string", "lsm_kernel_launches", "lsm_profile_start", "lsm_profile_stop",
             "lsm_adjoint_static", "lsm_born_gradient", "rls_window_solve_ex", "rls_multi_line_solve",
             "lsm_forward_ex", "lsm_adjoint_ex", "lsm_profile_start_classes", "lsm_autotune",
-            "lsm_autotune_reset", "lsm_autotune_gradient")
+            "lsm_autotune_reset", "lsm_autotune_gradient", "lsm_measure_fp32_peak",
+            "lsm_check_bounded_wait", "rls_window_solve_sharded")
 
-TRANSFORMS = {"fft": 0, "dft_bf16x3": 1, "dft_fp16x3": 2, "dft_bf16x1": 3}
+TRANSFORMS = {"fft": 0, "dft_bf16x3": 1, "dft_fp16x3": 2, "dft_bf16x1": 3, "dft_fp16x3_tcgen05": 4,
+              "dft_bf16x3_tcgen05": 5}
 
 LSM_PRECOND_NONE = 0
 LSM_PRECOND_ILLUMINATION = 1
@@ -128,6 +130,10 @@ class lsm_ckpt_tune_report(ctypes.Structure):
                 ("default_ms", ctypes.c_double)]
 
 
+# int allreduce(void* ctx, void* buf, size_t count, int is_double, void* stream)
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                                ctypes.c_void_p)
+
 _lib_handle = None
 
 
@@ -174,6 +180,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                      ctypes.POINTER(lsm_window_stats), ctypes.c_int, P, ctypes.c_size_t, P]
     lib.rls_window_solve_ex.restype = ctypes.c_int
     lib.rls_window_solve_ex.argtypes = list(lib.rls_window_solve.argtypes) + [ctypes.POINTER(lsm_solve_options)]
+    lib.rls_window_solve_sharded.restype = ctypes.c_int
+    lib.rls_window_solve_sharded.argtypes = list(lib.rls_window_solve.argtypes) + [ALLREDUCE_FN, ctypes.c_void_p]
     lib.rls_multi_line_solve.restype = ctypes.c_int
     lib.rls_multi_line_solve.argtypes = [ctypes.POINTER(lsm_line), ctypes.c_int, ctypes.POINTER(lsm_solve_options)]
     lib.lsm_autotune.restype = ctypes.c_int
@@ -196,6 +204,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lsm_profile_start_classes.argtypes = [ctypes.c_uint]
     lib.lsm_profile_stop.restype = ctypes.c_int
     lib.lsm_profile_stop.argtypes = [ctypes.POINTER(lsm_profile)]
+    lib.lsm_check_bounded_wait.restype = ctypes.c_int
+    lib.lsm_check_bounded_wait.argtypes = [ctypes.c_void_p]
+    lib.lsm_measure_fp32_peak.restype = ctypes.c_int
+    lib.lsm_measure_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                          ctypes.c_void_p]
     _lib_handle = lib
     return lib
 
@@ -296,6 +309,21 @@ def lsm_profile_stop() -> dict:
             for i, name in enumerate(KERNEL_CLASSES)}
 
 
+def lsm_measure_fp32_peak(stream=None) -> dict:
+    """Measured FP32 FMA throughput of the current device in TFLOP/s: {"ffma": scalar FMA
+    instructions, "ffma2": paired FP32 FMA instructions} (see include/lsm.h)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().lsm_measure_fp32_peak(ctypes.byref(a), ctypes.byref(b), _stream(stream)),
+           "lsm_measure_fp32_peak")
+    return {"ffma": float(a.value), "ffma2": float(b.value)}
+
+
+def lsm_check_bounded_wait(stream=None) -> int:
+    """Run the bounded-wait self-check (see include/lsm.h); returns its status code, LSM_ERR_TIMEOUT
+    being the expected one."""
+    return int(load_library().lsm_check_bounded_wait(_stream(stream)))
+
+
 def lsm_num_windows(ns: int, K: int, slide: int) -> int:
     return int(load_library().lsm_num_windows(int(ns), int(K), int(slide)))
 
@@ -379,6 +407,40 @@ def rls_window_solve(grid, slowness, freqs, geom, d, lam, K, slide, cg_tol, max_
     out = [stats[i].as_dict() for i in range(max(0, last - first_window))]
     if st != LSM_OK and (st != LSM_ERR_BREAKDOWN or raise_on_breakdown):
         raise LsmError(st, "rls_window_solve")
+    return st, out
+
+
+def rls_window_solve_sharded(grid, slowness, freqs, geom, d, lam, K, slide, cg_tol, max_iter, m_inout, workspace,
+                             allreduce, first_window=0, n_windows=0, stream=None, raise_on_breakdown=True):
+    """This rank's share of a sliding-window solve sharded by frequency (see include/lsm.h): `freqs`
+    and `d` hold this rank's frequencies.  `allreduce(buf, count, is_double, stream)` must replace the
+    `count` float32 / float64 values at device address `buf` by their sum over the ranks, ordered on
+    the CUDA stream `stream` (integer handles).  Returns (status, [stats dicts])."""
+    lib = load_library()
+    nwin = lib.lsm_num_windows(int(geom.c.ns), int(K), int(slide))
+    cap = max(nwin, 1)
+    stats = (lsm_window_stats * cap)()
+    failures = []
+
+    def hook(_ctx, buf, count, is_double, st):
+        try:
+            allreduce(int(buf or 0), int(count), int(is_double), int(st or 0))
+            return 0
+        except Exception as exc:  # reported after the call; the library stops the solve
+            failures.append(exc)
+            return 1
+
+    cb = ALLREDUCE_FN(hook)
+    st = lib.rls_window_solve_sharded(ctypes.byref(grid.c), _ptr(slowness), ctypes.byref(freqs.c),
+                                      ctypes.byref(geom.c), _ptr(d), float(lam), int(K), int(slide), float(cg_tol),
+                                      int(max_iter), int(first_window), int(n_windows), _ptr(m_inout), stats, cap,
+                                      _ptr(workspace), _nbytes(workspace), _stream(stream), cb, None)
+    if failures:
+        raise RuntimeError("allreduce callback failed") from failures[0]
+    last = nwin if n_windows <= 0 else min(nwin, first_window + n_windows)
+    out = [stats[i].as_dict() for i in range(max(0, last - first_window))]
+    if st != LSM_OK and (st != LSM_ERR_BREAKDOWN or raise_on_breakdown):
+        raise LsmError(st, "rls_window_solve_sharded")
     return st, out
 
 

@@ -11,8 +11,10 @@ from .survey import (  # noqa: F401
     config_tiny,
     config_realistic,
     config_precision,
+    config_midsize,
     config_precision_subsample,
     config_batching_lines,
+    config_batching_lines_reduced,
     random_case,
     ricker_spectrum,
     linear_frequencies,

@@ -12,8 +12,11 @@ dataset is not available, so every workload here is synthetic and seeded.  The r
   5 % nonzeros drawn from N(0, 0.1) (seed 2) plus three dipping layers (dips 5-20 degrees,
   amplitudes 0.05-0.1); 96 shots; 128 frequencies 3-40 Hz; 2 % noise; window 16, slide 8.
 * precision (1024 x 512, 6 m): the realistic construction, 192 shots, 256 frequencies 3-60 Hz.
+* midsize (128 x 64, 8 m): the realistic construction, 16 shots, 32 frequencies 3-40 Hz,
+  window 8, slide 4, CG to 1e-3 (the tolerance-stopped solve the oracle can still run).
 * batching: eight lines with nx in {256, 384, 512, 640, 768, 896, 1024, 1024}, nz = nx / 2,
-  shots U{64..200}, frequencies U{96..192}, window U{4..32}, slide = ceil(window / 2) (seed 3).
+  shots U{64..200}, frequencies U{96..192}, window U{4..32}, slide = ceil(window / 2) (seed 3);
+  the reduced form keeps each line's first three windows of shots and every other frequency.
 
 Shots sit at grid columns floor((i + 1/2) nx / ns); receivers at every grid column.  The
 frequency axis is linear with both ends included.  The wavelet is the zero-phase spectrum of a
@@ -204,6 +207,13 @@ def config_precision() -> Survey:
     return _realistic_like("precision", 1024, 512, 6.0, 6.0, 192, 3.0, 60.0, 256, 16, 8)
 
 
+def config_midsize() -> Survey:
+    """The realistic construction at 128 x 64 (8 m), 16 shots, 32 frequencies 3-40 Hz, window 8,
+    slide 4, CG to 1e-3: small enough for the FP64 oracle to run the whole tolerance-stopped
+    sliding solve (three windows of a few dozen iterations each)."""
+    return _realistic_like("midsize", 128, 64, 8.0, 8.0, 16, 3.0, 40.0, 32, 8, 4)
+
+
 def config_precision_subsample(nx: int = 128) -> Survey:
     """The precision workload's construction (6 m grid, 3-60 Hz) subsampled to nx x 64, 6 shots,
     10 frequencies: small enough for the FP64 oracle, used to compare the transform precisions."""
@@ -221,6 +231,22 @@ def config_batching_lines():
         slide = (window + 1) // 2
         out.append(_realistic_like(f"line{i}", nx, nx // 2, 8.0, 8.0, ns, 3.0, 40.0, nw, window,
                                    slide, seed_v=10 + i, seed_m=20 + i, noise_seed=30 + i))
+    return out
+
+
+def config_batching_lines_reduced(max_windows: int = 3, freq_stride: int = 2):
+    """The batching workload cut down for a bounded benchmark: the same eight lines (widths, nz,
+    window K, slide, velocity, reflectivity and noise seeds), each keeping only the shots of its
+    first `max_windows` windows and every `freq_stride`-th frequency of its axis."""
+    out = []
+    for sv in config_batching_lines():
+        keep = min(sv.ns, sv.window + (max_windows - 1) * sv.slide)
+        sv.src_ix = centred_shots(sv.nx, keep)
+        sv.rec_ix = full_spread_receivers(sv.nx, keep)
+        sv.freqs = sv.freqs[::freq_stride].copy()
+        sv.wavelet = ricker_spectrum(sv.freqs)
+        sv.name = sv.name + "-reduced"
+        out.append(sv)
     return out
 
 

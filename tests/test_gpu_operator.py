@@ -225,3 +225,41 @@ def test_largest_workload_full_size_sampled_items(torch_cuda):
     lhs = O.real_dot(got, dd.astype(np.complex128))
     rhs = O.real_dot(m, _gpu_adjoint(torch_cuda, ds, dd, shot0, K))
     assert abs(lhs - rhs) <= 1e-4 * abs(lhs)
+
+
+BATCHING_LINES = list(range(8))
+
+
+@pytest.mark.parametrize("line", BATCHING_LINES, ids=lambda i: f"line{i}")
+def test_batching_line_full_size_sampled_items(torch_cuda, line):
+    """Every line of the eight-line batching workload (nx 256 ... 1024 including the mixed-radix
+    384, 640, 768 and 896, nz = nx/2) at its full size: one window of the line's K shots and all
+    its frequencies, in the launch configuration its solve uses.  A is compared with the oracle on
+    sampled (shot, frequency) rows, A^T on data that is zero except at sampled items, and the
+    dot-product property is checked on the whole window."""
+    from synth import config_batching_lines
+    sv = config_batching_lines()[line]
+    ds = device_survey(sv)
+    K = sv.window
+    shot0 = sv.slide  # the second window
+    m = np.asarray(sv.reflectivity, dtype=np.float32).astype(np.float64)
+    got = _gpu_forward(torch_cuda, ds, m, shot0, K)
+    samples = [(0, 0), (K // 2, sv.nw // 2), (K - 1, sv.nw - 1)]
+    op = oracle_operator(sv)
+    for ishot, iw in samples:
+        ref = op.with_freqs([iw]).forward(m, shots=[shot0 + ishot])[0, 0]
+        assert rel_l2(got[ishot, iw], ref) <= TOL, (ishot, iw)
+    rng = np.random.default_rng(40 + line)
+    d = np.zeros((K, sv.nw, sv.nx), dtype=np.complex64)
+    ref = np.zeros((sv.nz, sv.nx))
+    for ishot, iw in samples[1:]:
+        row = (rng.normal(size=sv.nx) + 1j * rng.normal(size=sv.nx)).astype(np.complex64)
+        d[ishot, iw] = row
+        ref += op.with_freqs([iw]).adjoint(row[None, None, :].astype(np.complex128), shots=[shot0 + ishot])
+    img = _gpu_adjoint(torch_cuda, ds, d, shot0, K)
+    assert rel_l2(img, ref) <= TOL
+    dd = (rng.normal(size=(K, sv.nw, sv.nx)) + 1j * rng.normal(size=(K, sv.nw, sv.nx))).astype(np.complex64)
+    lhs = O.real_dot(got, dd.astype(np.complex128))
+    rhs = O.real_dot(m, _gpu_adjoint(torch_cuda, ds, dd, shot0, K))
+    assert abs(lhs - rhs) <= 1e-4 * abs(lhs)
+    torch_cuda.cuda.empty_cache()

@@ -4,8 +4,7 @@ on the realistic 512 x 256 synthetic survey that stands in for Marmousi.
 
 The paper reports no numbers, only that LSM and BR-RLS honour the data and recover the reflectivity
 better than the adjoint, and that BR-RLS is comparable to LSM.  This test measures model error and
-data misfit for the three images and checks those qualitative claims; the numbers are printed and
-recorded in DESIGN.md.
+data misfit for the three images and checks those qualitative claims; the numbers are printed.
 """
 
 import json

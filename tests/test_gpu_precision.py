@@ -5,7 +5,7 @@ precision workload's construction (6 m grid, layered velocity with anomalies, 3-
 The relative L2 error of A and A^T is measured for every precision and checked against a bound per
 precision: FP32 FFT 1e-4 (the float32 bar), split FP16 x3 1e-4, split BF16 x3 1e-3, plain BF16 0.2
 (one 8-bit-mantissa product per transform, two transforms per depth step, 64 depth steps).
-The measured errors are printed and recorded in the design doc.
+The measured errors are printed as JSON, one line per width.
 """
 
 import json
