@@ -281,8 +281,8 @@ static SweepShape tc5_shape(int nx, int nshots, int nw) {
     SweepShape s;
     s.warps = 4;
     s.blocks = (nshots * nw + 7) / 8;
-    s.wslots = 0;
-    s.smem = nx_ops(nx)->tc5_smem;
+    s.wslots = std::min(nw, (8 + nshots - 1) / nshots + 1);  // frequencies a CTA's 8 items can span
+    s.smem = nx_ops(nx)->tc5_smem(s.wslots);
     return s;
 }
 
@@ -532,6 +532,7 @@ cudaError_t launch_any(int mode, int transform, SweepArgs& a, int n, int num_sms
         return launch_sweep(mode, a, sh, st);
     }
     const SweepShape sh = tc_shape(a.nx, mode, n, a.nw, num_sms, transform);
+    a.wslots = sh.wslots;
     if (blocks) *blocks = sh.blocks;
     return nx_ops(a.nx)->tc_sweep(mode, transform, a, sh, st);
 }
@@ -808,10 +809,8 @@ int lsm_born_gradient(const lsm_grid* grid, const float* slowness, const double*
 static cudaError_t time_shape(int mode, int transform, SweepArgs a, const SweepShape& sh, cudaStream_t st,
                               cudaEvent_t e0, cudaEvent_t e1, int reps, double* ms) {
     auto launch = [&]() -> cudaError_t {
-        if (transform == 0) {
-            a.wslots = sh.wslots;
-            return launch_sweep(mode, a, sh, st);
-        }
+        a.wslots = sh.wslots;
+        if (transform == 0) return launch_sweep(mode, a, sh, st);
         return nx_ops(a.nx)->tc_sweep(mode, transform, a, sh, st);
     };
     cudaError_t e = launch();

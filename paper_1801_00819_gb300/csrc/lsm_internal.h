@@ -114,7 +114,7 @@ struct NxOps {
     size_t (*tc_smem)(int mode, int warps);
     size_t (*gradient_smem)(int warps, int wslots);
     bool has_tc5;                 // tcgen05 transform variants exist for this nx
-    size_t tc5_smem;              // their dynamic shared memory per CTA
+    size_t (*tc5_smem)(int wslots);  // their dynamic shared memory per CTA
 };
 // The operations for nx, or nullptr when nx is not supported.
 const NxOps* nx_ops(int nx);

@@ -600,12 +600,16 @@ struct Dispatch {
     static cudaError_t tc5_launch(const SweepArgs& a, const SweepShape& sh, cudaStream_t st) {
         if constexpr (kTc5) {
             static DeviceOnce configured;
+            // the kernel also holds a few bytes of static shared memory (its mbarrier and TMEM address),
+            // so the dynamic limit stays below the 227 KB a block can have
+            constexpr int kMaxDyn = 200 * 1024;
             cudaError_t e = configured.run([] {
                 return cudaFuncSetAttribute(tc5_sweep_kernel<N, PREC, MODE>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc5_smem_bytes<N>());
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn);
             });
             if (e != cudaSuccess) return e;
-            if (sh.smem != tc5_smem_bytes<N>() || sh.warps != 4) return cudaErrorInvalidValue;
+            if (sh.smem != tc5_smem_bytes<N>(a.wslots) || sh.smem > (size_t)kMaxDyn || sh.warps != 4)
+                return cudaErrorInvalidValue;
             ProfScope prof_(MODE == MODE_SOURCE ? KC_SOURCE : MODE == MODE_ADJOINT ? KC_ADJOINT : KC_FORWARD, st);
             tc5_sweep_kernel<N, PREC, MODE><<<sh.blocks, 128, sh.smem, st>>>(a);
             count_launch();
@@ -633,6 +637,11 @@ struct Dispatch {
             case PREC_BF16X3_TC5: return tc5_mode<PREC_BF16X3_TC5>(mode, a, sh, st);
             default: return cudaErrorInvalidValue;
         }
+    }
+
+    static size_t tc5_smem(int wslots) {
+        if constexpr (kTc5) return tc5_smem_bytes<N>(wslots);
+        else return 0;
     }
 
     static size_t tc_smem(int mode, int warps) {
@@ -730,5 +739,5 @@ struct Dispatch {
                                       max_warps_##NN, smem_##NN, tables_grad_##NN, gradient_##NN,  \
                                       gradient_max_warps_##NN, Dispatch<NN>::kTc, tables_natural_##NN, \
                                       tc_sweep_##NN, tc_smem_##NN, gradient_smem_##NN,            \
-                                      Dispatch<NN>::kTc5, Dispatch<NN>::kTc5 ? tc5_smem_bytes<512>() : 0}; \
+                                      Dispatch<NN>::kTc5, Dispatch<NN>::tc5_smem};                 \
     }

@@ -35,6 +35,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "lsm_async.cuh"
 #include "lsm_fft.cuh"
 #include "lsm_internal.h"
 #include "lsm_tc.cuh"
@@ -52,17 +53,20 @@ struct Tc5Shape {
     static constexpr int ITEMS = 8;           // items per CTA
     static constexpr int THREADS = 128;
     // shared memory (bytes from the 1024-aligned base): the constant B operands of the left product
-    // (32 rows x 64 K = 4 KB) and of the right product (64 rows x 128 K = 16 KB), the A operand (two 128-row K blocks: the two left tiles, or the hi and lo halves of the
-    // right tile), the twiddles in both index orders and the adjoint's per-warp image rows
+    // (32 rows x 64 K = 4 KB) and of the right product (64 rows x 128 K = 16 KB), the A operand
+    // (two 128-row K blocks: the two left tiles, or the hi and lo halves of the right tile; the
+    // adjoint's per-warp image rows use it between depth steps), the twiddles in both index orders,
+    // then the staged phase-shift and split-step rows of the CTA's frequencies: per frequency slot one
+    // 4 KB Phi row and one 4 KB D row
     static constexpr int A_BYTES = 2 * 128 * 128;
     static constexpr int OFF_BLF = 0;
     static constexpr int OFF_BRF = OFF_BLF + 32 * 128;
     static constexpr int OFF_A = OFF_BRF + 2 * 64 * 128;
     static constexpr int OFF_TW = OFF_A + A_BYTES;             // w^(k1 n2) as [k1][n2] float2
     static constexpr int OFF_TWT = OFF_TW + 16 * R * 8;        // the same as [n2][k1]
-    static constexpr int OFF_IMG = OFF_TWT + 16 * R * 8;       // adjoint: [4 warps][N] float
-    static constexpr int BYTES = OFF_IMG + 4 * N * 4;
-    static constexpr size_t SMEM = (size_t)BYTES + 1024;       // + alignment slack
+    static constexpr int OFF_STG = OFF_TWT + 16 * R * 8;       // [wslots][Phi row, D row]
+    static constexpr int SLOT_BYTES = 2 * N * 8;
+    static_assert(OFF_A % 1024 == 0, "operand tiles are 1024-byte aligned");
     // TMEM columns: left accumulators [tile][acc][32], right accumulators [acc][64]
     static constexpr uint32_t TM_L = 0;
     static constexpr uint32_t TM_R = 128;
@@ -74,16 +78,19 @@ struct Tc5Split {
     static constexpr bool FP16 = PREC == PREC_FP16X3_TC5;
     // packed 16-bit pair (lo half = first value) of hi parts and of lo parts of (x0, x1)
     static __device__ __forceinline__ void split(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+        const float2 x = make_float2(x0, x1);
         if constexpr (FP16) {
             const __half2 h = __floats2half2_rn(x0, x1);
             const float2 hf = __half22float2(h);
-            const __half2 l = __floats2half2_rn((x0 - hf.x) * 2048.f, (x1 - hf.y) * 2048.f);
+            // (x - hi) 2^11 as one paired multiply and one paired fused multiply-add
+            const float2 r = __ffma2_rn(hf, make_float2(-2048.f, -2048.f), __fmul2_rn(x, make_float2(2048.f, 2048.f)));
+            const __half2 l = __floats2half2_rn(r.x, r.y);
             hi = *reinterpret_cast<const uint32_t*>(&h);
             lo = *reinterpret_cast<const uint32_t*>(&l);
         } else {
             const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
-            const float2 hf = __bfloat1622float2(h);
-            const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+            const float2 r = __ffma2_rn(__bfloat1622float2(h), make_float2(-1.f, -1.f), x);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(r.x, r.y);
             hi = *reinterpret_cast<const uint32_t*>(&h);
             lo = *reinterpret_cast<const uint32_t*>(&l);
         }
@@ -158,7 +165,22 @@ __device__ __forceinline__ void tc5_issue(uint32_t d0, uint32_t d1, uint32_t a_b
 }
 
 template <int N>
-constexpr size_t tc5_smem_bytes() { return Tc5Shape<N>::SMEM; }
+constexpr size_t tc5_smem_bytes(int wslots) {
+    return (size_t)Tc5Shape<N>::OFF_STG + (size_t)wslots * Tc5Shape<N>::SLOT_BYTES + 1024;
+}
+
+// acc0 + 2^-11 acc1 over 32 columns (FP16's two accumulators), as paired FMAs
+__device__ __forceinline__ void tc5_combine(float (&y)[32], const float (&y2)[32]) {
+#pragma unroll
+    for (int i = 0; i < 32; i += 2) {
+        const float2 v = __ffma2_rn(make_float2(y2[i], y2[i + 1]), make_float2(1.f / 2048.f, 1.f / 2048.f),
+                                    make_float2(y[i], y[i + 1]));
+        y[i] = v.x;
+        y[i + 1] = v.y;
+    }
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p)); }
 
 template <int N, int PREC, int MODE>
 __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
@@ -173,13 +195,18 @@ __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
     const uint32_t sbase = umma::smem_u32(base);
     float2* TW = reinterpret_cast<float2*>(base + S::OFF_TW);    // [k1][n2]
     float2* TWT = reinterpret_cast<float2*>(base + S::OFF_TWT);  // [n2][k1]
-    float* img = reinterpret_cast<float*>(base + S::OFF_IMG);    // [4][N]
+    unsigned char* stg = base + S::OFF_STG;
     unsigned char* Abuf = base + S::OFF_A;
+    float* img = reinterpret_cast<float*>(Abuf);                 // [4][N], between depth steps only
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nitems = a.nshots * a.nw;
     const int shot0 = a.shot0_dev ? __ldg(a.shot0_dev) : a.shot0;
     const int nz = a.nz;
+    // frequencies of the CTA's items (frequency-major item order): slots w_first .. w_last
+    const int w_first = min((int)blockIdx.x * S::ITEMS, nitems - 1) / a.nshots;
+    const int w_last = (min(((int)blockIdx.x + 1) * S::ITEMS, nitems) - 1) / a.nshots;
+    const int nslots = w_last - w_first + 1;  // <= a.wslots
 
     // ---- set-up: constants, barrier, TMEM
     tc5_build_dft<PREC>(base + S::OFF_BLF, 16, -1, 32);
@@ -209,17 +236,49 @@ __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
     for (int tau = 0; tau < 2; ++tau) {
         itemL[tau] = blockIdx.x * S::ITEMS + 4 * tau + warp;
         okL[tau] = itemL[tau] < nitems;
-        iwL[tau] = okL[tau] ? itemL[tau] / a.nshots : 0;
+        iwL[tau] = okL[tau] ? itemL[tau] / a.nshots : w_first;
         shotL[tau] = okL[tau] ? shot0 + (itemL[tau] - iwL[tau] * a.nshots) : shot0;
     }
     // item of this thread in the right-product layout: row t = 16 item + k1
     const int itemR = blockIdx.x * S::ITEMS + tid / 16;
     const int k1R = tid % 16;
-    const int iwR = itemR < nitems ? itemR / a.nshots : 0;
+    const int iwR = itemR < nitems ? itemR / a.nshots : w_first;
     const int n2 = lane;
 
     // the wavefield: u[tau][n1] = x[R n1 + n2] of item 4 tau + warp
     float2 u[2][16];
+
+    // staging of the Phi (which = 0) or D (which = 1) rows of depth `row` for the CTA's frequencies,
+    // one cp.async group
+    auto stage_rows = [&](int row, int which) {
+        constexpr int CH = N * 8 / 16;  // 16-byte chunks per row
+        for (int c = tid; c < nslots * CH; c += blockDim.x) {
+            const int sl = c / CH, ch = c - sl * CH;
+            const float2* src = (which ? a.dss : a.phi) + ((size_t)(w_first + sl) * nz + row) * N + 2 * ch;
+            cp_async16(stg + sl * S::SLOT_BYTES + which * (N * 8) + ch * 16, src);
+        }
+        cp_async_commit();
+    };
+    auto phi_s = [&](int iw) { return reinterpret_cast<const float2*>(stg + (iw - w_first) * S::SLOT_BYTES); };
+    auto dss_s = [&](int iw) {
+        return reinterpret_cast<const float2*>(stg + (iw - w_first) * S::SLOT_BYTES + N * 8);
+    };
+    auto srow = [&](int tau, int jz) -> float2* {
+        const int slot = shotL[tau] % a.ring;
+        return a.S + (((size_t)slot * a.nw + iwL[tau]) * nz + jz) * (size_t)N;
+    };
+    // the source-wavefield rows of depth jz of all eight items into L2 (two 128-byte lines a thread)
+    auto prefetch_srows = [&](int jz) {
+        const int item = blockIdx.x * S::ITEMS + tid / 16;
+        if (item < nitems && jz >= 0 && jz < nz) {
+            const int iw = item / a.nshots;
+            const int slot = (shot0 + item - iw * a.nshots) % a.ring;
+            const unsigned char* row =
+                reinterpret_cast<const unsigned char*>(a.S + (((size_t)slot * a.nw + iw) * nz + jz) * (size_t)N);
+            prefetch_l2(row + (tid % 16) * 256);
+            prefetch_l2(row + (tid % 16) * 256 + 128);
+        }
+    };
 
     // wait for the MMAs of a stage; every thread agrees on the outcome
     // (the phase advances only when every thread saw it complete, so that after a failure every
@@ -234,8 +293,11 @@ __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
     constexpr uint32_t IDESC_L = umma::idesc_f16(!FP16, 128, 32);
     constexpr uint32_t IDESC_R = umma::idesc_f16(!FP16, 128, 64);
 
-    // one depth step on u: F^-1 (phi . F u) (conj(phi) when CONJ); phi rows of depth jz
-    auto transform_step = [&](int jz, bool conj_phi) -> bool {
+    // One depth step on u: F^-1 (phi . F u) (conj(phi) when conj_phi) with the staged Phi row of this
+    // step.  Staging: the D row d_row (>= 0) is requested after the first barrier and the Phi row
+    // phi_next (>= 0) of the next step once this step's Phi row has been read; every staged row has
+    // landed and is visible to all threads when the step returns.
+    auto transform_step = [&](bool conj_phi, int d_row, int phi_next) -> bool {
         // FP16: per-item power-of-two scale (the item is this warp's 32 lanes in each tile)
         int ex[2] = {0, 0};
         if constexpr (FP16) {
@@ -250,7 +312,7 @@ __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
                 ex[tau] = max(-100, min(ex[tau], 100));
                 const float down = ldexpf(1.f, -ex[tau]);
 #pragma unroll
-                for (int n1 = 0; n1 < 16; ++n1) u[tau][n1] = make_float2(u[tau][n1].x * down, u[tau][n1].y * down);
+                for (int n1 = 0; n1 < 16; ++n1) u[tau][n1] = __fmul2_rn(u[tau][n1], make_float2(down, down));
             }
         }
         // (1) left operand tiles: row t, K = [hi: (re, im) of n1 = 0..15 | lo: same]
@@ -263,7 +325,8 @@ __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) SP::split(u[tau][4 * c + q].x, u[tau][4 * c + q].y, h[q], l[q]);
                 *reinterpret_cast<uint4*>(tile + umma::sw128_offset(tid, 8 * c)) = make_uint4(h[0], h[1], h[2], h[3]);
-                *reinterpret_cast<uint4*>(tile + umma::sw128_offset(tid, 32 + 8 * c)) = make_uint4(l[0], l[1], l[2], l[3]);
+                *reinterpret_cast<uint4*>(tile + umma::sw128_offset(tid, 32 + 8 * c)) =
+                    make_uint4(l[0], l[1], l[2], l[3]);
             }
         }
         umma::fence_smem_to_async();
@@ -277,6 +340,7 @@ __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
                                 sbase + S::OFF_A + tau * 16384, 128, sbase + S::OFF_BLF, 32, 32, IDESC_L);
             umma::mma_commit(&bar);
         }
+        if (d_row >= 0) stage_rows(d_row, 1);
         if (!stage_wait()) return false;
         // (2) Y[k1][n2] of both tiles -> twiddle -> right operand rows (item, k1), K = 2 n2 + q
 #pragma unroll
@@ -286,8 +350,7 @@ __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
             if constexpr (FP16) {
                 float y2[32];
                 umma::tmem_ld32(tmem + lane_base + S::TM_L + tau * 64 + 32, y2);
-#pragma unroll
-                for (int i = 0; i < 32; ++i) y[i] = fmaf(y2[i], 1.f / 2048.f, y[i]);
+                tc5_combine(y, y2);
             }
             const int row0 = (4 * tau + warp) * 16;
 #pragma unroll
@@ -299,6 +362,7 @@ __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
                 *reinterpret_cast<uint32_t*>(Abuf + 16384 + umma::sw128_offset(row0 + k1, 2 * n2)) = l;
             }
         }
+        cp_async_wait_all();  // this step's Phi row (requested a step earlier) has landed
         umma::fence_smem_to_async();
         umma::fence_before_sync();
         __syncthreads();
@@ -309,9 +373,9 @@ __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
             umma::mma_commit(&bar);
         }
         if (!stage_wait()) return false;
-        // (3) Z[k1][k2] (row t) -> phase shift -> right operand of the inverse, same rows
+        // (3) Z[k1][k2] (row t) -> phase shift -> right operand of the inverse (conjugated), same rows
         {
-            const float2* prow = a.phi + ((size_t)iwR * nz + jz) * N;
+            const float2* prow = phi_s(iwR);
 #pragma unroll
             for (int half = 0; half < 2; ++half) {  // k2 = 16 half .. 16 half + 15
                 float z[32];
@@ -319,8 +383,7 @@ __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
                 if constexpr (FP16) {
                     float z2[32];
                     umma::tmem_ld32(tmem + lane_base + S::TM_R + 64 + 32 * half, z2);
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) z[i] = fmaf(z2[i], 1.f / 2048.f, z[i]);
+                    tc5_combine(z, z2);
                 }
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {  // chunk: k2 = 16 half + 4 c .. + 3
@@ -328,7 +391,7 @@ __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int k2l = 4 * c + q;
-                        const float2 p = __ldg(prow + k1R + 16 * (16 * half + k2l));
+                        const float2 p = prow[k1R + 16 * (16 * half + k2l)];
                         const float2 zz = make_float2(z[2 * k2l], z[2 * k2l + 1]);
                         const float2 v = conj_phi ? cmulc(zz, p) : cmul(zz, p);
                         SP::split(v.x, -v.y, h[q], l[q]);  // conjugated: the inverse runs on F_R
@@ -349,9 +412,10 @@ __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
                             IDESC_R);
             umma::mma_commit(&bar);
         }
+        if (phi_next >= 0) stage_rows(phi_next, 0);  // this step's Phi row has been read
         if (!stage_wait()) return false;
-        // (4) the accumulator holds conj(Y'') (row t = (item, k1), columns n2); conj(Y''') = conj(Y'') w^(k1 n2)
-        // is the left operand of the inverse, rows (item, n2), K = 2 k1 + q
+        // (4) the accumulator holds conj(Y2) for Y2 = Z conj(F_R) (row t = (item, k1), columns n2); the
+        // inverse left product takes conj(Y2 w^-(k1 n2)) = conj(Y2) w^(k1 n2), rows (item, n2), K = 2 k1 + q
         {
             const int item_local = tid / 16;
             unsigned char* tile = Abuf + (item_local / 4) * 16384;
@@ -363,8 +427,7 @@ __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
                 if constexpr (FP16) {
                     float y2[32];
                     umma::tmem_ld32(tmem + lane_base + S::TM_R + 64 + 32 * half, y2);
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) y[i] = fmaf(y2[i], 1.f / 2048.f, y[i]);
+                    tc5_combine(y, y2);
                 }
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
@@ -397,35 +460,32 @@ __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
             if constexpr (FP16) {
                 float x2[32];
                 umma::tmem_ld32(tmem + lane_base + S::TM_L + tau * 64 + 32, x2);
-#pragma unroll
-                for (int i = 0; i < 32; ++i) x[i] = fmaf(x2[i], 1.f / 2048.f, x[i]);
+                tc5_combine(x, x2);
             }
             const float up = FP16 ? ldexpf(1.f, ex[tau]) : 1.f;
 #pragma unroll
             for (int n1 = 0; n1 < 16; ++n1) u[tau][n1] = make_float2(x[2 * n1] * up, -x[2 * n1 + 1] * up);
         }
+        cp_async_wait_all();  // the rows staged during this step have landed
         umma::fence_before_sync();
-        __syncthreads();  // every TMEM read is done before the next stage's MMAs overwrite it
+        __syncthreads();  // TMEM reads done before the next MMAs; staged rows visible to every thread
         return true;
     };
 
-    auto mul_d = [&](int jz, bool conj) {
+    auto mul_d = [&](bool conj) {
 #pragma unroll
         for (int tau = 0; tau < 2; ++tau) {
-            const float2* drow = a.dss + ((size_t)iwL[tau] * nz + jz) * N;
+            const float2* drow = dss_s(iwL[tau]);
 #pragma unroll
             for (int n1 = 0; n1 < 16; ++n1) {
-                const float2 dd = __ldg(drow + R * n1 + n2);
+                const float2 dd = drow[R * n1 + n2];
                 u[tau][n1] = conj ? cmulc(u[tau][n1], dd) : cmul(u[tau][n1], dd);
             }
         }
     };
-    auto srow = [&](int tau, int jz) -> float2* {
-        const int slot = shotL[tau] % a.ring;
-        return a.S + (((size_t)slot * a.nw + iwL[tau]) * nz + jz) * (size_t)N;
-    };
 
     if constexpr (MODE == MODE_SOURCE) {
+        // step j (0 .. nz-2) propagates S_j to S_{j+1} with the rows of depth j
 #pragma unroll
         for (int tau = 0; tau < 2; ++tau) {
             const int xs = okL[tau] ? __ldg(a.src_ix + shotL[tau]) : -1;
@@ -433,28 +493,38 @@ __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
 #pragma unroll
             for (int n1 = 0; n1 < 16; ++n1) u[tau][n1] = (R * n1 + n2 == xs) ? w : make_float2(0.f, 0.f);
         }
+        if (nz > 1) stage_rows(0, 0);
+        cp_async_wait_all();
+        __syncthreads();
         for (int jz = 0; jz < nz; ++jz) {
 #pragma unroll
             for (int tau = 0; tau < 2; ++tau)
                 if (okL[tau]) {
                     float2* row = srow(tau, jz);
 #pragma unroll
-                    for (int n1 = 0; n1 < 16; ++n1) __stcs(row + R * n1 + n2, alive ? u[tau][n1] : make_float2(NAN, NAN));
+                    for (int n1 = 0; n1 < 16; ++n1)
+                        __stcs(row + R * n1 + n2, alive ? u[tau][n1] : make_float2(NAN, NAN));
                 }
             if (jz + 1 < nz && alive) {
-                alive = transform_step(jz, false);
-                mul_d(jz, false);
+                alive = transform_step(false, jz, jz + 2 < nz ? jz + 1 : -1);
+                mul_d(false);
             }
         }
     } else if constexpr (MODE == MODE_ADJOINT) {
-        // receivers at every column (the tensor-core variants take no receiver list)
+        // step j (0 .. nz-2): image term of depth j, then R_{j+1} = P_j^H R_j with the rows of depth j
+        // (receivers at every column: the tensor-core variants take no receiver list)
 #pragma unroll
         for (int tau = 0; tau < 2; ++tau) {
             const float2* drow = a.din + ((size_t)(shotL[tau] - shot0) * a.nw + iwL[tau]) * a.nrec;
 #pragma unroll
-            for (int n1 = 0; n1 < 16; ++n1)
-                u[tau][n1] = okL[tau] ? __ldcs(drow + R * n1 + n2) : make_float2(0.f, 0.f);
+            for (int n1 = 0; n1 < 16; ++n1) u[tau][n1] = okL[tau] ? __ldcs(drow + R * n1 + n2) : make_float2(0.f, 0.f);
         }
+        if (nz > 1) {
+            stage_rows(0, 0);
+            stage_rows(0, 1);
+        }
+        cp_async_wait_all();
+        __syncthreads();
         float* part = a.part + (size_t)blockIdx.x * nz * N;
         for (int jz = 0; jz < nz; ++jz) {
             float c[16];
@@ -470,6 +540,7 @@ __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
                         c[n1] += fmaf(s.x, u[tau][n1].x, s.y * u[tau][n1].y);
                     }
                 }
+            prefetch_srows(jz + 1);
 #pragma unroll
             for (int n1 = 0; n1 < 16; ++n1) img[warp * N + R * n1 + n2] = alive ? c[n1] : NAN;
             __syncthreads();
@@ -481,26 +552,35 @@ __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
 #pragma unroll
                     for (int w2 = 1; w2 < 4; ++w2) {
                         const float4 v4 = rows4[w2 * (N / 4) + x4];
-                        acc.x += v4.x; acc.y += v4.y; acc.z += v4.z; acc.w += v4.w;
+                        acc.x += v4.x;
+                        acc.y += v4.y;
+                        acc.z += v4.z;
+                        acc.w += v4.w;
                     }
                     prow[x4] = acc;
                 }
             }
-            __syncthreads();  // the image rows are read before the next depth overwrites them
+            __syncthreads();  // the image rows (in the operand buffer) are read before it is rewritten
             if (jz + 1 < nz && alive) {
-                mul_d(jz, true);
-                alive = transform_step(jz, true);
+                mul_d(true);
+                // the next step's D row is requested once this one has been applied
+                alive = transform_step(true, jz + 2 < nz ? jz + 1 : -1, jz + 2 < nz ? jz + 1 : -1);
             }
         }
     } else {  // MODE_FORWARD
+        // U_j = P_j U_{j+1} + S_j m_j from the deepest row up; step k = nz-2-j uses the rows of depth j
 #pragma unroll
         for (int tau = 0; tau < 2; ++tau)
 #pragma unroll
             for (int n1 = 0; n1 < 16; ++n1) u[tau][n1] = make_float2(0.f, 0.f);
+        if (nz > 1) stage_rows(nz - 2, 0);
+        cp_async_wait_all();
+        __syncthreads();
         for (int jz = nz - 1; jz >= 0; --jz) {
+            prefetch_srows(jz);
             if (jz + 1 < nz && alive) {
-                alive = transform_step(jz, false);
-                mul_d(jz, false);
+                alive = transform_step(false, jz, jz >= 1 ? jz - 1 : -1);
+                mul_d(false);
             }
             const float* mrow = a.m + (size_t)jz * N;
 #pragma unroll
@@ -527,6 +607,7 @@ __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
 
     // ---- tear-down: a stage that ran out of time may still have MMAs in flight; wait for them
     // (bounded) before the columns are freed, and record the failure
+    cp_async_wait_all();
     if (!alive) {
         if (tid == 0 && a.dev_err) atomicExch(a.dev_err, 1);
         umma::mbar_wait(&bar, phase);

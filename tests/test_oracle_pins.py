@@ -344,6 +344,21 @@ def test_warm_start_reduces_iterations_on_tiny_config():
     assert warm_its < cold_its
 
 
+def test_reference_slowness_is_least_squares_constant_of_each_row():
+    """The split-step reference slowness of depth row j is the constant that fits that row of the
+    slowness best in least squares (library lstsq on a column of ones): the phase screen
+    D_j = exp(i w (s - s_ref) dz) then has zero mean phase across x, which the operator's
+    coefficient rows show directly."""
+    sv = random_case(48, 10, 2, 3, seed=17)
+    op = _op(sv)
+    ones = np.ones((sv.nx, 1))
+    for j in range(sv.nz):
+        fit = np.linalg.lstsq(ones, op.s[j], rcond=None)[0][0]
+        assert abs(op.sref[j] - fit) <= 1e-15 * abs(fit)
+        _, dj = op.coefficients(j)
+        assert np.all(np.abs(np.angle(dj).sum(axis=1)) <= 1e-9)
+
+
 # ---------------------------------------------------------------- planted mistakes
 
 
@@ -384,6 +399,12 @@ def test_planted_transposed_image_index_fails_shift_pin(monkeypatch):
     monkeypatch.setattr(O.SplitStepOperator, "forward", bad)
     op, d = _tiny_problem(seed=1)
     assert _dot_test_error(op) > 1e-6
+
+
+def test_planted_minimum_reference_slowness_fails_least_squares_pin(monkeypatch):
+    monkeypatch.setattr(O, "reference_slowness", lambda s: s.min(axis=1))
+    with pytest.raises(AssertionError):
+        test_reference_slowness_is_least_squares_constant_of_each_row()
 
 
 def test_planted_unconjugated_inner_product_fails_cholesky_pin(monkeypatch):
