@@ -478,11 +478,13 @@ def gpu_arm(args):
                    "dft_bf16x3_tcgen05": "tcgen05.mma four-step DFT products, TMEM accumulators (lsm_tc5.cuh)"}
         # per-launch times of the window's sweeps with every transform (3 event-timed launches each,
         # after one untimed; the plain FFT sweeps for comparison)
-        sweep_ms = {"fft": {k: round(v["ms"], 4) for k, v in
-                            L.lsm_autotune(ds.grid, ds.slowness, ds.freqs, ds.geom, K, ws).items()}}
+        sweeps = ("source", "adjoint", "forward")
+        rep = L.lsm_autotune(ds.grid, ds.slowness, ds.freqs, ds.geom, K, ws)
+        sweep_ms = {"fft": {k: round(rep[k]["ms"], 4) for k in sweeps}}
+        sweep_ms["fft"]["points_per_thread"] = rep["tile"]["points_per_thread"]
         for transform in kernels:
             rep = L.lsm_autotune(ds.grid, ds.slowness, ds.freqs, ds.geom, K, ws, transform=transform)
-            sweep_ms[transform] = {k: round(v["ms"], 4) for k, v in rep.items()}
+            sweep_ms[transform] = {k: round(rep[k]["ms"], 4) for k in sweeps}
         torch.cuda.synchronize()
         out["variants"]["sweep_launch_ms_by_transform"] = sweep_ms
         for transform in kernels:
@@ -619,8 +621,11 @@ def tune_lines(lsm, lines):
     tuned = []
     for pr in lines:
         rep = lsm.lsm_autotune(pr.grid, pr.slowness, pr.freqs, pr.geom, pr.K, pr.workspace)
-        entry = {"nx": pr.grid.c.nx, "K": pr.K, "warps": {k: v["warps"] for k, v in rep.items()},
-                 "heuristic_warps": {k: v["heuristic_warps"] for k, v in rep.items()}}
+        sweeps = ("source", "adjoint", "forward")
+        entry = {"nx": pr.grid.c.nx, "K": pr.K, "warps": {k: rep[k]["warps"] for k in sweeps},
+                 "heuristic_warps": {k: rep[k]["heuristic_warps"] for k in sweeps},
+                 "points_per_thread": rep["tile"]["points_per_thread"],
+                 "default_points_per_thread": rep["tile"]["default_points_per_thread"]}
         if pr.slide != pr.K:
             entry["refill_source_warps"] = lsm.lsm_autotune(pr.grid, pr.slowness, pr.freqs, pr.geom, pr.slide,
                                                             pr.workspace)["source"]["warps"]

@@ -382,34 +382,54 @@ typedef struct {
 int rls_multi_line_solve(lsm_line* lines, int nlines, const lsm_solve_options* options);
 
 /*
- * Launch-shape autotuning (an implementation choice, not a step of the paper's method).  The depth
- * sweeps run a fixed number of (shot, frequency) items per warp, and the number of warps per block
- * sets how many items share a block's staged coefficient rows and how the launch fills the SMs;
- * the default spreads a launch evenly over the SMs.  lsm_autotune times every admissible number of
- * warps per block for the source, A^T and A sweeps of launches over `nshots` shots of this grid and
- * frequency set (for a solve: nshots = K), with the FP32 FFTs or, when options->transform selects
- * one, the tensor-core DFT products, and records the fastest.  From then on every launch on the
- * current device with the same (nx, mode, transform, nshots, nw) uses the recorded shape
- * (process-wide, thread safe); results stay within the same tolerances, but A^T's sum over block
- * partial images, and so its last bits, follow the shape.  The A^T candidates never use more
+ * Launch-shape and FFT-tile autotuning (an implementation choice, not a step of the paper's method).
+ * The depth sweeps run a fixed number of (shot, frequency) items per warp, and the number of warps
+ * per block sets how many items share a block's staged coefficient rows and how the launch fills the
+ * SMs; the default spreads a launch evenly over the SMs.  With the FP32 FFTs the FFT tile -- the
+ * points of a line each thread holds -- is tuned too: every width but 768, 896 and 1024 also has a
+ * compiled tile with half the default points per thread (twice the threads per item, a smaller or
+ * deeper FFT plan).  lsm_autotune times, for each tile, every admissible number of warps per block for
+ * the source, A^T and A sweeps of launches over `nshots` shots of this grid and frequency set (for a
+ * solve: nshots = K), with the FP32 FFTs or, when options->transform selects one, the tensor-core DFT
+ * products, and records the fastest shape per sweep and the tile whose best A plus best A^T is
+ * fastest.  From then on every call on the current device with the same (nx, nshots, nw) builds its
+ * coefficient tables for the recorded tile and every launch with the same (nx, mode, transform,
+ * tile, nshots, nw) uses the recorded shape (process-wide, thread safe); results stay within the
+ * same tolerances, but the FFT's rounding and A^T's sum over block partial images, and so their last
+ * bits, follow the tile and the shape.  The A^T candidates never use more
  * blocks than the default, so lsm_workspace_bytes is unchanged.  Needs a workspace of
  * lsm_workspace_bytes(grid, geom, freqs, nshots, LSM_OP_SOLVE); runs shots [0, nshots) on
  * zero-valued inputs, overwrites the workspace, and returns after synchronising the stream.
- * `report` (may be NULL) receives, per sweep, the chosen and the default warps per block with their
- * mean launch times in ms and the number of shapes timed.  lsm_autotune_reset forgets every
- * recorded shape.
+ * `report` (may be NULL) receives, per sweep of the chosen tile, the chosen and the default warps per
+ * block with their mean launch times in ms and the number of shapes timed, and the chosen and default
+ * tiles with their A + A^T times.  lsm_autotune_reset forgets every recorded shape and tile.
  */
 typedef struct {
     int warps, heuristic_warps, candidates;
     double ms, heuristic_ms;
 } lsm_tune_entry;
 typedef struct {
-    lsm_tune_entry source, adjoint, forward;
+    lsm_tune_entry source, adjoint, forward;  /* of the chosen FFT tile */
+    int points_per_thread;           /* the chosen FFT tile (register FFTs; the sweeps' own otherwise) */
+    int default_points_per_thread;   /* the default tile */
+    int tiles;                       /* FFT tiles timed (1 or 2) */
+    double tile_ms, default_tile_ms; /* best A + best A^T launch times, chosen and default tile */
 } lsm_tune_report;
 
 int lsm_autotune(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs,
                  const lsm_geom* geom, int nshots, const lsm_solve_options* options,
                  void* workspace, size_t workspace_bytes, void* stream, lsm_tune_report* report);
+
+/*
+ * The FFT tiles compiled for width nx: writes up to `cap` of them (points per thread, the default
+ * first) to `tiles` (may be NULL) and returns how many there are (1 or 2; 0 for an unsupported nx).
+ * lsm_set_fft_tile records `points_per_thread` as the tile of calls over `nshots` shots of nx columns
+ * and nw frequencies on the current device, as lsm_autotune would (LSM_ERR_ARG for a tile that is not
+ * compiled for nx, LSM_ERR_UNSUPPORTED_NX for an unsupported nx).  Launch shapes of that tile not
+ * tuned yet are the heuristic's.
+ */
+int lsm_fft_tiles(int nx, int* tiles, int cap);
+int lsm_set_fft_tile(int nx, int nshots, int nw, int points_per_thread);
 
 /*
  * Checkpoint stride and launch shape of lsm_born_gradient.  The gradient sweep keeps S and R at

@@ -16,6 +16,7 @@ from .lsm import (  # noqa: F401
     lsm_autotune_reset,
     lsm_autotune_gradient,
     lsm_born_gradient,
+    lsm_fft_tiles,
     lsm_forward,
     lsm_kernel_launches,
     lsm_measure_fp32_peak,

@@ -105,31 +105,59 @@ const NxOps* nx_ops(int nx) {
 
 bool nx_supported(int nx) { return nx_ops(nx) != nullptr; }
 
+// The register-FFT sweeps of nx with V points per thread (0: the default tile), or nullptr.
+const NxOps* fft_ops(int nx, int V) {
+    const NxOps* ops = nx_ops(nx);
+    if (!ops || V == 0 || V == ops->points_per_thread) return ops;
+    return ops->alt && ops->alt->points_per_thread == V ? ops->alt : nullptr;
+}
+
 // ------------------------------------------------------------------ launch shapes and their tuning
 // A launch shape is the number of warps per block (items per block = warps x items per warp); the
 // heuristic spreads a launch's warps evenly over the SMs.  lsm_autotune measures the alternatives
-// and records the fastest per (device, nx, sweep mode, transform, shots, frequencies); launches use
-// a recorded shape, the workspace layout always the heuristic one (the tuner never picks an adjoint
-// shape with more blocks, i.e. more partial images, than the heuristic's).
+// and records the fastest per (device, nx, sweep mode, transform, FFT tile, shots, frequencies);
+// launches use a recorded shape, the workspace layout always the heuristic one (the tuner never picks
+// an adjoint shape with more blocks, i.e. more partial images, than the heuristic's).  For the
+// register FFTs it also picks the FFT tile (points per thread) of a problem: the default or, where
+// one exists, the alternative with half the points per thread (twice the threads per item).  The
+// tile fixes the coefficient tables' order, so a call builds its tables for the recorded tile and
+// every sweep of the call uses it.
 struct TuneKey {
-    int dev, nx, mode, transform, nshots, nw;
+    int dev, nx, mode, transform, V, nshots, nw;
     bool operator<(const TuneKey& o) const {
-        return std::tie(dev, nx, mode, transform, nshots, nw) < std::tie(o.dev, o.nx, o.mode, o.transform, o.nshots, o.nw);
+        return std::tie(dev, nx, mode, transform, V, nshots, nw) <
+               std::tie(o.dev, o.nx, o.mode, o.transform, o.V, o.nshots, o.nw);
     }
 };
 static std::mutex g_tune_mu;
 static std::map<TuneKey, int> g_tune;
+struct TileKey {
+    int dev, nx, nshots, nw;
+    bool operator<(const TileKey& o) const {
+        return std::tie(dev, nx, nshots, nw) < std::tie(o.dev, o.nx, o.nshots, o.nw);
+    }
+};
+static std::map<TileKey, int> g_tile;  // guarded by g_tune_mu
 
-static TuneKey tune_key(int nx, int mode, int transform, int nshots, int nw) {
+static int current_device() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) cudaGetLastError();
-    return TuneKey{dev, nx, mode, transform, nshots, nw};
+    return dev;
 }
-static int tuned_warps(int nx, int mode, int transform, int nshots, int nw) {
-    const TuneKey k = tune_key(nx, mode, transform, nshots, nw);
+static TuneKey tune_key(int nx, int mode, int transform, int nshots, int nw, int V = 0) {
+    return TuneKey{current_device(), nx, mode, transform, V, nshots, nw};
+}
+static int tuned_warps(int nx, int mode, int transform, int nshots, int nw, int V = 0) {
+    const TuneKey k = tune_key(nx, mode, transform, nshots, nw, V);
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune.find(k);
     return it == g_tune.end() ? 0 : it->second;
+}
+// the FFT tile recorded for calls over nshots shots of this problem (0: the default)
+static int chosen_tile(int nx, int nshots, int nw) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tile.find(TileKey{current_device(), nx, nshots, nw});
+    return it == g_tile.end() ? 0 : it->second;
 }
 
 // Checkpoint stride of the gradient sweep (lsm_born_gradient): S and R are kept every c-th depth
@@ -173,8 +201,8 @@ static size_t ckpt_rows(int c, int nz) {
 }
 
 // most warps per block a sweep of this mode can take (registers, shared memory)
-static int sweep_max_warps(int nx, int mode, int nshots, int nw) {
-    const NxOps* ops = nx_ops(nx);
+static int sweep_max_warps(int nx, int mode, int nshots, int nw, int tile = 0) {
+    const NxOps* ops = fft_ops(nx, tile);
     const int V = ops->points_per_thread;
     const int ipw = 32 / (nx / V);
     auto wslots_of = [&](int w) { return std::min(nw, (w * ipw + nshots - 1) / nshots + 1); };
@@ -183,8 +211,8 @@ static int sweep_max_warps(int nx, int mode, int nshots, int nw) {
     return maxw;
 }
 
-static SweepShape sweep_shape_for(int nx, int mode, int nshots, int nw, int warps) {
-    const NxOps* ops = nx_ops(nx);
+static SweepShape sweep_shape_for(int nx, int mode, int nshots, int nw, int warps, int tile = 0) {
+    const NxOps* ops = fft_ops(nx, tile);
     const int ipw = 32 / (nx / ops->points_per_thread);
     const int warps_total = (nshots * nw + ipw - 1) / ipw;
     SweepShape s;
@@ -195,18 +223,18 @@ static SweepShape sweep_shape_for(int nx, int mode, int nshots, int nw, int warp
     return s;
 }
 
-SweepShape sweep_shape_heuristic(int nx, int mode, int nshots, int nw, int num_sms) {
-    const int ipw = 32 / (nx / nx_ops(nx)->points_per_thread);
+SweepShape sweep_shape_heuristic(int nx, int mode, int nshots, int nw, int num_sms, int tile = 0) {
+    const int ipw = 32 / (nx / fft_ops(nx, tile)->points_per_thread);
     const int warps_total = (nshots * nw + ipw - 1) / ipw;
     int warps = (warps_total + num_sms - 1) / num_sms;
-    warps = std::max(1, std::min(warps, sweep_max_warps(nx, mode, nshots, nw)));
-    return sweep_shape_for(nx, mode, nshots, nw, warps);
+    warps = std::max(1, std::min(warps, sweep_max_warps(nx, mode, nshots, nw, tile)));
+    return sweep_shape_for(nx, mode, nshots, nw, warps, tile);
 }
 
-SweepShape sweep_shape(int nx, int mode, int nshots, int nw, int num_sms) {
-    const int w = tuned_warps(nx, mode, 0, nshots, nw);
-    if (w > 0) return sweep_shape_for(nx, mode, nshots, nw, w);
-    return sweep_shape_heuristic(nx, mode, nshots, nw, num_sms);
+SweepShape sweep_shape(int nx, int mode, int nshots, int nw, int num_sms, int tile = 0) {
+    const int w = tuned_warps(nx, mode, 0, nshots, nw, tile);
+    if (w > 0) return sweep_shape_for(nx, mode, nshots, nw, w, tile);
+    return sweep_shape_heuristic(nx, mode, nshots, nw, num_sms, tile);
 }
 
 bool gradient_nx_supported(int nx) {
@@ -297,9 +325,9 @@ cudaError_t launch_tables_grad(const TableArgs& a, cudaStream_t st) { return nx_
 cudaError_t launch_gradient(const GradArgs& a, const SweepShape& sh, cudaStream_t st) {
     return nx_ops(a.nx)->gradient(a, sh, st);
 }
-cudaError_t launch_tables(const TableArgs& a, cudaStream_t st) { return nx_ops(a.nx)->tables(a, st); }
+cudaError_t launch_tables(const TableArgs& a, cudaStream_t st) { return fft_ops(a.nx, a.V)->tables(a, st); }
 cudaError_t launch_sweep(int mode, const SweepArgs& a, const SweepShape& sh, cudaStream_t st) {
-    return nx_ops(a.nx)->sweep(mode, a, sh, st);
+    return fft_ops(a.nx, a.V)->sweep(mode, a, sh, st);
 }
 
 // s_ref(z_j) = mean over x of s(x, z_j), summed in float64 (Examples section: split-step
@@ -381,6 +409,9 @@ Layout make_layout(const lsm_grid* g, const lsm_geom* geo, const lsm_freqs* f, i
     if (op == LSM_OP_ADJOINT || op == LSM_OP_SOLVE) {
         const SweepShape sh = sweep_shape_heuristic(g->nx, MODE_ADJOINT, nshots, (int)nw, num_sms);
         L.nparts = sh.blocks;
+        if (const NxOps* alt = nx_ops(g->nx)->alt)
+            L.nparts = std::max(L.nparts, sweep_shape_heuristic(g->nx, MODE_ADJOINT, nshots, (int)nw, num_sms,
+                                                                alt->points_per_thread).blocks);
         if (nx_ops(g->nx)->has_tc)
             L.nparts = std::max(L.nparts, tc_shape_heuristic(g->nx, MODE_ADJOINT, nshots, (int)nw, num_sms).blocks);
         if (nx_ops(g->nx)->has_tc5) L.nparts = std::max(L.nparts, tc5_shape(g->nx, nshots, (int)nw).blocks);
@@ -461,7 +492,8 @@ int validate_common(const lsm_grid* g, const lsm_freqs* f, const lsm_geom* geo) 
 enum TableOrder { TABLES_SWEEP = 0, TABLES_GRADIENT = 1, TABLES_NATURAL = 2 };
 
 int prepare(const lsm_grid* g, const float* slowness, const lsm_freqs* f, const lsm_geom* geo, const Layout& L,
-            char* ws, cudaStream_t st, const double* sref_override = nullptr, int table_order = TABLES_SWEEP) {
+            char* ws, cudaStream_t st, const double* sref_override = nullptr, int table_order = TABLES_SWEEP,
+            int tile = 0) {
     const size_t nw = (size_t)f->nw;
     // one staging copy of all host arrays (layout identical to the workspace prefix)
     const size_t head = L.sref;
@@ -485,6 +517,7 @@ int prepare(const lsm_grid* g, const float* slowness, const lsm_freqs* f, const 
         LSM_CHECK(cudaGetLastError());
     }
     TableArgs ta;
+    ta.V = tile;
     ta.nx = g->nx;
     ta.nz = g->nz;
     ta.nw = f->nw;
@@ -504,8 +537,10 @@ int prepare(const lsm_grid* g, const float* slowness, const lsm_freqs* f, const 
     return LSM_OK;
 }
 
-SweepArgs base_args(const lsm_grid* g, const lsm_freqs* f, const lsm_geom* geo, const Layout& L, char* ws) {
+SweepArgs base_args(const lsm_grid* g, const lsm_freqs* f, const lsm_geom* geo, const Layout& L, char* ws,
+                    int tile = 0) {
     SweepArgs a{};
+    a.V = tile;
     a.nx = g->nx;
     a.nz = g->nz;
     a.nw = f->nw;
@@ -526,7 +561,7 @@ SweepArgs base_args(const lsm_grid* g, const lsm_freqs* f, const lsm_geom* geo, 
 // transform: 0 = register FFT (FP32); otherwise the tensor-core precision variant (TcPrecision)
 cudaError_t launch_any(int mode, int transform, SweepArgs& a, int n, int num_sms, cudaStream_t st, int* blocks) {
     if (transform == 0) {
-        const SweepShape sh = sweep_shape(a.nx, mode, n, a.nw, num_sms);
+        const SweepShape sh = sweep_shape(a.nx, mode, n, a.nw, num_sms, a.V);
         a.wslots = sh.wslots;
         if (blocks) *blocks = sh.blocks;
         return launch_sweep(mode, a, sh, st);
@@ -612,9 +647,10 @@ int lsm_forward_ex(const lsm_grid* grid, const float* slowness, const lsm_freqs*
     if (workspace_bytes < L.total) return LSM_ERR_WORKSPACE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     char* ws = static_cast<char*>(workspace);
-    rc = prepare(grid, slowness, freqs, geom, L, ws, st, nullptr, transform ? TABLES_NATURAL : TABLES_SWEEP);
+    const int tile = transform ? 0 : chosen_tile(grid->nx, nshots, freqs->nw);
+    rc = prepare(grid, slowness, freqs, geom, L, ws, st, nullptr, transform ? TABLES_NATURAL : TABLES_SWEEP, tile);
     if (rc != LSM_OK) return rc;
-    SweepArgs a = base_args(grid, freqs, geom, L, ws);
+    SweepArgs a = base_args(grid, freqs, geom, L, ws, tile);
     LSM_CHECK(run_source(a, shot0, nshots, nsm, st, transform));
     LSM_CHECK(run_forward(a, shot0, nshots, m, reinterpret_cast<float2*>(d_out), nsm, st, transform));
     return LSM_OK;
@@ -642,9 +678,10 @@ int lsm_adjoint_ex(const lsm_grid* grid, const float* slowness, const lsm_freqs*
     if (workspace_bytes < L.total) return LSM_ERR_WORKSPACE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     char* ws = static_cast<char*>(workspace);
-    rc = prepare(grid, slowness, freqs, geom, L, ws, st, nullptr, transform ? TABLES_NATURAL : TABLES_SWEEP);
+    const int tile = transform ? 0 : chosen_tile(grid->nx, nshots, freqs->nw);
+    rc = prepare(grid, slowness, freqs, geom, L, ws, st, nullptr, transform ? TABLES_NATURAL : TABLES_SWEEP, tile);
     if (rc != LSM_OK) return rc;
-    SweepArgs a = base_args(grid, freqs, geom, L, ws);
+    SweepArgs a = base_args(grid, freqs, geom, L, ws, tile);
     LSM_CHECK(run_source(a, shot0, nshots, nsm, st, transform));
     int nparts = 0;
     LSM_CHECK(run_adjoint(a, shot0, nshots, reinterpret_cast<const float2*>(d), nsm, st, &nparts, transform));
@@ -717,10 +754,11 @@ int lsm_adjoint_static(const lsm_grid* grid, const float* slowness, const lsm_fr
     // the same set-up as lsm_adjoint: the host arrays are first copied into a host buffer owned by
     // this call (so the caller may change or free them as soon as the call returns), then the
     // reference slowness and the coefficient tables are built in the scratch
-    rc = prepare(grid, slowness, freqs, geom, L, ws, st, nullptr, TABLES_SWEEP);
+    const int tile = chosen_tile(grid->nx, nshots, freqs->nw);
+    rc = prepare(grid, slowness, freqs, geom, L, ws, st, nullptr, TABLES_SWEEP, tile);
     if (rc != LSM_OK) return rc;
     // every scratch region below is fully written before it is read: nothing needs clearing
-    SweepArgs a = base_args(grid, freqs, geom, L, ws);
+    SweepArgs a = base_args(grid, freqs, geom, L, ws, tile);
     LSM_CHECK(run_source(a, shot0, nshots, nsm, st));
     int nparts = 0;
     LSM_CHECK(run_adjoint(a, shot0, nshots, reinterpret_cast<const float2*>(d), nsm, st, &nparts));
@@ -850,78 +888,124 @@ int lsm_autotune(const lsm_grid* grid, const float* slowness, const lsm_freqs* f
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     char* ws = static_cast<char*>(workspace);
     const int nx = grid->nx, nw = freqs->nw;
+    // FFT tiles to try: the default, and the alternative where one exists (register FFTs only)
+    int tiles[2] = {0, 0};
+    int ntiles = 1;
+    if (transform == 0 && nx_ops(nx)->alt) tiles[ntiles++] = nx_ops(nx)->alt->points_per_thread;
     // forget earlier choices for this problem, so that the set-up below runs the heuristic shapes
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        for (int mode = 0; mode < 3; ++mode) g_tune.erase(tune_key(nx, mode, transform, nshots, nw));
+        for (int ti = 0; ti < ntiles; ++ti)
+            for (int mode = 0; mode < 3; ++mode) g_tune.erase(tune_key(nx, mode, transform, nshots, nw, tiles[ti]));
+        if (transform == 0) g_tile.erase(TileKey{current_device(), nx, nshots, nw});
     }
-    rc = prepare(grid, slowness, freqs, geom, L, ws, st, nullptr, transform ? TABLES_NATURAL : TABLES_SWEEP);
-    if (rc != LSM_OK) return rc;
-    SweepArgs a = base_args(grid, freqs, geom, L, ws);
-    a.shot0 = 0;
-    a.nshots = nshots;
-    a.m = reinterpret_cast<const float*>(ws + L.p);
-    a.dout = reinterpret_cast<float2*>(ws + L.q);
-    a.din = reinterpret_cast<const float2*>(ws + L.r);
-    const size_t nd = (size_t)nshots * nw * geom->nrec;
-    LSM_CHECK(cudaMemsetAsync(ws + L.p, 0, (size_t)nx * grid->nz * sizeof(float), st));
-    LSM_CHECK(cudaMemsetAsync(ws + L.r, 0, nd * sizeof(float2), st));
-    LSM_CHECK(run_source(a, 0, nshots, nsm, st, transform));  // the ring the A and A^T sweeps read
     EventPair ev;
     LSM_CHECK(cudaEventCreate(&ev.a));
     LSM_CHECK(cudaEventCreate(&ev.b));
     const int modes[3] = {MODE_SOURCE, MODE_ADJOINT, MODE_FORWARD};
-    lsm_tune_entry* out[3] = {report ? &report->source : nullptr, report ? &report->adjoint : nullptr,
-                              report ? &report->forward : nullptr};
-    for (int mi = 0; mi < 3; ++mi) {
-        const int mode = modes[mi];
-        if (is_tc5(transform)) {
-            // one fixed launch shape: timed for the report, nothing recorded
-            const SweepShape sh = tc5_shape(nx, nshots, nw);
-            double ms = 0.0;
-            LSM_CHECK(time_shape(mode, transform, a, sh, st, ev.a, ev.b, 3, &ms));
-            if (out[mi]) *out[mi] = lsm_tune_entry{sh.warps, sh.warps, 1, ms, ms};
-            continue;
-        }
-        const SweepShape h = transform ? tc_shape_heuristic(nx, mode, nshots, nw, nsm)
-                                       : sweep_shape_heuristic(nx, mode, nshots, nw, nsm);
-        const int maxw = transform ? 7 : sweep_max_warps(nx, mode, nshots, nw);
-        // the adjoint keeps at most the heuristic's number of blocks (partial images in the layout)
-        const int minw = mode == MODE_ADJOINT ? h.warps : 1;
-        int best_w = h.warps, ncand = 0;
-        double best_ms = 0.0, h_ms = 0.0;
-        for (int w = minw; w <= maxw; ++w) {
-            const SweepShape sh = transform ? tc_shape_for(nx, mode, nshots, nw, w)
-                                            : sweep_shape_for(nx, mode, nshots, nw, w);
-            if (sh.smem > 227 * 1024) continue;
-            double ms = 0.0;
-            LSM_CHECK(time_shape(mode, transform, a, sh, st, ev.a, ev.b, 3, &ms));
-            ++ncand;
-            if (w == h.warps) h_ms = ms;
-            if (ncand == 1 || ms < best_ms) {
-                best_ms = ms;
-                best_w = w;
+    lsm_tune_entry entries[2][3] = {};
+    double tile_ms[2] = {0.0, 0.0};  // best A + best A^T of each tile
+    for (int ti = 0; ti < ntiles; ++ti) {
+        const int tile = tiles[ti];
+        rc = prepare(grid, slowness, freqs, geom, L, ws, st, nullptr, transform ? TABLES_NATURAL : TABLES_SWEEP,
+                     tile);
+        if (rc != LSM_OK) return rc;
+        SweepArgs a = base_args(grid, freqs, geom, L, ws, tile);
+        a.shot0 = 0;
+        a.nshots = nshots;
+        a.m = reinterpret_cast<const float*>(ws + L.p);
+        a.dout = reinterpret_cast<float2*>(ws + L.q);
+        a.din = reinterpret_cast<const float2*>(ws + L.r);
+        const size_t nd = (size_t)nshots * nw * geom->nrec;
+        LSM_CHECK(cudaMemsetAsync(ws + L.p, 0, (size_t)nx * grid->nz * sizeof(float), st));
+        LSM_CHECK(cudaMemsetAsync(ws + L.r, 0, nd * sizeof(float2), st));
+        LSM_CHECK(run_source(a, 0, nshots, nsm, st, transform));  // the ring the A and A^T sweeps read
+        for (int mi = 0; mi < 3; ++mi) {
+            const int mode = modes[mi];
+            if (is_tc5(transform)) {
+                // one fixed launch shape: timed for the report, nothing recorded
+                const SweepShape sh = tc5_shape(nx, nshots, nw);
+                double ms = 0.0;
+                LSM_CHECK(time_shape(mode, transform, a, sh, st, ev.a, ev.b, 3, &ms));
+                entries[ti][mi] = lsm_tune_entry{sh.warps, sh.warps, 1, ms, ms};
+                continue;
             }
+            const SweepShape h = transform ? tc_shape_heuristic(nx, mode, nshots, nw, nsm)
+                                           : sweep_shape_heuristic(nx, mode, nshots, nw, nsm, tile);
+            const int maxw = transform ? 7 : sweep_max_warps(nx, mode, nshots, nw, tile);
+            // the adjoint keeps at most the heuristic's number of blocks (partial images in the layout)
+            const int minw = mode == MODE_ADJOINT ? h.warps : 1;
+            int best_w = h.warps, ncand = 0;
+            double best_ms = 0.0, h_ms = 0.0;
+            for (int w = minw; w <= maxw; ++w) {
+                const SweepShape sh = transform ? tc_shape_for(nx, mode, nshots, nw, w)
+                                                : sweep_shape_for(nx, mode, nshots, nw, w, tile);
+                if (sh.smem > 227 * 1024) continue;
+                double ms = 0.0;
+                LSM_CHECK(time_shape(mode, transform, a, sh, st, ev.a, ev.b, 3, &ms));
+                ++ncand;
+                if (w == h.warps) h_ms = ms;
+                if (ncand == 1 || ms < best_ms) {
+                    best_ms = ms;
+                    best_w = w;
+                }
+            }
+            {
+                std::lock_guard<std::mutex> lock(g_tune_mu);
+                g_tune[tune_key(nx, mode, transform, nshots, nw, tile)] = best_w;
+            }
+            entries[ti][mi] = lsm_tune_entry{best_w, h.warps, ncand, best_ms, h_ms};
+            if (mode != MODE_SOURCE) tile_ms[ti] += best_ms;
         }
-        {
-            std::lock_guard<std::mutex> lock(g_tune_mu);
-            g_tune[tune_key(nx, mode, transform, nshots, nw)] = best_w;
-        }
-        if (out[mi]) {
-            out[mi]->warps = best_w;
-            out[mi]->heuristic_warps = h.warps;
-            out[mi]->ms = best_ms;
-            out[mi]->heuristic_ms = h_ms;
-            out[mi]->candidates = ncand;
-        }
+    }
+    int pick = 0;
+    if (ntiles > 1 && tile_ms[1] < tile_ms[0]) pick = 1;
+    if (transform == 0) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tile[TileKey{current_device(), nx, nshots, nw}] = tiles[pick];
+    }
+    if (report) {
+        report->source = entries[pick][0];
+        report->adjoint = entries[pick][1];
+        report->forward = entries[pick][2];
+        report->points_per_thread = tiles[pick] ? tiles[pick] : nx_ops(nx)->points_per_thread;
+        report->default_points_per_thread = nx_ops(nx)->points_per_thread;
+        report->tiles = ntiles;
+        report->tile_ms = tile_ms[pick];
+        report->default_tile_ms = tile_ms[0];
     }
     LSM_CHECK(cudaStreamSynchronize(st));
     return LSM_OK;
 }
 
+int lsm_set_fft_tile(int nx, int nshots, int nw, int points_per_thread) {
+    const NxOps* ops = nx_ops(nx);
+    if (!ops) return LSM_ERR_UNSUPPORTED_NX;
+    if (nshots < 1 || nw < 1) return LSM_ERR_ARG;
+    const NxOps* t = fft_ops(nx, points_per_thread);
+    if (!t) return LSM_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tile[TileKey{current_device(), nx, nshots, nw}] = t == ops ? 0 : points_per_thread;
+    return LSM_OK;
+}
+
+int lsm_fft_tiles(int nx, int* tiles, int cap) {
+    const NxOps* ops = nx_ops(nx);
+    if (!ops) return 0;
+    int n = 0;
+    if (tiles && cap > n) tiles[n] = ops->points_per_thread;
+    ++n;
+    if (ops->alt) {
+        if (tiles && cap > n) tiles[n] = ops->alt->points_per_thread;
+        ++n;
+    }
+    return n;
+}
+
 void lsm_autotune_reset(void) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune.clear();
+    g_tile.clear();
     g_ckpt_tune.clear();
 }
 
@@ -1204,9 +1288,10 @@ static int window_solve(const lsm_grid* grid, const float* slowness, const lsm_f
 
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     char* ws = static_cast<char*>(workspace);
-    rc = prepare(grid, slowness, freqs, geom, L, ws, st, nullptr, transform ? TABLES_NATURAL : TABLES_SWEEP);
+    const int tile = transform ? 0 : chosen_tile(grid->nx, K, freqs->nw);
+    rc = prepare(grid, slowness, freqs, geom, L, ws, st, nullptr, transform ? TABLES_NATURAL : TABLES_SWEEP, tile);
     if (rc != LSM_OK) return rc;
-    SweepArgs a = base_args(grid, freqs, geom, L, ws);
+    SweepArgs a = base_args(grid, freqs, geom, L, ws, tile);
 
     const int n = grid->nx * grid->nz;
     const size_t nd = (size_t)K * freqs->nw * geom->nrec;

@@ -46,6 +46,7 @@ struct SweepArgs {
     double lam;                    // Tikhonov weight lambda
     CgState* cg;                   // gamma (read); delta, alpha and the breakdown flag (block 0 writes)
     int* dev_err;                  // set to 1 by a kernel whose bounded wait on the tensor core ran out
+    int V;                         // FFT tile (points per thread) of the register-FFT sweeps; 0: default
 };
 
 // Arguments of the gradient kernel (lsm_grad.cuh) over the items of shots [shot0, shot0+nshots).
@@ -72,6 +73,7 @@ struct GradArgs {
 };
 
 struct TableArgs {
+    int V;                   // FFT tile whose register order the Phi table follows; 0: default
     int nx, nz, nw;
     float dx, dz;
     const float* slowness;   // [nz][nx]
@@ -115,6 +117,8 @@ struct NxOps {
     size_t (*gradient_smem)(int warps, int wslots);
     bool has_tc5;                 // tcgen05 transform variants exist for this nx
     size_t (*tc5_smem)(int wslots);  // their dynamic shared memory per CTA
+    const NxOps* alt;             // the sweeps with the alternative FFT tile (only tables, sweep,
+                                  // max_warps and smem set), or nullptr
 };
 // The operations for nx, or nullptr when nx is not supported.
 const NxOps* nx_ops(int nx);
@@ -130,6 +134,16 @@ constexpr int points_per_thread(int nx) {
     if (q == 1) return nx >= 512 ? 32 : 16;
     int v = q == 7 ? 4 * q : 8 * q;
     while (nx / v > 32) v *= 2;
+    return v;
+}
+
+// The alternative FFT tile of the sweep kernels: half the points per thread (twice the threads per
+// (shot, frequency) item) where that plan exists -- V/2 a multiple of the odd factor with at least two
+// power-of-two points left, and at most 32 threads per item; 0 where it does not (nx = 768, 896, 1024).
+constexpr int alt_points_per_thread(int nx) {
+    const int q = odd_factor(nx);
+    const int v = points_per_thread(nx) / 2;
+    if (v < 2 || v % q != 0 || v / q < 2 || nx % v != 0 || nx / v > 32) return 0;
     return v;
 }
 

@@ -103,10 +103,13 @@ __device__ __forceinline__ void step_down_adjoint(float2 (&v)[V], const Twiddles
 
 // ------------------------------------------------------------------ shared-memory layout
 
-// Threads per block the kernel is compiled for: 32 points per thread need up to ~250 registers,
-// which leaves room for 8 warps per SM; 16 points per thread fit 16 warps at 128 registers.
-template <int V>
-constexpr int sweep_max_threads() { return V >= 24 ? 256 : 512; }
+// Threads per block the kernel is compiled for: 24 or more points per thread need up to ~250
+// registers, which leaves room for 8 warps per SM; 16 points per thread fit 16 warps at 128
+// registers, except with 32 threads per item and 16 to 20 points per thread (the alternative tiles at
+// nx = 512 and 640: deeper plans whose twiddles need more registers), which are compiled for 12 warps
+// at up to 168 registers.
+template <int N, int V>
+constexpr int sweep_max_threads() { return V >= 24 ? 256 : (V >= 16 && N / V == 32 ? 384 : 512); }
 
 // Image rows of the adjoint: each warp writes SPW rows per depth (its items' imaging terms; with
 // more than two items per warp they are first summed pairwise by shuffles), at a row stride of
@@ -142,7 +145,7 @@ constexpr size_t sweep_smem_bytes(int warps, int wslots, int mode) {
 }
 
 template <int N, int V, int MODE>
-__global__ void __launch_bounds__(sweep_max_threads<V>()) sweep_kernel(const SweepArgs a) {
+__global__ void __launch_bounds__(sweep_max_threads<N, V>()) sweep_kernel(const SweepArgs a) {
     using P = Plan<N, V>;
     constexpr int T = P::T;
     constexpr int IPW = 32 / T;
@@ -497,9 +500,9 @@ __global__ void tables_kernel(const TableArgs a) {
     }
 }
 
-template <int N>
+template <int N, int VV = points_per_thread(N)>
 struct Dispatch {
-    static constexpr int V = points_per_thread(N);
+    static constexpr int V = VV;
 
     static cudaError_t tables(const TableArgs& a, cudaStream_t st) {
         const size_t total = (size_t)a.nw * a.nz * N;
@@ -539,7 +542,7 @@ struct Dispatch {
         cudaFuncAttributes attr;
         if (cudaFuncGetAttributes(&attr, sweep_kernel<N, V, MODE>) != cudaSuccess) {
             cudaGetLastError();
-            return sweep_max_threads<V>() / 32;
+            return sweep_max_threads<N, V>() / 32;
         }
         int w = attr.maxThreadsPerBlock / 32;
         return w < 1 ? 1 : w;
@@ -735,9 +738,22 @@ struct Dispatch {
     static size_t gradient_smem_##NN(int warps, int wslots) {                                     \
         return Dispatch<NN>::gradient_smem(warps, wslots);                                        \
     }                                                                                             \
+    using DispatchAlt_##NN = Dispatch<NN, alt_points_per_thread(NN) ? alt_points_per_thread(NN) : points_per_thread(NN)>; \
+    static cudaError_t alt_tables_##NN(const TableArgs& a, cudaStream_t st) { return DispatchAlt_##NN::tables(a, st); } \
+    static cudaError_t alt_sweep_##NN(int mode, const SweepArgs& a, const SweepShape& sh, cudaStream_t st) { \
+        return DispatchAlt_##NN::sweep_any(mode, a, sh, st);                                      \
+    }                                                                                             \
+    static int alt_max_warps_##NN(int mode) { return DispatchAlt_##NN::max_warps(mode); }         \
+    static size_t alt_smem_##NN(int mode, int warps, int wslots) {                                \
+        return sweep_smem_bytes<NN, DispatchAlt_##NN::V>(warps, wslots, mode);                    \
+    }                                                                                             \
+    static const NxOps kNxOpsAlt_##NN = {NN, DispatchAlt_##NN::V, false, alt_tables_##NN, alt_sweep_##NN, \
+                                         alt_max_warps_##NN, alt_smem_##NN, nullptr, nullptr, nullptr, false, \
+                                         nullptr, nullptr, nullptr, nullptr, false, nullptr, nullptr};     \
     extern const NxOps kNxOps_##NN = {NN, Dispatch<NN>::V, Dispatch<NN>::kGrad, tables_##NN, sweep_##NN,        \
                                       max_warps_##NN, smem_##NN, tables_grad_##NN, gradient_##NN,  \
                                       gradient_max_warps_##NN, Dispatch<NN>::kTc, tables_natural_##NN, \
                                       tc_sweep_##NN, tc_smem_##NN, gradient_smem_##NN,            \
-                                      Dispatch<NN>::kTc5, Dispatch<NN>::tc5_smem};                 \
+                                      Dispatch<NN>::kTc5, Dispatch<NN>::tc5_smem,                  \
+                                      alt_points_per_thread(NN) ? &kNxOpsAlt_##NN : nullptr};       \
     }

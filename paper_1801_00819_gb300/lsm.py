@@ -35,7 +35,7 @@ EXPORTED = ("lsm_workspace_bytes", "lsm_forward", "lsm_adjoint", "lsm_num_window
             "lsm_adjoint_static", "lsm_born_gradient", "rls_window_solve_ex", "rls_multi_line_solve",
             "lsm_forward_ex", "lsm_adjoint_ex", "lsm_profile_start_classes", "lsm_autotune",
             "lsm_autotune_reset", "lsm_autotune_gradient", "lsm_measure_fp32_peak",
-            "lsm_check_bounded_wait", "rls_window_solve_sharded")
+            "lsm_check_bounded_wait", "rls_window_solve_sharded", "lsm_fft_tiles", "lsm_set_fft_tile")
 
 TRANSFORMS = {"fft": 0, "dft_bf16x3": 1, "dft_fp16x3": 2, "dft_bf16x1": 3, "dft_fp16x3_tcgen05": 4,
               "dft_bf16x3_tcgen05": 5}
@@ -121,7 +121,9 @@ class lsm_tune_entry(ctypes.Structure):
 
 
 class lsm_tune_report(ctypes.Structure):
-    _fields_ = [("source", lsm_tune_entry), ("adjoint", lsm_tune_entry), ("forward", lsm_tune_entry)]
+    _fields_ = [("source", lsm_tune_entry), ("adjoint", lsm_tune_entry), ("forward", lsm_tune_entry),
+                ("points_per_thread", ctypes.c_int), ("default_points_per_thread", ctypes.c_int),
+                ("tiles", ctypes.c_int), ("tile_ms", ctypes.c_double), ("default_tile_ms", ctypes.c_double)]
 
 
 class lsm_ckpt_tune_report(ctypes.Structure):
@@ -192,6 +194,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lsm_autotune_gradient.argtypes = [ctypes.POINTER(lsm_grid), ctypes.c_void_p, ctypes.POINTER(lsm_freqs),
                                           ctypes.POINTER(lsm_geom), ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
                                           ctypes.c_void_p, ctypes.POINTER(lsm_ckpt_tune_report)]
+    lib.lsm_fft_tiles.restype = ctypes.c_int
+    lib.lsm_fft_tiles.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+    lib.lsm_set_fft_tile.restype = ctypes.c_int
+    lib.lsm_set_fft_tile.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.lsm_autotune_reset.restype = None
     lib.lsm_autotune_reset.argtypes = []
     lib.lsm_status_string.restype = ctypes.c_char_p
@@ -478,16 +484,20 @@ def rls_multi_line_solve(problems, preconditioner=None, precond_eps=1e-2, raise_
 
 
 def lsm_autotune(grid, slowness, freqs, geom, nshots, workspace, stream=None, transform="fft") -> dict:
-    """Time every admissible launch shape of the source, A^T and A sweeps for launches over `nshots`
-    shots and record the fastest for later launches (see include/lsm.h).  `workspace` must hold
+    """Time every admissible FFT tile and launch shape of the source, A^T and A sweeps for launches over
+    `nshots` shots and record the fastest for later calls (see include/lsm.h).  `workspace` must hold
     lsm_workspace_bytes(..., nshots, LSM_OP_SOLVE).  Returns {sweep: {warps, heuristic_warps,
-    candidates, ms, heuristic_ms}}."""
+    candidates, ms, heuristic_ms}} for the chosen tile, and "tile": {points_per_thread,
+    default_points_per_thread, tiles, a_plus_at_ms, default_a_plus_at_ms}."""
     rep = lsm_tune_report()
     st = load_library().lsm_autotune(ctypes.byref(grid.c), _ptr(slowness), ctypes.byref(freqs.c),
                                       ctypes.byref(geom.c), int(nshots), ctypes.byref(_options(transform=transform)),
                                       _ptr(workspace), _nbytes(workspace), _stream(stream), ctypes.byref(rep))
     _check(st, "lsm_autotune")
-    return {"source": rep.source.as_dict(), "adjoint": rep.adjoint.as_dict(), "forward": rep.forward.as_dict()}
+    return {"source": rep.source.as_dict(), "adjoint": rep.adjoint.as_dict(), "forward": rep.forward.as_dict(),
+            "tile": {"points_per_thread": int(rep.points_per_thread),
+                     "default_points_per_thread": int(rep.default_points_per_thread), "tiles": int(rep.tiles),
+                     "a_plus_at_ms": float(rep.tile_ms), "default_a_plus_at_ms": float(rep.default_tile_ms)}}
 
 
 def lsm_autotune_gradient(grid, slowness, freqs, geom, nshots, workspace, stream=None) -> dict:
@@ -503,6 +513,20 @@ def lsm_autotune_gradient(grid, slowness, freqs, geom, nshots, workspace, stream
     return {"stride": int(rep.stride), "default_stride": int(rep.default_stride), "warps": int(rep.warps),
             "default_warps": int(rep.default_warps), "candidates": int(rep.candidates), "ms": float(rep.ms),
             "default_ms": float(rep.default_ms)}
+
+
+def lsm_fft_tiles(nx: int) -> list:
+    """The FFT tiles (points per thread) compiled for width nx, the default first."""
+    buf = (ctypes.c_int * 2)()
+    n = load_library().lsm_fft_tiles(int(nx), buf, 2)
+    return [int(buf[i]) for i in range(min(n, 2))]
+
+
+def lsm_set_fft_tile(nx: int, nshots: int, nw: int, points_per_thread: int) -> None:
+    """Record the FFT tile of calls over `nshots` shots of nx columns and nw frequencies (see
+    include/lsm.h), as lsm_autotune would."""
+    _check(load_library().lsm_set_fft_tile(int(nx), int(nshots), int(nw), int(points_per_thread)),
+           "lsm_set_fft_tile")
 
 
 def lsm_autotune_reset() -> None:

@@ -39,7 +39,7 @@ def test_header_declares_expected_entry_points():
                                             "lsm_forward_ex", "lsm_adjoint_ex", "lsm_profile_start_classes",
                                             "lsm_autotune", "lsm_autotune_reset", "lsm_autotune_gradient",
                                             "lsm_measure_fp32_peak", "lsm_check_bounded_wait",
-                                            "rls_window_solve_sharded"])
+                                            "rls_window_solve_sharded", "lsm_fft_tiles", "lsm_set_fft_tile"])
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -121,6 +121,23 @@ def test_static_scratch_variant_rejects_oversize_problems_before_launch(lib):
         lib.lsm_adjoint_static(g, fake, f, geo, fake, fake, 0, 16, stream=0)
     assert ei.value.status == lib.LSM_ERR_WORKSPACE
     assert lib.lsm_kernel_launches() == before
+
+
+def test_fft_tiles_of_every_width(lib):
+    """Every width has its default tile and, except 768, 896 and 1024, one with half the points per
+    thread (at most 32 threads per item, a multiple of the odd factor)."""
+    for nx in (16, 32, 64, 128, 256, 512, 1024, 48, 96, 192, 384, 768, 80, 160, 320, 640, 112, 224, 448, 896):
+        tiles = lib.lsm_fft_tiles(nx)
+        assert tiles[0] == (32 if nx in (512, 1024) else tiles[0])
+        if nx in (768, 896, 1024):
+            assert len(tiles) == 1
+        else:
+            assert len(tiles) == 2 and tiles[1] * 2 == tiles[0] and nx // tiles[1] <= 32
+    assert lib.lsm_fft_tiles(40) == []
+    with pytest.raises(lib.LsmError):
+        lib.lsm_set_fft_tile(512, 16, 128, 8)   # no such tile at 512
+    lib.lsm_set_fft_tile(512, 16, 128, 16)
+    lib.lsm_autotune_reset()
 
 
 def test_tensor_core_transform_validation(lib):
