@@ -232,7 +232,10 @@ def gpu_arm(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1801_00819_gb300 import build as B
-    B.build()
+    if rank == 0:  # one process brings the in-tree library up to date; the others wait for it
+        B.build()
+    if world > 1:
+        dist.barrier()
 
     sv = workload(args.workload, rank)
     s32 = np.asarray(sv.slowness, dtype=np.float32)

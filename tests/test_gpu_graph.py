@@ -159,3 +159,19 @@ def test_default_is_graph_unless_sweeps_are_timed(torch_cuda):
     prof = L.lsm_profile_stop()
     assert prof["adjoint"]["launches"] == 3 * (2 + sv.cg_iters)  # the host-driven loop, every sweep timed
     np.testing.assert_array_equal(m_a, m_b)
+
+
+def test_graph_tcgen05_transform_bitwise_equal_to_host_loop(torch_cuda):
+    """The tcgen05 transforms (nx = 512) inside the graph-replayed CG iterations: the same images and
+    statistics as the host-driven loop, with tolerance stopping."""
+    sv = random_case(512, 12, 5, 6, seed=93)
+    op = oracle_operator(sv)
+    d, lam = _data(sv, op)
+    ds = device_survey(sv)
+    for transform in ("dft_fp16x3_tcgen05", "dft_bf16x3_tcgen05"):
+        s_e, m_e, st_e = _solve(torch_cuda, ds, d, lam, 3, 2, 2e-2, 20, transform=transform, cuda_graph=False)
+        s_g, m_g, st_g = _solve(torch_cuda, ds, d, lam, 3, 2, 2e-2, 20, transform=transform, cuda_graph=True)
+        assert s_e == s_g == 0
+        np.testing.assert_array_equal(m_e, m_g)
+        _same_stats(st_e, st_g)
+        assert all(0 < w["iters"] < 20 for w in st_g)
