@@ -490,6 +490,7 @@ def gpu_arm(args):
             sweep_ms[transform] = {k: round(rep[k]["ms"], 4) for k in sweeps}
         torch.cuda.synchronize()
         out["variants"]["sweep_launch_ms_by_transform"] = sweep_ms
+        out["variants"]["sweep_launch_ms_by_transform_precision_1024"] = precision_sweeps_variant(L, torch, kernels)
         for transform in kernels:
             m.zero_()
             torch.cuda.synchronize()
@@ -642,6 +643,26 @@ def line_units(lines, stats_per_line):
         per_pass = pr.K * pr.freqs.c.nw * pr.grid.c.nz
         total += sum((w["n_forward"] + w["n_adjoint"]) / 2 * per_pass for w in st)
     return total
+
+
+def precision_sweeps_variant(L, torch, transforms):
+    """Per-launch times of the sweeps of one window of the precision workload (1024 x 512, 256
+    frequencies 3-60 Hz, 4 shots: 1,024 items) with the FP32 FFT and every tensor-core transform
+    (lsm_autotune's report: 3 event-timed launches each after one untimed)."""
+    from paper_1801_00819_gb300.device import to_device, workspace
+    from synth import config_precision
+
+    sv = config_precision()
+    K = 4
+    ds = to_device(sv.nx, sv.nz, sv.dx, sv.dz, sv.slowness, sv.src_ix, sv.rec_ix, sv.freqs, sv.wavelet)
+    ws = workspace(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, K, L.LSM_OP_SOLVE))
+    out = {"workload": f"{sv.nx} x {sv.nz}, {K} shots x {sv.nw} frequencies"}
+    for transform in ["fft"] + list(transforms):
+        rep = L.lsm_autotune(ds.grid, ds.slowness, ds.freqs, ds.geom, K, ws, transform=transform)
+        out[transform] = {k: round(rep[k]["ms"], 4) for k in ("source", "adjoint", "forward")}
+    torch.cuda.synchronize()
+    del ws
+    return out
 
 
 def batching_reduced_variant(L, torch, args):

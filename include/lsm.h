@@ -274,10 +274,11 @@ int lsm_profile_stop(lsm_profile* out);
 /*
  *     LSM_TRANSFORM_DFT_FP16X3_TCGEN05, _BF16X3_TCGEN05: the same four-step DFT products, split FP16
  *     (lo scaled by 2^11, two accumulators) or split BF16 three-term, on the fifth-generation tensor
- *     cores: tcgen05.mma issued by one thread per 128-thread CTA with 128-byte-swizzled operands in
- *     shared memory and FP32 accumulators in tensor memory, eight (shot, frequency) items per CTA
- *     stacked as the MMA's 128 rows.  nx = 512 only (LSM_ERR_UNSUPPORTED_NX otherwise), receivers at
- *     every column.  Every wait of these kernels on the tensor core is bounded (about a second);
+ *     cores: tcgen05.mma issued by one thread per CTA with 128-byte-swizzled operands in shared
+ *     memory and FP32 accumulators in tensor memory, eight (shot, frequency) items per 128-thread
+ *     CTA stacked as the MMAs' 128-row tiles (16 items at nx = 128; a 256-thread CTA at nx = 1024;
+ *     lsm_tcgen05_shape gives the launch shape).  nx = 128, 256, 512 and 1024 (LSM_ERR_UNSUPPORTED_NX otherwise), receivers at every
+ *     column.  Every wait of these kernels on the tensor core is bounded (about a second);
  *     one that runs out leaves NaN in the call's outputs, and rls_window_solve_ex then returns
  *     LSM_ERR_TIMEOUT.
  */
@@ -430,6 +431,17 @@ int lsm_autotune(const lsm_grid* grid, const float* slowness, const lsm_freqs* f
  */
 int lsm_fft_tiles(int nx, int* tiles, int cap);
 int lsm_set_fft_tile(int nx, int nshots, int nw, int points_per_thread);
+
+/*
+ * Launch shape of the tcgen05 transform variants for a call over `nshots` shots of nx columns and
+ * nw frequencies (host only; no device is touched): (shot, frequency) items per CTA, threads per
+ * CTA, CTAs, frequency slots whose Phi and D rows a CTA stages in shared memory (0: the rows are
+ * read from global memory because a CTA's frequencies would not fit its shared memory) and its
+ * dynamic shared-memory bytes.  Any output pointer may be NULL.  LSM_ERR_UNSUPPORTED_NX for a width
+ * without tcgen05 variants, LSM_ERR_ARG for nshots < 1 or nw < 1.
+ */
+int lsm_tcgen05_shape(int nx, int nshots, int nw, int* items, int* threads, int* blocks, int* wslots,
+                      size_t* smem_bytes);
 
 /*
  * Checkpoint stride and launch shape of lsm_born_gradient.  The gradient sweep keeps S and R at

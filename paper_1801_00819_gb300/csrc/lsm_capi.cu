@@ -301,16 +301,23 @@ SweepShape tc_shape_heuristic(int nx, int mode, int nshots, int nw, int num_sms)
     return tc_shape_for(nx, mode, nshots, nw, warps);
 }
 
-// tcgen05 variants: a fixed shape of 8 items per 128-thread CTA
+// tcgen05 variants: a fixed shape per width (items and threads per CTA); a CTA whose frequencies'
+// staged Phi and D rows would not fit its shared memory reads them from global memory (wslots 0)
 static bool is_tc5(int transform) {
     return transform == LSM_TRANSFORM_DFT_FP16X3_TCGEN05 || transform == LSM_TRANSFORM_DFT_BF16X3_TCGEN05;
 }
 static SweepShape tc5_shape(int nx, int nshots, int nw) {
+    const NxOps* ops = nx_ops(nx);
+    const int items = ops->tc5_items;
     SweepShape s;
-    s.warps = 4;
-    s.blocks = (nshots * nw + 7) / 8;
-    s.wslots = std::min(nw, (8 + nshots - 1) / nshots + 1);  // frequencies a CTA's 8 items can span
-    s.smem = nx_ops(nx)->tc5_smem(s.wslots);
+    s.warps = ops->tc5_threads / 32;
+    s.blocks = (nshots * nw + items - 1) / items;
+    s.wslots = std::min(nw, (items + nshots - 1) / nshots + 1);  // frequencies a CTA's items can span
+    s.smem = ops->tc5_smem(s.wslots);
+    if (s.smem > kTc5MaxDynSmem) {
+        s.wslots = 0;
+        s.smem = ops->tc5_smem(0);
+    }
     return s;
 }
 
@@ -1000,6 +1007,20 @@ int lsm_fft_tiles(int nx, int* tiles, int cap) {
         ++n;
     }
     return n;
+}
+
+int lsm_tcgen05_shape(int nx, int nshots, int nw, int* items, int* threads, int* blocks, int* wslots,
+                      size_t* smem_bytes) {
+    const NxOps* ops = nx_ops(nx);
+    if (!ops || !ops->has_tc5) return LSM_ERR_UNSUPPORTED_NX;
+    if (nshots < 1 || nw < 1) return LSM_ERR_ARG;
+    const SweepShape sh = tc5_shape(nx, nshots, nw);
+    if (items) *items = ops->tc5_items;
+    if (threads) *threads = sh.warps * 32;
+    if (blocks) *blocks = sh.blocks;
+    if (wslots) *wslots = sh.wslots;
+    if (smem_bytes) *smem_bytes = sh.smem;
+    return LSM_OK;
 }
 
 void lsm_autotune_reset(void) {

@@ -116,10 +116,16 @@ struct NxOps {
     size_t (*tc_smem)(int mode, int warps);
     size_t (*gradient_smem)(int warps, int wslots);
     bool has_tc5;                 // tcgen05 transform variants exist for this nx
-    size_t (*tc5_smem)(int wslots);  // their dynamic shared memory per CTA
+    size_t (*tc5_smem)(int wslots);  // their dynamic shared memory per CTA (wslots 0: rows unstaged)
+    int tc5_items;                // their (shot, frequency) items per CTA
+    int tc5_threads;              // and threads per CTA
     const NxOps* alt;             // the sweeps with the alternative FFT tile (only tables, sweep,
                                   // max_warps and smem set), or nullptr
 };
+// Dynamic shared memory a tcgen05 sweep CTA may take: the 227 KB opt-in limit less a margin for
+// the kernel's static shared memory.
+constexpr size_t kTc5MaxDynSmem = 227 * 1024 - 1024;
+
 // The operations for nx, or nullptr when nx is not supported.
 const NxOps* nx_ops(int nx);
 

@@ -596,25 +596,24 @@ struct Dispatch {
         }
     }
 
-    // tcgen05 transform variants (nx = 512): 8 items per 128-thread CTA
-    static constexpr bool kTc5 = N == 512;
+    // tcgen05 transform variants (nx = 128, 256, 512, 1024): 8 items per CTA (16 at nx = 128), 128
+    // threads (256 at nx = 1024)
+    static constexpr bool kTc5 = tc5_width(N);
 
     template <int PREC, int MODE>
     static cudaError_t tc5_launch(const SweepArgs& a, const SweepShape& sh, cudaStream_t st) {
         if constexpr (kTc5) {
+            using S5 = Tc5Shape<N>;
             static DeviceOnce configured;
-            // the kernel also holds a few bytes of static shared memory (its mbarrier and TMEM address),
-            // so the dynamic limit stays below the 227 KB a block can have
-            constexpr int kMaxDyn = 200 * 1024;
             cudaError_t e = configured.run([] {
                 return cudaFuncSetAttribute(tc5_sweep_kernel<N, PREC, MODE>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn);
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTc5MaxDynSmem);
             });
             if (e != cudaSuccess) return e;
-            if (sh.smem != tc5_smem_bytes<N>(a.wslots) || sh.smem > (size_t)kMaxDyn || sh.warps != 4)
+            if (sh.smem != tc5_smem_bytes<N>(a.wslots) || sh.smem > kTc5MaxDynSmem || sh.warps != S5::THREADS / 32)
                 return cudaErrorInvalidValue;
             ProfScope prof_(MODE == MODE_SOURCE ? KC_SOURCE : MODE == MODE_ADJOINT ? KC_ADJOINT : KC_FORWARD, st);
-            tc5_sweep_kernel<N, PREC, MODE><<<sh.blocks, 128, sh.smem, st>>>(a);
+            tc5_sweep_kernel<N, PREC, MODE><<<sh.blocks, S5::THREADS, sh.smem, st>>>(a);
             count_launch();
             return cudaGetLastError();
         } else {
@@ -644,6 +643,14 @@ struct Dispatch {
 
     static size_t tc5_smem(int wslots) {
         if constexpr (kTc5) return tc5_smem_bytes<N>(wslots);
+        else return 0;
+    }
+    static constexpr int tc5_items() {
+        if constexpr (kTc5) return Tc5Shape<N>::ITEMS;
+        else return 0;
+    }
+    static constexpr int tc5_threads() {
+        if constexpr (kTc5) return Tc5Shape<N>::THREADS;
         else return 0;
     }
 
@@ -749,11 +756,12 @@ struct Dispatch {
     }                                                                                             \
     static const NxOps kNxOpsAlt_##NN = {NN, DispatchAlt_##NN::V, false, alt_tables_##NN, alt_sweep_##NN, \
                                          alt_max_warps_##NN, alt_smem_##NN, nullptr, nullptr, nullptr, false, \
-                                         nullptr, nullptr, nullptr, nullptr, false, nullptr, nullptr};     \
+                                         nullptr, nullptr, nullptr, nullptr, false, nullptr, 0, 0, nullptr}; \
     extern const NxOps kNxOps_##NN = {NN, Dispatch<NN>::V, Dispatch<NN>::kGrad, tables_##NN, sweep_##NN,        \
                                       max_warps_##NN, smem_##NN, tables_grad_##NN, gradient_##NN,  \
                                       gradient_max_warps_##NN, Dispatch<NN>::kTc, tables_natural_##NN, \
                                       tc_sweep_##NN, tc_smem_##NN, gradient_smem_##NN,            \
                                       Dispatch<NN>::kTc5, Dispatch<NN>::tc5_smem,                  \
+                                      Dispatch<NN>::tc5_items(), Dispatch<NN>::tc5_threads(),      \
                                       alt_points_per_thread(NN) ? &kNxOpsAlt_##NN : nullptr};       \
     }

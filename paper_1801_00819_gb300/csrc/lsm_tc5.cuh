@@ -1,6 +1,6 @@
 // Depth sweeps with the lateral transforms as DFT-matrix products on the fifth-generation tensor
 // cores (tcgen05: single-thread MMAs with shared-memory operands and TMEM accumulators), a precision
-// variant of the split-step depth step (Examples section).
+// variant of the split-step depth step (Examples section), for nx = 16 R with R = 8, 16, 32, 64.
 //
 // Four-step factorisation, N = 16 R: an item's points x[R n1 + n2] form X[n1][n2] (16 x R) and
 //   forward  Y = F16 X,  Y'[k1][n2] = Y[k1][n2] w^(k1 n2),  Z = Y' F_R,  Z[k1][k2] = x^[k1 + 16 k2],
@@ -21,12 +21,13 @@
 // through conj(M conj(F)) = conj(conj(M) F): the operand is written conjugated and the accumulator
 // read back conjugated, so only F16 and F_R are kept in shared memory.
 //
-// One CTA of 128 threads runs 8 (shot, frequency) items through the whole depth loop.  The left
-// products (16-point, contraction over n1) take rows (item, n2): two tiles of 128 rows, four items
-// each, and thread t owns row t of both tiles, i.e. column n2 = t % 32 of items t / 32 and
-// 4 + t / 32; the wavefield lives in those registers between depth steps.  The right products
-// (R-point, contraction over n2) take rows (item, k1): one tile of 8 x 16 rows, thread t owns row t.
-// The passage between the two row layouts goes through the shared-memory operand tile.  One thread
+// A CTA runs ITEMS (shot, frequency) items through the whole depth loop (16 at R = 8, else 8).  The
+// left products (16-point, contraction over n1) take rows (item, n2), ITEMS R rows in 128-row tiles;
+// the right products (R-point, contraction over n2) take rows (item, k1), ITEMS 16 rows.  Each group
+// of 128 threads (one at R <= 32, two at R = 64) owns one TMEM lane per thread: thread r of a group
+// owns row r of its left tiles -- the wavefield lives in those registers between depth steps -- and
+// row r of the right tiles (at R = 64 the two groups split the right product's columns).  The
+// passage between the two row layouts goes through the shared-memory operand tiles.  One thread
 // issues the MMAs of a stage and commits them to an mbarrier that every thread waits on (bounded:
 // a wait that runs out sets the error flag, the CTA stops and writes NaN to its outputs).
 #pragma once
@@ -46,31 +47,49 @@ namespace lsm {
 // tcgen05 transform precisions (numbering continues TcPrecision)
 enum Tc5Precision { PREC_FP16X3_TC5 = 4, PREC_BF16X3_TC5 = 5 };
 
+// Widths with a tcgen05 transform: N = 16 R, R = 8 .. 64 (the right product's N = 2 R must be a
+// multiple of 16 for M = 128, and a CTA's right operand rows must fill 128-row tiles).
+constexpr bool tc5_width(int n) { return n == 128 || n == 256 || n == 512 || n == 1024; }
+
 template <int N>
 struct Tc5Shape {
-    static_assert(N == 512, "tcgen05 transforms: nx = 512");
-    static constexpr int R = N / 16;          // 32
-    static constexpr int ITEMS = 8;           // items per CTA
-    static constexpr int THREADS = 128;
+    static_assert(tc5_width(N), "tcgen05 transforms: nx = 128, 256, 512 or 1024");
+    static constexpr int R = N / 16;
+    static constexpr int ITEMS = R == 8 ? 16 : 8;     // items per CTA
+    static constexpr int GROUPS = R == 64 ? 2 : 1;    // 128-thread groups
+    static constexpr int THREADS = 128 * GROUPS;
+    static constexpr int LT = ITEMS * R / 128;        // left tiles (128 rows (item, n2) each)
+    static constexpr int LTT = LT / GROUPS;           // left tiles per thread
+    static constexpr int RT = ITEMS * 16 / 128;       // right tiles (128 rows (item, k1) each)
+    static constexpr int RCOLS = 2 * R / GROUPS;      // right-product columns per thread
+    static constexpr int RCH = RCOLS >= 32 ? 32 : RCOLS;  // columns per TMEM load of the right product
+    static constexpr int KB_R = (4 * R + 63) / 64;    // 64-element K blocks of a right operand row
+    static constexpr int LTILE = 128 * 128;           // bytes of a left tile (K = 64: hi 32 | lo 32)
+    static constexpr int RTILE = KB_R * 128 * 128;    // bytes of a right tile (K = 4 R: hi 2R | lo 2R)
     // shared memory (bytes from the 1024-aligned base): the constant B operands of the left product
-    // (32 rows x 64 K = 4 KB) and of the right product (64 rows x 128 K = 16 KB), the A operand
-    // (two 128-row K blocks: the two left tiles, or the hi and lo halves of the right tile; the
-    // adjoint's per-warp image rows use it between depth steps), the twiddles in both index orders,
-    // then the staged phase-shift and split-step rows of the CTA's frequencies: per frequency slot one
-    // 4 KB Phi row and one 4 KB D row
-    static constexpr int A_BYTES = 2 * 128 * 128;
+    // (32 rows x 64 K) and of the right product (2 R rows x 4 R K), the A operand (the left tiles or
+    // the right tiles; the adjoint's four image rows use it between depth steps), the twiddles in both
+    // index orders, then the staged phase-shift and split-step rows of the CTA's frequencies: per
+    // frequency slot one Phi row and one D row
     static constexpr int OFF_BLF = 0;
     static constexpr int OFF_BRF = OFF_BLF + 32 * 128;
-    static constexpr int OFF_A = OFF_BRF + 2 * 64 * 128;
+    static constexpr int BRF_BYTES = KB_R * 2 * R * 128;
+    static constexpr int OFF_A = (OFF_BRF + BRF_BYTES + 1023) / 1024 * 1024;
+    static constexpr int A_BYTES = LT * LTILE > RT * RTILE ? LT * LTILE : RT * RTILE;
     static constexpr int OFF_TW = OFF_A + A_BYTES;             // w^(k1 n2) as [k1][n2] float2
     static constexpr int OFF_TWT = OFF_TW + 16 * R * 8;        // the same as [n2][k1]
     static constexpr int OFF_STG = OFF_TWT + 16 * R * 8;       // [wslots][Phi row, D row]
     static constexpr int SLOT_BYTES = 2 * N * 8;
     static_assert(OFF_A % 1024 == 0, "operand tiles are 1024-byte aligned");
-    // TMEM columns: left accumulators [tile][acc][32], right accumulators [acc][64]
+    static_assert(4 * N * 4 <= A_BYTES, "the adjoint's image rows fit the operand buffer");
+    // TMEM columns: left accumulators [tile][acc][32], right accumulators [tile][acc][2R]; at R = 64
+    // both sets take the same columns (an accumulator is read out before the next product is issued)
     static constexpr uint32_t TM_L = 0;
-    static constexpr uint32_t TM_R = 128;
-    static constexpr uint32_t TM_COLS = 256;
+    static constexpr uint32_t TM_R = R == 64 ? 0 : (uint32_t)(64 * LT);
+    static constexpr uint32_t TM_NEED = R == 64 ? (uint32_t)(64 * LT) : (uint32_t)(64 * LT + 4 * R * RT);
+    static constexpr uint32_t TM_COLS = TM_NEED <= 32 ? 32 : TM_NEED <= 64 ? 64 : TM_NEED <= 128 ? 128 : 256;
+    static_assert(TM_NEED <= 256 && 4 * R * RT <= 256, "accumulators fit 256 TMEM columns");
+    static constexpr int MIN_BLOCKS = R == 64 ? 1 : 2;
 };
 
 template <int PREC>
@@ -143,7 +162,7 @@ __device__ void tc5_build_dft(unsigned char* base, int L, int sgn, int kper) {
 }
 
 // Issue the three split products of one stage: D (+)= A[k ranges] B[k ranges]; A and B are K-major
-// 128B-swizzled operands whose K axis is [hi (kper) | lo (kper)] in blocks of 64; kper = 32 or 64.
+// 128B-swizzled operands whose K axis is [hi (kper) | lo (kper)] in blocks of 64; kper a multiple of 16.
 template <int PREC>
 __device__ __forceinline__ void tc5_issue(uint32_t d0, uint32_t d1, uint32_t a_base, int a_rows, uint32_t b_base,
                                           int b_rows, int kper, uint32_t idesc) {
@@ -164,15 +183,18 @@ __device__ __forceinline__ void tc5_issue(uint32_t d0, uint32_t d1, uint32_t a_b
                       umma::desc_sw128(kaddr(b_base, b_rows, 16 * s)), idesc, true);
 }
 
+// Dynamic shared memory of a CTA whose items span `wslots` frequencies; wslots = 0: the Phi and D
+// rows are read from global memory (L2) instead of being staged.
 template <int N>
 constexpr size_t tc5_smem_bytes(int wslots) {
     return (size_t)Tc5Shape<N>::OFF_STG + (size_t)wslots * Tc5Shape<N>::SLOT_BYTES + 1024;
 }
 
-// acc0 + 2^-11 acc1 over 32 columns (FP16's two accumulators), as paired FMAs
-__device__ __forceinline__ void tc5_combine(float (&y)[32], const float (&y2)[32]) {
+// acc0 + 2^-11 acc1 over C columns (FP16's two accumulators), as paired FMAs
+template <int C>
+__device__ __forceinline__ void tc5_combine(float (&y)[C], const float (&y2)[C]) {
 #pragma unroll
-    for (int i = 0; i < 32; i += 2) {
+    for (int i = 0; i < C; i += 2) {
         const float2 v = __ffma2_rn(make_float2(y2[i], y2[i + 1]), make_float2(1.f / 2048.f, 1.f / 2048.f),
                                     make_float2(y[i], y[i + 1]));
         y[i] = v.x;
@@ -180,17 +202,38 @@ __device__ __forceinline__ void tc5_combine(float (&y)[32], const float (&y2)[32
     }
 }
 
+// C consecutive accumulator columns of this thread's lane (C = 16 or 32)
+template <int C>
+__device__ __forceinline__ void tc5_ld(uint32_t taddr, float (&v)[C]) {
+    static_assert(C == 16 || C == 32, "TMEM loads of 16 or 32 columns");
+    if constexpr (C == 32) umma::tmem_ld32(taddr, v);
+    else umma::tmem_ld16(taddr, v);
+}
+
+// the accumulator columns [col, col + C) of this lane, FP16's two accumulators combined
+template <int C, bool FP16>
+__device__ __forceinline__ void tc5_read(uint32_t taddr, uint32_t acc1_offset, float (&v)[C]) {
+    tc5_ld<C>(taddr, v);
+    if constexpr (FP16) {
+        float v2[C];
+        tc5_ld<C>(taddr + acc1_offset, v2);
+        tc5_combine<C>(v, v2);
+    }
+}
+
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p)); }
 
 template <int N, int PREC, int MODE>
-__global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
+__global__ void __launch_bounds__(Tc5Shape<N>::THREADS, Tc5Shape<N>::MIN_BLOCKS) tc5_sweep_kernel(const SweepArgs a) {
     using S = Tc5Shape<N>;
     using SP = Tc5Split<PREC>;
     constexpr bool FP16 = SP::FP16;
-    constexpr int R = S::R;
+    constexpr int R = S::R, ITEMS = S::ITEMS, LT = S::LT, LTT = S::LTT, RT = S::RT;
+    constexpr int RCOLS = S::RCOLS, RCH = S::RCH;
     extern __shared__ unsigned char tc5_smem_raw[];
     __shared__ uint64_t bar;
     __shared__ uint32_t tslot;
+    __shared__ float wmax[S::THREADS / 32][LTT];  // R = 64: each warp's maxima (an item spans two warps)
     unsigned char* base = tc5_smem_raw + ((1024u - (umma::smem_u32(tc5_smem_raw) & 1023u)) & 1023u);
     const uint32_t sbase = umma::smem_u32(base);
     float2* TW = reinterpret_cast<float2*>(base + S::OFF_TW);    // [k1][n2]
@@ -200,23 +243,26 @@ __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
     float* img = reinterpret_cast<float*>(Abuf);                 // [4][N], between depth steps only
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int grp = tid >> 7;  // 128-thread group
+    const int r = tid & 127;   // this thread's TMEM lane: row r of the tiles
     const int nitems = a.nshots * a.nw;
     const int shot0 = a.shot0_dev ? __ldg(a.shot0_dev) : a.shot0;
     const int nz = a.nz;
+    const bool staged = a.wslots > 0;
     // frequencies of the CTA's items (frequency-major item order): slots w_first .. w_last
-    const int w_first = min((int)blockIdx.x * S::ITEMS, nitems - 1) / a.nshots;
-    const int w_last = (min(((int)blockIdx.x + 1) * S::ITEMS, nitems) - 1) / a.nshots;
-    const int nslots = w_last - w_first + 1;  // <= a.wslots
+    const int w_first = min((int)blockIdx.x * ITEMS, nitems - 1) / a.nshots;
+    const int w_last = (min(((int)blockIdx.x + 1) * ITEMS, nitems) - 1) / a.nshots;
+    const int nslots = w_last - w_first + 1;  // <= a.wslots when staged
 
     // ---- set-up: constants, barrier, TMEM
     tc5_build_dft<PREC>(base + S::OFF_BLF, 16, -1, 32);
-    tc5_build_dft<PREC>(base + S::OFF_BRF, R, -1, 64);
+    tc5_build_dft<PREC>(base + S::OFF_BRF, R, -1, 2 * R);
     for (int idx = tid; idx < 16 * R; idx += blockDim.x) {
-        const int k1 = idx / R, n2 = idx % R;
+        const int k1 = idx / R, nn = idx % R;
         float sn, cs;
-        sincospif(-2.0f * (float)((k1 * n2) % N) / (float)N, &sn, &cs);
+        sincospif(-2.0f * (float)((k1 * nn) % N) / (float)N, &sn, &cs);
         TW[idx] = make_float2(cs, sn);
-        TWT[n2 * 16 + k1] = make_float2(cs, sn);
+        TWT[nn * 16 + k1] = make_float2(cs, sn);
     }
     umma::fence_smem_to_async();
     if (tid == 0) umma::mbar_init(&bar, 1);
@@ -225,32 +271,40 @@ __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
     __syncthreads();
     umma::fence_after_sync();
     const uint32_t tmem = tslot;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     uint32_t phase = 0;
     bool alive = true;
 
-    // items of this thread in the left-product layout: tile tau holds items 4 tau + warp, column n2
-    int itemL[2], iwL[2], shotL[2];
-    bool okL[2];
+    // this thread's rows of the left tiles: slot i is row r of tile grp LTT + i, i.e. column n2 of
+    // the CTA's item (128 tile + r) / R
+    const int n2 = r % R;
+    int itemL[LTT], iwL[LTT], shotL[LTT];
+    bool okL[LTT];
 #pragma unroll
-    for (int tau = 0; tau < 2; ++tau) {
-        itemL[tau] = blockIdx.x * S::ITEMS + 4 * tau + warp;
-        okL[tau] = itemL[tau] < nitems;
-        iwL[tau] = okL[tau] ? itemL[tau] / a.nshots : w_first;
-        shotL[tau] = okL[tau] ? shot0 + (itemL[tau] - iwL[tau] * a.nshots) : shot0;
+    for (int i = 0; i < LTT; ++i) {
+        itemL[i] = blockIdx.x * ITEMS + (128 * (grp * LTT + i) + r) / R;
+        okL[i] = itemL[i] < nitems;
+        iwL[i] = okL[i] ? itemL[i] / a.nshots : w_first;
+        shotL[i] = okL[i] ? shot0 + (itemL[i] - iwL[i] * a.nshots) : shot0;
     }
-    // item of this thread in the right-product layout: row t = 16 item + k1
-    const int itemR = blockIdx.x * S::ITEMS + tid / 16;
-    const int k1R = tid % 16;
-    const int iwR = itemR < nitems ? itemR / a.nshots : w_first;
-    const int n2 = lane;
+    // rows of the right tiles: row r of tile sigma is (item (128 sigma + r) / 16, k1 = r % 16); this
+    // thread reads the complex columns kb .. kb + RCOLS / 2 of it
+    const int k1R = r % 16;
+    const int kb = grp * (R / S::GROUPS);
+    int iwR[RT];
+#pragma unroll
+    for (int sg = 0; sg < RT; ++sg) {
+        const int item = blockIdx.x * ITEMS + (128 * sg + r) / 16;
+        iwR[sg] = item < nitems ? item / a.nshots : w_first;
+    }
 
-    // the wavefield: u[tau][n1] = x[R n1 + n2] of item 4 tau + warp
-    float2 u[2][16];
+    // the wavefield: u[i][n1] = x[R n1 + n2] of the item of left slot i
+    float2 u[LTT][16];
 
     // staging of the Phi (which = 0) or D (which = 1) rows of depth `row` for the CTA's frequencies,
-    // one cp.async group
+    // one cp.async group (nothing when the rows are read from global memory)
     auto stage_rows = [&](int row, int which) {
+        if (!staged) return;
         constexpr int CH = N * 8 / 16;  // 16-byte chunks per row
         for (int c = tid; c < nslots * CH; c += blockDim.x) {
             const int sl = c / CH, ch = c - sl * CH;
@@ -259,24 +313,32 @@ __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
         }
         cp_async_commit();
     };
-    auto phi_s = [&](int iw) { return reinterpret_cast<const float2*>(stg + (iw - w_first) * S::SLOT_BYTES); };
-    auto dss_s = [&](int iw) {
-        return reinterpret_cast<const float2*>(stg + (iw - w_first) * S::SLOT_BYTES + N * 8);
+    // the Phi and D rows of depth j at frequency iw
+    auto phi_s = [&](int iw, int j) -> const float2* {
+        if (staged) return reinterpret_cast<const float2*>(stg + (iw - w_first) * S::SLOT_BYTES);
+        return a.phi + ((size_t)iw * nz + j) * N;
     };
-    auto srow = [&](int tau, int jz) -> float2* {
-        const int slot = shotL[tau] % a.ring;
-        return a.S + (((size_t)slot * a.nw + iwL[tau]) * nz + jz) * (size_t)N;
+    auto dss_s = [&](int iw, int j) -> const float2* {
+        if (staged) return reinterpret_cast<const float2*>(stg + (iw - w_first) * S::SLOT_BYTES + N * 8);
+        return a.dss + ((size_t)iw * nz + j) * N;
     };
-    // the source-wavefield rows of depth jz of all eight items into L2 (two 128-byte lines a thread)
+    auto srow = [&](int i, int jz) -> float2* {
+        const int slot = shotL[i] % a.ring;
+        return a.S + (((size_t)slot * a.nw + iwL[i]) * nz + jz) * (size_t)N;
+    };
+    // the source-wavefield rows of depth jz of all the CTA's items into L2, one 128-byte line at a time
     auto prefetch_srows = [&](int jz) {
-        const int item = blockIdx.x * S::ITEMS + tid / 16;
-        if (item < nitems && jz >= 0 && jz < nz) {
-            const int iw = item / a.nshots;
-            const int slot = (shot0 + item - iw * a.nshots) % a.ring;
-            const unsigned char* row =
-                reinterpret_cast<const unsigned char*>(a.S + (((size_t)slot * a.nw + iw) * nz + jz) * (size_t)N);
-            prefetch_l2(row + (tid % 16) * 256);
-            prefetch_l2(row + (tid % 16) * 256 + 128);
+        constexpr int LINES = N * 8 / 128;
+        if (jz < 0 || jz >= nz) return;
+        for (int l = tid; l < ITEMS * LINES; l += blockDim.x) {
+            const int item = blockIdx.x * ITEMS + l / LINES;
+            if (item < nitems) {
+                const int iw = item / a.nshots;
+                const int slot = (shot0 + item - iw * a.nshots) % a.ring;
+                const unsigned char* row =
+                    reinterpret_cast<const unsigned char*>(a.S + (((size_t)slot * a.nw + iw) * nz + jz) * (size_t)N);
+                prefetch_l2(row + (l % LINES) * 128);
+            }
         }
     };
 
@@ -290,181 +352,181 @@ __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
         if (all) phase ^= 1u;
         return all;
     };
-    constexpr uint32_t IDESC_L = umma::idesc_f16(!FP16, 128, 32);
-    constexpr uint32_t IDESC_R = umma::idesc_f16(!FP16, 128, 64);
-
-    // One depth step on u: F^-1 (phi . F u) (conj(phi) when conj_phi) with the staged Phi row of this
-    // step.  Staging: the D row d_row (>= 0) is requested after the first barrier and the Phi row
-    // phi_next (>= 0) of the next step once this step's Phi row has been read; every staged row has
-    // landed and is visible to all threads when the step returns.
-    auto transform_step = [&](bool conj_phi, int d_row, int phi_next) -> bool {
-        // FP16: per-item power-of-two scale (the item is this warp's 32 lanes in each tile)
-        int ex[2] = {0, 0};
-        if constexpr (FP16) {
-#pragma unroll
-            for (int tau = 0; tau < 2; ++tau) {
-                float mx = 0.f;
-#pragma unroll
-                for (int n1 = 0; n1 < 16; ++n1) mx = fmaxf(mx, fmaxf(fabsf(u[tau][n1].x), fabsf(u[tau][n1].y)));
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-                if (mx > 0.f && mx <= 3.0e38f) frexpf(mx, &ex[tau]);
-                ex[tau] = max(-100, min(ex[tau], 100));
-                const float down = ldexpf(1.f, -ex[tau]);
-#pragma unroll
-                for (int n1 = 0; n1 < 16; ++n1) u[tau][n1] = __fmul2_rn(u[tau][n1], make_float2(down, down));
-            }
-        }
-        // (1) left operand tiles: row t, K = [hi: (re, im) of n1 = 0..15 | lo: same]
-#pragma unroll
-        for (int tau = 0; tau < 2; ++tau) {
-            unsigned char* tile = Abuf + tau * 16384;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {  // chunk c: n1 = 4c .. 4c+3
-                uint32_t h[4], l[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) SP::split(u[tau][4 * c + q].x, u[tau][4 * c + q].y, h[q], l[q]);
-                *reinterpret_cast<uint4*>(tile + umma::sw128_offset(tid, 8 * c)) = make_uint4(h[0], h[1], h[2], h[3]);
-                *reinterpret_cast<uint4*>(tile + umma::sw128_offset(tid, 32 + 8 * c)) =
-                    make_uint4(l[0], l[1], l[2], l[3]);
-            }
-        }
+    // operand writes visible to the tensor core, then one thread issues a stage's products
+    auto issue_left = [&]() {
         umma::fence_smem_to_async();
         umma::fence_before_sync();
         __syncthreads();
         if (tid == 0) {
             umma::fence_after_sync();
+            constexpr uint32_t IDESC_L = umma::idesc_f16(!FP16, 128, 32);
 #pragma unroll
-            for (int tau = 0; tau < 2; ++tau)
+            for (int tau = 0; tau < LT; ++tau)
                 tc5_issue<PREC>(tmem + S::TM_L + tau * 64, tmem + S::TM_L + tau * 64 + 32,
-                                sbase + S::OFF_A + tau * 16384, 128, sbase + S::OFF_BLF, 32, 32, IDESC_L);
+                                sbase + S::OFF_A + tau * S::LTILE, 128, sbase + S::OFF_BLF, 32, 32, IDESC_L);
             umma::mma_commit(&bar);
         }
+    };
+    auto issue_right = [&]() {
+        umma::fence_smem_to_async();
+        umma::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            umma::fence_after_sync();
+            constexpr uint32_t IDESC_R = umma::idesc_f16(!FP16, 128, 2 * R);
+#pragma unroll
+            for (int sg = 0; sg < RT; ++sg)
+                tc5_issue<PREC>(tmem + S::TM_R + sg * 4 * R, tmem + S::TM_R + sg * 4 * R + 2 * R,
+                                sbase + S::OFF_A + sg * S::RTILE, 128, sbase + S::OFF_BRF, 2 * R, 2 * R, IDESC_R);
+            umma::mma_commit(&bar);
+        }
+    };
+    // 32-bit (re, im) pair / 16-byte chunk of K elements at element e of row rr of the tile at `tile`
+    auto kput32 = [](unsigned char* tile, int rr, int e, uint32_t v) {
+        *reinterpret_cast<uint32_t*>(tile + (e / 64) * (128 * 128) + umma::sw128_offset(rr, e % 64)) = v;
+    };
+    auto kput128 = [](unsigned char* tile, int rr, int e, uint4 v) {
+        *reinterpret_cast<uint4*>(tile + (e / 64) * (128 * 128) + umma::sw128_offset(rr, e % 64)) = v;
+    };
+
+    // One depth step on u: F^-1 (phi . F u) (conj(phi) when conj_phi) with the Phi row of depth j.
+    // Staging: the D row d_row (>= 0) is requested after the first barrier and the Phi row phi_next
+    // (>= 0) of the next step once this step's Phi row has been read; every staged row has landed and
+    // is visible to all threads when the step returns.
+    auto transform_step = [&](bool conj_phi, int j, int d_row, int phi_next) -> bool {
+        // FP16: per-item power-of-two scale (an item is R consecutive rows of a left tile: R lanes of
+        // a warp up to R = 32, two warps at R = 64)
+        int ex[LTT];
+#pragma unroll
+        for (int i = 0; i < LTT; ++i) ex[i] = 0;
+        if constexpr (FP16) {
+            float mx[LTT];
+#pragma unroll
+            for (int i = 0; i < LTT; ++i) {
+                mx[i] = 0.f;
+#pragma unroll
+                for (int n1 = 0; n1 < 16; ++n1) mx[i] = fmaxf(mx[i], fmaxf(fabsf(u[i][n1].x), fabsf(u[i][n1].y)));
+#pragma unroll
+                for (int o = (R < 32 ? R : 32) / 2; o > 0; o >>= 1)
+                    mx[i] = fmaxf(mx[i], __shfl_xor_sync(0xffffffffu, mx[i], o));
+            }
+            if constexpr (R == 64) {
+                if (lane == 0) {
+#pragma unroll
+                    for (int i = 0; i < LTT; ++i) wmax[warp][i] = mx[i];
+                }
+                __syncthreads();
+#pragma unroll
+                for (int i = 0; i < LTT; ++i) mx[i] = fmaxf(mx[i], wmax[warp ^ 1][i]);
+            }
+#pragma unroll
+            for (int i = 0; i < LTT; ++i) {
+                if (mx[i] > 0.f && mx[i] <= 3.0e38f) frexpf(mx[i], &ex[i]);
+                ex[i] = max(-100, min(ex[i], 100));
+                const float down = ldexpf(1.f, -ex[i]);
+#pragma unroll
+                for (int n1 = 0; n1 < 16; ++n1) u[i][n1] = __fmul2_rn(u[i][n1], make_float2(down, down));
+            }
+        }
+        // (1) left operand tiles: row r, K = [hi: (re, im) of n1 = 0..15 | lo: same]
+#pragma unroll
+        for (int i = 0; i < LTT; ++i) {
+            unsigned char* tile = Abuf + (grp * LTT + i) * S::LTILE;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {  // chunk c: n1 = 4c .. 4c+3
+                uint32_t h[4], l[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) SP::split(u[i][4 * c + q].x, u[i][4 * c + q].y, h[q], l[q]);
+                kput128(tile, r, 8 * c, make_uint4(h[0], h[1], h[2], h[3]));
+                kput128(tile, r, 32 + 8 * c, make_uint4(l[0], l[1], l[2], l[3]));
+            }
+        }
+        issue_left();
         if (d_row >= 0) stage_rows(d_row, 1);
         if (!stage_wait()) return false;
-        // (2) Y[k1][n2] of both tiles -> twiddle -> right operand rows (item, k1), K = 2 n2 + q
+        // (2) Y[k1][n2] of this thread's left rows -> twiddle -> right operand rows (item, k1),
+        // K = 2 n2 + q
 #pragma unroll
-        for (int tau = 0; tau < 2; ++tau) {
+        for (int i = 0; i < LTT; ++i) {
+            const int tau = grp * LTT + i;
             float y[32];
-            umma::tmem_ld32(tmem + lane_base + S::TM_L + tau * 64, y);
-            if constexpr (FP16) {
-                float y2[32];
-                umma::tmem_ld32(tmem + lane_base + S::TM_L + tau * 64 + 32, y2);
-                tc5_combine(y, y2);
-            }
-            const int row0 = (4 * tau + warp) * 16;
+            tc5_read<32, FP16>(tmem + lane_base + S::TM_L + tau * 64, 32, y);
+            const int item_local = (128 * tau + r) / R;
 #pragma unroll
             for (int k1 = 0; k1 < 16; ++k1) {
                 const float2 v = cmul(make_float2(y[2 * k1], y[2 * k1 + 1]), TW[k1 * R + n2]);
                 uint32_t h, l;
                 SP::split(v.x, v.y, h, l);
-                *reinterpret_cast<uint32_t*>(Abuf + umma::sw128_offset(row0 + k1, 2 * n2)) = h;
-                *reinterpret_cast<uint32_t*>(Abuf + 16384 + umma::sw128_offset(row0 + k1, 2 * n2)) = l;
+                const int rho = item_local * 16 + k1;
+                unsigned char* tile = Abuf + (rho >> 7) * S::RTILE;
+                kput32(tile, rho & 127, 2 * n2, h);
+                kput32(tile, rho & 127, 2 * R + 2 * n2, l);
             }
         }
         cp_async_wait_all();  // this step's Phi row (requested a step earlier) has landed
-        umma::fence_smem_to_async();
-        umma::fence_before_sync();
-        __syncthreads();
-        if (tid == 0) {
-            umma::fence_after_sync();
-            tc5_issue<PREC>(tmem + S::TM_R, tmem + S::TM_R + 64, sbase + S::OFF_A, 128, sbase + S::OFF_BRF, 64, 64,
-                            IDESC_R);
-            umma::mma_commit(&bar);
-        }
+        issue_right();
         if (!stage_wait()) return false;
-        // (3) Z[k1][k2] (row t) -> phase shift -> right operand of the inverse (conjugated), same rows
-        {
-            const float2* prow = phi_s(iwR);
+        // (3) Z[k1][k2] (row r of each right tile, columns kb ..) -> phase shift -> right operand of
+        // the inverse (conjugated), same rows
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {  // k2 = 16 half .. 16 half + 15
-                float z[32];
-                umma::tmem_ld32(tmem + lane_base + S::TM_R + 32 * half, z);
-                if constexpr (FP16) {
-                    float z2[32];
-                    umma::tmem_ld32(tmem + lane_base + S::TM_R + 64 + 32 * half, z2);
-                    tc5_combine(z, z2);
-                }
+        for (int sg = 0; sg < RT; ++sg) {
+            const float2* prow = phi_s(iwR[sg], j);
+            unsigned char* tile = Abuf + sg * S::RTILE;
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {  // chunk: k2 = 16 half + 4 c .. + 3
+            for (int h0 = 0; h0 < RCOLS / RCH; ++h0) {
+                float z[RCH];
+                tc5_read<RCH, FP16>(tmem + lane_base + S::TM_R + sg * 4 * R + 2 * kb + h0 * RCH, 2 * R, z);
+#pragma unroll
+                for (int c = 0; c < RCH / 8; ++c) {  // chunk: 4 complex columns
+                    const int k20 = kb + h0 * (RCH / 2) + 4 * c;
                     uint32_t h[4], l[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const int k2l = 4 * c + q;
-                        const float2 p = prow[k1R + 16 * (16 * half + k2l)];
-                        const float2 zz = make_float2(z[2 * k2l], z[2 * k2l + 1]);
+                        const float2 p = prow[k1R + 16 * (k20 + q)];
+                        const float2 zz = make_float2(z[2 * (4 * c + q)], z[2 * (4 * c + q) + 1]);
                         const float2 v = conj_phi ? cmulc(zz, p) : cmul(zz, p);
                         SP::split(v.x, -v.y, h[q], l[q]);  // conjugated: the inverse runs on F_R
                     }
-                    const int kel = 32 * half + 8 * c;  // K element of the chunk within the hi block
-                    *reinterpret_cast<uint4*>(Abuf + umma::sw128_offset(tid, kel)) = make_uint4(h[0], h[1], h[2], h[3]);
-                    *reinterpret_cast<uint4*>(Abuf + 16384 + umma::sw128_offset(tid, kel)) =
-                        make_uint4(l[0], l[1], l[2], l[3]);
+                    kput128(tile, r, 2 * k20, make_uint4(h[0], h[1], h[2], h[3]));
+                    kput128(tile, r, 2 * R + 2 * k20, make_uint4(l[0], l[1], l[2], l[3]));
                 }
             }
         }
-        umma::fence_smem_to_async();
-        umma::fence_before_sync();
-        __syncthreads();
-        if (tid == 0) {
-            umma::fence_after_sync();
-            tc5_issue<PREC>(tmem + S::TM_R, tmem + S::TM_R + 64, sbase + S::OFF_A, 128, sbase + S::OFF_BRF, 64, 64,
-                            IDESC_R);
-            umma::mma_commit(&bar);
-        }
+        issue_right();
         if (phi_next >= 0) stage_rows(phi_next, 0);  // this step's Phi row has been read
         if (!stage_wait()) return false;
-        // (4) the accumulator holds conj(Y2) for Y2 = Z conj(F_R) (row t = (item, k1), columns n2); the
+        // (4) the accumulator holds conj(Y2) for Y2 = Z conj(F_R) (rows (item, k1), columns n2); the
         // inverse left product takes conj(Y2 w^-(k1 n2)) = conj(Y2) w^(k1 n2), rows (item, n2), K = 2 k1 + q
-        {
-            const int item_local = tid / 16;
-            unsigned char* tile = Abuf + (item_local / 4) * 16384;
-            const int rowb = (item_local % 4) * 32;
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {  // n2 = 16 half .. 16 half + 15
-                float y[32];
-                umma::tmem_ld32(tmem + lane_base + S::TM_R + 32 * half, y);
-                if constexpr (FP16) {
-                    float y2[32];
-                    umma::tmem_ld32(tmem + lane_base + S::TM_R + 64 + 32 * half, y2);
-                    tc5_combine(y, y2);
-                }
+        for (int sg = 0; sg < RT; ++sg) {
+            const int item_local = (128 * sg + r) / 16;
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int nn = 16 * half + i;
-                    const float2 v = cmul(make_float2(y[2 * i], y[2 * i + 1]), TWT[nn * 16 + k1R]);
+            for (int h0 = 0; h0 < RCOLS / RCH; ++h0) {
+                float y[RCH];
+                tc5_read<RCH, FP16>(tmem + lane_base + S::TM_R + sg * 4 * R + 2 * kb + h0 * RCH, 2 * R, y);
+#pragma unroll
+                for (int q = 0; q < RCH / 2; ++q) {
+                    const int nn = kb + h0 * (RCH / 2) + q;
+                    const float2 v = cmul(make_float2(y[2 * q], y[2 * q + 1]), TWT[nn * 16 + k1R]);
                     uint32_t h, l;
                     SP::split(v.x, v.y, h, l);
-                    *reinterpret_cast<uint32_t*>(tile + umma::sw128_offset(rowb + nn, 2 * k1R)) = h;
-                    *reinterpret_cast<uint32_t*>(tile + umma::sw128_offset(rowb + nn, 32 + 2 * k1R)) = l;
+                    const int rho = item_local * R + nn;
+                    unsigned char* tile = Abuf + (rho >> 7) * S::LTILE;
+                    kput32(tile, rho & 127, 2 * k1R, h);
+                    kput32(tile, rho & 127, 32 + 2 * k1R, l);
                 }
             }
         }
-        umma::fence_smem_to_async();
-        umma::fence_before_sync();
-        __syncthreads();
-        if (tid == 0) {
-            umma::fence_after_sync();
-#pragma unroll
-            for (int tau = 0; tau < 2; ++tau)
-                tc5_issue<PREC>(tmem + S::TM_L + tau * 64, tmem + S::TM_L + tau * 64 + 32,
-                                sbase + S::OFF_A + tau * 16384, 128, sbase + S::OFF_BLF, 32, 32, IDESC_L);
-            umma::mma_commit(&bar);
-        }
+        issue_left();
         if (!stage_wait()) return false;
-        // (5) x'[R n1 + n2] = conj(accumulator) of both tiles back into the registers
+        // (5) x'[R n1 + n2] = conj(accumulator) of this thread's left rows back into the registers
 #pragma unroll
-        for (int tau = 0; tau < 2; ++tau) {
+        for (int i = 0; i < LTT; ++i) {
             float x[32];
-            umma::tmem_ld32(tmem + lane_base + S::TM_L + tau * 64, x);
-            if constexpr (FP16) {
-                float x2[32];
-                umma::tmem_ld32(tmem + lane_base + S::TM_L + tau * 64 + 32, x2);
-                tc5_combine(x, x2);
-            }
-            const float up = FP16 ? ldexpf(1.f, ex[tau]) : 1.f;
+            tc5_read<32, FP16>(tmem + lane_base + S::TM_L + (grp * LTT + i) * 64, 32, x);
+            const float up = FP16 ? ldexpf(1.f, ex[i]) : 1.f;
 #pragma unroll
-            for (int n1 = 0; n1 < 16; ++n1) u[tau][n1] = make_float2(x[2 * n1] * up, -x[2 * n1 + 1] * up);
+            for (int n1 = 0; n1 < 16; ++n1) u[i][n1] = make_float2(x[2 * n1] * up, -x[2 * n1 + 1] * up);
         }
         cp_async_wait_all();  // the rows staged during this step have landed
         umma::fence_before_sync();
@@ -472,14 +534,14 @@ __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
         return true;
     };
 
-    auto mul_d = [&](bool conj) {
+    auto mul_d = [&](bool conj, int j) {
 #pragma unroll
-        for (int tau = 0; tau < 2; ++tau) {
-            const float2* drow = dss_s(iwL[tau]);
+        for (int i = 0; i < LTT; ++i) {
+            const float2* drow = dss_s(iwL[i], j);
 #pragma unroll
             for (int n1 = 0; n1 < 16; ++n1) {
                 const float2 dd = drow[R * n1 + n2];
-                u[tau][n1] = conj ? cmulc(u[tau][n1], dd) : cmul(u[tau][n1], dd);
+                u[i][n1] = conj ? cmulc(u[i][n1], dd) : cmul(u[i][n1], dd);
             }
         }
     };
@@ -487,37 +549,37 @@ __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
     if constexpr (MODE == MODE_SOURCE) {
         // step j (0 .. nz-2) propagates S_j to S_{j+1} with the rows of depth j
 #pragma unroll
-        for (int tau = 0; tau < 2; ++tau) {
-            const int xs = okL[tau] ? __ldg(a.src_ix + shotL[tau]) : -1;
-            const float2 w = okL[tau] ? __ldg(a.wavelet + iwL[tau]) : make_float2(0.f, 0.f);
+        for (int i = 0; i < LTT; ++i) {
+            const int xs = okL[i] ? __ldg(a.src_ix + shotL[i]) : -1;
+            const float2 w = okL[i] ? __ldg(a.wavelet + iwL[i]) : make_float2(0.f, 0.f);
 #pragma unroll
-            for (int n1 = 0; n1 < 16; ++n1) u[tau][n1] = (R * n1 + n2 == xs) ? w : make_float2(0.f, 0.f);
+            for (int n1 = 0; n1 < 16; ++n1) u[i][n1] = (R * n1 + n2 == xs) ? w : make_float2(0.f, 0.f);
         }
         if (nz > 1) stage_rows(0, 0);
         cp_async_wait_all();
         __syncthreads();
         for (int jz = 0; jz < nz; ++jz) {
 #pragma unroll
-            for (int tau = 0; tau < 2; ++tau)
-                if (okL[tau]) {
-                    float2* row = srow(tau, jz);
+            for (int i = 0; i < LTT; ++i)
+                if (okL[i]) {
+                    float2* row = srow(i, jz);
 #pragma unroll
                     for (int n1 = 0; n1 < 16; ++n1)
-                        __stcs(row + R * n1 + n2, alive ? u[tau][n1] : make_float2(NAN, NAN));
+                        __stcs(row + R * n1 + n2, alive ? u[i][n1] : make_float2(NAN, NAN));
                 }
             if (jz + 1 < nz && alive) {
-                alive = transform_step(false, jz, jz + 2 < nz ? jz + 1 : -1);
-                mul_d(false);
+                alive = transform_step(false, jz, jz, jz + 2 < nz ? jz + 1 : -1);
+                mul_d(false, jz);
             }
         }
     } else if constexpr (MODE == MODE_ADJOINT) {
         // step j (0 .. nz-2): image term of depth j, then R_{j+1} = P_j^H R_j with the rows of depth j
         // (receivers at every column: the tensor-core variants take no receiver list)
 #pragma unroll
-        for (int tau = 0; tau < 2; ++tau) {
-            const float2* drow = a.din + ((size_t)(shotL[tau] - shot0) * a.nw + iwL[tau]) * a.nrec;
+        for (int i = 0; i < LTT; ++i) {
+            const float2* drow = a.din + ((size_t)(shotL[i] - shot0) * a.nw + iwL[i]) * a.nrec;
 #pragma unroll
-            for (int n1 = 0; n1 < 16; ++n1) u[tau][n1] = okL[tau] ? __ldcs(drow + R * n1 + n2) : make_float2(0.f, 0.f);
+            for (int n1 = 0; n1 < 16; ++n1) u[i][n1] = okL[i] ? __ldcs(drow + R * n1 + n2) : make_float2(0.f, 0.f);
         }
         if (nz > 1) {
             stage_rows(0, 0);
@@ -526,23 +588,33 @@ __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
         cp_async_wait_all();
         __syncthreads();
         float* part = a.part + (size_t)blockIdx.x * nz * N;
+        // image row slot of this warp: four slots, each covering every column once
+        const int islot = R == 64 ? warp >> 1 : warp;
         for (int jz = 0; jz < nz; ++jz) {
             float c[16];
 #pragma unroll
             for (int n1 = 0; n1 < 16; ++n1) c[n1] = 0.f;
 #pragma unroll
-            for (int tau = 0; tau < 2; ++tau)
-                if (okL[tau]) {
-                    const float2* row = srow(tau, jz);
+            for (int i = 0; i < LTT; ++i)
+                if (okL[i]) {
+                    const float2* row = srow(i, jz);
 #pragma unroll
                     for (int n1 = 0; n1 < 16; ++n1) {
                         const float2 s = __ldcs(row + R * n1 + n2);
-                        c[n1] += fmaf(s.x, u[tau][n1].x, s.y * u[tau][n1].y);
+                        c[n1] += fmaf(s.x, u[i][n1].x, s.y * u[i][n1].y);
                     }
                 }
             prefetch_srows(jz + 1);
+            // below R = 32 a warp holds 32 / R items: lanes of equal n2 are summed first
 #pragma unroll
-            for (int n1 = 0; n1 < 16; ++n1) img[warp * N + R * n1 + n2] = alive ? c[n1] : NAN;
+            for (int off = R; off < 32; off <<= 1) {
+#pragma unroll
+                for (int n1 = 0; n1 < 16; ++n1) c[n1] += __shfl_xor_sync(0xffffffffu, c[n1], off);
+            }
+            if (R >= 32 || lane < R) {
+#pragma unroll
+                for (int n1 = 0; n1 < 16; ++n1) img[islot * N + R * n1 + n2] = alive ? c[n1] : NAN;
+            }
             __syncthreads();
             {
                 const float4* rows4 = reinterpret_cast<const float4*>(img);
@@ -562,46 +634,46 @@ __global__ void __launch_bounds__(128, 2) tc5_sweep_kernel(const SweepArgs a) {
             }
             __syncthreads();  // the image rows (in the operand buffer) are read before it is rewritten
             if (jz + 1 < nz && alive) {
-                mul_d(true);
+                mul_d(true, jz);
                 // the next step's D row is requested once this one has been applied
-                alive = transform_step(true, jz + 2 < nz ? jz + 1 : -1, jz + 2 < nz ? jz + 1 : -1);
+                alive = transform_step(true, jz, jz + 2 < nz ? jz + 1 : -1, jz + 2 < nz ? jz + 1 : -1);
             }
         }
     } else {  // MODE_FORWARD
         // U_j = P_j U_{j+1} + S_j m_j from the deepest row up; step k = nz-2-j uses the rows of depth j
 #pragma unroll
-        for (int tau = 0; tau < 2; ++tau)
+        for (int i = 0; i < LTT; ++i)
 #pragma unroll
-            for (int n1 = 0; n1 < 16; ++n1) u[tau][n1] = make_float2(0.f, 0.f);
+            for (int n1 = 0; n1 < 16; ++n1) u[i][n1] = make_float2(0.f, 0.f);
         if (nz > 1) stage_rows(nz - 2, 0);
         cp_async_wait_all();
         __syncthreads();
         for (int jz = nz - 1; jz >= 0; --jz) {
             prefetch_srows(jz);
             if (jz + 1 < nz && alive) {
-                alive = transform_step(false, jz, jz >= 1 ? jz - 1 : -1);
-                mul_d(false);
+                alive = transform_step(false, jz, jz, jz >= 1 ? jz - 1 : -1);
+                mul_d(false, jz);
             }
             const float* mrow = a.m + (size_t)jz * N;
 #pragma unroll
-            for (int tau = 0; tau < 2; ++tau)
-                if (okL[tau]) {
-                    const float2* row = srow(tau, jz);
+            for (int i = 0; i < LTT; ++i)
+                if (okL[i]) {
+                    const float2* row = srow(i, jz);
 #pragma unroll
                     for (int n1 = 0; n1 < 16; ++n1) {
                         const float2 s = __ldcs(row + R * n1 + n2);
                         const float mm = __ldg(mrow + R * n1 + n2);
-                        u[tau][n1].x = fmaf(s.x, mm, u[tau][n1].x);
-                        u[tau][n1].y = fmaf(s.y, mm, u[tau][n1].y);
+                        u[i][n1].x = fmaf(s.x, mm, u[i][n1].x);
+                        u[i][n1].y = fmaf(s.y, mm, u[i][n1].y);
                     }
                 }
         }
 #pragma unroll
-        for (int tau = 0; tau < 2; ++tau)
-            if (okL[tau]) {
-                float2* orow = a.dout + ((size_t)(shotL[tau] - shot0) * a.nw + iwL[tau]) * a.nrec;
+        for (int i = 0; i < LTT; ++i)
+            if (okL[i]) {
+                float2* orow = a.dout + ((size_t)(shotL[i] - shot0) * a.nw + iwL[i]) * a.nrec;
 #pragma unroll
-                for (int n1 = 0; n1 < 16; ++n1) orow[R * n1 + n2] = alive ? u[tau][n1] : make_float2(NAN, NAN);
+                for (int n1 = 0; n1 < 16; ++n1) orow[R * n1 + n2] = alive ? u[i][n1] : make_float2(NAN, NAN);
             }
     }
 

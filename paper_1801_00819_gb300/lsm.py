@@ -35,7 +35,7 @@ EXPORTED = ("lsm_workspace_bytes", "lsm_forward", "lsm_adjoint", "lsm_num_window
             "lsm_adjoint_static", "lsm_born_gradient", "rls_window_solve_ex", "rls_multi_line_solve",
             "lsm_forward_ex", "lsm_adjoint_ex", "lsm_profile_start_classes", "lsm_autotune",
             "lsm_autotune_reset", "lsm_autotune_gradient", "lsm_measure_fp32_peak",
-            "lsm_check_bounded_wait", "rls_window_solve_sharded", "lsm_fft_tiles", "lsm_set_fft_tile")
+            "lsm_check_bounded_wait", "rls_window_solve_sharded", "lsm_fft_tiles", "lsm_set_fft_tile", "lsm_tcgen05_shape")
 
 TRANSFORMS = {"fft": 0, "dft_bf16x3": 1, "dft_fp16x3": 2, "dft_bf16x1": 3, "dft_fp16x3_tcgen05": 4,
               "dft_bf16x3_tcgen05": 5}
@@ -198,6 +198,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lsm_fft_tiles.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int]
     lib.lsm_set_fft_tile.restype = ctypes.c_int
     lib.lsm_set_fft_tile.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.lsm_tcgen05_shape.restype = ctypes.c_int
+    lib.lsm_tcgen05_shape.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int] + \
+        [ctypes.POINTER(ctypes.c_int)] * 4 + [ctypes.POINTER(ctypes.c_size_t)]
     lib.lsm_autotune_reset.restype = None
     lib.lsm_autotune_reset.argtypes = []
     lib.lsm_status_string.restype = ctypes.c_char_p
@@ -520,6 +523,16 @@ def lsm_fft_tiles(nx: int) -> list:
     buf = (ctypes.c_int * 2)()
     n = load_library().lsm_fft_tiles(int(nx), buf, 2)
     return [int(buf[i]) for i in range(min(n, 2))]
+
+
+def lsm_tcgen05_shape(nx: int, nshots: int, nw: int) -> dict:
+    """Launch shape of the tcgen05 transform variants for nshots x nw items of width nx (host only)."""
+    v = [ctypes.c_int() for _ in range(4)]
+    smem = ctypes.c_size_t()
+    _check(load_library().lsm_tcgen05_shape(int(nx), int(nshots), int(nw), *[ctypes.byref(x) for x in v],
+                                            ctypes.byref(smem)), "lsm_tcgen05_shape")
+    return {"items": v[0].value, "threads": v[1].value, "blocks": v[2].value, "wslots": v[3].value,
+            "smem_bytes": int(smem.value)}
 
 
 def lsm_set_fft_tile(nx: int, nshots: int, nw: int, points_per_thread: int) -> None:

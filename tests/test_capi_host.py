@@ -39,7 +39,8 @@ def test_header_declares_expected_entry_points():
                                             "lsm_forward_ex", "lsm_adjoint_ex", "lsm_profile_start_classes",
                                             "lsm_autotune", "lsm_autotune_reset", "lsm_autotune_gradient",
                                             "lsm_measure_fp32_peak", "lsm_check_bounded_wait",
-                                            "rls_window_solve_sharded", "lsm_fft_tiles", "lsm_set_fft_tile"])
+                                            "rls_window_solve_sharded", "lsm_fft_tiles", "lsm_set_fft_tile",
+                                            "lsm_tcgen05_shape"])
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -247,3 +248,26 @@ def test_gradient_stride_tuning_validation_before_any_launch(lib):
     assert ei.value.status == lib.LSM_ERR_WORKSPACE
     lib.lsm_autotune_reset()
     assert lib.lsm_kernel_launches() == before
+
+
+def test_tcgen05_launch_shapes(lib):
+    """The tcgen05 variants' launch shape per width (host only): items and threads per CTA, CTAs,
+    and the fall-back to unstaged Phi and D rows when a CTA's frequencies would not fit its shared
+    memory (nx = 1024 windows of one or two shots)."""
+    for nx, items, threads in ((128, 16, 128), (256, 8, 128), (512, 8, 128), (1024, 8, 256)):
+        sh = lib.lsm_tcgen05_shape(nx, 16, 128)
+        assert (sh["items"], sh["threads"]) == (items, threads)
+        assert sh["blocks"] == (16 * 128 + items - 1) // items and sh["wslots"] == 2
+        assert sh["smem_bytes"] <= 227 * 1024 - 1024
+    assert lib.lsm_tcgen05_shape(1024, 3, 10)["wslots"] == 4
+    assert lib.lsm_tcgen05_shape(1024, 2, 10)["wslots"] == 0
+    assert lib.lsm_tcgen05_shape(1024, 1, 10)["wslots"] == 0
+    assert lib.lsm_tcgen05_shape(512, 1, 10)["wslots"] == 9
+    assert lib.lsm_tcgen05_shape(128, 1, 40)["wslots"] == 17
+    assert lib.lsm_tcgen05_shape(512, 2, 3)["wslots"] == 3  # at most nw
+    for nx in (64, 384, 2048):
+        with pytest.raises(lib.LsmError) as ei:
+            lib.lsm_tcgen05_shape(nx, 4, 4)
+        assert ei.value.status == lib.LSM_ERR_UNSUPPORTED_NX
+    with pytest.raises(lib.LsmError):
+        lib.lsm_tcgen05_shape(512, 0, 4)

@@ -3,10 +3,12 @@ products issued with tcgen05.mma (operands in shared memory, FP32 accumulators i
 split FP16 and split BF16 three-term products, against the FP64 oracle.
 
 Bounds are the precision study's: split FP16 x3 within the float32 bar 1e-4, split BF16 x3 1e-3.
-The kernels take nx = 512 (the realistic workload's width); cases cover a ragged item count (items
-that do not fill the last CTA's eight rows), the precision workload's construction at 512 x 64, the
-realistic window at full size on sampled items, scale invariance of the FP16 block scale, and the
-sliding solve.
+The kernels take nx = 128, 256, 512 and 1024 (16 items per CTA at 128, 8 above; two 128-thread
+groups at 1024).  Cases cover ragged item counts (items that do not fill the last CTA), the
+precision workload's 128 x 64 subsample and its construction at 512 x 64, nx = 1024 with the Phi
+and D rows staged in shared memory and read from global memory (windows of one or two shots), the
+realistic window and the precision workload's 1024 x 512 window at full size on sampled items, scale
+invariance of the FP16 block scale, and the sliding solve.
 """
 
 import json
@@ -21,6 +23,10 @@ from tests._helpers import device_survey, oracle_operator, rel_l2
 pytestmark = pytest.mark.gpu
 
 BOUNDS = {"dft_fp16x3_tcgen05": 1e-4, "dft_bf16x3_tcgen05": 1e-3}
+# 512 depth steps of 1024 columns: the split products' errors accumulate over four products per step
+# (measured: FP16 x3 2.2e-4 and BF16 x3 4.7e-4 on the worst sampled item, the same for the mma.sync
+# form of each precision; the FP32 FFT 5.3e-5)
+FULL_SIZE_BOUNDS = {"dft_fp16x3_tcgen05": 5e-4, "dft_bf16x3_tcgen05": 1e-3}
 
 
 @pytest.fixture(scope="module")
@@ -45,13 +51,21 @@ def _run(torch, ds, m, d, shot0, nshots, transform):
     return out.cpu().numpy().astype(np.complex128), img.cpu().numpy().astype(np.float64)
 
 
+OPERATOR_CASES = {
+    "subsample128": lambda: config_precision_subsample(128),   # 128 x 64, 60 items: 4 CTAs of 16, last 12
+    "subsample512": lambda: config_precision_subsample(512),   # 512 x 64, 60 items: 8 CTAs of 8, last 4
+    "ragged128": lambda: random_case(128, 20, 3, 7, seed=510),  # 21 items: the second CTA holds 5
+    "ragged256": lambda: random_case(256, 20, 3, 5, seed=511),  # 15 items: the second CTA holds 7
+    "ragged512": lambda: random_case(512, 24, 3, 5, seed=512),
+    "staged1024": lambda: random_case(1024, 16, 3, 5, seed=514),  # 3 shots: rows staged (4 slots)
+    "direct1024": lambda: random_case(1024, 12, 2, 5, seed=517),  # 2 shots: rows read from global memory
+}
+
+
 @pytest.mark.parametrize("transform", list(BOUNDS))
-@pytest.mark.parametrize("case", ["subsample", "ragged"])
+@pytest.mark.parametrize("case", list(OPERATOR_CASES))
 def test_tcgen05_operator_against_oracle(torch_cuda, transform, case):
-    if case == "subsample":
-        sv = config_precision_subsample(512)        # 512 x 64, 6 shots x 10 frequencies: 60 items
-    else:
-        sv = random_case(512, 24, 3, 5, seed=512)   # 15 items: the second CTA holds 7
+    sv = OPERATOR_CASES[case]()
     op = oracle_operator(sv)
     ds = device_survey(sv)
     rng = np.random.default_rng(3)
@@ -64,10 +78,12 @@ def test_tcgen05_operator_against_oracle(torch_cuda, transform, case):
     assert ef <= BOUNDS[transform] and ea <= BOUNDS[transform], (ef, ea)
 
 
-def test_tcgen05_fp16_is_scale_invariant(torch_cuda):
+@pytest.mark.parametrize("nx", [128, 512, 1024])
+def test_tcgen05_fp16_is_scale_invariant(torch_cuda, nx):
     """A(c m) = c A(m): wavefields of 1e-6 and 1e4 times the natural size keep FP16 x3's error
-    (the per-item power-of-two scale before each depth step)."""
-    sv = random_case(512, 16, 2, 6, seed=513)
+    (the per-item power-of-two scale before each depth step; at nx = 1024 an item's scale is agreed
+    between the two warps that hold it)."""
+    sv = random_case(nx, 16, 3, 6, seed=513)
     op = oracle_operator(sv)
     ds = device_survey(sv)
     rng = np.random.default_rng(4)
@@ -105,17 +121,53 @@ def test_tcgen05_realistic_window_sampled_items(torch_cuda):
 
 
 @pytest.mark.parametrize("transform", list(BOUNDS))
-def test_tcgen05_sliding_solve(torch_cuda, transform):
+def test_tcgen05_precision_workload_full_size_sampled_items(torch_cuda, transform):
+    """The precision workload at full size, 1024 x 512 with 256 frequencies (3-60 Hz), one window of
+    4 shots from shot 80 (1,024 items, 128 CTAs of 256 threads, Phi and D rows staged): A on sampled
+    (shot, frequency) rows and A^T on data that is zero except at sampled items, against the oracle
+    item by item.  The FP32 FFT and the mma.sync form of the same precision run beside it; the
+    tcgen05 form computes the same split products, so its error stays within 1.25x of the mma.sync
+    form's."""
+    from synth import config_precision
+    sv = config_precision()
+    ds = device_survey(sv)
+    K, shot0 = 4, 80
+    m = np.asarray(sv.reflectivity, dtype=np.float32).astype(np.float64)
+    samples = [(0, 0), (1, 131), (3, 255)]
+    rng = np.random.default_rng(7)
+    d = np.zeros((K, sv.nw, sv.nx), dtype=np.complex64)
+    op = oracle_operator(sv)
+    ref_img = np.zeros((sv.nz, sv.nx))
+    for ishot, iw in samples[1:]:
+        row = (rng.normal(size=sv.nx) + 1j * rng.normal(size=sv.nx)).astype(np.complex64)
+        d[ishot, iw] = row
+        ref_img += op.with_freqs([iw]).adjoint(row[None, None, :].astype(np.complex128), shots=[shot0 + ishot])
+    ref_f = [op.with_freqs([iw]).forward(m, shots=[shot0 + ishot])[0, 0] for ishot, iw in samples]
+    report = {}
+    for tr in ("fft", transform.replace("_tcgen05", ""), transform):
+        got_f, got_a = _run(torch_cuda, ds, m, d, shot0, K, tr)
+        report[tr] = {"forward": [rel_l2(got_f[ishot, iw], ref) for (ishot, iw), ref in zip(samples, ref_f)],
+                      "adjoint": rel_l2(got_a, ref_img)}
+    print(json.dumps({"case": "precision_1024x512", "relative_l2_error": report}))
+    errs, ea = report[transform]["forward"], report[transform]["adjoint"]
+    assert max(errs) <= FULL_SIZE_BOUNDS[transform] and ea <= FULL_SIZE_BOUNDS[transform], report
+    legacy = report[transform.replace("_tcgen05", "")]
+    assert max(errs) <= 1.25 * max(legacy["forward"]) and ea <= 1.25 * legacy["adjoint"], report
+
+
+@pytest.mark.parametrize("nx", [128, 512])
+@pytest.mark.parametrize("transform", list(BOUNDS))
+def test_tcgen05_sliding_solve(torch_cuda, transform, nx):
     """The sliding-window CG solve with the tcgen05 transforms against the oracle's, on the precision
-    workload's construction at 512 x 64 (6 shots, 10 frequencies 3-60 Hz, window 3 / slide 2, 6
-    iterations per window); the FP32 FFT solve of the same problem is printed beside it.  With the
+    workload's construction at 128 x 64 and 512 x 64 (6 shots, 10 frequencies 3-60 Hz, window 3 /
+    slide 2, 6 iterations per window); the FP32 FFT solve of the same problem is printed beside it.  With the
     data-scaled lambda this problem's six-iterate CG is ill conditioned (the FP32 FFT solve itself
     lands 5.5e-4 from the oracle, and 1e-2 of the top eigenvalue still amplifies the operators'
     errors 10-150 times), so lambda is 1e-1 of the top eigenvalue of A^T A here.  The mma.sync
     transform of the same precision is printed beside it."""
     import paper_1801_00819_gb300 as L
     torch = torch_cuda
-    sv = config_precision_subsample(512)
+    sv = config_precision_subsample(nx)
     op = oracle_operator(sv)
     clean = op.forward(np.asarray(sv.reflectivity, dtype=np.float32).astype(np.float64))
     d = (clean + sv.noise_pct * np.sqrt(np.mean(np.abs(clean) ** 2)) * sv.noise()).astype(np.complex64)
@@ -137,13 +189,14 @@ def test_tcgen05_sliding_solve(torch_cuda, transform):
         torch.cuda.synchronize()
         assert [s["start"] for s in stats] == [s.start for s in st_ref]
         errs[tr] = rel_l2(m.cpu().numpy().astype(np.float64), m_ref)
-    print(json.dumps({"solve_relative_l2_error": errs}))
+    print(json.dumps({"nx": nx, "solve_relative_l2_error": errs}))
     assert errs[transform] <= BOUNDS[transform], errs
 
 
-def test_tcgen05_other_widths_rejected_before_launch(torch_cuda):
+@pytest.mark.parametrize("nx", [64, 384])
+def test_tcgen05_other_widths_rejected_before_launch(torch_cuda, nx):
     import paper_1801_00819_gb300 as L
-    sv = random_case(256, 8, 2, 3, seed=515)
+    sv = random_case(nx, 8, 2, 3, seed=515)
     ds = device_survey(sv)
     ws = torch_cuda.empty(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, 2, L.LSM_OP_FORWARD),
                           dtype=torch_cuda.uint8, device="cuda")
