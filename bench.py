@@ -694,6 +694,12 @@ def batching_reduced_variant(L, torch, args):
         torch.cuda.synchronize()
         return lsm.rls_multi_line_solve(lines)[1]
 
+    def one_graph():
+        for pr in lines:
+            pr.m_inout.zero_()
+        torch.cuda.synchronize()
+        return lsm.rls_multi_line_solve(lines, cuda_graph="solve")[1]
+
     def timed(fn):
         best, stats = None, None
         for _ in range(2):
@@ -711,6 +717,9 @@ def batching_reduced_variant(L, torch, args):
     imgs_loop = [pr.m_inout.clone() for pr in lines]
     t_tog, st_tog = timed(together)
     same = all(torch.equal(a, pr.m_inout) for a, pr in zip(imgs_loop, lines))
+    one_graph()
+    t_one, st_one = timed(one_graph)
+    same_one = all(torch.equal(a, pr.m_inout) for a, pr in zip(imgs_loop, lines))
     out = {"workload": "batching (reduced): the 8 lines nx 256-1024 (incl. 384, 640, 768, 896), nz = nx/2, "
                        "each line's first 3 windows of K 4-32 shots, every other frequency (52-91), CG to 1e-3",
            "lines": [{"nx": pr.grid.c.nx, "shots": pr.geom.c.ns, "freqs": pr.freqs.c.nw, "K": pr.K,
@@ -722,6 +731,12 @@ def batching_reduced_variant(L, torch, args):
            "units_per_s_looped": round(line_units(lines, st_loop) / t_loop, 1),
            "max_final_rel_res": max(w["rel_res"] for st in st_tog for w in st),
            "images_bitwise_equal": bool(same),
+           "one_graph_ms": round(1e3 * t_one, 1),
+           "speedup_one_graph_vs_looped": round(t_loop / t_one, 3),
+           "one_graph_images_bitwise_equal": bool(same_one),
+           "one_graph": "every window of every line in one CUDA graph launch (cuda_graph=\"solve\"): the "
+                        "lines as independent branches, each window's CG iterations a conditional WHILE node; "
+                        "graph capture and instantiation inside the timed call",
            "timing": "host wall clock around each whole solve, GPU synchronised on both sides, best of 2",
            "autotune": tuned}
     del lines
@@ -733,7 +748,8 @@ def batching_arm(args):
     """Eight independent survey lines (nx 256..1024 incl. 384, 640, 768, 896; K 4..32), every window
     to 1e-3: one step solves all lines concurrently (rls_multi_line_solve, a stream per line); the
     comparison loops the plain per-line solve over the same lines.  Both run the host-driven CG loop;
-    a third arm runs the concurrent solve with graph-replayed CG iterations."""
+    a third arm runs the concurrent solve with graph-replayed CG iterations, a fourth every window of
+    every line as one graph launch."""
     import torch
 
     import paper_1801_00819_gb300 as L
@@ -783,6 +799,13 @@ def batching_arm(args):
     st_graph = [concurrent(graph=True) for _ in range(args.steps)][-1]
     torch.cuda.synchronize()
     t_graph = (time.perf_counter() - t0) / args.steps
+    # every window of every line as one graph launch (no host worker threads)
+    concurrent(graph="solve")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st_one = [concurrent(graph="solve") for _ in range(args.steps)][-1]
+    torch.cuda.synchronize()
+    t_one = (time.perf_counter() - t0) / args.steps
     t0 = time.perf_counter()
     st_seq = sequential()
     torch.cuda.synchronize()
@@ -806,6 +829,11 @@ def batching_arm(args):
            "speedup_concurrent_cuda_graph_vs_sequential": round(t_seq / t_graph, 3),
            "cuda_graph_same_iterations": [[w["iters"] for w in st] for st in st_graph] ==
                                          [[w["iters"] for w in st] for st in st_conc],
+           "one_graph_ms": round(1e3 * t_one, 1),
+           "one_graph_units_per_s": round(units_of(st_one) / t_one, 1),
+           "speedup_one_graph_vs_sequential": round(t_seq / t_one, 3),
+           "one_graph_same_iterations": [[w["iters"] for w in st] for st in st_one] ==
+                                        [[w["iters"] for w in st] for st in st_conc],
            "autotune": tuned or None}
     print(json.dumps(out), flush=True)
 

@@ -289,16 +289,27 @@ int lsm_profile_stop(lsm_profile* out);
 #define LSM_TRANSFORM_DFT_FP16X3_TCGEN05 4
 #define LSM_TRANSFORM_DFT_BF16X3_TCGEN05 5
 /*
- *   cuda_graph: > 0 runs each window's CG iterations as one CUDA graph -- a conditional WHILE
- *     node whose body is one iteration (A, the vector updates, A^T, the stopping test evaluated on
- *     the device) -- so the host waits once per window instead of once per iteration.  The kernels
- *     and their order are those of the host-driven loop, so results and iteration counts are
- *     identical.  The graph is built once per call on a private stream; kernels inside it are not
- *     seen by lsm_profile_start / lsm_profile_stop.  < 0 runs the host-driven loop (the host reads
- *     the stopping test back after every iteration).  0, the default (also for rls_window_solve and
- *     NULL options), runs the graph unless lsm_profile_start / lsm_profile_start_classes is timing
- *     the A or A^T sweeps, which needs the host-driven loop.
+ *   cuda_graph: LSM_CUDA_GRAPH_WINDOW (1) runs each window's CG iterations as one CUDA graph -- a
+ *     conditional WHILE node whose body is one iteration (A, the vector updates, A^T, the stopping
+ *     test evaluated on the device) -- so the host waits once per window instead of once per
+ *     iteration.  The kernels and their order are those of the host-driven loop, so results and
+ *     iteration counts are identical.  The graph is built once per call on a private stream; kernels
+ *     inside it are not seen by lsm_profile_start / lsm_profile_stop.  LSM_CUDA_GRAPH_SOLVE (2) runs
+ *     the whole call as one graph launch: every window's set-up launches, its loop test and WHILE
+ *     node, and a node that records its outcome in the workspace, chained window after window (for
+ *     rls_multi_line_solve: every line's chain as an independent branch of the same graph, launched
+ *     once on lines[0].stream after each line's tables are built on its own stream), so the host
+ *     waits once per call; same kernels, order, results and iteration counts again, window
+ *     statistics as usual except `ms` = 0 (the windows are not timed one by one); after a window
+ *     breaks down the later windows of that line run no iterations, and the call returns
+ *     LSM_ERR_BREAKDOWN with statistics up to that window.  < 0 runs the host-driven loop (the host
+ *     reads the stopping test back after every iteration).  0, the default (also for
+ *     rls_window_solve and NULL options), runs the per-window graph unless lsm_profile_start /
+ *     lsm_profile_start_classes is timing the A or A^T sweeps, which needs the host-driven loop.
+ *     Values above 2: LSM_ERR_ARG.
  */
+#define LSM_CUDA_GRAPH_WINDOW 1
+#define LSM_CUDA_GRAPH_SOLVE 2
 typedef struct {
     int preconditioner;
     double precond_eps;
@@ -353,9 +364,10 @@ int rls_window_solve_sharded(const lsm_grid* grid, const float* slowness, const 
 /*
  * Several independent survey lines solved together (batching): each line is a complete
  * rls_window_solve_ex problem with its own grid (any supported nx), data, window length K, slide,
- * tolerance, image, statistics, workspace and stream.  The lines run concurrently, one host worker
- * thread per line issuing that line's kernels on that line's stream, so small lines overlap on the
- * GPU instead of running one after another.  Every line's result is bitwise identical to solving it
+ * tolerance, image, statistics, workspace and stream.  The lines run concurrently, so small lines
+ * overlap on the GPU instead of running one after another: by default one host worker thread per
+ * line issues that line's kernels on that line's stream; with options->cuda_graph =
+ * LSM_CUDA_GRAPH_SOLVE every window of every line is one graph launched once (see cuda_graph).  Every line's result is bitwise identical to solving it
  * alone with rls_window_solve_ex.  Streams must be distinct (and not the legacy default stream) for
  * the lines to overlap.  Fields are the arguments of rls_window_solve_ex; `status` receives the
  * line's return code.  Returns LSM_OK when every line succeeded, else the first failing line's

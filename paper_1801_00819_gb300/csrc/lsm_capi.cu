@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <thread>
@@ -387,6 +388,7 @@ struct Layout {
     size_t ctrl;                   // solve: window start read by graph-replayed sweeps
     size_t err;                    // int: set by a tcgen05 sweep whose bounded wait ran out
     size_t img, qqt;               // sharded solve: local image, all-reduced ||q||^2
+    size_t wrec, halt;             // whole-solve graph: per-window records, breakdown halt flag
     size_t total;
     int ring, nparts;
 };
@@ -454,6 +456,9 @@ Layout make_layout(const lsm_grid* g, const lsm_geom* geo, const lsm_freqs* f, i
         L.sz = take(kImgRedBlocks * sizeof(double));
         L.img = take(plane * sizeof(float));  // sharded solve: this rank's image before the all-reduce
         L.qqt = take(sizeof(double));         // sharded solve: ||q||^2 summed over the ranks
+        // whole-solve graph: every window's outcome (at most ns + 1 windows) and the halt flag
+        L.wrec = take((size_t)(geo->ns + 1) * sizeof(WindowRecord));
+        L.halt = take(sizeof(int));
     } else if (op == LSM_OP_ADJOINT) {
         L.ss = take(kImgRedBlocks * sizeof(double));
     }
@@ -1276,120 +1281,181 @@ static int build_cg_graph(CgGraph& G, SweepArgs a, int K, int nsm, int transform
     return LSM_OK;
 }
 
-// The sliding-window solve; `shard_fn` (with `shard_ctx`) set: this rank's share of a solve sharded
-// by frequency (plain CG, FP32 FFT transforms, host-driven loop).
-static int window_solve(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs, const lsm_geom* geom,
-                        const float* d, double lambda, int K, int slide, double cg_tol, int max_iter,
-                        int first_window, int n_windows, float* m_inout, lsm_window_stats* stats, int stats_cap,
-                        void* workspace, size_t workspace_bytes, void* stream, const lsm_solve_options* options,
-                        lsm_allreduce_fn shard_fn, void* shard_ctx) {
+// One line's prepared sliding-window solve: its arguments, workspace layout and device vectors.
+struct SolveCtx {
+    const lsm_grid* grid = nullptr;
+    const lsm_freqs* freqs = nullptr;
+    const lsm_geom* geom = nullptr;
+    const float2* dall = nullptr;
+    double lambda = 0.0, cg_tol = 0.0, precond_eps = 0.0;
+    int K = 0, slide = 0, max_iter = 0, first = 0, last = 0;
+    float* m = nullptr;
+    lsm_window_stats* stats = nullptr;
+    int stats_cap = 0;
+    Layout L{};
+    char* ws = nullptr;
+    SweepArgs a{};
+    int transform = 0, nsm = 0, n = 0, graph_opt = 0;
+    size_t nd = 0, shot_stride = 0;
+    float *p = nullptr, *s = nullptr, *minv = nullptr;
+    float2 *r = nullptr, *q = nullptr;
+    double *qq = nullptr, *pp = nullptr, *ss = nullptr, *sz = nullptr;
+    CgState* state = nullptr;
+    int* shot0_dev = nullptr;
+    WindowRecord* wrec = nullptr;
+    int* halt = nullptr;
+};
+
+// Argument checks, the coefficient tables and the device vectors of one line's solve; c.first ==
+// c.last when the call has no window to solve.  `sharded`: the caller sums A^T images and ||q||^2
+// over ranks (plain CG, FP32 FFT transforms, host-driven loop).
+static int solve_init(SolveCtx& c, const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs,
+                      const lsm_geom* geom, const float* d, double lambda, int K, int slide, double cg_tol,
+                      int max_iter, int first_window, int n_windows, float* m_inout, lsm_window_stats* stats,
+                      int stats_cap, void* workspace, size_t workspace_bytes, cudaStream_t st,
+                      const lsm_solve_options* options, bool sharded) {
     int rc = validate_common(grid, freqs, geom);
     if (rc != LSM_OK) return rc;
     if (!aligned16(slowness) || !aligned16(d) || !aligned16(m_inout) || !aligned16(workspace)) return LSM_ERR_ARG;
     if (!std::isfinite(lambda) || lambda < 0.0 || !std::isfinite(cg_tol) || cg_tol < 0.0 || max_iter < 0)
         return LSM_ERR_ARG;
     const int precond = options ? options->preconditioner : LSM_PRECOND_NONE;
-    const double precond_eps = options ? options->precond_eps : 0.0;
+    c.precond_eps = options ? options->precond_eps : 0.0;
     if (precond != LSM_PRECOND_NONE && precond != LSM_PRECOND_ILLUMINATION) return LSM_ERR_ARG;
-    if (precond == LSM_PRECOND_ILLUMINATION && !(precond_eps > 0.0 && std::isfinite(precond_eps))) return LSM_ERR_ARG;
-    int transform = 0;
-    rc = transform_of(options, grid, geom, &transform);
+    if (precond == LSM_PRECOND_ILLUMINATION && !(c.precond_eps > 0.0 && std::isfinite(c.precond_eps)))
+        return LSM_ERR_ARG;
+    rc = transform_of(options, grid, geom, &c.transform);
     if (rc != LSM_OK) return rc;
-    if (shard_fn && (transform != 0 || precond != LSM_PRECOND_NONE)) return LSM_ERR_ARG;
+    if (sharded && (c.transform != 0 || precond != LSM_PRECOND_NONE)) return LSM_ERR_ARG;
+    c.graph_opt = options ? options->cuda_graph : 0;
+    if (c.graph_opt > LSM_CUDA_GRAPH_SOLVE) return LSM_ERR_ARG;
     const int ns = geom->ns;
     const int nwin = lsm_num_windows(ns, K, slide);
     if (nwin == 0) return LSM_ERR_ARG;
     if (first_window < 0 || first_window > nwin) return LSM_ERR_ARG;
     if (stats_cap < 0 || (stats_cap > 0 && !stats)) return LSM_ERR_ARG;
-    const int last = n_windows <= 0 ? nwin : std::min(nwin, first_window + n_windows);
-    const int nsm = num_sms_current();
-    const Layout L = make_layout(grid, geom, freqs, K, LSM_OP_SOLVE, nsm);
-    if (workspace_bytes < L.total) return LSM_ERR_WORKSPACE;
-    if (first_window == last) return LSM_OK;
+    c.grid = grid;
+    c.freqs = freqs;
+    c.geom = geom;
+    c.dall = reinterpret_cast<const float2*>(d);
+    c.lambda = lambda;
+    c.cg_tol = cg_tol;
+    c.K = K;
+    c.slide = slide;
+    c.max_iter = max_iter;
+    c.first = first_window;
+    c.last = n_windows <= 0 ? nwin : std::min(nwin, first_window + n_windows);
+    c.m = m_inout;
+    c.stats = stats;
+    c.stats_cap = stats_cap;
+    c.nsm = num_sms_current();
+    c.L = make_layout(grid, geom, freqs, K, LSM_OP_SOLVE, c.nsm);
+    if (workspace_bytes < c.L.total) return LSM_ERR_WORKSPACE;
+    if (c.first == c.last) return LSM_OK;
 
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    char* ws = static_cast<char*>(workspace);
-    const int tile = transform ? 0 : chosen_tile(grid->nx, K, freqs->nw);
-    rc = prepare(grid, slowness, freqs, geom, L, ws, st, nullptr, transform ? TABLES_NATURAL : TABLES_SWEEP, tile);
+    c.ws = static_cast<char*>(workspace);
+    const int tile = c.transform ? 0 : chosen_tile(grid->nx, K, freqs->nw);
+    rc = prepare(grid, slowness, freqs, geom, c.L, c.ws, st, nullptr, c.transform ? TABLES_NATURAL : TABLES_SWEEP,
+                 tile);
     if (rc != LSM_OK) return rc;
-    SweepArgs a = base_args(grid, freqs, geom, L, ws, tile);
+    c.a = base_args(grid, freqs, geom, c.L, c.ws, tile);
+    char* ws = c.ws;
+    const Layout& L = c.L;
+    c.n = grid->nx * grid->nz;
+    c.nd = (size_t)K * freqs->nw * geom->nrec;
+    c.shot_stride = (size_t)freqs->nw * geom->nrec;
+    c.p = reinterpret_cast<float*>(ws + L.p);
+    c.s = reinterpret_cast<float*>(ws + L.s);
+    c.r = reinterpret_cast<float2*>(ws + L.r);
+    c.q = reinterpret_cast<float2*>(ws + L.q);
+    c.qq = reinterpret_cast<double*>(ws + L.qq);
+    c.pp = reinterpret_cast<double*>(ws + L.pp);
+    c.ss = reinterpret_cast<double*>(ws + L.ss);
+    c.state = reinterpret_cast<CgState*>(ws + L.state);
+    c.shot0_dev = reinterpret_cast<int*>(ws + L.ctrl);
+    c.wrec = reinterpret_cast<WindowRecord*>(ws + L.wrec);
+    c.halt = reinterpret_cast<int*>(ws + L.halt);
+    c.minv = precond == LSM_PRECOND_ILLUMINATION ? reinterpret_cast<float*>(ws + L.minv) : nullptr;
+    c.sz = c.minv ? reinterpret_cast<double*>(ws + L.sz) : nullptr;
+    return LSM_OK;
+}
 
-    const int n = grid->nx * grid->nz;
-    const size_t nd = (size_t)K * freqs->nw * geom->nrec;
-    const size_t shot_stride = (size_t)freqs->nw * geom->nrec;
-    float* p = reinterpret_cast<float*>(ws + L.p);
-    float* s = reinterpret_cast<float*>(ws + L.s);
-    float2* r = reinterpret_cast<float2*>(ws + L.r);
-    float2* q = reinterpret_cast<float2*>(ws + L.q);
-    double* qq = reinterpret_cast<double*>(ws + L.qq);
-    double* pp = reinterpret_cast<double*>(ws + L.pp);
-    double* ss = reinterpret_cast<double*>(ws + L.ss);
-    CgState* state = reinterpret_cast<CgState*>(ws + L.state);
-    int* shot0_dev = reinterpret_cast<int*>(ws + L.ctrl);
+// The set-up of window k (Eq. 10, Eq. 11): the source wavefields of the shots that enter the window
+// (the rank-`slide` update of the ring; prev_start is the previous window's first shot, -1 for none),
+// the illumination preconditioner when asked, b = A_k^T d_k and ||b||^2, r = d_k - A_k m,
+// s = A_k^T r - lambda m, p = s (or M^-1 s) and gamma (slot 0).  *start_out: the window's first shot.
+static cudaError_t window_setup(const SolveCtx& c, int k, int prev_start, const ShardHooks* shard, cudaStream_t st,
+                                int* start_out) {
+    const int start = window_start(k, c.geom->ns, c.K, c.slide);
+    *start_out = start;
+    const float2* dk = c.dall + (size_t)start * c.shot_stride;
+    const int new_from = prev_start < 0 ? start : std::max(start, prev_start + c.K);
+    cudaError_t e = cudaSuccess;
+    auto ok = [&](cudaError_t x) {
+        if (e == cudaSuccess) e = x;
+        return e == cudaSuccess;
+    };
+    if (new_from < start + c.K && !ok(run_source(c.a, new_from, start + c.K - new_from, c.nsm, st, c.transform)))
+        return e;
+    if (c.minv) {
+        // the ring now holds exactly this window's source wavefields
+        float* illum = reinterpret_cast<float*>(c.ws + c.L.illum);
+        float* bmax = reinterpret_cast<float*>(c.ws + c.L.bmax);
+        if (!ok(cg_illumination(c.a.S, c.K * c.freqs->nw, c.n, illum, bmax, st))) return e;
+        if (!ok(cg_precond_finalize(illum, c.n, bmax, c.precond_eps, c.minv, st))) return e;
+    }
+    int nparts = 0;
+    const float lamf = (float)c.lambda;
+    if (!ok(cg_zero_state(c.state, st))) return e;
+    // b = A_k^T d_k  ->  ||b||^2
+    if (!ok(run_adjoint(c.a, start, c.K, dk, c.nsm, st, &nparts, c.transform))) return e;
+    if (shard) ok(shard_reduce_image(shard, c.a.part, nparts, c.n, nullptr, 0.f, c.s, c.ss, st, nullptr, nullptr));
+    else ok(cg_reduce_image(c.a.part, nparts, c.n, nullptr, 0.f, 0, c.s, c.ss, st));
+    if (!ok(cg_store_sum(c.ss, c.state, st))) return e;
+    // r = d_k - A_k m
+    if (!ok(run_forward(c.a, start, c.K, c.m, c.q, c.nsm, st, c.transform))) return e;
+    if (!ok(cg_residual(dk, c.q, c.r, c.nd, st))) return e;
+    // s = A_k^T r - lambda m ; p = s ; gamma = ||s||^2
+    if (!ok(run_adjoint(c.a, start, c.K, c.r, c.nsm, st, &nparts, c.transform))) return e;
+    if (shard) ok(shard_reduce_image(shard, c.a.part, nparts, c.n, c.m, lamf, c.s, c.ss, st, c.minv, c.sz));
+    else ok(cg_reduce_image(c.a.part, nparts, c.n, c.m, lamf, 0, c.s, c.ss, st, c.minv, c.sz));
+    if (e != cudaSuccess) return e;
+    ok(cg_update_p(c.p, c.s, c.n, c.ss, 1, c.state, 1, 0, c.pp, st, c.minv, c.sz));
+    return e;
+}
+
+static CgVectors cg_vectors(const SolveCtx& c, const ShardHooks* shard) {
+    return CgVectors{c.m, c.p, c.s, c.r, c.q, c.qq, c.pp, c.ss, c.sz, c.minv, c.state, c.nd, c.n, c.lambda, shard};
+}
+
+// The sliding-window solve of one prepared line, window after window, with the host-driven CG loop
+// or each window's CG iterations as one CUDA graph; `shard` set: this rank's share of a solve
+// sharded by frequency (host-driven loop).
+static int window_loop(SolveCtx& c, cudaStream_t st, const ShardHooks* shard) {
     // cuda_graph > 0: graph; < 0: host-driven loop; 0: graph unless the sweeps are being event-timed
-    const int graph_opt = options ? options->cuda_graph : 0;
-    const bool use_graph = !shard_fn && (graph_opt > 0 || (graph_opt == 0 && !profiling_sweeps()));
-    ShardHooks hooks{shard_fn, shard_ctx, reinterpret_cast<float*>(ws + L.img), reinterpret_cast<double*>(ws + L.qqt)};
-    const ShardHooks* shard = shard_fn ? &hooks : nullptr;
+    const bool use_graph = !shard && (c.graph_opt > 0 || (c.graph_opt == 0 && !profiling_sweeps()));
     CgGraph graph;
-    float* minv = precond == LSM_PRECOND_ILLUMINATION ? reinterpret_cast<float*>(ws + L.minv) : nullptr;
-    double* sz = minv ? reinterpret_cast<double*>(ws + L.sz) : nullptr;
-    const float2* dall = reinterpret_cast<const float2*>(d);
-    const float lamf = (float)lambda;
-
     int prev_start = -1;
-    for (int k = first_window; k < last; ++k) {
+    for (int k = c.first; k < c.last; ++k) {
         const auto t0 = std::chrono::steady_clock::now();
-        const int start = window_start(k, ns, K, slide);
-        const float2* dk = dall + (size_t)start * shot_stride;
-        // rank-`slide` update: source wavefields of the shots that enter the window
-        const int new_from = prev_start < 0 ? start : std::max(start, prev_start + K);
-        if (new_from < start + K) LSM_CHECK(run_source(a, new_from, start + K - new_from, nsm, st, transform));
+        int start = 0;
+        LSM_CHECK(window_setup(c, k, prev_start, shard, st, &start));
         prev_start = start;
-        if (minv) {
-            // the ring now holds exactly this window's source wavefields
-            LSM_CHECK(cg_illumination(a.S, K * freqs->nw, n, reinterpret_cast<float*>(ws + L.illum),
-                                      reinterpret_cast<float*>(ws + L.bmax), st));
-            LSM_CHECK(cg_precond_finalize(reinterpret_cast<const float*>(ws + L.illum), n,
-                                          reinterpret_cast<const float*>(ws + L.bmax), precond_eps, minv, st));
-        }
-
-        int nparts = 0;
-        LSM_CHECK(cg_zero_state(state, st));
-        // b = A_k^T d_k  ->  ||b||^2
-        LSM_CHECK(run_adjoint(a, start, K, dk, nsm, st, &nparts, transform));
-        if (shard)
-            LSM_CHECK(shard_reduce_image(shard, a.part, nparts, n, nullptr, 0.f, s, ss, st, nullptr, nullptr));
-        else
-            LSM_CHECK(cg_reduce_image(a.part, nparts, n, nullptr, 0.f, 0, s, ss, st));
-        LSM_CHECK(cg_store_sum(ss, state, st));
-        // r = d_k - A_k m
-        LSM_CHECK(run_forward(a, start, K, m_inout, q, nsm, st, transform));
-        LSM_CHECK(cg_residual(dk, q, r, nd, st));
-        // s = A_k^T r - lambda m ; p = s ; gamma = ||s||^2
-        LSM_CHECK(run_adjoint(a, start, K, r, nsm, st, &nparts, transform));
-        if (shard)
-            LSM_CHECK(shard_reduce_image(shard, a.part, nparts, n, m_inout, lamf, s, ss, st, minv, sz));
-        else
-            LSM_CHECK(cg_reduce_image(a.part, nparts, n, m_inout, lamf, 0, s, ss, st, minv, sz));
-        int gi = 0;
-        LSM_CHECK(cg_update_p(p, s, n, ss, 1, state, 1, gi, pp, st, minv, sz));
         CgState hs;
         double rel = 0.0, rel0 = 0.0;
-        int nfwd = 1, nadj = 2, it = 0;
+        int nfwd = 1, nadj = 2, it = 0, gi = 0;
         bool broke = false;
         if (use_graph) {
             // the iterations run on the device; the host waits once for the window
             if (!graph.exec) {
-                SweepArgs ag = a;
-                ag.shot0_dev = shot0_dev;
-                const CgVectors v{m_inout, p, s, r, q, qq, pp, ss, sz, minv, state, nd, n, lambda, nullptr};
-                rc = build_cg_graph(graph, ag, K, nsm, transform, v);
+                SweepArgs ag = c.a;
+                ag.shot0_dev = c.shot0_dev;
+                const int rc = build_cg_graph(graph, ag, c.K, c.nsm, c.transform, cg_vectors(c, nullptr));
                 if (rc != LSM_OK) return rc;
             }
-            LSM_CHECK(cg_loop_setup(state, shot0_dev, start, max_iter, cg_tol, st));
+            LSM_CHECK(cg_loop_setup(c.state, c.shot0_dev, start, c.max_iter, c.cg_tol, st));
             LSM_CHECK(cudaGraphLaunch(graph.exec, st));
-            LSM_CHECK(cudaMemcpyAsync(&hs, state, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+            LSM_CHECK(cudaMemcpyAsync(&hs, c.state, sizeof(CgState), cudaMemcpyDeviceToHost, st));
             LSM_CHECK(cudaStreamSynchronize(st));
             it = hs.iter;
             rel0 = hs.rel0;
@@ -1399,44 +1465,198 @@ static int window_solve(const lsm_grid* grid, const float* slowness, const lsm_f
             nadj += it;
             count_launch(1 + graph.body_launches * it);
         } else {
-        LSM_CHECK(cudaMemcpyAsync(&hs, state, sizeof(CgState), cudaMemcpyDeviceToHost, st));
-        LSM_CHECK(cudaStreamSynchronize(st));
-        const double bnorm = std::sqrt(hs.bb);
-        rel = bnorm > 0.0 ? std::sqrt(hs.ss[gi]) / bnorm : 0.0;
-        rel0 = rel;
-        broke = hs.breakdown != 0;
-        const CgVectors v{m_inout, p, s, r, q, qq, pp, ss, sz, minv, state, nd, n, lambda, shard};
-        while (!broke && it < max_iter && !(rel <= cg_tol)) {
-            LSM_CHECK(cg_iteration(a, start, K, nsm, transform, v, gi, st));
-            gi ^= 1;
-            ++nfwd;
-            ++nadj;
-            ++it;
-            LSM_CHECK(cudaMemcpyAsync(&hs, state, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+            LSM_CHECK(cudaMemcpyAsync(&hs, c.state, sizeof(CgState), cudaMemcpyDeviceToHost, st));
             LSM_CHECK(cudaStreamSynchronize(st));
-            broke = hs.breakdown != 0;
+            const double bnorm = std::sqrt(hs.bb);
             rel = bnorm > 0.0 ? std::sqrt(hs.ss[gi]) / bnorm : 0.0;
-        }
+            rel0 = rel;
+            broke = hs.breakdown != 0;
+            const CgVectors v = cg_vectors(c, shard);
+            while (!broke && it < c.max_iter && !(rel <= c.cg_tol)) {
+                LSM_CHECK(cg_iteration(c.a, start, c.K, c.nsm, c.transform, v, gi, st));
+                gi ^= 1;
+                ++nfwd;
+                ++nadj;
+                ++it;
+                LSM_CHECK(cudaMemcpyAsync(&hs, c.state, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+                LSM_CHECK(cudaStreamSynchronize(st));
+                broke = hs.breakdown != 0;
+                rel = bnorm > 0.0 ? std::sqrt(hs.ss[gi]) / bnorm : 0.0;
+            }
         }
         const auto t1 = std::chrono::steady_clock::now();
-        if (transform != 0) {
+        if (c.transform != 0) {
             // a tcgen05 sweep whose bounded wait on the tensor core ran out leaves NaN and this flag
             int err = 0;
-            LSM_CHECK(cudaMemcpyAsync(&err, ws + L.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+            LSM_CHECK(cudaMemcpyAsync(&err, c.ws + c.L.err, sizeof(int), cudaMemcpyDeviceToHost, st));
             LSM_CHECK(cudaStreamSynchronize(st));
             if (err) return LSM_ERR_TIMEOUT;
         }
-        const int idx = k - first_window;
-        if (idx < stats_cap) {
-            stats[idx].start = start;
-            stats[idx].iters = it;
-            stats[idx].rel_res0 = rel0;
-            stats[idx].rel_res = rel;
-            stats[idx].n_forward = nfwd;
-            stats[idx].n_adjoint = nadj;
-            stats[idx].ms = std::chrono::duration<float, std::milli>(t1 - t0).count();
+        const int idx = k - c.first;
+        if (idx < c.stats_cap) {
+            c.stats[idx].start = start;
+            c.stats[idx].iters = it;
+            c.stats[idx].rel_res0 = rel0;
+            c.stats[idx].rel_res = rel;
+            c.stats[idx].n_forward = nfwd;
+            c.stats[idx].n_adjoint = nadj;
+            c.stats[idx].ms = std::chrono::duration<float, std::milli>(t1 - t0).count();
         }
         if (broke) return LSM_ERR_BREAKDOWN;
+    }
+    return LSM_OK;
+}
+
+// Whole solves as one CUDA graph (cuda_graph = LSM_CUDA_GRAPH_SOLVE): per line a chain of windows --
+// the window's set-up launches (a child graph), the loop test and a conditional WHILE node whose body
+// is one CG iteration and the advancing test, then a node that records the window's outcome in the
+// workspace -- and the lines as independent branches of the same graph, so one launch runs every
+// window of every line with no host thread and no host wait in between.  The kernels of each window,
+// and their order, are those of the per-window graph, so results and iteration counts are identical.
+struct SolveGraph {
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    SolveGraph() = default;
+    SolveGraph(const SolveGraph&) = delete;
+    SolveGraph& operator=(const SolveGraph&) = delete;
+    ~SolveGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cs) cudaStreamDestroy(cs);
+    }
+};
+
+// Launches issued by `fn(stream)` recorded as a new graph (owned by the caller); *launches counts them.
+static int capture_new_graph(cudaStream_t cs, cudaGraph_t* out, int* launches,
+                             const std::function<cudaError_t(cudaStream_t)>& fn) {
+    *out = nullptr;
+    LSM_CHECK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    g_capturing = true;
+    g_captured_launches = 0;
+    const cudaError_t e = fn(cs);
+    g_capturing = false;
+    if (launches) *launches = g_captured_launches;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e_end = cudaStreamEndCapture(cs, &g);
+    if (e != cudaSuccess || e_end != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return LSM_ERR_CUDA;
+    }
+    *out = g;
+    return LSM_OK;
+}
+
+// `sub` added to `top` as a child-graph node after `dep` (none when null); `sub` is destroyed.
+static int add_child(cudaGraph_t top, cudaGraph_t sub, cudaGraphNode_t dep, cudaGraphNode_t* node) {
+    const cudaError_t e = cudaGraphAddChildGraphNode(node, top, dep ? &dep : nullptr, dep ? 1 : 0, sub);
+    cudaGraphDestroy(sub);
+    return e == cudaSuccess ? LSM_OK : LSM_ERR_CUDA;
+}
+
+struct ChainLaunches {
+    std::vector<int> setup;  // per window: set-up launches (with the loop set-up)
+    int body = 0;            // launches of one CG iteration with its test
+};
+
+static int add_solve_chain(SolveGraph& G, SolveCtx& c, ChainLaunches& nl) {
+    SweepArgs ag = c.a;
+    ag.shot0_dev = c.shot0_dev;
+    const CgVectors v = cg_vectors(c, nullptr);
+    cudaGraphNode_t prev = nullptr;
+    int prev_start = -1;
+    for (int k = c.first; k < c.last; ++k) {
+        // (1) set-up of the window (before the first one, the halt flag is cleared)
+        cudaGraph_t sub = nullptr;
+        int start = 0, nset = 0;
+        int rc = capture_new_graph(G.cs, &sub, &nset, [&](cudaStream_t cs) {
+            cudaError_t e = k == c.first ? cudaMemsetAsync(c.halt, 0, sizeof(int), cs) : cudaSuccess;
+            if (e == cudaSuccess) e = window_setup(c, k, prev_start, nullptr, cs, &start);
+            if (e == cudaSuccess) e = cg_loop_setup(c.state, c.shot0_dev, start, c.max_iter, c.cg_tol, cs, c.halt);
+            return e;
+        });
+        if (rc != LSM_OK) return rc;
+        nl.setup.push_back(nset);
+        cudaGraphNode_t n_setup = nullptr;
+        rc = add_child(G.graph, sub, prev, &n_setup);
+        if (rc != LSM_OK) return rc;
+        prev_start = start;
+        // (2) the CG iterations: the loop test, then WHILE { one iteration; the advancing test }
+        cudaGraphConditionalHandle handle = 0;
+        LSM_CHECK(cudaGraphConditionalHandleCreate(&handle, G.graph, 0, cudaGraphCondAssignDefault));
+        CgState* state = c.state;
+        int no_advance = 0;
+        void* test_args[] = {&state, &handle, &no_advance};
+        cudaKernelNodeParams kp;
+        cg_loop_test_node_params(&kp, test_args);
+        cudaGraphNode_t test0 = nullptr, loop = nullptr;
+        LSM_CHECK(cudaGraphAddKernelNode(&test0, G.graph, &n_setup, 1, &kp));
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = handle;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        LSM_CHECK(cudaGraphAddNode(&loop, G.graph, &test0, nullptr, 1, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];  // owned by the conditional node
+        LSM_CHECK(cudaStreamBeginCaptureToGraph(G.cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        g_capturing = true;
+        g_captured_launches = 0;
+        cudaError_t e = cg_iteration(ag, 0, c.K, c.nsm, c.transform, v, -1, G.cs);
+        if (e == cudaSuccess) e = cg_loop_test(c.state, handle, 1, G.cs);
+        g_capturing = false;
+        nl.body = g_captured_launches;
+        cudaGraph_t captured = nullptr;
+        const cudaError_t e_end = cudaStreamEndCapture(G.cs, &captured);
+        if (e != cudaSuccess || e_end != cudaSuccess) return LSM_ERR_CUDA;
+        // (3) the window's outcome (a breakdown halts the later windows: they run no iterations)
+        WindowRecord* rec = c.wrec + (k - c.first);
+        rc = capture_new_graph(G.cs, &sub, nullptr,
+                               [&](cudaStream_t cs) { return cg_record_window(c.state, rec, c.halt, cs); });
+        if (rc != LSM_OK) return rc;
+        rc = add_child(G.graph, sub, loop, &prev);
+        if (rc != LSM_OK) return rc;
+    }
+    return LSM_OK;
+}
+
+// Prepared solves run as one graph launch on `st`; every line's statistics are filled and its status
+// written to status[i].
+static int run_solve_graph(const std::vector<SolveCtx*>& lines, cudaStream_t st, std::vector<int>& status) {
+    SolveGraph G;
+    LSM_CHECK(cudaStreamCreateWithFlags(&G.cs, cudaStreamNonBlocking));
+    LSM_CHECK(cudaGraphCreate(&G.graph, 0));
+    std::vector<ChainLaunches> nl(lines.size());
+    for (size_t i = 0; i < lines.size(); ++i) {
+        const int rc = add_solve_chain(G, *lines[i], nl[i]);
+        if (rc != LSM_OK) return rc;
+    }
+    LSM_CHECK(cudaGraphInstantiate(&G.exec, G.graph, 0));
+    LSM_CHECK(cudaGraphLaunch(G.exec, st));
+    LSM_CHECK(cudaStreamSynchronize(st));
+    for (size_t i = 0; i < lines.size(); ++i) {
+        SolveCtx& c = *lines[i];
+        const int nwin = c.last - c.first;
+        std::vector<WindowRecord> rec((size_t)nwin);
+        LSM_CHECK(cudaMemcpy(rec.data(), c.wrec, (size_t)nwin * sizeof(WindowRecord), cudaMemcpyDeviceToHost));
+        int err = 0;
+        if (c.transform != 0) LSM_CHECK(cudaMemcpy(&err, c.ws + c.L.err, sizeof(int), cudaMemcpyDeviceToHost));
+        int rc = err ? LSM_ERR_TIMEOUT : LSM_OK;
+        for (int w = 0; w < nwin; ++w) {
+            count_launch(nl[i].setup[(size_t)w] + 2 + nl[i].body * rec[(size_t)w].iters);
+            if (rc != LSM_OK) continue;
+            if (w < c.stats_cap) {
+                lsm_window_stats& s = c.stats[w];
+                s.start = window_start(c.first + w, c.geom->ns, c.K, c.slide);
+                s.iters = rec[(size_t)w].iters;
+                s.rel_res0 = rec[(size_t)w].rel0;
+                s.rel_res = rec[(size_t)w].rel;
+                s.n_forward = 1 + s.iters;
+                s.n_adjoint = 2 + s.iters;
+                s.ms = 0.f;  // the windows of a whole-solve graph are not timed one by one
+            }
+            if (rec[(size_t)w].breakdown) rc = LSM_ERR_BREAKDOWN;
+        }
+        status[i] = rc;
     }
     return LSM_OK;
 }
@@ -1445,8 +1665,17 @@ int rls_window_solve_ex(const lsm_grid* grid, const float* slowness, const lsm_f
                         const float* d, double lambda, int K, int slide, double cg_tol, int max_iter,
                         int first_window, int n_windows, float* m_inout, lsm_window_stats* stats, int stats_cap,
                         void* workspace, size_t workspace_bytes, void* stream, const lsm_solve_options* options) {
-    return window_solve(grid, slowness, freqs, geom, d, lambda, K, slide, cg_tol, max_iter, first_window, n_windows,
-                        m_inout, stats, stats_cap, workspace, workspace_bytes, stream, options, nullptr, nullptr);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    SolveCtx c;
+    int rc = solve_init(c, grid, slowness, freqs, geom, d, lambda, K, slide, cg_tol, max_iter, first_window,
+                        n_windows, m_inout, stats, stats_cap, workspace, workspace_bytes, st, options, false);
+    if (rc != LSM_OK || c.first == c.last) return rc;
+    if (c.graph_opt == LSM_CUDA_GRAPH_SOLVE) {
+        std::vector<int> status(1, LSM_OK);
+        rc = run_solve_graph({&c}, st, status);
+        return rc != LSM_OK ? rc : status[0];
+    }
+    return window_loop(c, st, nullptr);
 }
 
 int rls_window_solve_sharded(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs,
@@ -1455,9 +1684,14 @@ int rls_window_solve_sharded(const lsm_grid* grid, const float* slowness, const 
                              int stats_cap, void* workspace, size_t workspace_bytes, void* stream,
                              lsm_allreduce_fn allreduce, void* allreduce_ctx) {
     if (!allreduce) return LSM_ERR_ARG;
-    return window_solve(grid, slowness, freqs, geom, d, lambda, K, slide, cg_tol, max_iter, first_window, n_windows,
-                        m_inout, stats, stats_cap, workspace, workspace_bytes, stream, nullptr, allreduce,
-                        allreduce_ctx);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    SolveCtx c;
+    const int rc = solve_init(c, grid, slowness, freqs, geom, d, lambda, K, slide, cg_tol, max_iter, first_window,
+                              n_windows, m_inout, stats, stats_cap, workspace, workspace_bytes, st, nullptr, true);
+    if (rc != LSM_OK || c.first == c.last) return rc;
+    ShardHooks hooks{allreduce, allreduce_ctx, reinterpret_cast<float*>(c.ws + c.L.img),
+                     reinterpret_cast<double*>(c.ws + c.L.qqt)};
+    return window_loop(c, st, &hooks);
 }
 
 int rls_window_solve(const lsm_grid* grid, const float* slowness, const lsm_freqs* freqs, const lsm_geom* geom,
@@ -1475,22 +1709,46 @@ int rls_multi_line_solve(lsm_line* lines, int nlines, const lsm_solve_options* o
         cudaGetLastError();
         return LSM_ERR_CUDA;
     }
-    auto solve_line = [&](int i) {
-        lsm_line& l = lines[i];
-        if (cudaSetDevice(dev) != cudaSuccess) {
-            cudaGetLastError();
-            l.status = LSM_ERR_CUDA;
-            return;
+    if (options && options->cuda_graph == LSM_CUDA_GRAPH_SOLVE) {
+        // every line prepared on its own stream, then all of them in one graph launched on the first
+        std::vector<SolveCtx> ctx((size_t)nlines);
+        std::vector<SolveCtx*> todo;
+        std::vector<int> idx;
+        for (int i = 0; i < nlines; ++i) {
+            lsm_line& l = lines[i];
+            cudaStream_t st = reinterpret_cast<cudaStream_t>(l.stream);
+            l.status = solve_init(ctx[(size_t)i], &l.grid, l.slowness, &l.freqs, &l.geom, l.d, l.lambda, l.K, l.slide,
+                                  l.cg_tol, l.max_iter, 0, 0, l.m_inout, l.stats, l.stats_cap, l.workspace,
+                                  l.workspace_bytes, st, options, false);
+            if (l.status == LSM_OK && cudaStreamSynchronize(st) != cudaSuccess) l.status = LSM_ERR_CUDA;
+            if (l.status == LSM_OK && ctx[(size_t)i].first < ctx[(size_t)i].last) {
+                todo.push_back(&ctx[(size_t)i]);
+                idx.push_back(i);
+            }
         }
-        l.status = rls_window_solve_ex(&l.grid, l.slowness, &l.freqs, &l.geom, l.d, l.lambda, l.K, l.slide,
-                                       l.cg_tol, l.max_iter, 0, 0, l.m_inout, l.stats, l.stats_cap, l.workspace,
-                                       l.workspace_bytes, l.stream, options);
-    };
-    std::vector<std::thread> workers;
-    workers.reserve((size_t)nlines);
-    for (int i = 1; i < nlines; ++i) workers.emplace_back(solve_line, i);
-    solve_line(0);
-    for (auto& w : workers) w.join();
+        if (!todo.empty()) {
+            std::vector<int> status(todo.size(), LSM_OK);
+            const int rc = run_solve_graph(todo, reinterpret_cast<cudaStream_t>(lines[0].stream), status);
+            for (size_t j = 0; j < todo.size(); ++j) lines[idx[j]].status = rc != LSM_OK ? rc : status[j];
+        }
+    } else {
+        auto solve_line = [&](int i) {
+            lsm_line& l = lines[i];
+            if (cudaSetDevice(dev) != cudaSuccess) {
+                cudaGetLastError();
+                l.status = LSM_ERR_CUDA;
+                return;
+            }
+            l.status = rls_window_solve_ex(&l.grid, l.slowness, &l.freqs, &l.geom, l.d, l.lambda, l.K, l.slide,
+                                           l.cg_tol, l.max_iter, 0, 0, l.m_inout, l.stats, l.stats_cap, l.workspace,
+                                           l.workspace_bytes, l.stream, options);
+        };
+        std::vector<std::thread> workers;
+        workers.reserve((size_t)nlines);
+        for (int i = 1; i < nlines; ++i) workers.emplace_back(solve_line, i);
+        solve_line(0);
+        for (auto& w : workers) w.join();
+    }
     for (int i = 0; i < nlines; ++i)
         if (lines[i].status != LSM_OK) return lines[i].status;
     return LSM_OK;

@@ -330,11 +330,12 @@ __global__ void zero_state_kernel(CgState* st) {
     }
 }
 
-__global__ void loop_setup_kernel(CgState* st, int* shot0_dev, int shot0, int max_iter, double tol) {
+__global__ void loop_setup_kernel(CgState* st, int* shot0_dev, int shot0, int max_iter, double tol,
+                                  const int* halt) {
     if (threadIdx.x == 0) {
         st->gi = 0;
         st->iter = 0;
-        st->max_iter = max_iter;
+        st->max_iter = (halt && *halt) ? 0 : max_iter;
         st->tol = tol;
         *shot0_dev = shot0;
     }
@@ -354,6 +355,16 @@ __global__ void loop_test_kernel(CgState* st, cudaGraphConditionalHandle handle,
     if (!advance) st->rel0 = rel;
     const bool cont = st->breakdown == 0 && st->iter < st->max_iter && !(rel <= st->tol);
     cudaGraphSetConditional(handle, cont ? 1u : 0u);
+}
+
+__global__ void record_window_kernel(const CgState* st, WindowRecord* rec, int* halt) {
+    if (threadIdx.x == 0) {
+        rec->iters = st->iter;
+        rec->breakdown = st->breakdown;
+        rec->rel0 = st->rel0;
+        rec->rel = st->rel;
+        if (st->breakdown) *halt = 1;
+    }
 }
 
 // ------------------------------------------------------------------ launchers
@@ -423,9 +434,17 @@ cudaError_t cg_zero_state(CgState* state, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t cg_loop_setup(CgState* state, int* shot0_dev, int shot0, int max_iter, double tol, cudaStream_t st) {
+cudaError_t cg_loop_setup(CgState* state, int* shot0_dev, int shot0, int max_iter, double tol, cudaStream_t st,
+                          const int* halt) {
     ProfScope prof_(KC_VECTOR, st);
-    loop_setup_kernel<<<1, 32, 0, st>>>(state, shot0_dev, shot0, max_iter, tol);
+    loop_setup_kernel<<<1, 32, 0, st>>>(state, shot0_dev, shot0, max_iter, tol, halt);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t cg_record_window(const CgState* state, WindowRecord* rec, int* halt, cudaStream_t st) {
+    ProfScope prof_(KC_VECTOR, st);
+    record_window_kernel<<<1, 32, 0, st>>>(state, rec, halt);
     count_launch();
     return cudaGetLastError();
 }

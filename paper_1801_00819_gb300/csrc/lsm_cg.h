@@ -56,10 +56,21 @@ cudaError_t cg_sum_partials(const double* part, int n, double* out, cudaStream_t
 // when `advance` is set (flips state->gi, counts the iteration), evaluates the stopping rule
 // ||s|| / ||A_k^T d_k|| <= tol, the iteration limit and the breakdown flag, and sets the conditional
 // handle of the enclosing WHILE node to 1 to continue or 0 to stop.
-cudaError_t cg_loop_setup(CgState* state, int* shot0_dev, int shot0, int max_iter, double tol, cudaStream_t st);
+// With `halt` given and set, the window gets no iterations (a whole-solve graph after a breakdown).
+cudaError_t cg_loop_setup(CgState* state, int* shot0_dev, int shot0, int max_iter, double tol, cudaStream_t st,
+                          const int* halt = nullptr);
 cudaError_t cg_loop_test(CgState* state, cudaGraphConditionalHandle handle, int advance, cudaStream_t st);
 // kernel-node parameters of cg_loop_test for explicit graph construction (args must outlive the call)
 void cg_loop_test_node_params(cudaKernelNodeParams* kp, void** args);
 cudaError_t cg_zero_state(CgState* state, cudaStream_t st);
+
+// One window's outcome, written on the device at the end of its CG loop (whole-solve graphs, where
+// the host reads every window's outcome once, after the last window).
+struct WindowRecord {
+    int iters, breakdown;
+    double rel0, rel;
+};
+// rec <- the state's iteration count, stopping ratios and breakdown flag; a breakdown also sets *halt
+cudaError_t cg_record_window(const CgState* state, WindowRecord* rec, int* halt, cudaStream_t st);
 
 }  // namespace lsm

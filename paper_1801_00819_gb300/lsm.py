@@ -42,6 +42,8 @@ TRANSFORMS = {"fft": 0, "dft_bf16x3": 1, "dft_fp16x3": 2, "dft_bf16x1": 3, "dft_
 
 LSM_PRECOND_NONE = 0
 LSM_PRECOND_ILLUMINATION = 1
+LSM_CUDA_GRAPH_WINDOW = 1
+LSM_CUDA_GRAPH_SOLVE = 2
 
 LSM_STATIC_SCRATCH_BYTES = 64 << 20
 
@@ -82,7 +84,18 @@ def _options(preconditioner=None, precond_eps=1e-2, transform="fft", cuda_graph=
         pc = LSM_PRECOND_ILLUMINATION
     else:
         raise ValueError(f"unknown preconditioner {preconditioner!r}")
-    graph = 0 if cuda_graph is None else (1 if cuda_graph else -1)  # None: the library's default
+    # None: the library's default; True: one graph per window's CG iterations; "solve": the whole
+    # call as one graph launch; False: the host-driven loop
+    if cuda_graph is None:
+        graph = 0
+    elif cuda_graph == "solve":
+        graph = LSM_CUDA_GRAPH_SOLVE
+    elif cuda_graph is True or cuda_graph == "window":
+        graph = LSM_CUDA_GRAPH_WINDOW
+    elif cuda_graph is False:
+        graph = -1
+    else:
+        raise ValueError(f"unknown cuda_graph {cuda_graph!r}")
     return lsm_solve_options(pc, float(precond_eps), TRANSFORMS[transform], graph)
 
 
@@ -396,9 +409,10 @@ def rls_window_solve(grid, slowness, freqs, geom, d, lam, K, slide, cg_tol, max_
 
     With the defaults this calls rls_window_solve; otherwise rls_window_solve_ex with the options:
     preconditioner="illumination" (diagonal source-illumination preconditioner, stabiliser
-    precond_eps times its maximum), a tensor-core `transform`, or cuda_graph=True / False (each
-    window's CG iterations replayed as one CUDA graph with a device-side stopping test, or the
-    host-driven loop; None: the graph unless the A / A^T sweeps are being event-timed).
+    precond_eps times its maximum), a tensor-core `transform`, or cuda_graph=True / "solve" / False
+    (each window's CG iterations replayed as one CUDA graph with a device-side stopping test, the
+    whole solve as one graph launch, or the host-driven loop; None: the per-window graph unless the
+    A / A^T sweeps are being event-timed).
     """
     lib = load_library()
     nwin = lib.lsm_num_windows(int(geom.c.ns), int(K), int(slide))
@@ -464,7 +478,8 @@ class LineProblem:
 
 def rls_multi_line_solve(problems, preconditioner=None, precond_eps=1e-2, raise_on_error=True, transform="fft",
                          cuda_graph=None):
-    """Solve several LineProblems concurrently; returns ([status], [[stats dicts]])."""
+    """Solve several LineProblems concurrently; returns ([status], [[stats dicts]]).  cuda_graph="solve"
+    runs every window of every line as one graph launch instead of one host worker per line."""
     lib = load_library()
     n = len(problems)
     arr = (lsm_line * n)()

@@ -1,5 +1,6 @@
 """CUDA-graph CG (lsm_solve_options.cuda_graph): each window's iterations replayed by a conditional
-WHILE node with the stopping test on the device (the default), against the host-driven loop
+WHILE node with the stopping test on the device (the default), and the whole solve -- of one line or
+of several -- as one graph launch (cuda_graph="solve"), against the host-driven loop
 (cuda_graph=False).  The graph runs the host-driven loop's kernels in
 the same order, so images must be bitwise identical and iteration counts equal, and both must match
 the FP64 oracle's solve."""
@@ -175,3 +176,106 @@ def test_graph_tcgen05_transform_bitwise_equal_to_host_loop(torch_cuda):
         np.testing.assert_array_equal(m_e, m_g)
         _same_stats(st_e, st_g)
         assert all(0 < w["iters"] < 20 for w in st_g)
+
+
+# ---------------------------------------------------------------- whole-solve graph (cuda_graph="solve")
+
+@pytest.mark.parametrize("kw", [{}, {"preconditioner": "illumination"}, {"transform": "dft_bf16x3_tcgen05"}],
+                         ids=["plain", "illumination", "tcgen05"])
+def test_solve_graph_bitwise_equal_to_host_loop(torch_cuda, kw):
+    """The whole solve as one graph launch (every window's set-up, WHILE node and outcome record
+    chained in one graph): the host-driven loop's images and statistics, with tolerance stopping."""
+    sv = random_case(128, 12, 7, 6, seed=95)
+    op = oracle_operator(sv)
+    d, lam = _data(sv, op)
+    ds = device_survey(sv)
+    s_e, m_e, st_e = _solve(torch_cuda, ds, d, lam, 3, 2, 2e-2, 20, cuda_graph=False, **kw)
+    s_g, m_g, st_g = _solve(torch_cuda, ds, d, lam, 3, 2, 2e-2, 20, cuda_graph="solve", **kw)
+    assert s_e == s_g == 0
+    np.testing.assert_array_equal(m_g, m_e)
+    _same_stats(st_g, st_e)
+    assert len(st_g) == 3 and all(0 < w["iters"] < 20 for w in st_g)
+    assert all(w["ms"] == 0.0 for w in st_g)
+
+
+def test_solve_graph_fixed_iterations_and_resume(torch_cuda):
+    """Fixed iteration counts (tol 0) on the tiny configuration, the whole call and a call resumed at
+    window 1 for two windows, each against the host-driven loop."""
+    sv = config_tiny()
+    op = oracle_operator(sv)
+    d, lam = _data(sv, op)
+    ds = device_survey(sv)
+    _, m_e, st_e = _solve(torch_cuda, ds, d, lam, sv.window, sv.slide, 0.0, sv.cg_iters, cuda_graph=False)
+    _, m_g, st_g = _solve(torch_cuda, ds, d, lam, sv.window, sv.slide, 0.0, sv.cg_iters, cuda_graph="solve")
+    np.testing.assert_array_equal(m_g, m_e)
+    _same_stats(st_g, st_e)
+    _, m_e1, st_e1 = _solve(torch_cuda, ds, d, lam, sv.window, sv.slide, 0.0, sv.cg_iters, cuda_graph=False,
+                            first_window=1, n_windows=2)
+    _, m_g1, st_g1 = _solve(torch_cuda, ds, d, lam, sv.window, sv.slide, 0.0, sv.cg_iters, cuda_graph="solve",
+                            first_window=1, n_windows=2)
+    np.testing.assert_array_equal(m_g1, m_e1)
+    _same_stats(st_g1[:2], st_e1[:2])
+
+
+def test_solve_graph_breakdown_halts_later_windows(torch_cuda):
+    """A window that breaks down ends the call with LSM_ERR_BREAKDOWN; the windows after it run no
+    iterations, so the image is the host-driven loop's (which stops there)."""
+    import paper_1801_00819_gb300 as L
+    sv = random_case(32, 8, 5, 4, seed=97)
+    ds = device_survey(sv)
+    rng = np.random.default_rng(1)
+    d = (rng.normal(size=(5, 4, 32)) + 1j * rng.normal(size=(5, 4, 32))).astype(np.complex64)
+    d[3, 2, 5] = np.nan  # shot 3: windows 1 (shots 1-3) and 2 (shots 2-4)
+    s_e, m_e, st_e = _solve(torch_cuda, ds, d, 1.0, 3, 1, 0.0, 3, cuda_graph=False, raise_on_breakdown=False)
+    s_g, m_g, st_g = _solve(torch_cuda, ds, d, 1.0, 3, 1, 0.0, 3, cuda_graph="solve", raise_on_breakdown=False)
+    assert s_e == s_g == L.lsm.LSM_ERR_BREAKDOWN
+    np.testing.assert_array_equal(m_g, m_e)
+    assert st_g[0]["iters"] == st_e[0]["iters"] == 3 and st_g[1]["iters"] == st_e[1]["iters"]
+
+
+def test_solve_graph_multi_line_equals_solo_host_loop(torch_cuda):
+    """Three lines of different widths and window lengths, every window of every line in one graph
+    launch: each line's image and statistics equal solving it alone with the host-driven loop."""
+    import paper_1801_00819_gb300 as L
+    from paper_1801_00819_gb300.device import to_device, workspace
+    lines = [random_case(nx, 10, 6, 5, seed=310 + nx) for nx in (64, 96, 256)]
+    probs, solo = [], []
+    for i, sv in enumerate(lines):
+        op = oracle_operator(sv)
+        d, lam = _data(sv, op)
+        ds = to_device(sv.nx, sv.nz, sv.dx, sv.dz, np.asarray(sv.slowness, np.float32), sv.src_ix, sv.rec_ix,
+                       sv.freqs, sv.wavelet)
+        K, slide = 2 + i, 1 + i % 2
+        _, m_solo, st_solo = _solve(torch_cuda, ds, d, lam, K, slide, 1e-2, 20, cuda_graph=False)
+        solo.append((m_solo, st_solo))
+        ws = workspace(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, K, L.LSM_OP_SOLVE))
+        m = torch_cuda.zeros((sv.nz, sv.nx), dtype=torch_cuda.float32, device="cuda")
+        probs.append(L.LineProblem(ds.grid, ds.slowness, ds.freqs, ds.geom, torch_cuda.as_tensor(d, device="cuda"),
+                                   lam, K, slide, 1e-2, 20, m, ws, torch_cuda.cuda.Stream()))
+    before = L.lsm_kernel_launches()
+    statuses, stats = L.rls_multi_line_solve(probs, cuda_graph="solve")
+    torch_cuda.cuda.synchronize()
+    assert statuses == [0, 0, 0]
+    assert L.lsm_kernel_launches() > before
+    for pr, st, (m_solo, st_solo) in zip(probs, stats, solo):
+        np.testing.assert_array_equal(pr.m_inout.cpu().numpy(), m_solo)
+        _same_stats(st, st_solo)
+
+
+def test_cuda_graph_option_out_of_range_is_rejected(torch_cuda):
+    import ctypes
+
+    import paper_1801_00819_gb300 as L
+    from paper_1801_00819_gb300 import lsm
+    sv = random_case(32, 8, 3, 4, seed=98)
+    ds = device_survey(sv)
+    ws = torch_cuda.empty(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, 2, L.LSM_OP_SOLVE),
+                          dtype=torch_cuda.uint8, device="cuda")
+    m = torch_cuda.zeros((sv.nz, sv.nx), dtype=torch_cuda.float32, device="cuda")
+    d = torch_cuda.zeros((3, 4, 32), dtype=torch_cuda.complex64, device="cuda")
+    opts = lsm.lsm_solve_options(0, 1e-2, 0, 3)
+    stats = (lsm.lsm_window_stats * 4)()
+    st = lsm.load_library().rls_window_solve_ex(
+        ctypes.byref(ds.grid.c), lsm._ptr(ds.slowness), ctypes.byref(ds.freqs.c), ctypes.byref(ds.geom.c), lsm._ptr(d),
+        1.0, 2, 1, 0.0, 2, 0, 0, lsm._ptr(m), stats, 4, lsm._ptr(ws), lsm._nbytes(ws), None, ctypes.byref(opts))
+    assert st == lsm.LSM_ERR_ARG
