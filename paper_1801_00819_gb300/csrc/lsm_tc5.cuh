@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(Tc5Shape<N>::THREADS, Tc5Shape<N>::MIN_BLOCKS)
     // ---- set-up: constants, barrier, TMEM
     tc5_build_dft<PREC>(base + S::OFF_BLF, 16, -1, 32);
     tc5_build_dft<PREC>(base + S::OFF_BRF, R, -1, 2 * R);
-    for (int idx = tid; idx < 16 * R; idx += blockDim.x) {
+    for (int idx = tid; idx < 16 * R; idx += S::THREADS) {
         const int k1 = idx / R, nn = idx % R;
         float sn, cs;
         sincospif(-2.0f * (float)((k1 * nn) % N) / (float)N, &sn, &cs);
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(Tc5Shape<N>::THREADS, Tc5Shape<N>::MIN_BLOCKS)
     auto stage_rows = [&](int row, int which) {
         if (!staged) return;
         constexpr int CH = N * 8 / 16;  // 16-byte chunks per row
-        for (int c = tid; c < nslots * CH; c += blockDim.x) {
+        for (int c = tid; c < nslots * CH; c += S::THREADS) {
             const int sl = c / CH, ch = c - sl * CH;
             const float2* src = (which ? a.dss : a.phi) + ((size_t)(w_first + sl) * nz + row) * N + 2 * ch;
             cp_async16(stg + sl * S::SLOT_BYTES + which * (N * 8) + ch * 16, src);
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(Tc5Shape<N>::THREADS, Tc5Shape<N>::MIN_BLOCKS)
     auto prefetch_srows = [&](int jz) {
         constexpr int LINES = N * 8 / 128;
         if (jz < 0 || jz >= nz) return;
-        for (int l = tid; l < ITEMS * LINES; l += blockDim.x) {
+        for (int l = tid; l < ITEMS * LINES; l += S::THREADS) {
             const int item = blockIdx.x * ITEMS + l / LINES;
             if (item < nitems) {
                 const int iw = item / a.nshots;
@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(Tc5Shape<N>::THREADS, Tc5Shape<N>::MIN_BLOCKS)
                 uint32_t h, l;
                 SP::split(v.x, v.y, h, l);
                 const int rho = item_local * 16 + k1;
-                unsigned char* tile = Abuf + (rho >> 7) * S::RTILE;
+                unsigned char* tile = Abuf + (RT == 1 ? 0 : (rho >> 7)) * S::RTILE;
                 kput32(tile, rho & 127, 2 * n2, h);
                 kput32(tile, rho & 127, 2 * R + 2 * n2, l);
             }
@@ -511,7 +511,7 @@ __global__ void __launch_bounds__(Tc5Shape<N>::THREADS, Tc5Shape<N>::MIN_BLOCKS)
                     uint32_t h, l;
                     SP::split(v.x, v.y, h, l);
                     const int rho = item_local * R + nn;
-                    unsigned char* tile = Abuf + (rho >> 7) * S::LTILE;
+                    unsigned char* tile = Abuf + (LT == 1 ? 0 : (rho >> 7)) * S::LTILE;
                     kput32(tile, rho & 127, 2 * k1R, h);
                     kput32(tile, rho & 127, 32 + 2 * k1R, l);
                 }
@@ -619,7 +619,7 @@ __global__ void __launch_bounds__(Tc5Shape<N>::THREADS, Tc5Shape<N>::MIN_BLOCKS)
             {
                 const float4* rows4 = reinterpret_cast<const float4*>(img);
                 float4* prow = reinterpret_cast<float4*>(part + (size_t)jz * N);
-                for (int x4 = tid; x4 < N / 4; x4 += blockDim.x) {
+                for (int x4 = tid; x4 < N / 4; x4 += S::THREADS) {
                     float4 acc = rows4[x4];
 #pragma unroll
                     for (int w2 = 1; w2 < 4; ++w2) {

@@ -1,6 +1,7 @@
 """Run one window of A and A^T on a synthetic survey, for timing and profiling the sweep kernels.
 
-    python -m paper_1801_00819_gb300.sweep_case [--workload realistic|tiny] [--reps N] [--gradient [--tune-gradient]]
+    python -m paper_1801_00819_gb300.sweep_case [--workload realistic|tiny|precision] [--reps N] [--shots K]
+        [--freq-stride S] [--transform T] [--gradient [--tune-gradient]]
 
 Prepares the workload's grid, velocity, geometry and frequencies on the device, random data for
 one window of K shots, then calls lsm_forward and lsm_adjoint through the C ABI `reps` times each
@@ -30,7 +31,10 @@ def main():
     ap.add_argument("--workload", default="realistic", choices=("realistic", "tiny", "precision"))
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--shots", type=int, default=0, help="shots per call (default: the window length)")
-    ap.add_argument("--transform", default="fft", help="fft, dft_bf16x3, dft_fp16x3 or dft_bf16x1")
+    ap.add_argument("--freq-stride", type=int, default=1,
+                    help="keep every n-th frequency of the workload (smaller captures)")
+    ap.add_argument("--transform", default="fft",
+                    help="fft, dft_bf16x3, dft_fp16x3, dft_bf16x1, dft_fp16x3_tcgen05 or dft_bf16x3_tcgen05")
     ap.add_argument("--gradient", action="store_true", help="also time lsm_born_gradient on the window")
     ap.add_argument("--tune-gradient", action="store_true",
                     help="with --gradient: record the fastest checkpoint stride (lsm_autotune_gradient) first")
@@ -43,6 +47,9 @@ def main():
     from synth import config_precision, config_realistic, config_tiny
 
     sv = {"realistic": config_realistic, "tiny": config_tiny, "precision": config_precision}[args.workload]()
+    if args.freq_stride > 1:
+        sv.freqs = sv.freqs[::args.freq_stride].copy()
+        sv.wavelet = sv.wavelet[::args.freq_stride].copy()
     K = args.shots or sv.window
     ds = to_device(sv.nx, sv.nz, sv.dx, sv.dz, sv.slowness, sv.src_ix, sv.rec_ix, sv.freqs, sv.wavelet)
     rng = np.random.default_rng(0)
