@@ -271,3 +271,19 @@ def test_tcgen05_launch_shapes(lib):
         assert ei.value.status == lib.LSM_ERR_UNSUPPORTED_NX
     with pytest.raises(lib.LsmError):
         lib.lsm_tcgen05_shape(512, 0, 4)
+
+
+def test_header_constants_match_binding(lib):
+    """Every integer #define LSM_* of include/lsm.h that the binding mirrors has the header's value,
+    and the status, op, transform and graph-mode codes are all mirrored."""
+    src = open(os.path.join(ROOT, "include", "lsm.h")).read()
+    defs = {m.group(1): int(m.group(2))
+            for m in re.finditer(r"#define\s+(LSM_[A-Z0-9_]+)\s+\(?(-?\d+)\)?(?=\s|$)", src, flags=re.M)}
+    assert defs, "no constants parsed"
+    assert "(64u << 20)" in src and lib.LSM_STATIC_SCRATCH_BYTES == 64 << 20
+    for name, value in defs.items():
+        if hasattr(lib, name):
+            assert getattr(lib, name) == value, name
+    for prefix in ("LSM_ERR_", "LSM_OP_", "LSM_CUDA_GRAPH_"):
+        for name in (n for n in defs if n.startswith(prefix)):
+            assert hasattr(lib, name), name
