@@ -436,15 +436,18 @@ __device__ __forceinline__ void fft_inverse(float2 (&v)[V], const Twiddles<N, V>
 }
 
 // One phase-shift step in the transform domain for two-stage plans, F^-1 (phi . F v): forward
-// first stage in registers, then, per last-stage butterfly (a runtime loop, so its code exists
-// once), forward last stage -> multiply by phi (or conj(phi)) -> inverse last stage in place in
-// the exchange buffer, then the inverse first stage in registers.  Equivalent to fft_forward, a
-// pointwise multiply in the digit-reversed register order, and fft_inverse; the smaller code
-// footprint keeps more of the depth loop in the instruction cache.  phi is indexed like the
-// register layout: phi[r * T + t] multiplies register r of thread t.
-template <int N, int V, bool CONJ>
+// first stage in registers, then, per last-stage butterfly, forward last stage -> multiply by phi
+// (or conj(phi)) -> inverse last stage in place in the exchange buffer, then the inverse first stage
+// in registers.  Equivalent to fft_forward, a pointwise multiply in the digit-reversed register
+// order, and fft_inverse.  phi is indexed like the register layout: phi[r * T + t] multiplies
+// register r of thread t.  UNROLL runs a thread's last-stage butterflies side by side (more
+// independent work while its own registers are parked in shared memory; source and forward sweeps
+// at nx = 512: 0.87 -> 0.83 and 0.83 -> 0.80 ms); without it they run as a runtime loop whose code
+// exists once, which the adjoint sweep, holding the next source-wavefield row in registers as well,
+// measured faster (0.855 against 0.866 ms).  mid() runs once the first stage's outputs are stored.
+template <int N, int V, bool CONJ, bool UNROLL, class Mid>
 __device__ __forceinline__ void phase_shift_two_stage(float2 (&v)[V], const Twiddles<N, V>& tw, float2* buf, int t,
-                                                      const float2* phi) {
+                                                      const float2* phi, Mid&& mid) {
     using P = Plan<N, V>;
     static_assert(P::NS == 2, "two-stage plans only");
     constexpr int R0 = P::R(0), R1 = P::R(1), M1 = P::M(1), L1 = P::L(1), T = P::T;
@@ -455,8 +458,8 @@ __device__ __forceinline__ void phase_shift_two_stage(float2 (&v)[V], const Twid
     __syncwarp();
     store_outputs<N, V, 0>(v, buf, t);
     __syncwarp();
-#pragma unroll 1
-    for (int i = 0; i < P::NB(1); ++i) {
+    mid();  // the caller's work for while the thread's registers are parked (e.g. loads to issue)
+    auto last_stage_block = [&](int i) {
         float2* blk = buf + (t + T * i) * L1;  // last-stage block, unit stride
         const int a0 = (t + T * i) * L1;
         float2 u[R1];
@@ -471,6 +474,13 @@ __device__ __forceinline__ void phase_shift_two_stage(float2 (&v)[V], const Twid
         small_dft<R1, true>(u);
 #pragma unroll
         for (int n2 = 0; n2 < R1; ++n2) blk[P::phys(a0 + n2) - a0] = u[n2];
+    };
+    if constexpr (UNROLL) {
+#pragma unroll
+        for (int i = 0; i < P::NB(1); ++i) last_stage_block(i);
+    } else {
+#pragma unroll 1
+        for (int i = 0; i < P::NB(1); ++i) last_stage_block(i);
     }
     __syncwarp();
     load_outputs<N, V, 0>(v, buf, t);

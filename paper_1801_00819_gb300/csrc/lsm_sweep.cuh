@@ -68,14 +68,24 @@ __device__ __forceinline__ double sweep_sum_partials(const double* __restrict__ 
     return tot;
 }
 
-// phi, dss: this depth's rows staged in shared memory
+// Whether a step issues the caller's loads for the step (mid) once its first stage has parked the
+// thread's registers in shared memory: two-stage plans of 1024 points, whose steps are long enough
+// to hide the loads' latency from there.
 template <int N, int V>
+constexpr bool step_loads_mid() {
+    return Plan<N, V>::NS == 2 && Plan<N, V>::NB(0) == 1 && N >= 1024;
+}
+
+// phi, dss: this depth's rows staged in shared memory; mid(): see step_loads_mid (otherwise the
+// caller issues its loads before the step and passes a no-op)
+template <int N, int V, class Mid>
 __device__ __forceinline__ void step_down(float2 (&v)[V], const Twiddles<N, V>& tw, float2* buf, int t,
-                                          const float2* phi, const float2* dss) {
+                                          const float2* phi, const float2* dss, Mid&& mid) {
     constexpr int T = Plan<N, V>::T;
     if constexpr (Plan<N, V>::NS == 2 && Plan<N, V>::NB(0) == 1) {
-        phase_shift_two_stage<N, V, false>(v, tw, buf, t, phi);
+        phase_shift_two_stage<N, V, false, true>(v, tw, buf, t, phi, mid);
     } else {
+        mid();
         fft_forward<N, V>(v, tw, buf, t);
 #pragma unroll
         for (int r = 0; r < V; ++r) v[r] = cmul(v[r], phi[t + T * r]);
@@ -85,14 +95,22 @@ __device__ __forceinline__ void step_down(float2 (&v)[V], const Twiddles<N, V>& 
     for (int r = 0; r < V; ++r) v[r] = cmul(v[r], dss[Plan<N, V>::xpos(t, r)]);
 }
 
-template <int N, int V>
+// mid(): the adjoint sweep's load of the next source row, issued inside the step where
+// step_loads_mid holds (A^T at 1024 x 512: 2.71 -> 2.63 ms) and before it otherwise, which leaves the
+// whole step to hide its latency (at 512 and 256 points the later load measured 5 and 15 % slower).
+template <int N, int V, class Mid>
 __device__ __forceinline__ void step_down_adjoint(float2 (&v)[V], const Twiddles<N, V>& tw, float2* buf, int t,
-                                                  const float2* phi, const float2* dss) {
+                                                  const float2* phi, const float2* dss, Mid&& mid) {
     constexpr int T = Plan<N, V>::T;
+    constexpr bool kTwoStage = Plan<N, V>::NS == 2 && Plan<N, V>::NB(0) == 1;
+    constexpr bool kLoadMid = step_loads_mid<N, V>();
+    if constexpr (!kLoadMid) mid();
 #pragma unroll
     for (int r = 0; r < V; ++r) v[r] = cmulc(v[r], dss[Plan<N, V>::xpos(t, r)]);
-    if constexpr (Plan<N, V>::NS == 2 && Plan<N, V>::NB(0) == 1) {
-        phase_shift_two_stage<N, V, true>(v, tw, buf, t, phi);
+    if constexpr (kLoadMid) {
+        phase_shift_two_stage<N, V, true, true>(v, tw, buf, t, phi, mid);
+    } else if constexpr (kTwoStage) {
+        phase_shift_two_stage<N, V, true, false>(v, tw, buf, t, phi, [] {});
     } else {
         fft_forward<N, V>(v, tw, buf, t);
 #pragma unroll
@@ -232,7 +250,7 @@ __global__ void __launch_bounds__(sweep_max_threads<N, V>()) sweep_kernel(const 
                     __syncthreads();
                     for (int k = j + DEP; k < j + 2 * DEP && k + 1 < nz; ++k) stage_rows(k, slot_of(k), false);
                 }
-                step_down<N, V>(v, tw, buf, t, phi_of(slot_of(j)), dss_of(slot_of(j)));
+                step_down<N, V>(v, tw, buf, t, phi_of(slot_of(j)), dss_of(slot_of(j)), [] {});
             }
         }
     } else if constexpr (MODE == MODE_ADJOINT) {
@@ -357,9 +375,10 @@ __global__ void __launch_bounds__(sweep_max_threads<N, V>()) sweep_kernel(const 
                 }
             }
             if (j + 1 < nz) {
-                // S_{j+1} is requested here so that its HBM latency hides behind the propagation step
-                load_row<N, V>(s, Sitem + (size_t)(j + 1) * N, t, ok);
-                step_down_adjoint<N, V>(v, tw, buf, t, phi_of(j & 1), dss_of(j & 1));
+                // S_{j+1} is requested with the propagation step so that its HBM latency hides
+                // behind it
+                step_down_adjoint<N, V>(v, tw, buf, t, phi_of(j & 1), dss_of(j & 1),
+                                        [&] { load_row<N, V>(s, Sitem + (size_t)(j + 1) * N, t, ok); });
             }
         }
     } else {  // MODE_FORWARD
@@ -373,10 +392,12 @@ __global__ void __launch_bounds__(sweep_max_threads<N, V>()) sweep_kernel(const 
         cp_async_commit();
         for (int k = 0; k < DEP && k + 1 < nz; ++k) stage_rows(nz - 2 - k, slot_of(k), true);
         for (int j = nz - 1; j >= 0; --j) {
-            // request S_j before propagating U_{j+1} so the load overlaps the step
+            // request S_j before (or, see step_loads_mid, during) propagating U_{j+1} so the load
+            // overlaps the step
             float2 s[V];
-            load_row<N, V>(s, Sitem + (size_t)j * N, t, ok);
+            auto load_s = [&] { load_row<N, V>(s, Sitem + (size_t)j * N, t, ok); };
             const int k = nz - 2 - j;  // -1 for the deepest row, which is not propagated
+            if (!step_loads_mid<N, V>() || k < 0) load_s();
             if (k < 0 || k % DEP == 0) {
                 cp_async_wait_all();
                 __syncthreads();
@@ -387,7 +408,10 @@ __global__ void __launch_bounds__(sweep_max_threads<N, V>()) sweep_kernel(const 
                     for (int k2 = k + DEP; k2 < k + 2 * DEP && k2 + 1 < nz; ++k2)
                         stage_rows(nz - 2 - k2, slot_of(k2), true);
                 }
-                step_down<N, V>(v, tw, buf, t, phi_of(slot_of(k)), dss_of(slot_of(k)));
+                if constexpr (step_loads_mid<N, V>())
+                    step_down<N, V>(v, tw, buf, t, phi_of(slot_of(k)), dss_of(slot_of(k)), load_s);
+                else
+                    step_down<N, V>(v, tw, buf, t, phi_of(slot_of(k)), dss_of(slot_of(k)), [] {});
                 mrow = mstage + slot_of(k) * N;
             } else {
                 mrow = mstage + DEP * N;
