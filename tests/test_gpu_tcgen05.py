@@ -59,6 +59,10 @@ OPERATOR_CASES = {
     "ragged512": lambda: random_case(512, 24, 3, 5, seed=512),
     "staged1024": lambda: random_case(1024, 16, 3, 5, seed=514),  # 3 shots: rows staged (4 slots)
     "direct1024": lambda: random_case(1024, 12, 2, 5, seed=517),  # 2 shots: rows read from global memory
+    # degenerate: one depth row (no propagation step), and one (shot, frequency) item with two depths
+    "nz1_128": lambda: random_case(128, 1, 2, 3, seed=518),
+    "one_item_1024": lambda: random_case(1024, 2, 1, 1, seed=519),
+    "one_item_256": lambda: random_case(256, 2, 1, 1, seed=520),
 }
 
 
