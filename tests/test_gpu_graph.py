@@ -279,3 +279,25 @@ def test_cuda_graph_option_out_of_range_is_rejected(torch_cuda):
         ctypes.byref(ds.grid.c), lsm._ptr(ds.slowness), ctypes.byref(ds.freqs.c), ctypes.byref(ds.geom.c), lsm._ptr(d),
         1.0, 2, 1, 0.0, 2, 0, 0, lsm._ptr(m), stats, 4, lsm._ptr(ws), lsm._nbytes(ws), None, ctypes.byref(opts))
     assert st == lsm.LSM_ERR_ARG
+
+
+def test_solve_graph_with_no_window_left_launches_nothing(torch_cuda):
+    """A call resumed after the last window (first_window = number of windows) returns at once in
+    every loop form: no launch, image unchanged."""
+    import paper_1801_00819_gb300 as L
+    sv = random_case(64, 8, 5, 3, seed=99)
+    op = oracle_operator(sv)
+    d, lam = _data(sv, op)
+    ds = device_survey(sv)
+    nwin = L.lsm.load_library().lsm_num_windows(sv.ns, 2, 1)
+    ws = torch_cuda.empty(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, 2, L.LSM_OP_SOLVE),
+                          dtype=torch_cuda.uint8, device="cuda")
+    m = torch_cuda.full((sv.nz, sv.nx), 0.25, dtype=torch_cuda.float32, device="cuda")
+    for mode in (False, True, "solve"):
+        before = L.lsm_kernel_launches()
+        status, stats = L.rls_window_solve(ds.grid, ds.slowness, ds.freqs, ds.geom,
+                                           torch_cuda.as_tensor(d, device="cuda"), lam, 2, 1, 0.0, 3, m, ws,
+                                           first_window=nwin, cuda_graph=mode)
+        torch_cuda.cuda.synchronize()
+        assert status == 0 and stats == [] and L.lsm_kernel_launches() == before
+    assert bool((m == 0.25).all())
