@@ -1,11 +1,12 @@
-"""The sliding-window solve sharded by frequency over two ranks (rls_window_solve_sharded), run as
-two processes on the one GPU that sum their images and ||q||^2 through gloo on host copies (the
-kernels of the two processes never wait on each other).  Each rank holds half of the frequencies;
-the two ranks must keep identical images, take the single-process solve's iteration counts and
-return its image and the FP64 oracle's.  The sharded solve adds the ranks' images and ||q||^2 in
-another order than the single process does (rank sums, then the two ranks), so its iterates differ
-in the last bits; over this solve's 22 iterations that grows to 1.1e-5, the same size as the float32
-solve's distance from the oracle (1.4e-5): both are bounded here by 5e-5 and 1e-4."""
+"""The sliding-window solve sharded by frequency over two and three ranks (rls_window_solve_sharded),
+run as processes on the one GPU that sum their images and ||q||^2 through gloo on host copies (the
+kernels of the processes never wait on each other).  Each rank holds a contiguous block of the
+frequencies (uneven blocks with three ranks); the ranks must keep identical images and statistics,
+take the single-process solve's iteration counts and return its image and the FP64 oracle's.  The sharded solve adds the ranks' images and ||q||^2 in
+another order than the single process does (rank sums, then the ranks), so its iterates differ in
+the last bits; over these solves' 21-22 iterations that grows to at most a few 1e-6 (measured 4.3e-6
+and 2.1e-6), below the float32 solve's distance from the oracle (up to 1.2e-5): both are bounded
+here by 5e-5 and 1e-4."""
 
 import json
 import os
@@ -21,11 +22,13 @@ from tests._helpers import device_survey, oracle_operator, rel_l2
 pytestmark = pytest.mark.gpu
 
 CASE = dict(nx=128, nz=24, ns=8, nw=12, seed=77)
+# three ranks on 13 frequencies: shards of 5, 4 and 4
+CASE3 = dict(nx=128, nz=24, ns=8, nw=13, seed=78)
 K, SLIDE, TOL, ITERS = 4, 2, 1e-2, 40
 
 
-def _problem():
-    sv = random_case(CASE["nx"], CASE["nz"], CASE["ns"], CASE["nw"], seed=CASE["seed"])
+def _problem(case=CASE):
+    sv = random_case(case["nx"], case["nz"], case["ns"], case["nw"], seed=case["seed"])
     op = oracle_operator(sv)
     clean = op.forward(np.asarray(sv.reflectivity, dtype=np.float32).astype(np.float64))
     d = (clean + sv.noise_pct * np.sqrt(np.mean(np.abs(clean) ** 2)) * sv.noise()).astype(np.complex64)
@@ -33,7 +36,7 @@ def _problem():
     return sv, op, d, lam
 
 
-def _rank_main(rank, world, port, out_dir, d_path, lam):
+def _rank_main(rank, world, port, out_dir, d_path, lam, case=CASE):
     import torch
     import torch.distributed as dist
 
@@ -45,7 +48,7 @@ def _rank_main(rank, world, port, out_dir, d_path, lam):
     torch.cuda.set_device(0)
     dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
     try:
-        sv = random_case(CASE["nx"], CASE["nz"], CASE["ns"], CASE["nw"], seed=CASE["seed"])
+        sv = random_case(case["nx"], case["nz"], case["ns"], case["nw"], seed=case["seed"])
         f0, f1 = frequency_shard(sv.nw, rank, world)
         ds = to_device(sv.nx, sv.nz, sv.dx, sv.dz, sv.slowness, sv.src_ix, sv.rec_ix, sv.freqs[f0:f1],
                        sv.wavelet[f0:f1])
@@ -63,20 +66,23 @@ def _rank_main(rank, world, port, out_dir, d_path, lam):
         dist.destroy_process_group()
 
 
-def test_two_rank_frequency_sharded_solve(tmp_path):
+@pytest.mark.parametrize("world", [2, 3])
+def test_frequency_sharded_solve(tmp_path, world):
+    """world = 2: 12 frequencies in two shards of 6; world = 3: 13 frequencies in shards of 5, 4, 4."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import torch.multiprocessing as mp
 
     import paper_1801_00819_gb300 as L
-    sv, op, d, lam = _problem()
+    case = CASE if world == 2 else CASE3
+    sv, op, d, lam = _problem(case)
     d_path = str(tmp_path / "d.npy")
     np.save(d_path, d)
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
         port = s.getsockname()[1]
-    mp.spawn(_rank_main, args=(2, port, str(tmp_path), d_path, lam), nprocs=2, join=True)
+    mp.spawn(_rank_main, args=(world, port, str(tmp_path), d_path, lam, case), nprocs=world, join=True)
 
     # the same solve in one process
     ds = device_survey(sv)
@@ -88,12 +94,15 @@ def test_two_rank_frequency_sharded_solve(tmp_path):
     torch.cuda.synchronize()
     single = m1.cpu().numpy().astype(np.float64)
     m_ref, st_ref = O.rls_solve(op, d.astype(np.complex128), lam, K, SLIDE, ITERS, tol=TOL)
-    ranks = [np.load(tmp_path / f"m{r}.npy").astype(np.float64) for r in range(2)]
-    stats = [json.load(open(tmp_path / f"stats{r}.json")) for r in range(2)]
+    ranks = [np.load(tmp_path / f"m{r}.npy").astype(np.float64) for r in range(world)]
+    stats = [json.load(open(tmp_path / f"stats{r}.json")) for r in range(world)]
     print(json.dumps({"iters": [[w["iters"] for w in st] for st in stats], "single": [w["iters"] for w in st1],
                       "oracle": [w.iters for w in st_ref], "vs_single": rel_l2(ranks[0], single),
                       "vs_oracle": rel_l2(ranks[0], m_ref)}))
-    np.testing.assert_array_equal(ranks[0], ranks[1])  # the ranks keep identical model-space vectors
+    for r in range(1, world):
+        np.testing.assert_array_equal(ranks[0], ranks[r])  # the ranks keep identical model-space vectors
+        assert [{k: v for k, v in w.items() if k != "ms"} for w in stats[r]] == \
+            [{k: v for k, v in w.items() if k != "ms"} for w in stats[0]]
     assert [w["iters"] for w in stats[0]] == [w["iters"] for w in st1] == [w.iters for w in st_ref]
     assert rel_l2(ranks[0], single) <= 5e-5
     assert rel_l2(ranks[0], m_ref) <= 1e-4
