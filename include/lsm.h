@@ -156,8 +156,8 @@ int lsm_adjoint(const lsm_grid* grid, const float* slowness, const lsm_freqs* fr
  *      complex gradients), or NULL to only model d;
  *   d_out: device complex64 [nshots][nw][nrec] or NULL (required when g is NULL);
  *   grad_m, grad_s: device float32 [nz][nx] or NULL; overwritten.
- * Workspace: lsm_workspace_bytes(..., nshots, LSM_OP_GRADIENT).  Gradients need nx <= 512
- * (LSM_ERR_UNSUPPORTED_NX otherwise); modelling supports every nx of lsm_forward.
+ * Workspace: lsm_workspace_bytes(..., nshots, LSM_OP_GRADIENT).  Gradients need a power-of-two nx
+ * from 16 to 1024 (LSM_ERR_UNSUPPORTED_NX otherwise); modelling supports every nx of lsm_forward.
  */
 int lsm_born_gradient(const lsm_grid* grid, const float* slowness, const double* sref,
                       const lsm_freqs* freqs, const lsm_geom* geom, const float* m,
@@ -467,8 +467,8 @@ int lsm_tcgen05_shape(int nx, int nshots, int nw, int* items, int* threads, int*
  * same (nx, nz, nshots, nw) use it.  lsm_workspace_bytes(..., LSM_OP_GRADIENT) already reserves
  * room for every candidate.  Needs a workspace of lsm_workspace_bytes(grid, geom, freqs, nshots,
  * LSM_OP_GRADIENT); runs shots [0, nshots) on zero-valued model and data-space gradient, overwrites
- * the workspace, and returns after synchronising the stream.  Gradients need nx <= 512
- * (LSM_ERR_UNSUPPORTED_NX otherwise).  `report` (may be NULL) receives the chosen and the default
+ * the workspace, and returns after synchronising the stream.  Gradients need a power-of-two nx from
+ * 16 to 1024 (LSM_ERR_UNSUPPORTED_NX otherwise).  `report` (may be NULL) receives the chosen and the default
  * stride and warps per block, their mean launch times in ms and the number of pairs timed.  The
  * gradients do not depend on the stride; the warps per block change the block partition of the
  * image sums and so their last bits.  lsm_autotune_reset also forgets these choices.

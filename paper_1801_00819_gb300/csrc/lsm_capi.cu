@@ -194,11 +194,11 @@ static int tuned_gradient_warps(int nx, int nz, int nshots, int nw) {
     auto it = g_ckpt_tune.find(k);
     return it == g_ckpt_tune.end() ? 0 : it->second.warps;
 }
-// rows of nx complex values one item keeps at stride c: S and R checkpoints, then the segment's
-// S rows (c + 1) and R rows (c)
+// rows of nx complex values one item keeps at stride c: S and R checkpoints, the segment's S rows
+// (c + 1) and R rows (c), and two parking rows (U and mu)
 static size_t ckpt_rows(int c, int nz) {
     c = std::min(c, nz);
-    return 2 * (size_t)((nz + c - 1) / c) + 2 * (size_t)c + 1;
+    return 2 * (size_t)((nz + c - 1) / c) + 2 * (size_t)c + 1 + 2;
 }
 
 // most warps per block a sweep of this mode can take (registers, shared memory)
@@ -246,7 +246,7 @@ bool gradient_nx_supported(int nx) {
 // gradient launch with `warps` warps per block (at most the heuristic's, so shared memory fits)
 static SweepShape gradient_shape_for(int nx, int nshots, int nw, int warps) {
     const NxOps* ops = nx_ops(nx);
-    const int V = gradient_points_per_thread();
+    const int V = gradient_points_per_thread(nx);
     const int ipw = 32 / (nx / V);
     const int warps_total = (nshots * nw + ipw - 1) / ipw;
     SweepShape s;
@@ -261,7 +261,7 @@ static SweepShape gradient_shape_for(int nx, int nshots, int nw, int warps) {
 // limits of one block
 SweepShape gradient_shape(int nx, int nshots, int nw, int num_sms) {
     const NxOps* ops = nx_ops(nx);
-    const int V = gradient_points_per_thread();
+    const int V = gradient_points_per_thread(nx);
     const int ipw = 32 / (nx / V);
     const int warps_total = (nshots * nw + ipw - 1) / ipw;
     int maxw = std::min(8, ops->gradient_max_warps());
@@ -803,6 +803,7 @@ static GradArgs grad_args(const lsm_grid* grid, const lsm_freqs* freqs, const ls
     const size_t ncp = (size_t)((grid->nz + c - 1) / c);
     ga.ckpt = reinterpret_cast<float2*>(ws + L.ckpt);
     ga.seg = ga.ckpt + items * 2 * ncp * grid->nx;
+    ga.park = ga.seg + items * (2 * (size_t)std::min(c, grid->nz) + 1) * grid->nx;
     ga.part_m = reinterpret_cast<float*>(ws + L.part);
     ga.part_s = reinterpret_cast<float*>(ws + L.part_s);
     return ga;

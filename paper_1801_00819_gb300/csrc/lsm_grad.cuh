@@ -169,11 +169,47 @@ __global__ void __launch_bounds__(256) gradient_kernel(const GradArgs a) {
         }
     }
 
-    // ---------------- phase 2: segments bottom-up
-    float2 U[V], mu[V];
+    // ---------------- phase 2: segments bottom-up.  Per segment the S and R rows are recomputed
+    // into the item's segment buffer, then two passes run up the segment: U (with dL/dm and the
+    // conj(R_j) P_j U_{j+1} term of dL/ds), then mu (the conj(mu_{j+1}) S_{j+1} term).  Only one of
+    // U and mu is in registers at a time; the other waits in the item's two parking rows.
+    float2 U[V];
 #pragma unroll
-    for (int r = 0; r < V; ++r) U[r] = mu[r] = make_float2(0.f, 0.f);
-    int depth_count = 0;  // barrier parity
+    for (int r = 0; r < V; ++r) U[r] = make_float2(0.f, 0.f);
+    float2* Upark = a.park + slot * 2 * N;
+    float2* Mpark = Upark + N;
+    grad_store<N, V>(Mpark, U, t, ok);  // mu below the deepest row: zero
+    int depth_count = 0;  // image-row buffer parity
+    // the block's rows of a gradient summed in warp order and written (or, add_to, added) to its
+    // partial row of depth j, four columns a thread
+    auto block_sum = [&](int b, int which, float* part, int j, bool add_to) {
+        const float4* rows = reinterpret_cast<const float4*>(img + (size_t)(b * 2 + which) * nwarps * N);
+        float4* prow = reinterpret_cast<float4*>(part + ((size_t)blockIdx.x * nz + j) * N);
+        for (int x4 = threadIdx.x; x4 < N / 4; x4 += blockDim.x) {
+            float4 acc = rows[x4];
+            for (int w2 = 1; w2 < nwarps; ++w2) {
+                const float4 u4 = rows[w2 * (N / 4) + x4];
+                acc.x += u4.x; acc.y += u4.y; acc.z += u4.z; acc.w += u4.w;
+            }
+            if (add_to) {
+                const float4 p4 = prow[x4];
+                acc.x += p4.x; acc.y += p4.y; acc.z += p4.z; acc.w += p4.w;
+            }
+            prow[x4] = acc;
+        }
+    };
+    // one gradient row per warp: the items of equal t summed by shuffles, then lane group 0 writes
+    auto warp_row = [&](float (&gv)[V], float* slab) {
+#pragma unroll
+        for (int off = T; off < 32; off <<= 1) {
+#pragma unroll
+            for (int r = 0; r < V; ++r) gv[r] += __shfl_xor_sync(0xffffffffu, gv[r], off);
+        }
+        if (sub == 0) {
+#pragma unroll
+            for (int r = 0; r < V; ++r) slab[t + T * r] = ok ? gv[r] : 0.f;
+        }
+    };
     for (int seg = ncp - 1; seg >= 0; --seg) {
         const int j0 = seg * c;
         const int j1 = min(j0 + c, nz);
@@ -213,96 +249,88 @@ __global__ void __launch_bounds__(256) gradient_kernel(const GradArgs a) {
                 }
             }
         }
-        // phase 2 of the segment: row j of step j is in buffer (j1 - 1 - j) % 2; rows j1 - 1 and
-        // j1 - 2 are staged up front, and row j - 2 replaces row j once every warp is past step j
-        __syncthreads();
-        stage_row(j1 - 1, 0);
-        if (j1 - 2 >= j0) stage_row(j1 - 2, 1);
-        cp_async_wait_all();
-        __syncthreads();
+        // each pass: row j of step j is in buffer (j1 - 1 - j) % 2; rows j1 - 1 and j1 - 2 are
+        // staged up front, and row j - 2 replaces row j once every warp is past step j
+        auto stage_pass = [&]() {
+            __syncthreads();
+            stage_row(j1 - 1, 0);
+            if (j1 - 2 >= j0) stage_row(j1 - 2, 1);
+            cp_async_wait_all();
+            __syncthreads();
+        };
+        // pass U: U_j = S_j m_j + P_j U_{j+1}; dL/dm_j = Re conj(S_j) R_j; dL/ds_j gets
+        // Re(i w dz conj(R_j) P_j U_{j+1}) = -w dz Im(conj(R_j) P_j U_{j+1})
+        stage_pass();
         for (int j = j1 - 1; j >= j0; --j, ++depth_count) {
             const float* mrow = a.m + (size_t)j * N;
-            // P_j U_{j+1} (zero at the deepest row)
             const int bj = (j1 - 1 - j) & 1;
             if (j + 1 < nz) grad_step<N, V, false>(U, tw, buf, t, phi_s(bj), dss_s(bj));
-            float2 Rj[V];
-            grad_load<N, V>(Rj, Rseg + (size_t)(j - j0) * N, t, ok);
             float gs[V], gm[V];
-#pragma unroll
-            for (int r = 0; r < V; ++r) gs[r] = fmaf(Rj[r].x, U[r].y, -Rj[r].y * U[r].x);  // Im conj(R) PU
-            if (j + 1 < nz) {
-                float2 S1[V];
-                grad_load<N, V>(S1, Sseg + (size_t)(j + 1 - j0) * N, t, ok);
-#pragma unroll
-                for (int r = 0; r < V; ++r) gs[r] += fmaf(mu[r].x, S1[r].y, -mu[r].y * S1[r].x);  // Im conj(mu) S1
-            }
-            {
-                float2 Sj[V];
-                grad_load<N, V>(Sj, Sseg + (size_t)(j - j0) * N, t, ok);
-#pragma unroll
-                for (int r = 0; r < V; ++r) {
-                    const float mm = __ldg(mrow + t + T * r);
-                    gm[r] = fmaf(Sj[r].x, Rj[r].x, Sj[r].y * Rj[r].y);
-                    U[r].x = fmaf(Sj[r].x, mm, U[r].x);
-                    U[r].y = fmaf(Sj[r].y, mm, U[r].y);
-                }
-            }
-            // Re(i z) = -Im(z)
-#pragma unroll
-            for (int r = 0; r < V; ++r) gs[r] = -wdz * gs[r];
-            // mu_j = m_j R_j + P_j^H mu_{j+1}
-            if (j + 1 < nz) {
-                grad_step<N, V, true>(mu, tw, buf, t, phi_s(bj), dss_s(bj));
-            } else {
-#pragma unroll
-                for (int r = 0; r < V; ++r) mu[r] = make_float2(0.f, 0.f);
-            }
+            const float2* Rrow = Rseg + (size_t)(j - j0) * N;
+            const float2* Srow = Sseg + (size_t)(j - j0) * N;
 #pragma unroll
             for (int r = 0; r < V; ++r) {
+                const float2 Rj = ok ? Rrow[t + T * r] : make_float2(0.f, 0.f);
+                const float2 Sj = ok ? Srow[t + T * r] : make_float2(0.f, 0.f);
                 const float mm = __ldg(mrow + t + T * r);
-                mu[r].x = fmaf(mm, Rj[r].x, mu[r].x);
-                mu[r].y = fmaf(mm, Rj[r].y, mu[r].y);
-            }
-            // sum both gradient rows over the block's items
-#pragma unroll
-            for (int off = T; off < 32; off <<= 1) {
-#pragma unroll
-                for (int r = 0; r < V; ++r) {
-                    gm[r] += __shfl_xor_sync(0xffffffffu, gm[r], off);
-                    gs[r] += __shfl_xor_sync(0xffffffffu, gs[r], off);
-                }
+                gs[r] = -wdz * fmaf(Rj.x, U[r].y, -Rj.y * U[r].x);
+                gm[r] = fmaf(Sj.x, Rj.x, Sj.y * Rj.y);
+                U[r].x = fmaf(Sj.x, mm, U[r].x);
+                U[r].y = fmaf(Sj.y, mm, U[r].y);
             }
             const int b = depth_count & 1;
-            float* slab_m = img + ((size_t)(b * 2 + 0) * nwarps + warp) * N;
-            float* slab_s = img + ((size_t)(b * 2 + 1) * nwarps + warp) * N;
-            if (sub == 0) {
+            warp_row(gm, img + ((size_t)(b * 2 + 0) * nwarps + warp) * N);
+            warp_row(gs, img + ((size_t)(b * 2 + 1) * nwarps + warp) * N);
+            cp_async_wait_all();
+            __syncthreads();  // gradient rows visible; row j - 1 staged and visible; every warp is past step j
+            if (j - 2 >= j0) stage_row(j - 2, bj);
+            block_sum(b, 0, a.part_m, j, false);
+            block_sum(b, 1, a.part_s, j, false);
+        }
+        // pass mu: mu_j = m_j R_j + P_j^H mu_{j+1}; dL/ds_j gets -w dz Im(conj(mu_{j+1}) S_{j+1}),
+        // added to the partial row pass U wrote
+        grad_store<N, V>(Upark, U, t, ok);
+        {
+            float2 mu[V];
+            grad_load<N, V>(mu, Mpark, t, ok);
+            stage_pass();
+            for (int j = j1 - 1; j >= j0; --j, ++depth_count) {
+                const float* mrow = a.m + (size_t)j * N;
+                const int bj = (j1 - 1 - j) & 1;
+                float gs[V];
+                if (j + 1 < nz) {
+                    const float2* S1row = Sseg + (size_t)(j + 1 - j0) * N;
+#pragma unroll
+                    for (int r = 0; r < V; ++r) {
+                        const float2 S1 = ok ? S1row[t + T * r] : make_float2(0.f, 0.f);
+                        gs[r] = -wdz * fmaf(mu[r].x, S1.y, -mu[r].y * S1.x);
+                    }
+                    grad_step<N, V, true>(mu, tw, buf, t, phi_s(bj), dss_s(bj));
+                } else {
+#pragma unroll
+                    for (int r = 0; r < V; ++r) {
+                        gs[r] = 0.f;
+                        mu[r] = make_float2(0.f, 0.f);
+                    }
+                }
+                const float2* Rrow = Rseg + (size_t)(j - j0) * N;
 #pragma unroll
                 for (int r = 0; r < V; ++r) {
-                    slab_m[t + T * r] = ok ? gm[r] : 0.f;
-                    slab_s[t + T * r] = ok ? gs[r] : 0.f;
+                    const float2 Rj = ok ? Rrow[t + T * r] : make_float2(0.f, 0.f);
+                    const float mm = __ldg(mrow + t + T * r);
+                    mu[r].x = fmaf(mm, Rj.x, mu[r].x);
+                    mu[r].y = fmaf(mm, Rj.y, mu[r].y);
                 }
+                const int b = depth_count & 1;
+                warp_row(gs, img + ((size_t)(b * 2 + 1) * nwarps + warp) * N);
+                cp_async_wait_all();
+                __syncthreads();
+                if (j - 2 >= j0) stage_row(j - 2, bj);
+                block_sum(b, 1, a.part_s, j, true);
             }
-            cp_async_wait_all();
-            __syncthreads();  // image rows visible; row j - 1 staged and visible; every warp is past step j
-            if (j - 2 >= j0) stage_row(j - 2, bj);
-            {
-                // the block's partial rows: the warps' rows summed in warp order, four columns a thread
-                const float4* rows_m = reinterpret_cast<const float4*>(img + (size_t)(b * 2 + 0) * nwarps * N);
-                const float4* rows_s = reinterpret_cast<const float4*>(img + (size_t)(b * 2 + 1) * nwarps * N);
-                float4* pm = reinterpret_cast<float4*>(a.part_m + ((size_t)blockIdx.x * nz + j) * N);
-                float4* ps = reinterpret_cast<float4*>(a.part_s + ((size_t)blockIdx.x * nz + j) * N);
-                for (int x4 = threadIdx.x; x4 < N / 4; x4 += blockDim.x) {
-                    float4 am = rows_m[x4], as = rows_s[x4];
-                    for (int w2 = 1; w2 < nwarps; ++w2) {
-                        const float4 um = rows_m[w2 * (N / 4) + x4], us = rows_s[w2 * (N / 4) + x4];
-                        am.x += um.x; am.y += um.y; am.z += um.z; am.w += um.w;
-                        as.x += us.x; as.y += us.y; as.z += us.z; as.w += us.w;
-                    }
-                    pm[x4] = am;
-                    ps[x4] = as;
-                }
-            }
+            grad_store<N, V>(Mpark, mu, t, ok);
         }
+        grad_load<N, V>(U, Upark, t, ok);
     }
     // U now holds U_0: the modelled data of this item
     if (a.dout) {

@@ -61,12 +61,13 @@ struct GradArgs {
     const int* rec_ix;
     const float2* wavelet;
     const float* freq_hz;          // device [nw]
-    const float2* phi;             // coefficient tables in the order of Plan<nx, 16>
+    const float2* phi;             // coefficient tables in the order of Plan<nx, gradient_points_per_thread(nx)>
     const float2* dss;
     const float* m;                // [nz][nx]
     const float2* g;               // dL/dRe d + i dL/dIm d, [nshots][nw][nrec]
     float2* ckpt;                  // [items][2][ceil(nz/c)][nx]
     float2* seg;                   // [items][2c+1][nx]
+    float2* park;                  // [items][2][nx]: U and mu while the other is in registers
     float* part_m;                 // [blocks][nz][nx]
     float* part_s;                 // [blocks][nz][nx]
     float2* dout;                  // optional modelled data [nshots][nw][nrec]
@@ -153,8 +154,9 @@ constexpr int alt_points_per_thread(int nx) {
     return v;
 }
 
-// Points per thread of the gradient kernel (it carries three wavefields in registers).
-constexpr int gradient_points_per_thread() { return 16; }
+// Points per thread of the gradient kernel (two wavefields in registers at a time): 32 from 512
+// columns (32 x 16 and 32 x 32 plans), 16 below.
+constexpr int gradient_points_per_thread(int nx) { return nx >= 512 ? 32 : 16; }
 bool gradient_nx_supported(int nx);
 SweepShape gradient_shape(int nx, int nshots, int nw, int num_sms);
 cudaError_t launch_tables_grad(const TableArgs& a, cudaStream_t st);

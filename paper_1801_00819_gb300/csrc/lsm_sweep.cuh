@@ -684,7 +684,7 @@ struct Dispatch {
     }
 
     // gradient kernel: 16 points per thread, so nx <= 512
-    static constexpr int VG = gradient_points_per_thread();
+    static constexpr int VG = gradient_points_per_thread(N);
     static constexpr bool kGrad = (N & (N - 1)) == 0 && N >= VG && N / VG <= 32;
 
     static cudaError_t tables_grad(const TableArgs& a, cudaStream_t st) {

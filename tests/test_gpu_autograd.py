@@ -38,7 +38,8 @@ def _problem(nx=64, nz=32, ns=4, nw=8, seed=11, rec=None):
     return sv, ds, op, m, dobs
 
 
-@pytest.mark.parametrize("shape", [(64, 32, 4, 8), (128, 40, 3, 5), (512, 18, 2, 3), (32, 17, 5, 6)],
+@pytest.mark.parametrize("shape", [(64, 32, 4, 8), (128, 40, 3, 5), (256, 21, 3, 4), (512, 18, 2, 3), (1024, 20, 2, 3),
+                                   (32, 17, 5, 6)],
                          ids=lambda s: "x".join(map(str, s)))
 def test_gradients_match_oracle(torch_cuda, shape):
     import paper_1801_00819_gb300 as L
@@ -177,3 +178,23 @@ def test_gradients_full_size_properties(torch_cuda):
     fd = (loss(ds.slowness + h * v) - loss(ds.slowness - h * v)) / (2.0 * h)
     analytic = float((gs.double() * v.double()).sum())
     assert abs(fd - analytic) <= 1e-3 * abs(analytic), (fd, analytic)
+
+
+@pytest.mark.parametrize("nx", [384, 896])
+def test_gradient_rejects_other_widths_before_launch(torch_cuda, nx):
+    """Gradients exist for power-of-two widths only: a mixed-radix width is refused on the host."""
+    import paper_1801_00819_gb300 as L
+    torch = torch_cuda
+    sv, ds, op, m, dobs = _problem(nx, 6, 1, 2, seed=nx)
+    ws = torch.empty(max(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, 1, L.LSM_OP_FORWARD), 256),
+                     dtype=torch.uint8, device="cuda")
+    mt = torch.as_tensor(m.astype(np.float32), device="cuda")
+    gt = torch.zeros((1, 2, op.nrec), dtype=torch.complex64, device="cuda")
+    gm = torch.empty_like(mt)
+    gs = torch.empty_like(mt)
+    before = L.lsm_kernel_launches()
+    with pytest.raises(L.LsmError) as ei:
+        L.lsm_born_gradient(ds.grid, ds.slowness, torch.as_tensor(op.sref, device="cuda"), ds.freqs, ds.geom, mt, gt,
+                            None, gm, gs, 0, 1, ws)
+    assert ei.value.status == L.lsm.LSM_ERR_UNSUPPORTED_NX
+    assert L.lsm_kernel_launches() == before
