@@ -698,7 +698,7 @@ int lsm_adjoint_ex(const lsm_grid* grid, const float* slowness, const lsm_freqs*
     int nparts = 0;
     LSM_CHECK(run_adjoint(a, shot0, nshots, reinterpret_cast<const float2*>(d), nsm, st, &nparts, transform));
     LSM_CHECK(cg_reduce_image(a.part, nparts, grid->nx * grid->nz, nullptr, 0.f, accumulate ? 1 : 0, m_out,
-                              reinterpret_cast<double*>(ws + L.ss), st));
+                              reinterpret_cast<double*>(ws + L.ss), st, nullptr, nullptr, nullptr, nullptr, true));
     return LSM_OK;
 }
 
@@ -1232,7 +1232,7 @@ static cudaError_t cg_iteration(SweepArgs a, int start, int K, int nsm, int tran
                                    v.state);
         else if (e == cudaSuccess)
             e = cg_reduce_image(a.part, nparts, v.n, v.m, (float)v.lambda, 0, v.s, v.ss, st, v.minv, v.sz, v.p,
-                                v.state);
+                                v.state, true);
     } else {
         e = run_forward(a, start, K, v.p, v.q, nsm, st, transform);
         if (e == cudaSuccess) e = cg_norm2_c64(v.q, v.nd, v.qq, st);
@@ -1411,7 +1411,8 @@ static cudaError_t window_setup(const SolveCtx& c, int k, int prev_start, const 
     // b = A_k^T d_k  ->  ||b||^2
     if (!ok(run_adjoint(c.a, start, c.K, dk, c.nsm, st, &nparts, c.transform))) return e;
     if (shard) ok(shard_reduce_image(shard, c.a.part, nparts, c.n, nullptr, 0.f, c.s, c.ss, st, nullptr, nullptr));
-    else ok(cg_reduce_image(c.a.part, nparts, c.n, nullptr, 0.f, 0, c.s, c.ss, st));
+    else ok(cg_reduce_image(c.a.part, nparts, c.n, nullptr, 0.f, 0, c.s, c.ss, st, nullptr, nullptr, nullptr, nullptr,
+                            true));
     if (!ok(cg_store_sum(c.ss, c.state, st))) return e;
     // r = d_k - A_k m
     if (!ok(run_forward(c.a, start, c.K, c.m, c.q, c.nsm, st, c.transform))) return e;
@@ -1419,7 +1420,7 @@ static cudaError_t window_setup(const SolveCtx& c, int k, int prev_start, const 
     // s = A_k^T r - lambda m ; p = s ; gamma = ||s||^2
     if (!ok(run_adjoint(c.a, start, c.K, c.r, c.nsm, st, &nparts, c.transform))) return e;
     if (shard) ok(shard_reduce_image(shard, c.a.part, nparts, c.n, c.m, lamf, c.s, c.ss, st, c.minv, c.sz));
-    else ok(cg_reduce_image(c.a.part, nparts, c.n, c.m, lamf, 0, c.s, c.ss, st, c.minv, c.sz));
+    else ok(cg_reduce_image(c.a.part, nparts, c.n, c.m, lamf, 0, c.s, c.ss, st, c.minv, c.sz, nullptr, nullptr, true));
     if (e != cudaSuccess) return e;
     ok(cg_update_p(c.p, c.s, c.n, c.ss, 1, c.state, 1, 0, c.pp, st, c.minv, c.sz));
     return e;

@@ -5,6 +5,8 @@
 // added in block order by whichever kernel consumes them, so every scalar is deterministic.
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include "lsm_cg.h"
 #include "lsm_internal.h"
 
@@ -54,7 +56,7 @@ __global__ void __launch_bounds__(kRedThreads) reduce_image_kernel(const float* 
                                                                const float* __restrict__ minv,
                                                                double* __restrict__ sz_part,
                                                               const float* __restrict__ pdir,
-                                                              const CgState* __restrict__ st) {
+                                                              const CgState* __restrict__ st, int discard) {
     __shared__ double sh[40];
     __shared__ float4 grp_sum[kImgGroups - 1][kImgCols];
     const float4* p4 = reinterpret_cast<const float4*>(part);
@@ -123,6 +125,13 @@ __global__ void __launch_bounds__(kRedThreads) reduce_image_kernel(const float* 
             }
         }
         __syncthreads();  // grp_sum is rewritten by the next pass
+        if (discard && (col & 7) == 0 && i < n4) {
+            // every thread of the block has used its loads of this pass (barrier above), so the
+            // partial rows are dead: their L2 lines are dropped without being written back to HBM
+            // (i is a multiple of 8 float4, and the host checked that every line starts on 128 bytes)
+            for (int c = grp; c < nparts; c += kImgGroups)
+                asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(p4 + (size_t)c * n4 + i) : "memory");
+        }
     }
     const double tot = block_sum(ss, sh);
     if (threadIdx.x == 0 && ss_part) ss_part[blockIdx.x] = tot;
@@ -371,10 +380,13 @@ __global__ void record_window_kernel(const CgState* st, WindowRecord* rec, int* 
 
 cudaError_t cg_reduce_image(const float* part, int nparts, int n, float* m, float lam, int acc, float* out,
                             double* ss_part, cudaStream_t st, const float* minv, double* sz_part, const float* p,
-                            const CgState* state) {
+                            const CgState* state, bool discard_part) {
     ProfScope prof_(KC_VECTOR, st);
+    // lines are dropped only when each partial plane is a whole number of 128-byte lines from a
+    // 128-byte boundary
+    const int discard = discard_part && ((uintptr_t)part & 127u) == 0 && (n / 4) % 8 == 0 && n % 4 == 0;
     reduce_image_kernel<<<kImgRedBlocks, kRedThreads, 0, st>>>(part, nparts, n / 4, m, lam, acc, out, ss_part, minv,
-                                                            sz_part, p, state);
+                                                            sz_part, p, state, discard);
     count_launch();
     return cudaGetLastError();
 }

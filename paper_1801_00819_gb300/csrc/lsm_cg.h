@@ -28,10 +28,12 @@ struct CgState {
 };
 
 // With p and state given (a CG iteration whose sweeps fold in the vector work), m += alpha p is
-// applied before s = sum - lambda m and m is written back; alpha is read from the state.
+// applied before s = sum - lambda m and m is written back; alpha is read from the state.  With
+// discard_part the partial planes are dead once read: their L2 lines are invalidated without a
+// write-back (the partials a sweep has just written, still in L2, then never reach HBM).
 cudaError_t cg_reduce_image(const float* part, int nparts, int n, float* m, float lam, int acc, float* out,
                             double* ss_part, cudaStream_t st, const float* minv = nullptr, double* sz_part = nullptr,
-                            const float* p = nullptr, const CgState* state = nullptr);
+                            const float* p = nullptr, const CgState* state = nullptr, bool discard_part = false);
 cudaError_t cg_norm2_c64(const float2* q, size_t n2, double* part, cudaStream_t st);
 cudaError_t cg_residual(const float2* d, const float2* q, float2* r, size_t n2, cudaStream_t st);
 cudaError_t cg_update_mr(float* m, const float* p, int n, float2* r, const float2* q, size_t n2,

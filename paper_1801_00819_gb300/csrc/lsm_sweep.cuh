@@ -213,13 +213,16 @@ __global__ void __launch_bounds__(sweep_max_threads<N, V>()) sweep_kernel(const 
         constexpr int CH = N / 2;  // 16-byte chunks per complex row
         float2* dst = stage + b * stage_buf;
         const int total = nslots * 2 * CH;
+        // the coefficient rows are read once per launch: evict-first in L2, so that they do not
+        // push out the partial image rows the image reduction reads back after the adjoint sweep
+        const unsigned long long pol = l2_evict_first_policy();
         for (int c = threadIdx.x; c < total; c += blockDim.x) {
             const int sl = c / (2 * CH);
             const int rem = c - sl * 2 * CH;
             const int which = rem / CH;
             const int ch = rem - which * CH;
             const float2* src = (which ? a.dss : a.phi) + ((size_t)(w_first + sl) * nz + row) * N + 2 * ch;
-            cp_async16(dst + (sl * 2 + which) * N + 2 * ch, src);
+            cp_async16_stream(dst + (sl * 2 + which) * N + 2 * ch, src, pol);
         }
         if (with_model) {
             for (int c = threadIdx.x; c < N / 4; c += blockDim.x)
@@ -358,7 +361,8 @@ __global__ void __launch_bounds__(sweep_max_threads<N, V>()) sweep_kernel(const 
             __syncthreads();  // image rows of depth j and staged rows of depth j are visible
             if (j + 2 < nz) stage_rows(j + 1, (j + 1) & 1, false);
             {
-                // the block's partial row: the image rows summed in a fixed order, four columns a thread
+                // the block's partial row: the image rows summed in a fixed order, four columns a thread,
+                // stored evict-last in L2 so that the image reduction launched next finds it there
                 const int nslab = nwarps * IR::SPW;
                 const float4* rows4 = reinterpret_cast<const float4*>(img + (size_t)(j & 1) * nslab * IR::SLAB);
                 float4* prow = reinterpret_cast<float4*>(part + (size_t)j * N);
@@ -371,7 +375,7 @@ __global__ void __launch_bounds__(sweep_max_threads<N, V>()) sweep_kernel(const 
                         acc.z += u4.z;
                         acc.w += u4.w;
                     }
-                    prow[x4] = acc;
+                    st_global_keep_l2(prow + x4, acc);
                 }
             }
             if (j + 1 < nz) {
