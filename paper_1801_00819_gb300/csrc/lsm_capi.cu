@@ -775,7 +775,7 @@ int lsm_adjoint_static(const lsm_grid* grid, const float* slowness, const lsm_fr
     int nparts = 0;
     LSM_CHECK(run_adjoint(a, shot0, nshots, reinterpret_cast<const float2*>(d), nsm, st, &nparts));
     LSM_CHECK(cg_reduce_image(a.part, nparts, grid->nx * grid->nz, nullptr, 0.f, accumulate ? 1 : 0, m_out,
-                              reinterpret_cast<double*>(ws + L.ss), st));
+                              reinterpret_cast<double*>(ws + L.ss), st, nullptr, nullptr, nullptr, nullptr, true));
     return LSM_OK;
 }
 
