@@ -261,6 +261,38 @@ struct Plan {
     }
 };
 
+// Pair plan: N = 512 at V = 16 points per thread, T = 32 threads (one warp) per transform.  It has
+// the stages of the 32-point plan, 512 = 32 x 16, but the two lanes t and t ^ 16 share each 32-point
+// first-stage DFT: with p = t mod 16 and h = t / 16, lane t holds x = p + 16 (2 r + h) = t + 32 r,
+// the even (h = 0) or odd (h = 1) points of column p's 32-point DFT, runs the 16-point DFT of its
+// half, and the lanes exchange half their outputs with one shuffle per value for the final radix-2
+// step, X[k] = E[k] + w^k O[k] and X[k + 16] = E[k] - w^k O[k] (w = exp(-2 pi i / 32)): lane h
+// produces k in [8h, 8h + 8) and k + 16.  Twice the threads per transform of the 32-point plan
+// without a third stage, so a window of few items fills twice the warps per SM.
+template <int N, int V>
+constexpr bool pair_plan() { return N == 512 && V == 16; }
+
+template <>
+struct Plan<512, 16> {
+    static constexpr int N = 512, V = 16, Q = 1, T = 32, VP2 = 16;
+    static constexpr int R(int s) { return s == 0 ? 32 : 16; }
+    static constexpr int L(int s) { return s == 0 ? 512 : 16; }
+    static constexpr int M(int s) { return s == 0 ? 16 : 1; }
+    static constexpr int NB(int) { return 1; }
+    static constexpr int NS = 2, RLAST = 16, R0 = 32, M0 = 16;
+    static constexpr bool TW_SMEM = false;
+    static constexpr int NTW = 16, TAB = 0;
+    static __device__ __forceinline__ int phys(int a) { return a + (a >> 4); }
+    static constexpr int BUF = N + N / 16;
+    static __host__ __device__ constexpr int xpos(int t, int r) { return t + T * r; }
+    // first-stage output (32-point DFT index k2) held in register i of lane t after the exchange
+    static __host__ __device__ constexpr int k2_of(int t, int i) { return (i & 7) + 8 * (t >> 4) + 16 * (i >> 3); }
+    // position 16 k2 + k1 holds frequency k2 + 32 k1
+    static __host__ __device__ constexpr int freq_of_position(int pos) { return (pos / 16) % 32 + 32 * (pos % 16); }
+    // lane t holds the last-stage block of positions 16 t .. 16 t + 15 (register r = k1)
+    static __host__ __device__ constexpr int position_of(int t, int r) { return 16 * t + r; }
+};
+
 template <int N, int V>
 struct Twiddles {
     using P = Plan<N, V>;
@@ -319,7 +351,19 @@ template <int N, int V>
 __device__ __forceinline__ void init_twiddles(Twiddles<N, V>& tw, int t, float2* table = nullptr) {
     tw.t = t;
     tw.table = table;
-    init_twiddles_stage<N, V, 0>(tw, t, table);
+    if constexpr (pair_plan<N, V>()) {
+        // first-stage twiddle exp(-2 pi i p k2 / 512) of each output register
+        const int p = t & 15;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int e = (p * Plan<N, V>::k2_of(t, i)) % 512;
+            float sn, cs;
+            sincospif(-2.0f * (float)e / 512.0f, &sn, &cs);
+            tw.w[i] = make_float2(cs, sn);
+        }
+    } else {
+        init_twiddles_stage<N, V, 0>(tw, t, table);
+    }
 }
 
 // ------------------------------------------------------------------ exchanges
@@ -487,6 +531,105 @@ __device__ __forceinline__ void phase_shift_two_stage(float2 (&v)[V], const Twid
 #pragma unroll
     for (int k2 = 1; k2 < R0; ++k2) v[k2] = cmulc(v[k2], tw.template at<0>(0, k2));
     small_dft<R0, true>(v);
+}
+
+
+// ------------------------------------------------------------------ pair plan step
+
+// w^J (forward, w = exp(-2 pi i / 32)) or its conjugate, and the same times w^8 = -i (or +i)
+template <int J, bool INV>
+struct PairConst {
+    static constexpr float c = (float)series_cos(turn_angle(J, 32));
+    static constexpr float s = INV ? (float)series_sin(turn_angle(J, 32)) : -(float)series_sin(turn_angle(J, 32));
+    // w^(J + 8) = w^J * (-i) forward, conj: * (+i)
+    static constexpr float c8 = INV ? -s : s;
+    static constexpr float s8 = INV ? c : -c;
+};
+
+__device__ __forceinline__ float2 shfl_pair(float2 v) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, 16), __shfl_xor_sync(0xffffffffu, v.y, 16));
+}
+
+// final radix-2 step of the forward 32-point DFT for output pair J: in, lane h holds E (h = 0) or
+// O (h = 1) at registers J and J + 8; out, register J holds X[J + 8h] and register J + 8 holds
+// X[J + 8h + 16]
+template <int J>
+__device__ __forceinline__ void pair_forward_radix2(float2 (&v)[16], bool h) {
+    const float2 keep = v[J], give = v[J + 8];
+    const float2 recv = shfl_pair(h ? keep : give);  // lane 0 gets O[J], lane 1 gets E[J + 8]
+    const float2 e = h ? recv : keep;                // E[J + 8h]
+    const float2 o = h ? give : recv;                // O[J + 8h]
+    using C = PairConst<J, false>;
+    const float2 w = h ? make_float2(C::c8, C::s8) : make_float2(C::c, C::s);
+    const float2 tw = cmul(o, w);
+    v[J] = __fadd2_rn(e, tw);
+    v[J + 8] = __ffma2_rn(tw, make_float2(-1.f, -1.f), e);
+}
+
+// first radix-2 step of the inverse 32-point DFT for pair J (the forward step undone): in, registers
+// J and J + 8 hold Y[J + 8h] and Y[J + 8h + 16]; out, lane 0 holds e[k] = Y[k] + Y[k + 16] and lane 1
+// o[k] = (Y[k] - Y[k + 16]) conj(w)^k at registers J (k = J) and J + 8 (k = J + 8)
+template <int J>
+__device__ __forceinline__ void pair_inverse_radix2(float2 (&v)[16], bool h) {
+    const float2 lo = v[J], hi = v[J + 8];
+    const float2 e = __fadd2_rn(lo, hi);
+    using C = PairConst<J, true>;
+    const float2 w = h ? make_float2(C::c8, C::s8) : make_float2(C::c, C::s);
+    const float2 o = cmul(__ffma2_rn(hi, make_float2(-1.f, -1.f), lo), w);
+    const float2 recv = shfl_pair(h ? e : o);  // lane 0 gets e[J + 8], lane 1 gets o[J]
+    v[J] = h ? recv : e;
+    v[J + 8] = h ? o : recv;
+}
+
+template <int... Js>
+__device__ __forceinline__ void pair_forward_radix2_all(float2 (&v)[16], bool h, std::integer_sequence<int, Js...>) {
+    (pair_forward_radix2<Js>(v, h), ...);
+}
+template <int... Js>
+__device__ __forceinline__ void pair_inverse_radix2_all(float2 (&v)[16], bool h, std::integer_sequence<int, Js...>) {
+    (pair_inverse_radix2<Js>(v, h), ...);
+}
+
+// One phase-shift step F^-1 (phi . F v) of the pair plan (N = 512, 16 points per thread): the
+// forward first stage (16-point DFT, radix-2 exchange across the lane pair, twiddles) into the
+// exchange buffer, mid(), then the lane's last-stage block (positions 16 t .. 16 t + 15: 16-point
+// DFT, phi or conj(phi), inverse 16-point DFT) in place, then the inverse first stage back into the
+// natural layout.  phi[r * 32 + t] multiplies register r of lane t's block.
+template <bool CONJ, class Mid>
+__device__ __forceinline__ void phase_shift_pair(float2 (&v)[16], const Twiddles<512, 16>& tw, float2* buf, int t,
+                                                 const float2* phi, Mid&& mid) {
+    using P = Plan<512, 16>;
+    const bool h = t >= 16;
+    const int p = t & 15;
+    small_dft<16, false>(v);
+    pair_forward_radix2_all(v, h, std::make_integer_sequence<int, 8>{});
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = cmul(v[i], tw.w[i]);
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) buf[P::phys(16 * P::k2_of(t, i) + p)] = v[i];
+    __syncwarp();
+    mid();
+    {
+        float2 u[16];
+        const int a0 = 16 * t;
+#pragma unroll
+        for (int n = 0; n < 16; ++n) u[n] = buf[P::phys(a0 + n)];
+        small_dft<16, false>(u);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const float2 ph = phi[k * 32 + t];
+            u[k] = CONJ ? cmulc(u[k], ph) : cmul(u[k], ph);
+        }
+        small_dft<16, true>(u);
+#pragma unroll
+        for (int n = 0; n < 16; ++n) buf[P::phys(a0 + n)] = u[n];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = cmulc(buf[P::phys(16 * P::k2_of(t, i) + p)], tw.w[i]);
+    pair_inverse_radix2_all(v, h, std::make_integer_sequence<int, 8>{});
+    small_dft<16, true>(v);
 }
 
 }  // namespace lsm

@@ -147,6 +147,7 @@ constexpr int points_per_thread(int nx) {
 // The alternative FFT tile of the sweep kernels: half the points per thread (twice the threads per
 // (shot, frequency) item) where that plan exists -- V/2 a multiple of the odd factor with at least two
 // power-of-two points left, and at most 32 threads per item; 0 where it does not (nx = 768, 896, 1024).
+// At nx = 512 it is the pair plan (32 x 16 with each 32-point first-stage DFT shared by two lanes).
 constexpr int alt_points_per_thread(int nx) {
     const int q = odd_factor(nx);
     const int v = points_per_thread(nx) / 2;

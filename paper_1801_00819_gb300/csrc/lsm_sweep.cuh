@@ -82,7 +82,9 @@ template <int N, int V, class Mid>
 __device__ __forceinline__ void step_down(float2 (&v)[V], const Twiddles<N, V>& tw, float2* buf, int t,
                                           const float2* phi, const float2* dss, Mid&& mid) {
     constexpr int T = Plan<N, V>::T;
-    if constexpr (Plan<N, V>::NS == 2 && Plan<N, V>::NB(0) == 1) {
+    if constexpr (pair_plan<N, V>()) {
+        phase_shift_pair<false>(v, tw, buf, t, phi, mid);
+    } else if constexpr (Plan<N, V>::NS == 2 && Plan<N, V>::NB(0) == 1) {
         phase_shift_two_stage<N, V, false, true>(v, tw, buf, t, phi, mid);
     } else {
         mid();
@@ -107,7 +109,9 @@ __device__ __forceinline__ void step_down_adjoint(float2 (&v)[V], const Twiddles
     if constexpr (!kLoadMid) mid();
 #pragma unroll
     for (int r = 0; r < V; ++r) v[r] = cmulc(v[r], dss[Plan<N, V>::xpos(t, r)]);
-    if constexpr (kLoadMid) {
+    if constexpr (pair_plan<N, V>()) {
+        phase_shift_pair<true>(v, tw, buf, t, phi, [] {});
+    } else if constexpr (kLoadMid) {
         phase_shift_two_stage<N, V, true, true>(v, tw, buf, t, phi, mid);
     } else if constexpr (kTwoStage) {
         phase_shift_two_stage<N, V, true, false>(v, tw, buf, t, phi, [] {});
@@ -123,11 +127,15 @@ __device__ __forceinline__ void step_down_adjoint(float2 (&v)[V], const Twiddles
 
 // Threads per block the kernel is compiled for: 24 or more points per thread need up to ~250
 // registers, which leaves room for 8 warps per SM; 16 points per thread fit 16 warps at 128
-// registers, except with 32 threads per item and 16 to 20 points per thread (the alternative tiles at
-// nx = 512 and 640: deeper plans whose twiddles need more registers), which are compiled for 12 warps
-// at up to 168 registers.
+// registers, except with 32 threads per item and 16 to 20 points per thread: the pair plan (the
+// alternative tile at nx = 512) is compiled for 14 warps, one block per SM for a window whose items
+// fill 13 to 14 warps per SM, at 128 registers (a register-file quarter then holds four warps), and
+// the alternative tile at 640, a deeper plan whose twiddles need more registers, for 12 warps at up
+// to 168 registers.
 template <int N, int V>
-constexpr int sweep_max_threads() { return V >= 24 ? 256 : (V >= 16 && N / V == 32 ? 384 : 512); }
+constexpr int sweep_max_threads() {
+    return V >= 24 ? 256 : pair_plan<N, V>() ? 448 : (V >= 16 && N / V == 32 ? 384 : 512);
+}
 
 // Image rows of the adjoint: each warp writes SPW rows per depth (its items' imaging terms; with
 // more than two items per warp they are first summed pairwise by shuffles), at a row stride of
