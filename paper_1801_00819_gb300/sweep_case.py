@@ -1,12 +1,13 @@
 """Run one window of A and A^T on a synthetic survey, for timing and profiling the sweep kernels.
 
     python -m paper_1801_00819_gb300.sweep_case [--workload realistic|tiny|precision] [--reps N] [--shots K]
-        [--freq-stride S] [--transform T] [--gradient [--tune-gradient]]
+        [--freq-stride S] [--transform T] [--tile V] [--gradient [--tune-gradient]]
 
 Prepares the workload's grid, velocity, geometry and frequencies on the device, random data for
 one window of K shots, then calls lsm_forward and lsm_adjoint through the C ABI `reps` times each
 (each call builds the coefficient tables, computes the window's source wavefields and runs one
-sweep).  Prints per-class kernel times from the library's event timing.  The inputs are random,
+sweep).  Prints per-class kernel times from the library's event timing.  --tile records the FFT
+tile (points per thread, one of lsm_fft_tiles(nx)) for the window's shape before the calls.  The inputs are random,
 so no modelling pass precedes the timed calls.  With --gradient it also calls lsm_born_gradient
 (d = A(s) m and the gradients for a random data-space gradient g) on the same window, with the
 reference slowness held at the row means of the model.
@@ -35,6 +36,8 @@ def main():
                     help="keep every n-th frequency of the workload (smaller captures)")
     ap.add_argument("--transform", default="fft",
                     help="fft, dft_bf16x3, dft_fp16x3, dft_bf16x1, dft_fp16x3_tcgen05 or dft_bf16x3_tcgen05")
+    ap.add_argument("--tile", type=int, default=0,
+                    help="FFT tile (points per thread) of the register-FFT sweeps; 0: the default")
     ap.add_argument("--gradient", action="store_true", help="also time lsm_born_gradient on the window")
     ap.add_argument("--tune-gradient", action="store_true",
                     help="with --gradient: record the fastest checkpoint stride (lsm_autotune_gradient) first")
@@ -52,6 +55,8 @@ def main():
         sv.wavelet = sv.wavelet[::args.freq_stride].copy()
     K = args.shots or sv.window
     ds = to_device(sv.nx, sv.nz, sv.dx, sv.dz, sv.slowness, sv.src_ix, sv.rec_ix, sv.freqs, sv.wavelet)
+    if args.tile:
+        L.lsm.lsm_set_fft_tile(sv.nx, K, sv.nw, args.tile)
     rng = np.random.default_rng(0)
     d = torch.as_tensor((rng.normal(size=(K, sv.nw, sv.nx)) + 1j * rng.normal(size=(K, sv.nw, sv.nx)))
                         .astype(np.complex64), device="cuda")
@@ -76,7 +81,8 @@ def main():
                                 ws_g)
     torch.cuda.synchronize()
     prof = L.lsm_profile_stop()
-    print(json.dumps({"workload": sv.name, "transform": args.transform, "K": K, "nw": sv.nw, "nz": sv.nz, "nx": sv.nx,
+    print(json.dumps({"workload": sv.name, "transform": args.transform, "tile": args.tile or L.lsm_fft_tiles(sv.nx)[0],
+                      "K": K, "nw": sv.nw, "nz": sv.nz, "nx": sv.nx,
                       "per_launch_ms": {k: (v["ms"] / v["launches"] if v["launches"] else 0.0)
                                         for k, v in prof.items()},
                       "gradient_stride_tune": tune}))

@@ -196,6 +196,42 @@ def test_alternative_fft_tile_matches_oracle(torch_cuda, case):
     assert rel_l2(img.cpu().numpy(), op.adjoint(d.astype(np.complex128))) <= 1e-4
 
 
+def test_pair_tile_partial_receivers_ragged_blocks(torch_cuda):
+    """The pair plan (the second tile at nx = 512: one item per warp, the 32-point first stage shared
+    by two lanes) with per-shot receiver subsets (a duplicated column included), a shot sub-range,
+    accumulation and a ragged last block (5 shots x 31 frequencies = 155 items, one per warp, in
+    blocks of 2 warps: the last block holds one item), against the FP64 oracle."""
+    import paper_1801_00819_gb300 as L
+    torch = torch_cuda
+    nx, nz, ns, nw = 512, 9, 6, 31
+    tiles = L.lsm_fft_tiles(nx)
+    assert tiles[1] == 16
+    L.lsm.lsm_set_fft_tile(nx, 5, nw, tiles[1])
+    sv = random_case(nx, nz, ns, nw, seed=612)
+    rng = np.random.default_rng(8)
+    nrec = 300
+    rec = np.stack([np.sort(rng.choice(nx, nrec, replace=False)) for _ in range(ns)]).astype(np.int32)
+    rec[2, 10] = rec[2, 11]
+    op = oracle_operator(sv, rec_ix=rec)
+    ds = device_survey(sv, rec_ix=rec)
+    ws = torch.empty(L.lsm_workspace_bytes(ds.grid, ds.geom, ds.freqs, 5, L.LSM_OP_ADJOINT), dtype=torch.uint8,
+                     device="cuda")
+    m = np.asarray(sv.reflectivity, dtype=np.float32)
+    out = torch.empty((5, nw, nrec), dtype=torch.complex64, device="cuda")
+    L.lsm_forward(ds.grid, ds.slowness, ds.freqs, ds.geom, torch.as_tensor(m, device="cuda"), out, 1, 5, ws)
+    d = (rng.normal(size=(5, nw, nrec)) + 1j * rng.normal(size=(5, nw, nrec))).astype(np.complex64)
+    base = rng.normal(size=(nz, nx)).astype(np.float32)
+    img = torch.as_tensor(base.copy(), device="cuda")
+    L.lsm_adjoint(ds.grid, ds.slowness, ds.freqs, ds.geom, torch.as_tensor(d, device="cuda"), img, 1, 5, ws,
+                  accumulate=True)
+    torch.cuda.synchronize()
+    shots = list(range(1, 6))
+    assert rel_l2(out.cpu().numpy(), op.forward(m.astype(np.float64), shots=shots)) <= 1e-4
+    ref = base.astype(np.float64) + op.adjoint(d.astype(np.complex128), shots=shots)
+    assert rel_l2(img.cpu().numpy().astype(np.float64) - base, ref - base) <= 1e-4
+    L.lsm.lsm_set_fft_tile(nx, 5, nw, tiles[0])
+
+
 def test_alternative_fft_tile_sliding_solve(torch_cuda):
     """A sliding solve whose coefficient tables and sweeps all use the alternative tile (window 3,
     slide 2: the refill sweeps over 2 shots run on the window's tables) against the oracle."""

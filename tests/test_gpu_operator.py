@@ -166,13 +166,25 @@ def test_tiny_config_operator(torch_cuda):
     assert rel_l2(_gpu_adjoint(torch_cuda, ds, d, 0, sv.ns), op.adjoint(d)) <= TOL
 
 
-def test_realistic_full_size_sampled_items(torch_cuda):
+@pytest.mark.parametrize("tile", [0, 1], ids=["default_tile", "pair_tile"])
+def test_realistic_full_size_sampled_items(torch_cuda, tile):
     """512 x 256, 128 frequencies, one 16-shot window in the solver's launch configuration:
     A is compared on sampled (shot, frequency) rows; A^T on data that is zero except at the
-    sampled items, which the oracle migrates one by one."""
+    sampled items, which the oracle migrates one by one.  Both FFT tiles: the default 32 points per
+    thread, and the pair plan (16 points, a whole warp per item, 14 warps per block)."""
+    import paper_1801_00819_gb300 as L
     sv = config_realistic()
     ds = device_survey(sv)
     K, shot0 = sv.window, 40
+    tiles = L.lsm_fft_tiles(sv.nx)
+    L.lsm.lsm_set_fft_tile(sv.nx, K, sv.nw, tiles[tile])
+    try:
+        _realistic_sampled_items(torch_cuda, sv, ds, K, shot0)
+    finally:
+        L.lsm.lsm_set_fft_tile(sv.nx, K, sv.nw, tiles[0])
+
+
+def _realistic_sampled_items(torch_cuda, sv, ds, K, shot0):
     m = np.asarray(sv.reflectivity, dtype=np.float32).astype(np.float64)
     got = _gpu_forward(torch_cuda, ds, m, shot0, K)
     samples = [(0, 0), (5, 37), (11, 90), (15, 127)]
