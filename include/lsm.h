@@ -400,8 +400,9 @@ int rls_multi_line_solve(lsm_line* lines, int nlines, const lsm_solve_options* o
  * per block sets how many items share a block's staged coefficient rows and how the launch fills the
  * SMs; the default spreads a launch evenly over the SMs.  With the FP32 FFTs the FFT tile -- the
  * points of a line each thread holds -- is tuned too: every width but 768, 896 and 1024 also has a
- * compiled tile with half the default points per thread (twice the threads per item, a smaller or
- * deeper FFT plan).  lsm_autotune times, for each tile, every admissible number of warps per block for
+ * compiled tile with half the default points per thread (twice the threads per item: a smaller or
+ * deeper FFT plan, or at nx = 512 the same 32 x 16 stages with each 32-point first-stage DFT shared
+ * by two lanes of the warp that holds the item).  lsm_autotune times, for each tile, every admissible number of warps per block for
  * the source, A^T and A sweeps of launches over `nshots` shots of this grid and frequency set (for a
  * solve: nshots = K), with the FP32 FFTs or, when options->transform selects one, the tensor-core DFT
  * products, and records the fastest shape per sweep and the tile whose best A plus best A^T is
