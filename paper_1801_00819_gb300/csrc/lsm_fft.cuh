@@ -533,6 +533,7 @@ __device__ __forceinline__ void phase_shift_two_stage(float2 (&v)[V], const Twid
     small_dft<R0, true>(v);
 }
 
+
 // ------------------------------------------------------------------ pair plan step
 
 // w^J (forward, w = exp(-2 pi i / 32)) or its conjugate, and the same times w^8 = -i (or +i)
